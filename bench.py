@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the unsplit geometric VOF hot path (LSGIR + FMFPA) on GB300.
+
+Metric: VOF cell-steps/s over reconstruct + advect (the paper's
+t_cpu = t_rec + t_adv), on the 3D deformation test (Sec. 4.2.3): uniform
+hexahedral grid on the unit cube, sphere r = 0.15 at (0.35, 0.35, 0.35),
+period T = 3, CFL 0.5, time steps from Eq. eq:cfl. Default grid 256^3
+(16.8 M cells), mixed precision (FP32 geometry, FP64 roots near F = 0/1,
+updates and sums) with the plain FP64 path measured beside it.
+
+A step is one iteration of the advection loop: faceflux + vofadv + taggrid +
+LSGIR + plane constant, i.e. every kernel of the hot path. Inputs (mesh,
+F, planes) are resident in HBM and far larger than L2 (the mesh arrays
+alone are ~10 GB at 256^3), so no L2 flush is needed between steps.
+
+Multi-GPU: the path runs one independent replica of the workload per rank
+(no data-path collective); value = total cell-steps of all ranks / the
+slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the
+host cores on the same workload, one full step per timed step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2111_01524_gb300 import inputs as I  # noqa: E402
+
+METRIC = "VOF cell-steps/s (recon+advect) mixed vs FP64 at stated F error; p50/p99 latency"
+UNIT = "cell-steps/s"
+# algorithmic work per unit (stated and derived in the design doc)
+FLOPS_PER_ACTIVE_FACE = 350.0      # FMFPA construction
+FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
+FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2
+N_SM = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gvof", choices=["gvof", "reference"])
+    p.add_argument("--grid", type=int, default=256)
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-steps", type=int, default=1)
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(grid):
+    mesh = I.hex_mesh(grid)
+    F0 = I.init_fraction(mesh, I.sphere((0.35, 0.35, 0.35), 0.15), levels=4)
+    return mesh, F0, I.deformation(3.0), 0.5, 3.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_steps(ctx, vel, cfl, t_end, t, n, stream, timing=False):
+    """n steps of the advection loop; returns new t and per-step ms (events)."""
+    import torch
+    evs = []
+    for _ in range(n):
+        dt = ctx.suggest_dt(vel, t, cfl, t_end)
+        if timing:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        ctx.step(vel, t, dt, stream=stream)
+        if timing:
+            e1.record(stream)
+            evs.append((e0, e1))
+        t += dt
+    return t, evs
+
+
+def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision):
+    """Roofline of the dominant kernel (see the design doc for the per-unit work)."""
+    ms, launches = phase["ms"], phase["launches"]
+    per_launch_ms = ms / max(launches, 1)
+    nc, nf, nv = grid_counts["n_cell"], grid_counts["n_face"], grid_counts["n_vert"]
+    name = phase["name"]
+    hbm_bytes = {
+        "cell_tags": nc * (8 + 1),
+        "node_tags": nv * (8 + 1) + 8 * nc * 4 + nc * 8,
+        "face_sweep": nf * (8 + 16 + 8 + 1 + 8 + 8) + nv,
+        "update": nc * (8 + 24 + 16 + 8) + nf * 16,
+    }
+    if name in hbm_bytes:
+        b = hbm_bytes[name]
+        achieved = b / (per_launch_ms * 1e-3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_bytes_per_launch": b, "peak_source": peak_kind}
+    # band kernels: plain ALU arithmetic
+    fl = (ctx_counts["n_active_faces"] * FLOPS_PER_ACTIVE_FACE
+          + ctx_counts["n_truncations"] * FLOPS_PER_TRUNCATION) / max(launches, 1)
+    mhz = clocks.get("sm_mhz") or 1900.0
+    lanes = FP32_LANES_PER_SM if precision == "mixed" else FP64_LANES_PER_SM
+    peak = N_SM * lanes * 2 * mhz * 1e6 / 1e12
+    achieved = fl / (per_launch_ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "algorithmic_flops_per_launch": fl,
+            "peak_source": f"{'FP32' if precision == 'mixed' else 'FP64'} FMA lanes x SMs x "
+                           f"median SM clock {mhz:.0f} MHz"}
+
+
+def cpu_baseline(mesh, F0, vel, cfl, t_end, steps):
+    import oracle
+    oracle.build()
+    om = oracle.Mesh(mesh)
+    st = om.reconstruct(F0)
+    t = 0.0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dt = om.suggest_dt(vel, t, cfl, t_end)
+        st = om.step(vel, t, dt, st)
+        t += dt
+    el = time.perf_counter() - t0
+    return {"value": om.n_cell * steps / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} full step(s) of the {round(om.n_cell ** (1 / 3))}^3 workload "
+                      f"from t=0 (FP64 C oracle, OpenMP; mesh build excluded)"}
+
+
+def main_reference(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    mesh, F0, vel, cfl, t_end = workload(a.grid)
+    import oracle
+    oracle.build()
+    om = oracle.Mesh(mesh)
+    st = om.reconstruct(F0)
+    t = 0.0
+    for _ in range(a.warmup):
+        dt = om.suggest_dt(vel, t, cfl, t_end)
+        st = om.step(vel, t, dt, st)
+        t += dt
+    lat = []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        s0 = time.perf_counter()
+        dt = om.suggest_dt(vel, t, cfl, t_end)
+        st = om.step(vel, t, dt, st)
+        t += dt
+        lat.append((time.perf_counter() - s0) * 1e3)
+    el = time.perf_counter() - t0
+    value = om.n_cell * a.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": el * 1e3 / a.steps,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"3D deformation, hex {a.grid}^3, T=3, "
+                                                        "CFL 0.5, sphere r=0.15",
+                                            "grid": a.grid, "cells": om.n_cell},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{a.steps} full steps of the {a.grid}^3 workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return main_reference(a)
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import vof as V
+    B.build()
+    mesh, F0, vel, cfl, t_end = workload(a.grid)
+    counts = I.mesh_counts(mesh)
+    prec = V.PREC_MIXED if a.precision == "mixed" else V.PREC_FP64
+    stream = torch.cuda.current_stream()
+    F0_dev = torch.from_numpy(F0).cuda()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def measure(precision, steps, warmup, with_phases):
+        ctx = V.Context(mesh, precision=precision)
+        ctx.set_fraction(F0_dev, stream=stream)
+        ctx.reconstruct(stream=stream)
+        t, _ = run_steps(ctx, vel, cfl, t_end, 0.0, warmup, stream)
+        barrier()
+        if with_phases:
+            ctx.set_timing(True)
+        clk = ClockSampler(local)
+        clk.start()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        t, evs = run_steps(ctx, vel, cfl, t_end, t, steps, stream, timing=True)
+        end.record(stream)
+        barrier()
+        clocks = clk.stop()
+        total_ms = start.elapsed_time(end)
+        per_step = [e0.elapsed_time(e1) for e0, e1 in evs]
+        phases = ctx.timing() if with_phases else None
+        if with_phases:
+            ctx.set_timing(False)
+        st = ctx.stats(stream=stream)
+        return ctx, total_ms, per_step, phases, clocks, st, t
+
+    ctx, total_ms, per_step, phases, clocks, stats, t_end_run = measure(prec, a.steps, a.warmup, True)
+    ms = total_ms
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = ws * counts["n_cell"] * a.steps / (ms * 1e-3)
+
+    # F error of the measured path against the FP64 GPU path and the oracle is
+    # established by the parity tests; here the path's own conservation is
+    # reported: relative change of sum(V F) over the run (clip and cut-off only)
+    g = ctx.geometry()
+    vol0 = float((g["cell_vol"] * F0).sum())
+    vol_rel = abs(stats["volume"] - vol0) / vol0
+
+    fp64 = None
+    if not a.no_fp64 and prec == V.PREC_MIXED:
+        fsteps = max(3, a.steps // 2)
+        ctx64, ms64, per64, ph64, clk64, st64, _ = measure(V.PREC_FP64, fsteps, a.warmup, False)
+        if dist is not None:
+            tt = torch.tensor([ms64], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms64 = float(tt.item())
+        v64 = ws * counts["n_cell"] * fsteps / (ms64 * 1e-3)
+        # mixed vs FP64 after the same number of steps from the same F0
+        ctxm, _, _, _, _, _, _ = measure(prec, fsteps, a.warmup, False)
+        Fm = ctxm.get_fraction()
+        F64 = ctx64.get_fraction()
+        fp64 = {"value": v64, "unit": UNIT, "steps": fsteps, "ms_per_step": ms64 / fsteps,
+                "mixed_over_fp64": value / v64,
+                "max_abs_F_diff_mixed_vs_fp64": float(np.abs(Fm - F64).max()),
+                "after_steps": fsteps + a.warmup}
+        del ctx64, ctxm
+
+    # end-to-end through the C-ABI with host buffers: each step copies F in
+    # from pinned host memory, runs reconstruct + advect, and reads F back
+    e2e = None
+    if not a.no_e2e:
+        ctxe = V.Context(mesh, precision=prec)
+        Fh = torch.from_numpy(F0.copy()).pin_memory().numpy()
+        ctxe.set_fraction(Fh, stream=stream)
+        t = 0.0
+        for _ in range(a.warmup):
+            ctxe.reconstruct(stream=stream)
+            dt = ctxe.suggest_dt(vel, t, cfl, t_end)
+            ctxe.advect(vel, t, dt, stream=stream)
+            t += dt
+        ctxe.get_fraction(out=Fh, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            ctxe.set_fraction(Fh, stream=stream)
+            ctxe.reconstruct(stream=stream)
+            dt = ctxe.suggest_dt(vel, t, cfl, t_end)
+            ctxe.advect(vel, t, dt, stream=stream)
+            ctxe.get_fraction(out=Fh, stream=stream)
+            t += dt
+        barrier()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([el], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": ws * counts["n_cell"] * a.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * counts["n_cell"],
+               "d2h_bytes_per_step": 8 * counts["n_cell"]}
+        del ctxe
+
+    peaks, peak_kind = measured_peaks()
+    dom = max(phases.items(), key=lambda kv: kv[1][0])
+    phase = {"name": dom[0], "ms": dom[1][0], "launches": dom[1][1]}
+    rl = roofline(stats, phase, counts, peaks, peak_kind, clocks, a.precision)
+    launches = sum(n for _, n in phases.values())
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, F0, vel, cfl, t_end, a.cpu_steps)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "p50_ms": float(np.percentile(per_step, 50)),
+            "p99_ms": float(np.percentile(per_step, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"3D deformation (Enright), uniform hex {a.grid}^3 on the "
+                                   f"unit cube, sphere r=0.15 at (0.35,0.35,0.35), T=3, CFL 0.5, "
+                                   f"steps from t=0",
+                       "grid": a.grid, "cells": counts["n_cell"], "faces": counts["n_face"],
+                       "precision": a.precision, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (mesh + state ~10 GB), no flush"},
+            "gpu_launches": launches,
+            "phases_ms": {k: v[0] for k, v in phases.items()},
+            "band": {"interfacial_cells": stats["n_interfacial"],
+                     "active_faces": stats["n_active_faces"],
+                     "truncations_per_step": stats["n_truncations"] / max(1, a.steps + a.warmup),
+                     "overflow": stats["n_overflow"]},
+            "volume_rel_change": vol_rel,
+            "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

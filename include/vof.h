@@ -1,0 +1,183 @@
+/*
+ * gvof: GB300 (sm_103a) CUDA library for the data-parallel hot path of the
+ * unsplit geometric volume-of-fluid method of arXiv 2111.01524 (gVOF):
+ * LSGIR reconstruction (Sec. 2.1.1) with a volume-enforcing plane constant
+ * (Sec. 2.1), FMFPA face-matched flux polyhedra (Sec. 2.2.2) truncated by
+ * the upstream cells' PLIC half-spaces (Sec. 2.2), and the conservative
+ * update of Eq. fnext with the final clip (Sec. 2.2).
+ *
+ * Conventions
+ *  - Mesh: OpenFOAM-like face-based polyhedral mesh (Sec. 3.1). Faces are
+ *    planar polygons; their nodes run counter-clockwise seen from outside
+ *    the owner cell, so the right-hand normal leaves the owner. A boundary
+ *    face has neighbour = -1. Cells must be convex (uniform hexahedra,
+ *    tetrahedra, any convex polyhedra); a non-convex cell is rejected by
+ *    vof_init with VOF_EINVAL.
+ *  - PLIC plane of an interfacial cell (Eq. plic-eq):  n.(x - xc) + C = 0,
+ *    xc = cell centroid, n = unit normal pointing into the fluid; the fluid
+ *    is the part of the cell where n.(x - xc) + C >= 0.
+ *  - Face volumes V_d (Eq. a-donacion) and V_F are positive when they leave
+ *    the owner cell.
+ *  - Tags (Sec. 3.3): -1 / 0 / 1 for empty / interfacial / full.
+ *  - Every function returns a vof_status; on failure vof_last_error() gives
+ *    a message (thread-local). No function aborts or traps the GPU.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Device work
+ *    is queued on it. A function given HOST buffers synchronises the stream
+ *    before returning; one given DEVICE buffers does not.
+ *  - Ownership: the caller owns every buffer it passes; the library copies
+ *    what it keeps. The context owns all device memory it allocates and
+ *    frees it in vof_destroy.
+ */
+#ifndef GVOF_VOF_H
+#define GVOF_VOF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VOF_OK = 0,
+  VOF_EINVAL = 1,    /* invalid argument or mesh */
+  VOF_ENOMEM = 2,    /* device or host allocation failed */
+  VOF_ECUDA = 3,     /* a CUDA call failed */
+  VOF_ECAPACITY = 4, /* a fixed-capacity buffer overflowed (see stats) */
+  VOF_ESTATE = 5     /* call out of order (e.g. advect before reconstruct) */
+} vof_status;
+
+enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED = 1 };
+enum { VOF_MEM_HOST = 0, VOF_MEM_DEVICE = 1 };
+enum { VOF_VEL_DEFORMATION = 1, VOF_VEL_ROTATION = 2, VOF_VEL_TRANSLATION = 3 };
+
+typedef struct vof_ctx vof_ctx;
+
+/* Face-based mesh (Sec. 3.1), HOST arrays, read during vof_init only.
+ * X: [3*n_vert] interleaved x,y,z. face_ptr: [n_face+1] CSR offsets into
+ * face_vert (3..8 nodes per face). owner, neighbour: [n_face]. */
+typedef struct {
+  int64_t n_vert, n_face, n_cell;
+  const double* X;
+  const int64_t* face_ptr;
+  const int32_t* face_vert;
+  const int32_t* owner;
+  const int32_t* neighbour;
+} vof_mesh_desc;
+
+/* eps: volume-fraction tolerance of Sec. 2.1 and Sec. 3.3 (paper: 1e-12).
+ * beta: LSGIR weight exponent of Eq. lsgir-beta (paper: 1.5).
+ * precision: VOF_PREC_FP64 (all geometry in FP64) or VOF_PREC_MIXED
+ * (geometry in FP32 in face- or cell-local scaled coordinates; FP64 for the
+ * plane constant of cells with F or 1-F below 1e-3, for V_d, for the
+ * per-face flux sums, the cell update and global sums). */
+typedef struct {
+  double eps;
+  double beta;
+  int32_t precision;
+  int32_t reserved[7];
+} vof_options;
+
+/* Prescribed velocity of the test problems (Sec. 4.2):
+ * DEFORMATION: Enright field of Sec. 4.2.3 with period `period`;
+ * ROTATION: u = -omega (y - center[1]), v = omega (x - center[0]), w = 0;
+ * TRANSLATION: u = u0. Velocities are evaluated exactly at face centres,
+ * edge centres and vertices at the mid-time t + dt/2 (Sec. 4.2). */
+typedef struct {
+  int32_t kind;
+  int32_t pad;
+  double period;
+  double omega;
+  double center[3];
+  double u0[3];
+} vof_velocity;
+
+/* Counters and sums of the last advect / reconstruct (vof_get_stats). */
+typedef struct {
+  int64_t n_interfacial;  /* cells with tag 0 */
+  int64_t n_active_faces; /* faces with tag 0 (geometric flux) */
+  int64_t n_truncations;  /* (face, cell) truncations evaluated */
+  int64_t n_overflow;     /* polyhedra that overflowed a buffer: their V_F is unreliable */
+  int64_t n_degenerate;   /* FMFPA side lines replaced by the streak-line point */
+  int64_t n_edgeon;       /* FMFPA faces whose back-traced loop was edge-on */
+  double volume;          /* sum over cells of V F (FP64, fixed-order) */
+  double ebound;          /* E_bound^Linf of Sec. 4.2 before the clip of the last advect */
+} vof_stats;
+
+/* Create a context: copies the mesh to the device and builds its derived
+ * connectivity (neigbcell, cell->face, cell->vertex, vertex->cell) and
+ * geometry (compgrid), Sec. 3.1. opt may be NULL (defaults). */
+vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out);
+void vof_destroy(vof_ctx* ctx);
+const char* vof_last_error(void);
+
+/* Volume fraction F [n_cell] (host or device pointer, see `mem`). Setting F
+ * invalidates the reconstruction: call vof_reconstruct next. */
+vof_status vof_set_fraction(vof_ctx* ctx, const double* F, int mem, void* stream);
+vof_status vof_get_fraction(vof_ctx* ctx, double* F, int mem, void* stream);
+
+/* taggrid (cut-off of F, node F* by inverse-distance weighting, node/face/
+ * cell tags; Sec. 2.1, Sec. 3.3) then LSGIR normals and plane constants of
+ * the interfacial cells (Secs. 2.1, 2.1.1). */
+vof_status vof_reconstruct(vof_ctx* ctx, void* stream);
+
+/* faceflux + vofadv (Sec. 3.5): V_d of every face (Eq. a-donacion), FMFPA
+ * flux polyhedra of the tag-0 faces truncated by the PLIC half-spaces of
+ * the overlapped cells (Sec. 2.2), V_F = 0 / V_d on tag -1 / 1 faces, then
+ * Eq. fnext and the clip to [0, 1]. Velocity at t + dt/2. Requires a
+ * reconstruction of the current F. */
+vof_status vof_advect(vof_ctx* ctx, const vof_velocity* vel, double t, double dt, void* stream);
+
+/* One iteration of the advection test loop (Algorithm alg:adv):
+ * vof_advect followed by vof_reconstruct. */
+vof_status vof_step(vof_ctx* ctx, const vof_velocity* vel, double t, double dt, void* stream);
+
+/* Time step of Eq. eq:cfl at time t: CFL times the smallest ratio, over the
+ * axes, of the smallest cell bounding-box size to the largest face-centre
+ * speed; refined once with the field at t + dt and cut to reach t_end.
+ * Host result; the first call for a velocity field runs a device sweep. */
+vof_status vof_suggest_dt(vof_ctx* ctx, const vof_velocity* vel, double t, double cfl,
+                          double t_end, double* dt);
+
+/* planes [4*n_cell]: nx, ny, nz, C per cell (zeros for non-interfacial). */
+vof_status vof_get_planes(vof_ctx* ctx, double* planes, int mem, void* stream);
+/* tags: any pointer may be NULL; sizes n_vert, n_face, n_cell. */
+vof_status vof_get_tags(vof_ctx* ctx, int8_t* tag_v, int8_t* tag_f, int8_t* tag_c, int mem,
+                        void* stream);
+/* face volumes of the last advect [n_face]; either pointer may be NULL. */
+vof_status vof_get_face_flux(vof_ctx* ctx, double* Vd, double* VF, int mem, void* stream);
+/* compgrid geometry: cell_vol [n_cell], cell_cen [3*n_cell], face_cen
+ * [3*n_face], face_nrm [3*n_face], face_area [n_face]; any may be NULL. */
+vof_status vof_get_geometry(vof_ctx* ctx, double* cell_vol, double* cell_cen, double* face_cen,
+                            double* face_nrm, double* face_area, int mem, void* stream);
+/* neigbcell CSR (cells sharing >= 1 node, self excluded, ascending), HOST
+ * buffers: ptr [n_cell+1]; idx [*count]. Pass idx = NULL to query count. */
+vof_status vof_get_neighbors(vof_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t* count);
+/* Overlap candidates of faces, computed by the same device routine the flux
+ * kernel uses: owner, neighbour and their node neighbours, ascending.
+ * faces: HOST [n]; out_ptr HOST [n+1]; out_idx HOST [cap]. */
+vof_status vof_get_candidates(vof_ctx* ctx, const int32_t* faces, int n, int64_t* out_ptr,
+                              int32_t* out_idx, int64_t cap);
+/* FMFPA flux polyhedra of the given faces built by the device routine the
+ * flux kernel uses (Sec. 2.2.2): verts HOST [n * 17 * 3] absolute
+ * coordinates, 2I+1 points per face (x_1..x_I, back-traced x_{I+1}..x_{2I},
+ * apex), padded with zeros; counts HOST [n] receives I. */
+vof_status vof_get_flux_polyhedra(vof_ctx* ctx, const vof_velocity* vel, double t, double dt,
+                                  const int32_t* faces, int n, double* verts, int32_t* counts);
+/* counters and global sums (synchronises the stream). */
+vof_status vof_get_stats(vof_ctx* ctx, vof_stats* out, void* stream);
+/* Per-phase device timing with CUDA events recorded on the launching
+ * stream around each kernel of the step (off by default). Phases:
+ * 0 cell tags, 1 node tags, 2 reconstruct (LSGIR + plane constant),
+ * 3 face sweep, 4 flux (FMFPA + truncation), 5 update. vof_get_timing
+ * synchronises, returns the accumulated milliseconds and launch counts of
+ * the first n phases and resets them. */
+enum { VOF_PHASE_CELL_TAGS = 0, VOF_PHASE_NODE_TAGS = 1, VOF_PHASE_RECONSTRUCT = 2,
+       VOF_PHASE_FACE_SWEEP = 3, VOF_PHASE_FLUX = 4, VOF_PHASE_UPDATE = 5, VOF_NUM_PHASES = 6 };
+vof_status vof_set_timing(vof_ctx* ctx, int on);
+vof_status vof_get_timing(vof_ctx* ctx, double* ms, int64_t* launches, int n);
+/* bytes of device memory held by the context */
+int64_t vof_device_bytes(const vof_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

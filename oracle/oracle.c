@@ -129,29 +129,36 @@ orc_mesh* orc_mesh_build(int64_t nv, const double* X, int64_t nf,
     if (nbr[f] >= 0) m->cf[fill[nbr[f]]++] = (int32_t)f;
   }
 
-  /* cell -> vertices */
+  /* cell -> vertices (per-cell sorted unique; counted, then filled) */
   m->cv_ptr = (int64_t*)calloc(nc + 1, sizeof(int64_t));
-  int64_t tot = 0;
-  for (int64_t c = 0; c < nc; ++c)
+  int64_t* rawp = (int64_t*)calloc(nc + 1, sizeof(int64_t));
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t s = 0;
     for (int64_t q = m->cf_ptr[c]; q < m->cf_ptr[c + 1]; ++q) {
       int32_t f = m->cf[q];
-      tot += fptr[f + 1] - fptr[f];
+      s += fptr[f + 1] - fptr[f];
     }
-  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (tot > 0 ? tot : 1));
-  int64_t pos = 0;
+    rawp[c + 1] = rawp[c] + s;
+  }
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (rawp[nc] > 0 ? rawp[nc] : 1));
+  int64_t* ucnt = (int64_t*)malloc(sizeof(int64_t) * nc);
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) {
-    int64_t start = pos;
+    int64_t pos = rawp[c];
     for (int64_t q = m->cf_ptr[c]; q < m->cf_ptr[c + 1]; ++q) {
       int32_t f = m->cf[q];
       for (int64_t k = fptr[f]; k < fptr[f + 1]; ++k) tmp[pos++] = fvert[k];
     }
-    int64_t u = sort_unique(tmp + start, pos - start);
-    pos = start + u;
-    m->cv_ptr[c + 1] = pos;
+    ucnt[c] = sort_unique(tmp + rawp[c], rawp[c + 1] - rawp[c]);
   }
+  for (int64_t c = 0; c < nc; ++c) m->cv_ptr[c + 1] = m->cv_ptr[c] + ucnt[c];
+  int64_t pos = m->cv_ptr[nc];
   m->cv = (int32_t*)malloc(sizeof(int32_t) * (pos > 0 ? pos : 1));
-  memcpy(m->cv, tmp, sizeof(int32_t) * pos);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c)
+    memcpy(m->cv + m->cv_ptr[c], tmp + rawp[c], sizeof(int32_t) * ucnt[c]);
   free(tmp);
+  free(rawp);
 
   /* vertex -> cells (cells visited in ascending order) */
   m->vc_ptr = (int64_t*)calloc(nv + 1, sizeof(int64_t));
@@ -165,36 +172,44 @@ orc_mesh* orc_mesh_build(int64_t nv, const double* X, int64_t nf,
       m->vc[vfill[m->cv[q]]++] = (int32_t)c;
   free(vfill);
 
-  /* neigbcell: cells sharing at least one node (Sec. 3.1) */
+  /* neigbcell: cells sharing at least one node (Sec. 3.1); two passes */
   m->nb_ptr = (int64_t*)calloc(nc + 1, sizeof(int64_t));
-  int64_t cap = 1024;
-  int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * cap);
-  int64_t nbcap = 32 * nc, nbn = 0;
-  m->nb = (int32_t*)malloc(sizeof(int32_t) * nbcap);
-  for (int64_t c = 0; c < nc; ++c) {
-    int64_t k = 0;
-    for (int64_t q = m->cv_ptr[c]; q < m->cv_ptr[c + 1]; ++q) {
-      int32_t v = m->cv[q];
-      for (int64_t r = m->vc_ptr[v]; r < m->vc_ptr[v + 1]; ++r) {
-        if (k == cap) { cap *= 2; buf = (int32_t*)realloc(buf, sizeof(int32_t) * cap); }
-        buf[k++] = m->vc[r];
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      for (int64_t c = 0; c < nc; ++c) m->nb_ptr[c + 1] = m->nb_ptr[c] + ucnt[c];
+      m->nb = (int32_t*)malloc(sizeof(int32_t) * (m->nb_ptr[nc] > 0 ? m->nb_ptr[nc] : 1));
+    }
+#pragma omp parallel
+    {
+      int64_t cap = 1024;
+      int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * cap);
+#pragma omp for schedule(dynamic, 1024)
+      for (int64_t c = 0; c < nc; ++c) {
+        int64_t k = 0;
+        for (int64_t q = m->cv_ptr[c]; q < m->cv_ptr[c + 1]; ++q) {
+          int32_t v = m->cv[q];
+          for (int64_t r = m->vc_ptr[v]; r < m->vc_ptr[v + 1]; ++r) {
+            if (k == cap) { cap *= 2; buf = (int32_t*)realloc(buf, sizeof(int32_t) * cap); }
+            buf[k++] = m->vc[r];
+          }
+        }
+        k = sort_unique(buf, k);
+        if (pass == 0) { ucnt[c] = k - 1; continue; }
+        int64_t w = m->nb_ptr[c];
+        for (int64_t i = 0; i < k; ++i)
+          if (buf[i] != c) m->nb[w++] = buf[i];
       }
+      free(buf);
     }
-    k = sort_unique(buf, k);
-    for (int64_t i = 0; i < k; ++i) {
-      if (buf[i] == c) continue;
-      if (nbn == nbcap) { nbcap *= 2; m->nb = (int32_t*)realloc(m->nb, sizeof(int32_t) * nbcap); }
-      m->nb[nbn++] = buf[i];
-    }
-    m->nb_ptr[c + 1] = nbn;
   }
-  free(buf);
+  free(ucnt);
 
   /* face geometry (compgrid) */
   m->fc = (double*)malloc(sizeof(double) * 3 * nf);
   m->fn = (double*)malloc(sizeof(double) * 3 * nf);
   m->fa = (double*)malloc(sizeof(double) * nf);
   m->fp0 = (double*)malloc(sizeof(double) * 3 * nf);
+#pragma omp parallel for schedule(static)
   for (int64_t f = 0; f < nf; ++f) {
     int64_t b = fptr[f], I = fptr[f + 1] - b;
     double p0[3] = {0, 0, 0};
@@ -239,6 +254,7 @@ orc_mesh* orc_mesh_build(int64_t nv, const double* X, int64_t nf,
   m->cvol = (double*)malloc(sizeof(double) * nc);
   m->bbox = (double*)malloc(sizeof(double) * 6 * nc);
   m->convex = (uint8_t*)malloc(nc);
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) {
     double r[3] = {0, 0, 0};
     int64_t ncv = m->cv_ptr[c + 1] - m->cv_ptr[c];
@@ -343,12 +359,14 @@ int orc_candidates(const orc_mesh* m, int64_t f, int32_t* out, int cap) {
 void orc_taggrid(const orc_mesh* m, double eps, double* F, double* Fnode,
                  int8_t* tag_v, int8_t* tag_f, int8_t* tag_c) {
   /* cut-off of uniform cells (Sec. 2.1) and cell tags */
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < m->nc; ++c) {
     if (F[c] < eps) { F[c] = 0.0; tag_c[c] = -1; }
     else if (F[c] > 1.0 - eps) { F[c] = 1.0; tag_c[c] = 1; }
     else tag_c[c] = 0;
   }
   /* node values by inverse-distance weighting, node tags */
+#pragma omp parallel for schedule(static)
   for (int64_t v = 0; v < m->nv; ++v) {
     double num = 0, den = 0;
     for (int64_t q = m->vc_ptr[v]; q < m->vc_ptr[v + 1]; ++q) {
@@ -363,6 +381,7 @@ void orc_taggrid(const orc_mesh* m, double eps, double* F, double* Fnode,
     if (Fnode) Fnode[v] = fs;
     tag_v[v] = (int8_t)(fs < eps ? -1 : (fs > 1.0 - eps ? 1 : 0));
   }
+#pragma omp parallel for schedule(static)
   for (int64_t f = 0; f < m->nf; ++f) {
     int all_m = 1, all_p = 1;
     for (int64_t k = m->fptr[f]; k < m->fptr[f + 1]; ++k) {
@@ -926,13 +945,16 @@ void orc_vofadv(const orc_mesh* m, const double* Vd, const double* VF, double* F
 
 /* ------------------------------------------------------ time step (Eq eq:cfl) */
 static void max_face_speed(const orc_mesh* m, const orc_velocity* v, double t, double um[3]) {
-  um[0] = um[1] = um[2] = 0.0;
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : m0, m1, m2)
   for (int64_t f = 0; f < m->nf; ++f) {
     double u[3];
     orc_velocity_eval(v, m->fc + 3 * f, t, u);
-    for (int d = 0; d < 3; ++d)
-      if (fabs(u[d]) > um[d]) um[d] = fabs(u[d]);
+    if (fabs(u[0]) > m0) m0 = fabs(u[0]);
+    if (fabs(u[1]) > m1) m1 = fabs(u[1]);
+    if (fabs(u[2]) > m2) m2 = fabs(u[2]);
   }
+  um[0] = m0; um[1] = m1; um[2] = m2;
 }
 
 static double dt_from(const double hmin[3], const double um[3], double cfl) {

@@ -1,0 +1,522 @@
+// C-ABI entry points of the gvof library (declared in include/vof.h).
+#include <stdio.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mesh_host.h"
+#include "vof_common.cuh"
+
+using namespace gvof;
+
+namespace {
+
+thread_local std::string g_err;
+
+vof_status fail(vof_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(VOF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(vof_ctx* c, T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)n);
+  if (e == cudaSuccess) c->bytes += (int64_t)(sizeof(T) * (size_t)n);
+  return e;
+}
+
+void free_all(vof_ctx* c) {
+  void* ptrs[] = {c->x, c->y, c->z, c->fptr, c->fvert, c->own, c->nbr, c->fcx, c->fcy, c->fcz,
+                  c->fnx, c->fny, c->fnz, c->fa, c->cf_ptr, c->cf, c->cv_ptr, c->cv, c->vc_ptr,
+                  c->vc, c->nb_ptr, c->nb, c->ccx, c->ccy, c->ccz, c->cvol, c->bb, c->convex,
+                  c->F, c->nx, c->ny, c->nz, c->C, c->tv, c->tf, c->tc, c->Vd, c->VF, c->srate,
+                  c->icells, c->afaces, c->cnt, c->red};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->pinned) cudaFreeHost(c->pinned);
+}
+
+cudaMemcpyKind kind_to_dev(int mem) {
+  return mem == VOF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_dev(int mem) {
+  return mem == VOF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+__global__ void k_pack_planes(int64_t nc, const int8_t* tc, const double* nx, const double* ny,
+                              const double* nz, const double* C, double* out) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    bool i = tc[c] == 0;
+    out[4 * c + 0] = i ? nx[c] : 0.0;
+    out[4 * c + 1] = i ? ny[c] : 0.0;
+    out[4 * c + 2] = i ? nz[c] : 0.0;
+    out[4 * c + 3] = i ? C[c] : 0.0;
+  }
+}
+
+bool same_vel(const Vel& a, const Vel& b) {
+  return a.kind == b.kind && a.period == b.period && a.omega == b.omega && a.cx == b.cx &&
+         a.cy == b.cy && a.cz == b.cz && a.ux == b.ux && a.uy == b.uy && a.uz == b.uz;
+}
+
+vof_status ensure_velocity(vof_ctx* c, const vof_velocity* vel, cudaStream_t s) {
+  if (!vel) return fail(VOF_EINVAL, "velocity is NULL");
+  if (vel->kind < VOF_VEL_DEFORMATION || vel->kind > VOF_VEL_TRANSLATION)
+    return fail(VOF_EINVAL, "unknown velocity kind");
+  if (vel->kind == VOF_VEL_DEFORMATION && !(vel->period > 0))
+    return fail(VOF_EINVAL, "deformation period must be > 0");
+  Vel v = to_vel(*vel);
+  if (c->vel_valid && same_vel(v, c->vel_cached)) return VOF_OK;
+  CK(launch_velocity_setup(c, v, s));
+  unsigned long long* h = (unsigned long long*)c->pinned;
+  CK(cudaMemcpyAsync(h, c->cnt + kUmax, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int d = 0; d < 3; ++d) {
+    long long bits = (long long)h[d];
+    double x;
+    std::memcpy(&x, &bits, sizeof x);
+    c->umax0[d] = x;
+  }
+  c->vel_cached = v;
+  c->vel_valid = true;
+  return VOF_OK;
+}
+
+// record an event pair around one launch when timing is on
+struct PhaseTimer {
+  vof_ctx* c;
+  cudaStream_t s;
+  int slot;
+  PhaseTimer(vof_ctx* c_, int phase, cudaStream_t s_) : c(c_), s(s_), slot(-1) {
+    if (!c->timing) return;
+    if (c->n_ev_pairs >= 256) flush_timing(c);
+    slot = c->n_ev_pairs++;
+    c->ev_phase[slot] = phase;
+    cudaEventRecord(c->ev[2 * slot], s);
+  }
+  ~PhaseTimer() {
+    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+  }
+  static void flush_timing(vof_ctx* c) {
+    for (int i = 0; i < c->n_ev_pairs; ++i) {
+      cudaEventSynchronize(c->ev[2 * i + 1]);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]);
+      c->phase_ms[c->ev_phase[i]] += ms;
+      c->phase_n[c->ev_phase[i]] += 1;
+    }
+    c->n_ev_pairs = 0;
+  }
+};
+
+double dt_from(const double hmin[3], const double um[3], double cfl) {
+  double dt = 1e300;
+  for (int d = 0; d < 3; ++d)
+    if (um[d] > 0.0) dt = std::min(dt, hmin[d] / um[d]);
+  return dt * cfl;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vof_last_error(void) { return g_err.c_str(); }
+
+int64_t vof_device_bytes(const vof_ctx* c) { return c ? c->bytes : 0; }
+
+vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out) {
+  if (!mesh || !out) return fail(VOF_EINVAL, "mesh or out is NULL");
+  *out = nullptr;
+  const int64_t nv = mesh->n_vert, nf = mesh->n_face, nc = mesh->n_cell;
+  if (nv <= 0 || nf <= 0 || nc <= 0) return fail(VOF_EINVAL, "empty mesh");
+  if (nv >= (1LL << 31) || nf >= (1LL << 31) || nc >= (1LL << 31))
+    return fail(VOF_EINVAL, "mesh too large for 32-bit indices");
+  if (!mesh->X || !mesh->face_ptr || !mesh->face_vert || !mesh->owner || !mesh->neighbour)
+    return fail(VOF_EINVAL, "mesh array is NULL");
+  if (mesh->face_ptr[0] != 0) return fail(VOF_EINVAL, "face_ptr[0] != 0");
+  int maxI = 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    int64_t I = mesh->face_ptr[f + 1] - mesh->face_ptr[f];
+    if (I < 3 || I > kMaxFaceVerts)
+      return fail(VOF_EINVAL, "face " + std::to_string(f) + " has " + std::to_string(I) +
+                                  " nodes (3..8 supported)");
+    maxI = std::max<int>(maxI, (int)I);
+    int32_t o = mesh->owner[f], n = mesh->neighbour[f];
+    if (o < 0 || o >= nc || n >= nc || n == o)
+      return fail(VOF_EINVAL, "face " + std::to_string(f) + ": bad owner/neighbour");
+  }
+  const int64_t nfv = mesh->face_ptr[nf];
+  for (int64_t k = 0; k < nfv; ++k)
+    if (mesh->face_vert[k] < 0 || mesh->face_vert[k] >= nv)
+      return fail(VOF_EINVAL, "face_vert entry out of range");
+  vof_options o;
+  if (opt) o = *opt;
+  else {
+    std::memset(&o, 0, sizeof o);
+    o.eps = 1e-12;
+    o.beta = 1.5;
+    o.precision = VOF_PREC_FP64;
+  }
+  if (!(o.eps > 0 && o.eps < 0.5) || !(o.beta > 0) ||
+      (o.precision != VOF_PREC_FP64 && o.precision != VOF_PREC_MIXED))
+    return fail(VOF_EINVAL, "bad options");
+
+  HostConn hc;
+  std::string err;
+  if (!build_connectivity(nv, nf, nc, mesh->face_ptr, mesh->face_vert, mesh->owner,
+                          mesh->neighbour, hc, err))
+    return fail(VOF_EINVAL, err);
+  if (hc.max_cell_faces > 32 || hc.max_cell_verts > 32 || hc.max_cell_entries > 128)
+    return fail(VOF_EINVAL, "cell too large (<= 32 faces, 32 nodes, 128 face-node entries)");
+
+  vof_ctx* c = new vof_ctx();
+  std::memset((void*)c, 0, sizeof(vof_ctx));
+  c->nv = nv; c->nf = nf; c->nc = nc; c->nfv = nfv;
+  c->ncf = hc.cf_ptr[nc]; c->ncv = hc.cv_ptr[nc]; c->nvc = hc.vc_ptr[nv]; c->nnb = hc.nb_ptr[nc];
+  c->opt = o;
+  c->max_face_verts = maxI;
+  c->max_cell_faces = hc.max_cell_faces;
+  c->max_cell_verts = hc.max_cell_verts;
+  cudaGetDevice(&c->device);
+  auto cleanup = [&](vof_status s, const std::string& m) {
+    free_all(c);
+    delete c;
+    return fail(s, m);
+  };
+#define CKI(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      vof_status s_ = (e_ == cudaErrorMemoryAllocation) ? VOF_ENOMEM : VOF_ECUDA;          \
+      return cleanup(s_, std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    }                                                                                      \
+  } while (0)
+  CKI(dalloc(c, &c->x, nv)); CKI(dalloc(c, &c->y, nv)); CKI(dalloc(c, &c->z, nv));
+  CKI(dalloc(c, &c->fptr, nf + 1)); CKI(dalloc(c, &c->fvert, nfv));
+  CKI(dalloc(c, &c->own, nf)); CKI(dalloc(c, &c->nbr, nf));
+  CKI(dalloc(c, &c->fcx, nf)); CKI(dalloc(c, &c->fcy, nf)); CKI(dalloc(c, &c->fcz, nf));
+  CKI(dalloc(c, &c->fnx, nf)); CKI(dalloc(c, &c->fny, nf)); CKI(dalloc(c, &c->fnz, nf));
+  CKI(dalloc(c, &c->fa, nf));
+  CKI(dalloc(c, &c->cf_ptr, nc + 1)); CKI(dalloc(c, &c->cf, c->ncf));
+  CKI(dalloc(c, &c->cv_ptr, nc + 1)); CKI(dalloc(c, &c->cv, c->ncv));
+  CKI(dalloc(c, &c->vc_ptr, nv + 1)); CKI(dalloc(c, &c->vc, c->nvc));
+  CKI(dalloc(c, &c->nb_ptr, nc + 1)); CKI(dalloc(c, &c->nb, c->nnb));
+  CKI(dalloc(c, &c->ccx, nc)); CKI(dalloc(c, &c->ccy, nc)); CKI(dalloc(c, &c->ccz, nc));
+  CKI(dalloc(c, &c->cvol, nc)); CKI(dalloc(c, &c->bb, 6 * nc)); CKI(dalloc(c, &c->convex, nc));
+  CKI(dalloc(c, &c->F, nc));
+  CKI(dalloc(c, &c->nx, nc)); CKI(dalloc(c, &c->ny, nc)); CKI(dalloc(c, &c->nz, nc));
+  CKI(dalloc(c, &c->C, nc));
+  CKI(dalloc(c, &c->tv, nv)); CKI(dalloc(c, &c->tf, nf)); CKI(dalloc(c, &c->tc, nc));
+  CKI(dalloc(c, &c->Vd, nf)); CKI(dalloc(c, &c->VF, nf)); CKI(dalloc(c, &c->srate, nf));
+  CKI(dalloc(c, &c->icells, nc)); CKI(dalloc(c, &c->afaces, nf));
+  CKI(dalloc(c, &c->cnt, kNCnt)); CKI(dalloc(c, &c->red, kRedSlots));
+  CKI(cudaMallocHost(&c->pinned, 4096));
+
+  // SoA vertex coordinates
+  {
+    std::vector<double> t(nv);
+    for (int d = 0; d < 3; ++d) {
+      for (int64_t v = 0; v < nv; ++v) t[v] = mesh->X[3 * v + d];
+      CKI(cudaMemcpy(d == 0 ? c->x : (d == 1 ? c->y : c->z), t.data(), sizeof(double) * nv,
+                     cudaMemcpyHostToDevice));
+    }
+  }
+  CKI(cudaMemcpy(c->fptr, mesh->face_ptr, sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->fvert, mesh->face_vert, sizeof(int32_t) * nfv, cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->own, mesh->owner, sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->nbr, mesh->neighbour, sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->cf_ptr, hc.cf_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->cf, hc.cf.data(), sizeof(int32_t) * c->ncf, cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->cv_ptr, hc.cv_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->cv, hc.cv.data(), sizeof(int32_t) * c->ncv, cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->vc_ptr, hc.vc_ptr.data(), sizeof(int64_t) * (nv + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->vc, hc.vc.data(), sizeof(int32_t) * c->nvc, cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->nb_ptr, hc.nb_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemcpy(c->nb, hc.nb.data(), sizeof(int32_t) * c->nnb, cudaMemcpyHostToDevice));
+  CKI(cudaMemset(c->cnt, 0, sizeof(unsigned long long) * kNCnt));
+  CKI(cudaMemset(c->red, 0, sizeof(double) * kRedSlots));
+  CKI(cudaMemset(c->F, 0, sizeof(double) * nc));
+  CKI(cudaMemset(c->nx, 0, sizeof(double) * nc));
+  CKI(cudaMemset(c->ny, 0, sizeof(double) * nc));
+  CKI(cudaMemset(c->nz, 0, sizeof(double) * nc));
+  CKI(cudaMemset(c->C, 0, sizeof(double) * nc));
+  CKI(cudaMemset(c->tc, 0xff, nc));
+  CKI(cudaMemset(c->Vd, 0, sizeof(double) * nf));
+  CKI(cudaMemset(c->VF, 0, sizeof(double) * nf));
+  CKI(launch_face_geometry(c, 0));
+  CKI(launch_cell_geometry(c, 0));
+  CKI(cudaDeviceSynchronize());
+  {
+    std::vector<uint8_t> cvx(nc);
+    CKI(cudaMemcpy(cvx.data(), c->convex, nc, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nc; ++k)
+      if (!cvx[k]) return cleanup(VOF_EINVAL, "cell " + std::to_string(k) + " is not convex");
+    std::vector<double> bb(6 * nc);
+    CKI(cudaMemcpy(bb.data(), c->bb, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost));
+    for (int d = 0; d < 3; ++d) {
+      double h = 1e300;
+      for (int64_t k = 0; k < nc; ++k) h = std::min(h, bb[(3 + d) * nc + k] - bb[d * nc + k]);
+      c->hmin[d] = h;
+    }
+  }
+#undef CKI
+  *out = c;
+  return VOF_OK;
+}
+
+vof_status vof_set_timing(vof_ctx* c, int on) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (on && !c->timing) {
+    for (int i = 0; i < 2 * 256; ++i) CK(cudaEventCreate(&c->ev[i]));
+    c->n_ev_pairs = 0;
+    for (int i = 0; i < 8; ++i) { c->phase_ms[i] = 0; c->phase_n[i] = 0; }
+    c->timing = true;
+  } else if (!on && c->timing) {
+    PhaseTimer::flush_timing(c);
+    for (int i = 0; i < 2 * 256; ++i) cudaEventDestroy(c->ev[i]);
+    c->timing = false;
+  }
+  return VOF_OK;
+}
+
+vof_status vof_get_timing(vof_ctx* c, double* ms, int64_t* launches, int n) {
+  if (!c || n < 0 || n > VOF_NUM_PHASES) return fail(VOF_EINVAL, "bad argument");
+  if (c->timing) PhaseTimer::flush_timing(c);
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = c->phase_ms[i];
+    if (launches) launches[i] = c->phase_n[i];
+    c->phase_ms[i] = 0;
+    c->phase_n[i] = 0;
+  }
+  return VOF_OK;
+}
+
+void vof_destroy(vof_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  if (c->timing) vof_set_timing(c, 0);
+  free_all(c);
+  delete c;
+}
+
+vof_status vof_set_fraction(vof_ctx* c, const double* F, int mem, void* stream) {
+  if (!c || !F) return fail(VOF_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(c->F, F, sizeof(double) * c->nc, kind_to_dev(mem), s));
+  if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
+  c->recon_valid = false;
+  return VOF_OK;
+}
+
+vof_status vof_get_fraction(vof_ctx* c, double* F, int mem, void* stream) {
+  if (!c || !F) return fail(VOF_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(F, c->F, sizeof(double) * c->nc, kind_from_dev(mem), s));
+  if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
+  return VOF_OK;
+}
+
+vof_status vof_reconstruct(vof_ctx* c, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  cudaStream_t s = (cudaStream_t)stream;
+  { PhaseTimer t(c, VOF_PHASE_CELL_TAGS, s); CK(launch_cell_tags(c, s)); }
+  { PhaseTimer t(c, VOF_PHASE_NODE_TAGS, s); CK(launch_node_tags(c, s)); }
+  { PhaseTimer t(c, VOF_PHASE_RECONSTRUCT, s); CK(launch_reconstruct(c, s)); }
+  c->recon_valid = true;
+  return VOF_OK;
+}
+
+vof_status vof_advect(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (!c->recon_valid) return fail(VOF_ESTATE, "advect needs a reconstruction of the current F");
+  if (!(dt >= 0)) return fail(VOF_EINVAL, "dt must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  vof_status st = ensure_velocity(c, vel, s);
+  if (st != VOF_OK) return st;
+  const double g = time_factor(c->vel_cached, t + 0.5 * dt);
+  { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s); CK(launch_face_sweep(c, g, dt, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, c->vel_cached, g, dt, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_UPDATE, s); CK(launch_update(c, s)); }
+  c->recon_valid = false;
+  return VOF_OK;
+}
+
+vof_status vof_step(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
+  vof_status st = vof_advect(c, vel, t, dt, stream);
+  if (st != VOF_OK) return st;
+  return vof_reconstruct(c, stream);
+}
+
+vof_status vof_suggest_dt(vof_ctx* c, const vof_velocity* vel, double t, double cfl,
+                          double t_end, double* dt) {
+  if (!c || !dt) return fail(VOF_EINVAL, "NULL argument");
+  if (!(cfl > 0)) return fail(VOF_EINVAL, "cfl must be > 0");
+  vof_status st = ensure_velocity(c, vel, 0);
+  if (st != VOF_OK) return st;
+  const Vel& v = c->vel_cached;
+  double um[3];
+  double g0 = std::fabs(time_factor(v, t));
+  for (int d = 0; d < 3; ++d) um[d] = g0 * c->umax0[d];
+  double d1 = dt_from(c->hmin, um, cfl);
+  if (t + d1 > t_end) d1 = t_end - t;
+  double g1 = std::fabs(time_factor(v, t + d1));
+  for (int d = 0; d < 3; ++d) um[d] = std::max(um[d], g1 * c->umax0[d]);
+  double d2 = dt_from(c->hmin, um, cfl);
+  double r = std::min(d1, d2);
+  if (t + r > t_end) r = t_end - t;
+  *dt = r;
+  return VOF_OK;
+}
+
+vof_status vof_get_planes(vof_ctx* c, double* planes, int mem, void* stream) {
+  if (!c || !planes) return fail(VOF_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* dst = planes;
+  if (mem != VOF_MEM_DEVICE) CK(cudaMallocAsync((void**)&dst, sizeof(double) * 4 * c->nc, s));
+  k_pack_planes<<<kSMs * 8, 256, 0, s>>>(c->nc, c->tc, c->nx, c->ny, c->nz, c->C, dst);
+  CK(cudaGetLastError());
+  if (mem != VOF_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(planes, dst, sizeof(double) * 4 * c->nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(dst, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return VOF_OK;
+}
+
+vof_status vof_get_tags(vof_ctx* c, int8_t* tv, int8_t* tf, int8_t* tc, int mem, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (tv) CK(cudaMemcpyAsync(tv, c->tv, c->nv, kind_from_dev(mem), s));
+  if (tf) CK(cudaMemcpyAsync(tf, c->tf, c->nf, kind_from_dev(mem), s));
+  if (tc) CK(cudaMemcpyAsync(tc, c->tc, c->nc, kind_from_dev(mem), s));
+  if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
+  return VOF_OK;
+}
+
+vof_status vof_get_face_flux(vof_ctx* c, double* Vd, double* VF, int mem, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (Vd) CK(cudaMemcpyAsync(Vd, c->Vd, sizeof(double) * c->nf, kind_from_dev(mem), s));
+  if (VF) CK(cudaMemcpyAsync(VF, c->VF, sizeof(double) * c->nf, kind_from_dev(mem), s));
+  if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
+  return VOF_OK;
+}
+
+vof_status vof_get_geometry(vof_ctx* c, double* cell_vol, double* cell_cen, double* face_cen,
+                            double* face_nrm, double* face_area, int mem, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemcpyKind k = kind_from_dev(mem);
+  if (cell_vol) CK(cudaMemcpyAsync(cell_vol, c->cvol, sizeof(double) * c->nc, k, s));
+  if (face_area) CK(cudaMemcpyAsync(face_area, c->fa, sizeof(double) * c->nf, k, s));
+  const double* cc[3] = {c->ccx, c->ccy, c->ccz};
+  const double* fc[3] = {c->fcx, c->fcy, c->fcz};
+  const double* fn[3] = {c->fnx, c->fny, c->fnz};
+  for (int d = 0; d < 3; ++d) {
+    if (cell_cen)
+      CK(cudaMemcpy2DAsync(cell_cen + d, 3 * sizeof(double), cc[d], sizeof(double), sizeof(double),
+                           c->nc, k, s));
+    if (face_cen)
+      CK(cudaMemcpy2DAsync(face_cen + d, 3 * sizeof(double), fc[d], sizeof(double), sizeof(double),
+                           c->nf, k, s));
+    if (face_nrm)
+      CK(cudaMemcpy2DAsync(face_nrm + d, 3 * sizeof(double), fn[d], sizeof(double), sizeof(double),
+                           c->nf, k, s));
+  }
+  if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
+  return VOF_OK;
+}
+
+vof_status vof_get_neighbors(vof_ctx* c, int64_t* ptr, int32_t* idx, int64_t* count) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (count) *count = c->nnb;
+  if (ptr) CK(cudaMemcpy(ptr, c->nb_ptr, sizeof(int64_t) * (c->nc + 1), cudaMemcpyDeviceToHost));
+  if (idx) CK(cudaMemcpy(idx, c->nb, sizeof(int32_t) * c->nnb, cudaMemcpyDeviceToHost));
+  return VOF_OK;
+}
+
+vof_status vof_get_candidates(vof_ctx* c, const int32_t* faces, int n, int64_t* out_ptr,
+                              int32_t* out_idx, int64_t cap) {
+  if (!c || !faces || !out_ptr || n < 0) return fail(VOF_EINVAL, "bad argument");
+  for (int i = 0; i < n; ++i)
+    if (faces[i] < 0 || faces[i] >= c->nf) return fail(VOF_EINVAL, "face index out of range");
+  if (n == 0) { out_ptr[0] = 0; return VOF_OK; }
+  const int64_t stride = 128;
+  int32_t *df, *dout, *dcnt;
+  CK(cudaMalloc(&df, sizeof(int32_t) * n));
+  CK(cudaMalloc(&dout, sizeof(int32_t) * n * stride));
+  CK(cudaMalloc(&dcnt, sizeof(int32_t) * n));
+  CK(cudaMemcpy(df, faces, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  CK(launch_candidates(c, df, n, stride, dout, dcnt, 0));
+  std::vector<int32_t> h(n * stride), hc(n);
+  CK(cudaMemcpy(h.data(), dout, sizeof(int32_t) * n * stride, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hc.data(), dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  cudaFree(df); cudaFree(dout); cudaFree(dcnt);
+  out_ptr[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    if (hc[i] > stride) return fail(VOF_ECAPACITY, "more than 128 candidates for a face");
+    out_ptr[i + 1] = out_ptr[i] + hc[i];
+    if (out_idx) {
+      if (out_ptr[i + 1] > cap) return fail(VOF_ECAPACITY, "out_idx too small");
+      std::memcpy(out_idx + out_ptr[i], h.data() + i * stride, sizeof(int32_t) * hc[i]);
+    }
+  }
+  return VOF_OK;
+}
+
+vof_status vof_get_flux_polyhedra(vof_ctx* c, const vof_velocity* vel, double t, double dt,
+                                  const int32_t* faces, int n, double* verts, int32_t* counts) {
+  if (!c || !faces || !verts || !counts || n < 0) return fail(VOF_EINVAL, "bad argument");
+  for (int i = 0; i < n; ++i)
+    if (faces[i] < 0 || faces[i] >= c->nf) return fail(VOF_EINVAL, "face index out of range");
+  vof_status st = ensure_velocity(c, vel, 0);
+  if (st != VOF_OK) return st;
+  if (n == 0) return VOF_OK;
+  const int NBV = 2 * kMaxFaceVerts + 1;
+  int32_t *df, *dcnt;
+  double* dv;
+  CK(cudaMalloc(&df, sizeof(int32_t) * n));
+  CK(cudaMalloc(&dcnt, sizeof(int32_t) * n));
+  CK(cudaMalloc(&dv, sizeof(double) * n * NBV * 3));
+  CK(cudaMemset(dv, 0, sizeof(double) * n * NBV * 3));
+  CK(cudaMemcpy(df, faces, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  const double g = time_factor(c->vel_cached, t + 0.5 * dt);
+  CK(launch_polyhedra(c, c->vel_cached, g, dt, df, n, dv, dcnt, 0));
+  CK(cudaMemcpy(verts, dv, sizeof(double) * n * NBV * 3, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(counts, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  cudaFree(df); cudaFree(dcnt); cudaFree(dv);
+  return VOF_OK;
+}
+
+vof_status vof_get_stats(vof_ctx* c, vof_stats* out, void* stream) {
+  if (!c || !out) return fail(VOF_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_volume_sum(c, s));
+  unsigned long long* h = (unsigned long long*)c->pinned;
+  double* hd = (double*)((char*)c->pinned + 1024);
+  CK(cudaMemcpyAsync(h, c->cnt, sizeof(unsigned long long) * kNCnt, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hd, c->red + kRedSlots - 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out->n_interfacial = (int64_t)h[kNIcells];
+  out->n_active_faces = (int64_t)h[kNAfaces];
+  out->n_truncations = (int64_t)h[kNTrunc];
+  out->n_overflow = (int64_t)h[kNOverflow];
+  out->n_degenerate = (int64_t)h[kNDegen];
+  out->n_edgeon = (int64_t)h[kNEdgeOn];
+  out->volume = hd[0];
+  out->ebound = hd[1];
+  return VOF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Set-up kernels: face and cell geometry (the compgrid routine of Sec. 3.1)
+// and the per-face flux rate of a separable velocity field.
+#include "vof_common.cuh"
+
+namespace gvof {
+namespace {
+
+// face vector area, unit normal (out of the owner), area and area centroid
+// from the fan of triangles about the vertex average
+__global__ void k_face_geometry(DevMesh M, double* fcx, double* fcy, double* fcz, double* fnx,
+                                double* fny, double* fnz, double* fa) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M.nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = M.fptr[f];
+    int I = (int)(M.fptr[f + 1] - b);
+    double px = 0, py = 0, pz = 0;
+    for (int i = 0; i < I; ++i) {
+      int v = M.fvert[b + i];
+      px += M.x[v]; py += M.y[v]; pz += M.z[v];
+    }
+    px /= I; py /= I; pz /= I;
+    double Ax = 0, Ay = 0, Az = 0;
+    for (int i = 0; i < I; ++i) {
+      int va = M.fvert[b + i], vb = M.fvert[b + (i + 1 == I ? 0 : i + 1)];
+      double ax = M.x[va] - px, ay = M.y[va] - py, az = M.z[va] - pz;
+      double bx = M.x[vb] - px, by = M.y[vb] - py, bz = M.z[vb] - pz;
+      Ax += 0.5 * (ay * bz - az * by);
+      Ay += 0.5 * (az * bx - ax * bz);
+      Az += 0.5 * (ax * by - ay * bx);
+    }
+    double A = sqrt(Ax * Ax + Ay * Ay + Az * Az);
+    double nx = Ax / A, ny = Ay / A, nz = Az / A;
+    double cx = 0, cy = 0, cz = 0, ws = 0;
+    for (int i = 0; i < I; ++i) {
+      int va = M.fvert[b + i], vb = M.fvert[b + (i + 1 == I ? 0 : i + 1)];
+      double ax = M.x[va] - px, ay = M.y[va] - py, az = M.z[va] - pz;
+      double bx = M.x[vb] - px, by = M.y[vb] - py, bz = M.z[vb] - pz;
+      double w = 0.5 * (nx * (ay * bz - az * by) + ny * (az * bx - ax * bz) + nz * (ax * by - ay * bx));
+      ws += w;
+      cx += w * (ax + bx) / 3.0;
+      cy += w * (ay + by) / 3.0;
+      cz += w * (az + bz) / 3.0;
+    }
+    fcx[f] = px + cx / ws; fcy[f] = py + cy / ws; fcz[f] = pz + cz / ws;
+    fnx[f] = nx; fny[f] = ny; fnz[f] = nz;
+    fa[f] = A;
+  }
+}
+
+// cell volume and centroid from signed tetrahedra (vertex average, face
+// vertex average, edge), bounding box, and a convexity flag
+__global__ void k_cell_geometry(DevMesh M, double* ccx, double* ccy, double* ccz, double* cvol,
+                                double* bb, uint8_t* convex) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v0 = M.cv_ptr[c], v1 = M.cv_ptr[c + 1];
+    double rx = 0, ry = 0, rz = 0;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t q = v0; q < v1; ++q) {
+      int v = M.cv[q];
+      double p[3] = {M.x[v], M.y[v], M.z[v]};
+      rx += p[0]; ry += p[1]; rz += p[2];
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = fmin(lo[d], p[d]);
+        hi[d] = fmax(hi[d], p[d]);
+      }
+    }
+    double nvc = (double)(v1 - v0);
+    rx /= nvc; ry /= nvc; rz /= nvc;
+    double vol = 0, mx = 0, my = 0, mz = 0;
+    for (int64_t q = M.cf_ptr[c]; q < M.cf_ptr[c + 1]; ++q) {
+      int fs = M.cf[q];
+      bool out = fs >= 0;
+      int f = out ? fs : ~fs;
+      int64_t b = M.fptr[f];
+      int I = (int)(M.fptr[f + 1] - b);
+      double px = 0, py = 0, pz = 0;
+      for (int i = 0; i < I; ++i) {
+        int v = M.fvert[b + i];
+        px += M.x[v]; py += M.y[v]; pz += M.z[v];
+      }
+      px = px / I - rx; py = py / I - ry; pz = pz / I - rz;
+      for (int i = 0; i < I; ++i) {
+        int va = M.fvert[b + i], vb = M.fvert[b + (i + 1 == I ? 0 : i + 1)];
+        if (!out) { int t = va; va = vb; vb = t; }
+        double ax = M.x[va] - rx, ay = M.y[va] - ry, az = M.z[va] - rz;
+        double bx = M.x[vb] - rx, by = M.y[vb] - ry, bz = M.z[vb] - rz;
+        double v6 = px * (ay * bz - az * by) + py * (az * bx - ax * bz) + pz * (ax * by - ay * bx);
+        double v = v6 / 6.0;
+        vol += v;
+        mx += v * (px + ax + bx) * 0.25;
+        my += v * (py + ay + by) * 0.25;
+        mz += v * (pz + az + bz) * 0.25;
+      }
+    }
+    cvol[c] = vol;
+    ccx[c] = rx + mx / vol; ccy[c] = ry + my / vol; ccz[c] = rz + mz / vol;
+    for (int d = 0; d < 3; ++d) {
+      bb[d * M.nc + c] = lo[d];
+      bb[(3 + d) * M.nc + c] = hi[d];
+    }
+    // convex: no vertex lies outside the plane of any of its faces
+    double h = cbrt(fabs(vol));
+    uint8_t cvx = 1;
+    for (int64_t q = M.cf_ptr[c]; q < M.cf_ptr[c + 1] && cvx; ++q) {
+      int fs = M.cf[q];
+      int f = fs >= 0 ? fs : ~fs;
+      double s = fs >= 0 ? 1.0 : -1.0;
+      // face centroid is not yet available here; use its first vertex
+      int va = M.fvert[M.fptr[f]];
+      double nx = 0, ny = 0, nz = 0;
+      {
+        int64_t b = M.fptr[f];
+        int I = (int)(M.fptr[f + 1] - b);
+        for (int i = 0; i < I; ++i) {
+          int p = M.fvert[b + i], r = M.fvert[b + (i + 1 == I ? 0 : i + 1)];
+          nx += M.y[p] * M.z[r] - M.z[p] * M.y[r];
+          ny += M.z[p] * M.x[r] - M.x[p] * M.z[r];
+          nz += M.x[p] * M.y[r] - M.y[p] * M.x[r];
+        }
+        double l = sqrt(nx * nx + ny * ny + nz * nz);
+        nx /= l; ny /= l; nz /= l;
+      }
+      for (int64_t p = v0; p < v1; ++p) {
+        int v = M.cv[p];
+        double d = s * ((M.x[v] - M.x[va]) * nx + (M.y[v] - M.y[va]) * ny + (M.z[v] - M.z[va]) * nz);
+        if (d > 1e-10 * h) { cvx = 0; break; }
+      }
+    }
+    convex[c] = cvx;
+  }
+}
+
+// flux rate (u0(x_f).n_f) A_f of every face and max |u0| per axis over the
+// face centres (for Eq. eq:cfl)
+__global__ void k_velocity_setup(DevMesh M, Vel v, double* srate, unsigned long long* umax) {
+  double m0 = 0, m1 = 0, m2 = 0;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M.nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    double u, w, s;
+    vel0<double>(v, M.fcx[f], M.fcy[f], M.fcz[f], u, w, s);
+    srate[f] = (u * M.fnx[f] + w * M.fny[f] + s * M.fnz[f]) * M.fa[f];
+    m0 = fmax(m0, fabs(u)); m1 = fmax(m1, fabs(w)); m2 = fmax(m2, fabs(s));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmax(m0, __shfl_xor_sync(GVOF_FULL, m0, o));
+    m1 = fmax(m1, __shfl_xor_sync(GVOF_FULL, m1, o));
+    m2 = fmax(m2, __shfl_xor_sync(GVOF_FULL, m2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(umax + 0, (unsigned long long)__double_as_longlong(m0));
+    atomicMax(umax + 1, (unsigned long long)__double_as_longlong(m1));
+    atomicMax(umax + 2, (unsigned long long)__double_as_longlong(m2));
+  }
+}
+
+inline int grid_for(int64_t n, int bs) {
+  int64_t g = (n + bs - 1) / bs;
+  int64_t cap = (int64_t)kSMs * 16;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s) {
+  k_face_geometry<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->fcx, c->fcy, c->fcz,
+                                                       c->fnx, c->fny, c->fnz, c->fa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_geometry(const vof_ctx* c, cudaStream_t s) {
+  k_cell_geometry<<<grid_for(c->nc, 256), 256, 0, s>>>(mesh_view(c), c->ccx, c->ccy, c->ccz,
+                                                       c->cvol, c->bb, c->convex);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_velocity_setup(const vof_ctx* c, const Vel& v, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->cnt + kUmax, 0, 3 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_velocity_setup<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), v, c->srate,
+                                                        c->cnt + kUmax);
+  return cudaGetLastError();
+}
+
+}  // namespace gvof

@@ -1,0 +1,215 @@
+// Full-grid sweeps of one step: tags (Sec. 3.3), the face sweep that forms
+// V_d (Eq. a-donacion) and the shortcut fluxes of tag -1/1 faces, and the
+// cell update of Eq. fnext with the final clip (Sec. 2.2). These kernels
+// are HBM-bound: one thread per cell / node / face, coalesced SoA loads,
+// warp-aggregated compaction of the band work lists.
+#include "vof_common.cuh"
+
+namespace gvof {
+namespace {
+
+inline int grid_for(int64_t n, int bs) {
+  int64_t g = (n + bs - 1) / bs;
+  int64_t cap = (int64_t)kSMs * 16;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// append `item` to list when `pred` holds; one atomic per warp
+__device__ __forceinline__ void warp_append(bool pred, int32_t item, int32_t* list,
+                                            unsigned long long* counter) {
+  unsigned m = __ballot_sync(GVOF_FULL, pred);
+  if (m == 0) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(GVOF_FULL, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1))] = item;
+}
+
+// cut-off of uniform cells and cell tags (Sec. 2.1, Sec. 3.3); interfacial
+// cells are appended to the band list
+__global__ void k_cell_tags(int64_t nc, double eps, double* F, int8_t* tc, int32_t* icells,
+                            unsigned long long* cnt) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += stride) {
+    int64_t c = base + threadIdx.x;
+    bool in = c < nc;
+    int8_t t = -1;
+    if (in) {
+      double f = F[c];
+      if (f < eps) { t = -1; if (f != 0.0) F[c] = 0.0; }
+      else if (f > 1.0 - eps) { t = 1; if (f != 1.0) F[c] = 1.0; }
+      else t = 0;
+      tc[c] = t;
+    }
+    warp_append(in && t == 0, (int32_t)c, icells, cnt + kNIcells);
+  }
+}
+
+// node value F* by inverse-distance weighting of the cells sharing the node
+// and node tags (Sec. 3.3). Nodes whose cells are all empty or all full take
+// F* = 0 or 1 exactly without forming the weights.
+template <typename G>
+__global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < M.nv;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q0 = M.vc_ptr[v], q1 = M.vc_ptr[v + 1];
+    bool allz = true, allo = true;
+    for (int64_t q = q0; q < q1; ++q) {
+      double f = F[M.vc[q]];
+      allz &= (f == 0.0);
+      allo &= (f == 1.0);
+    }
+    int8_t t;
+    if (allz) t = -1;
+    else if (allo) t = 1;
+    else {
+      double xv = M.x[v], yv = M.y[v], zv = M.z[v];
+      double num = 0.0, den = 0.0;
+      for (int64_t q = q0; q < q1; ++q) {
+        int c = M.vc[q];
+        G dx = (G)(xv - M.ccx[c]), dy = (G)(yv - M.ccy[c]), dz = (G)(zv - M.ccz[c]);
+        G r2 = dx * dx + dy * dy + dz * dz;
+        double w = (double)(G(1) / sqrt(r2));
+        num += w * F[c];
+        den += w;
+      }
+      double fs = num / den;
+      t = fs < eps ? -1 : (fs > 1.0 - eps ? 1 : 0);
+    }
+    tv[v] = t;
+  }
+}
+
+// face sweep: face tags from node tags, V_d = g(t+dt/2) (u0.n) A dt,
+// V_F = 0 on tag -1 faces, V_F = V_d on tag 1 faces (no geometry, Sec. 3.3);
+// tag 0 faces are appended to the active list for the flux kernel
+__global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate, double gdt,
+                             int8_t* tf, double* Vd, double* VF, int32_t* afaces,
+                             unsigned long long* cnt) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < M.nf; base += stride) {
+    int64_t f = base + threadIdx.x;
+    bool in = f < M.nf;
+    int8_t t = 0;
+    if (in) {
+      int64_t b = M.fptr[f], e = M.fptr[f + 1];
+      bool allm = true, allp = true;
+      for (int64_t k = b; k < e; ++k) {
+        int8_t x = tv[M.fvert[k]];
+        allm &= (x == -1);
+        allp &= (x == 1);
+      }
+      t = allm ? -1 : (allp ? 1 : 0);
+      double vd = srate[f] * gdt;
+      tf[f] = t;
+      Vd[f] = vd;
+      if (t == -1) VF[f] = 0.0;
+      else if (t == 1) VF[f] = vd;
+    }
+    warp_append(in && t == 0, (int32_t)f, afaces, cnt + kNAfaces);
+  }
+}
+
+// Eq. fnext and the clip of Sec. 2.2; red[] receives per-block partial
+// E_bound maxima (before the clip)
+__global__ void k_update(DevMesh M, double* F, const double* Vd, const double* VF,
+                         double* red) {
+  double eb = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double vdt = 0.0, vft = 0.0;
+    for (int64_t q = M.cf_ptr[c]; q < M.cf_ptr[c + 1]; ++q) {
+      int fs = M.cf[q];
+      if (fs >= 0) { vdt += Vd[fs]; vft += VF[fs]; }
+      else { vdt -= Vd[~fs]; vft -= VF[~fs]; }
+    }
+    double V = M.cvol[c];
+    double h = vdt / (2.0 * V);
+    double fn = (F[c] * (1.0 + h) - vft / V) / (1.0 - h);
+    eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
+    F[c] = fmax(fmin(fn, 1.0), 0.0);
+  }
+  for (int o = 16; o > 0; o >>= 1) eb = fmax(eb, __shfl_xor_sync(GVOF_FULL, eb, o));
+  __shared__ double s[32];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) s[w] = eb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, s[i]);
+    red[kRedSlots / 2 + blockIdx.x] = m;
+  }
+}
+
+// sum of V F in a fixed order: per-block partials then one block
+__global__ void k_volume_partial(DevMesh M, const double* F, double* red) {
+  double acc = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
+       c += (int64_t)gridDim.x * blockDim.x)
+    acc += M.cvol[c] * F[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(GVOF_FULL, acc, o);
+  __shared__ double s[32];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) s[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s[i];
+    red[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_volume_final(double* red, int nblocks, int neb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < nblocks; ++i) t += red[i];
+  double eb = 0.0;
+  for (int i = 0; i < neb; ++i) eb = fmax(eb, red[kRedSlots / 2 + i]);
+  red[kRedSlots - 2] = t;
+  red[kRedSlots - 1] = eb;
+}
+
+constexpr int kUpdBlocks = kSMs * 4;  // fixed, <= kRedSlots/2 - 2
+
+}  // namespace
+
+cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->cnt + kNIcells, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_cell_tags<<<grid_for(c->nc, 256), 256, 0, s>>>(c->nc, c->opt.eps, c->F, c->tc, c->icells,
+                                                   c->cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s) {
+  if (c->opt.precision == VOF_PREC_MIXED)
+    k_node_tags<float><<<grid_for(c->nv, 256), 256, 0, s>>>(mesh_view(c), c->F, c->opt.eps, c->tv);
+  else
+    k_node_tags<double><<<grid_for(c->nv, 256), 256, 0, s>>>(mesh_view(c), c->F, c->opt.eps, c->tv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_sweep(const vof_ctx* c, double g_half, double dt, cudaStream_t s) {
+  // counters of this advect: active faces, truncations, overflow, fallbacks
+  static_assert(kNAfaces + 1 == kNTrunc && kNTrunc + 3 == kNEdgeOn, "counter layout");
+  cudaError_t e = cudaMemsetAsync(c->cnt + kNAfaces, 0, 5 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->srate, g_half * dt,
+                                                    c->tf, c->Vd, c->VF, c->afaces, c->cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const vof_ctx* c, cudaStream_t s) {
+  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->Vd, c->VF, c->red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s) {
+  k_volume_partial<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->red);
+  k_volume_final<<<1, 32, 0, s>>>(c->red, kUpdBlocks, kUpdBlocks);
+  return cudaGetLastError();
+}
+
+}  // namespace gvof

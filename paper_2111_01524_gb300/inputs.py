@@ -23,9 +23,10 @@ Every mesh is returned as a dict of numpy arrays:
   face_vert  int32   [...]        face node loops
   owner      int32   [n_face]
   neighbour  int32   [n_face]     -1 on the domain boundary
-  cell_tets  float64 [n_tet, 4, 3] a tetrahedral decomposition of the cells
-  cell_of_tet int32  [n_tet]      (used only by ``init_fraction``)
   n_cell     int
+  cell_tets  callable(cells) -> (tets [m, 4, 3], cell of each tet [m]): a
+             tetrahedral decomposition of the given cells (``init_fraction``)
+  cell_corners callable(cells) -> vertex ids of the cells' corners (or None)
 """
 from __future__ import annotations
 
@@ -97,11 +98,13 @@ def _grid_vertices(n, lo, hi, jitter, rng):
 
 
 def _vid(n, i, j, k):
-    return i + (n + 1) * (j + (n + 1) * k)
+    n1 = np.int64(n + 1)
+    return i + n1 * (j + n1 * k)
 
 
 def _cid(n, i, j, k):
-    return i + n * (j + n * k)
+    n0 = np.int64(n)
+    return i + n0 * (j + n0 * k)
 
 
 def _hex_faces(n):
@@ -199,12 +202,37 @@ def hex_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.0, seed=0):
     X, h = _grid_vertices(n, lo, hi, jitter, rng)
     L, owner, nbr = _hex_faces(n)
     ptr, fv = _csr(L)
-    corner = _hex_cell_corners(n)
-    tets = _kuhn_tets_of_cubes(corner)
-    cell = np.arange(n ** 3, dtype=np.int32)
-    tv = np.concatenate(tets)
+
+    def corners(cells):
+        cells = np.asarray(cells, np.int64)
+        i, j, k = cells % n, (cells // n) % n, cells // (n * n)
+        ids = [_vid(n, i + (b & 1), j + ((b >> 1) & 1), k + ((b >> 2) & 1)) for b in range(8)]
+        return np.stack(ids, axis=1)
+
+    def tets(cells):
+        c = corners(cells)
+        T = []
+        for p in _KUHN_PATHS:
+            a = [0, 0, 0]
+            v = [c[:, 0]]
+            for ax in p:
+                a[ax] = 1
+                v.append(c[:, a[0] + 2 * a[1] + 4 * a[2]])
+            T.append(np.stack(v, axis=1))
+        T = np.stack(T, axis=1).reshape(-1, 4)
+        return X[T], np.repeat(np.asarray(cells, np.int64), 6)
+
+    box = None
+    if jitter == 0.0:
+        lo_ = np.asarray(lo, np.float64)
+
+        def box(cells):
+            cells = np.asarray(cells, np.int64)
+            ijk = np.stack([cells % n, (cells // n) % n, cells // (n * n)], axis=1)
+            return lo_ + ijk * h, h
+
     return dict(X=X, face_ptr=ptr, face_vert=fv, owner=owner, neighbour=nbr,
-                n_cell=n ** 3, cell_tets=X[tv], cell_of_tet=np.tile(cell, 6),
+                n_cell=n ** 3, cell_corners=corners, cell_tets=tets, cell_box=box,
                 kind="hex", n=n, h=h)
 
 
@@ -254,9 +282,17 @@ def kuhn_tet_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.2, seed=0)
     owner_s[swap], nbr_s[swap] = neighbour[swap], owner[swap]
     loops[swap] = fl[o2]
     ptr, fv = _csr(loops)
+
+    def corners(cells):
+        return T[np.asarray(cells, np.int64)]
+
+    def tets(cells):
+        cells = np.asarray(cells, np.int64)
+        return X[T[cells]], cells
+
     return dict(X=X, face_ptr=ptr, face_vert=fv, owner=owner_s.astype(np.int32),
-                neighbour=nbr_s.astype(np.int32), n_cell=nt, cell_tets=X[T],
-                cell_of_tet=np.arange(nt, dtype=np.int32), kind="tet", n=n, h=h)
+                neighbour=nbr_s.astype(np.int32), n_cell=nt, cell_corners=corners,
+                cell_tets=tets, kind="tet", n=n, h=h)
 
 
 def trihex_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.3, seed=0):
@@ -301,11 +337,26 @@ def trihex_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.3, seed=0):
             break
     else:  # pragma: no cover
         raise RuntimeError("could not generate a valid distorted grid")
-    cot = np.concatenate([t_owner, t_nbr[inner]]).astype(np.int32)
+    cot = np.concatenate([t_owner, t_nbr[inner]]).astype(np.int64)
+    order = np.argsort(cot, kind="stable")
+    P, cot = P[order], cot[order]
+    start = np.searchsorted(cot, np.arange(nc + 1))
     ptr, fv = _csr(tri.astype(np.int32))
+
+    def tets(cells):
+        cells = np.asarray(cells, np.int64)
+        if len(cells) == 0:
+            return P[:0], cot[:0]
+        idx = np.concatenate([np.arange(start[c], start[c + 1]) for c in cells])
+        return P[idx], cot[idx]
+
+    def points(cells):
+        T, _ = tets(cells)
+        return T.reshape(len(cells), -1, 3)
+
     return dict(X=Xall, face_ptr=ptr, face_vert=fv, owner=t_owner.astype(np.int32),
-                neighbour=t_nbr.astype(np.int32), n_cell=nc, cell_tets=P,
-                cell_of_tet=cot, kind="trihex", n=n, h=h)
+                neighbour=t_nbr.astype(np.int32), n_cell=nc, cell_corners=None,
+                cell_tets=tets, cell_points=points, kind="trihex", n=n, h=h)
 
 
 def mesh_counts(mesh):
@@ -358,22 +409,71 @@ def _subdivide_tets(P):
     return np.concatenate([np.stack(k, axis=1) for k in kids])
 
 
-def init_fraction(mesh, body, levels=4, chunk=1 << 20):
+def init_fraction(mesh, body, levels=4, chunk=1 << 18):
     """Initial F per cell: adaptive refinement of the cells' tetrahedra.
 
-    A tetrahedron whose circumscribing ball (about its centroid) lies on one
-    side of the body is counted whole; the others are split 8-fold, up to
-    ``levels`` times, and the leaves are classified by their centroid.
+    Cells whose bounding ball lies on one side of the body are 0 or 1; the
+    others are split into tetrahedra, and a tetrahedron whose ball (about its
+    centroid) lies on one side is counted whole while the rest are split
+    8-fold, up to ``levels`` times; leaves are classified by their centroid.
     Returns F (float64 [n_cell]) with values in [0, 1].
     """
-    T = mesh["cell_tets"]
-    cot = mesh["cell_of_tet"].astype(np.int64)
     nc = int(mesh["n_cell"])
-    vol_cell = np.bincount(cot, weights=np.abs(_tet_volumes(T)), minlength=nc)
-    inside = np.zeros(nc)
-    for s in range(0, T.shape[0], chunk):
-        P = T[s:s + chunk]
-        owner = cot[s:s + chunk]
+    X = mesh["X"]
+    F = np.zeros(nc)
+    band = []
+    for s in range(0, nc, chunk):
+        cells = np.arange(s, min(nc, s + chunk))
+        if mesh.get("cell_corners") is not None:
+            P = X[mesh["cell_corners"](cells)]
+        else:
+            P = mesh["cell_points"](cells)
+        cen = P.mean(axis=1)
+        r = np.sqrt(np.max(np.sum((P - cen[:, None, :]) ** 2, axis=2), axis=1))
+        d = body.dist(cen)
+        F[cells[d < -r]] = 1.0
+        band.append(cells[np.abs(d) <= r])
+    band = np.concatenate(band) if band else np.zeros(0, np.int64)
+    if mesh.get("cell_box") is not None:
+        # axis-aligned boxes: octree refinement with exact box volumes
+        step = max(1, chunk // 16)
+        for s in range(0, len(band), step):
+            cells = band[s:s + step]
+            lo, h = mesh["cell_box"](cells)
+            m = len(cells)
+            own = np.arange(m)
+            size = np.asarray(h, np.float64).copy()
+            inside = np.zeros(m)
+            for level in range(levels + 1):
+                if lo.shape[0] == 0:
+                    break
+                cen = lo + 0.5 * size
+                r = 0.5 * float(np.linalg.norm(size))
+                d = body.dist(cen)
+                v = float(np.prod(size))
+                full = d < -r
+                inside += np.bincount(own[full], minlength=m) * v
+                cut = ~(full | (d > r))
+                if level == levels:
+                    inside += np.bincount(own[cut & (d < 0.0)], minlength=m) * v
+                    break
+                lo, own = lo[cut], own[cut]
+                size = 0.5 * size
+                offs = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)],
+                                np.float64) * size
+                lo = (lo[:, None, :] + offs[None, :, :]).reshape(-1, 3)
+                own = np.repeat(own, 8)
+            F[cells] = inside / float(np.prod(h))
+        return np.clip(F, 0.0, 1.0)
+    step = max(1, chunk // 64)
+    for s in range(0, len(band), step):
+        cells = band[s:s + step]
+        T, owner = mesh["cell_tets"](cells)
+        local = np.searchsorted(cells, owner)
+        m = len(cells)
+        vol_cell = np.bincount(local, weights=np.abs(_tet_volumes(T)), minlength=m)
+        inside = np.zeros(m)
+        P, own = T, local
         for level in range(levels + 1):
             if P.shape[0] == 0:
                 break
@@ -382,13 +482,13 @@ def init_fraction(mesh, body, levels=4, chunk=1 << 20):
             d = body.dist(cen)
             v = np.abs(_tet_volumes(P))
             full = d < -r
-            inside += np.bincount(owner[full], weights=v[full], minlength=nc)
+            inside += np.bincount(own[full], weights=v[full], minlength=m)
             cut = ~(full | (d > r))
             if level == levels:
                 leaf_in = cut & (d < 0.0)
-                inside += np.bincount(owner[leaf_in], weights=v[leaf_in], minlength=nc)
+                inside += np.bincount(own[leaf_in], weights=v[leaf_in], minlength=m)
                 break
             P = _subdivide_tets(P[cut])
-            owner = np.tile(owner[cut], 8)
-    F = inside / vol_cell
+            own = np.tile(own[cut], 8)
+        F[cells] = inside / vol_cell
     return np.clip(F, 0.0, 1.0)

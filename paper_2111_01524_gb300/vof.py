@@ -1,0 +1,285 @@
+"""Thin ctypes binding of the gvof CUDA library (``include/vof.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. Device buffers are torch tensors (PyTorch provides device
+memory and streams); host buffers are numpy arrays. The library must have
+been built (``paper_2111_01524_gb300.build.build()``); there is no CPU
+fallback, and loading fails loudly if the shared library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VOF_OK, VOF_EINVAL, VOF_ENOMEM, VOF_ECUDA, VOF_ECAPACITY, VOF_ESTATE = range(6)
+PREC_FP64, PREC_MIXED = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+NB_VERTS = 17  # 2 * 8 + 1 polyhedron slots per face in vof_get_flux_polyhedra
+
+_lib = None
+
+
+class VofError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gvof error {status}: {msg}")
+        self.status = status
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("n_vert", C.c_int64), ("n_face", C.c_int64), ("n_cell", C.c_int64),
+                ("X", C.c_void_p), ("face_ptr", C.c_void_p), ("face_vert", C.c_void_p),
+                ("owner", C.c_void_p), ("neighbour", C.c_void_p)]
+
+
+class _Opt(C.Structure):
+    _fields_ = [("eps", C.c_double), ("beta", C.c_double), ("precision", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class _Vel(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("period", C.c_double),
+                ("omega", C.c_double), ("center", C.c_double * 3), ("u0", C.c_double * 3)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_interfacial", C.c_int64), ("n_active_faces", C.c_int64),
+                ("n_truncations", C.c_int64), ("n_overflow", C.c_int64),
+                ("n_degenerate", C.c_int64), ("n_edgeon", C.c_int64),
+                ("volume", C.c_double), ("ebound", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Open libgvof.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"gvof CUDA library not built: {path} is missing "
+                               "(run paper_2111_01524_gb300.build.build())")
+        L = C.CDLL(path)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.vof_last_error.restype = C.c_char_p
+        L.vof_init.argtypes = [vp, vp, C.POINTER(vp)]
+        L.vof_destroy.argtypes = [vp]
+        L.vof_destroy.restype = None
+        L.vof_set_fraction.argtypes = [vp, vp, i32, vp]
+        L.vof_get_fraction.argtypes = [vp, vp, i32, vp]
+        L.vof_reconstruct.argtypes = [vp, vp]
+        L.vof_advect.argtypes = [vp, vp, dbl, dbl, vp]
+        L.vof_step.argtypes = [vp, vp, dbl, dbl, vp]
+        L.vof_suggest_dt.argtypes = [vp, vp, dbl, dbl, dbl, C.POINTER(dbl)]
+        L.vof_get_planes.argtypes = [vp, vp, i32, vp]
+        L.vof_get_tags.argtypes = [vp, vp, vp, vp, i32, vp]
+        L.vof_get_face_flux.argtypes = [vp, vp, vp, i32, vp]
+        L.vof_get_geometry.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
+        L.vof_get_neighbors.argtypes = [vp, vp, vp, C.POINTER(i64)]
+        L.vof_get_candidates.argtypes = [vp, vp, C.c_int, vp, vp, i64]
+        L.vof_get_flux_polyhedra.argtypes = [vp, vp, dbl, dbl, vp, C.c_int, vp, vp]
+        L.vof_get_stats.argtypes = [vp, C.POINTER(Stats), vp]
+        L.vof_set_timing.argtypes = [vp, C.c_int]
+        L.vof_get_timing.argtypes = [vp, vp, vp, C.c_int]
+        L.vof_device_bytes.restype = i64
+        L.vof_device_bytes.argtypes = [vp]
+        for name in ("vof_init", "vof_set_fraction", "vof_get_fraction", "vof_reconstruct",
+                     "vof_advect", "vof_step", "vof_suggest_dt", "vof_get_planes",
+                     "vof_get_tags", "vof_get_face_flux", "vof_get_geometry",
+                     "vof_get_neighbors", "vof_get_candidates", "vof_get_flux_polyhedra",
+                     "vof_get_stats", "vof_set_timing", "vof_get_timing"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != VOF_OK:
+        raise VofError(status, lib().vof_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _mem(a):
+    return MEM_DEVICE if hasattr(a, "data_ptr") and a.is_cuda else MEM_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def velocity_struct(v):
+    s = _Vel()
+    s.kind = v.kind
+    s.period = v.period
+    s.omega = v.omega
+    for i in range(3):
+        s.center[i] = v.center[i]
+        s.u0[i] = v.u0[i]
+    return s
+
+
+class Context:
+    """A mesh resident on the device with its VOF state (one vof_ctx)."""
+
+    def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5):
+        L = lib()
+        self._X = np.ascontiguousarray(mesh["X"], np.float64)
+        self._fp = np.ascontiguousarray(mesh["face_ptr"], np.int64)
+        self._fv = np.ascontiguousarray(mesh["face_vert"], np.int32)
+        self._own = np.ascontiguousarray(mesh["owner"], np.int32)
+        self._nbr = np.ascontiguousarray(mesh["neighbour"], np.int32)
+        md = _Mesh(self._X.shape[0], self._own.shape[0], int(mesh["n_cell"]), _ptr(self._X).value,
+                   _ptr(self._fp).value, _ptr(self._fv).value, _ptr(self._own).value,
+                   _ptr(self._nbr).value)
+        opt = _Opt()
+        opt.eps, opt.beta, opt.precision = eps, beta, precision
+        h = C.c_void_p()
+        _check(L.vof_init(C.byref(md), C.byref(opt), C.byref(h)))
+        self._h = h
+        self.n_vert, self.n_face, self.n_cell = md.n_vert, md.n_face, md.n_cell
+        self.precision = precision
+        # the host copies are not needed after init
+        del self._X, self._fp, self._fv, self._own, self._nbr
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vof_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self):
+        return lib().vof_device_bytes(self._h)
+
+    # --- state
+    def set_fraction(self, F, stream=None):
+        if not hasattr(F, "data_ptr"):
+            F = np.ascontiguousarray(F, np.float64)
+        _check(lib().vof_set_fraction(self._h, _ptr(F), _mem(F), _stream(stream)))
+
+    def get_fraction(self, out=None, stream=None):
+        if out is None:
+            out = np.empty(self.n_cell)
+        _check(lib().vof_get_fraction(self._h, _ptr(out), _mem(out), _stream(stream)))
+        return out
+
+    # --- the method
+    def reconstruct(self, stream=None):
+        _check(lib().vof_reconstruct(self._h, _stream(stream)))
+
+    def advect(self, vel, t, dt, stream=None):
+        v = velocity_struct(vel)
+        _check(lib().vof_advect(self._h, C.byref(v), t, dt, _stream(stream)))
+
+    def step(self, vel, t, dt, stream=None):
+        v = velocity_struct(vel)
+        _check(lib().vof_step(self._h, C.byref(v), t, dt, _stream(stream)))
+
+    def suggest_dt(self, vel, t, cfl, t_end):
+        v = velocity_struct(vel)
+        d = C.c_double()
+        _check(lib().vof_suggest_dt(self._h, C.byref(v), t, cfl, t_end, C.byref(d)))
+        return d.value
+
+    # --- read-back
+    def planes(self, stream=None):
+        out = np.empty((self.n_cell, 4))
+        _check(lib().vof_get_planes(self._h, _ptr(out), MEM_HOST, _stream(stream)))
+        return out
+
+    def tags(self, stream=None):
+        tv = np.empty(self.n_vert, np.int8)
+        tf = np.empty(self.n_face, np.int8)
+        tc = np.empty(self.n_cell, np.int8)
+        _check(lib().vof_get_tags(self._h, _ptr(tv), _ptr(tf), _ptr(tc), MEM_HOST, _stream(stream)))
+        return tv, tf, tc
+
+    def face_flux(self, stream=None):
+        Vd = np.empty(self.n_face)
+        VF = np.empty(self.n_face)
+        _check(lib().vof_get_face_flux(self._h, _ptr(Vd), _ptr(VF), MEM_HOST, _stream(stream)))
+        return Vd, VF
+
+    def geometry(self, stream=None):
+        g = dict(cell_vol=np.empty(self.n_cell), cell_cen=np.empty((self.n_cell, 3)),
+                 face_cen=np.empty((self.n_face, 3)), face_nrm=np.empty((self.n_face, 3)),
+                 face_area=np.empty(self.n_face))
+        _check(lib().vof_get_geometry(self._h, _ptr(g["cell_vol"]), _ptr(g["cell_cen"]),
+                                      _ptr(g["face_cen"]), _ptr(g["face_nrm"]),
+                                      _ptr(g["face_area"]), MEM_HOST, _stream(stream)))
+        return g
+
+    def neighbors(self):
+        n = C.c_int64()
+        _check(lib().vof_get_neighbors(self._h, None, None, C.byref(n)))
+        ptr = np.empty(self.n_cell + 1, np.int64)
+        idx = np.empty(max(n.value, 1), np.int32)
+        _check(lib().vof_get_neighbors(self._h, _ptr(ptr), _ptr(idx), C.byref(n)))
+        return ptr, idx[:n.value]
+
+    def candidates(self, faces):
+        faces = np.ascontiguousarray(faces, np.int32)
+        ptr = np.empty(len(faces) + 1, np.int64)
+        _check(lib().vof_get_candidates(self._h, _ptr(faces), len(faces), _ptr(ptr), None, 0))
+        idx = np.empty(max(int(ptr[-1]), 1), np.int32)
+        _check(lib().vof_get_candidates(self._h, _ptr(faces), len(faces), _ptr(ptr), _ptr(idx),
+                                        idx.shape[0]))
+        return [idx[ptr[i]:ptr[i + 1]].copy() for i in range(len(faces))]
+
+    def flux_polyhedra(self, vel, t, dt, faces):
+        faces = np.ascontiguousarray(faces, np.int32)
+        verts = np.zeros((len(faces), NB_VERTS, 3))
+        counts = np.empty(len(faces), np.int32)
+        v = velocity_struct(vel)
+        _check(lib().vof_get_flux_polyhedra(self._h, C.byref(v), t, dt, _ptr(faces), len(faces),
+                                            _ptr(verts), _ptr(counts)))
+        return [verts[i, :2 * counts[i] + 1].copy() if counts[i] > 0 else None
+                for i in range(len(faces))]
+
+    PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update")
+
+    def set_timing(self, on=True):
+        _check(lib().vof_set_timing(self._h, 1 if on else 0))
+
+    def timing(self):
+        """Accumulated per-phase device milliseconds and launch counts since
+        the last call (CUDA events on the launching stream)."""
+        ms = np.zeros(len(self.PHASES))
+        n = np.zeros(len(self.PHASES), np.int64)
+        _check(lib().vof_get_timing(self._h, _ptr(ms), _ptr(n), len(self.PHASES)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PHASES)}
+
+    def stats(self, stream=None):
+        s = Stats()
+        _check(lib().vof_get_stats(self._h, C.byref(s), _stream(stream)))
+        return s.as_dict()

@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances: connectivity, candidate lists and tags bit-exact; FP64 path F
+within 1e-12 absolute (spec bound), per-face volumes within 1e-12 of
+the cell volume; mixed path F within 1e-6 (spec bound).
+"""
+import numpy as np
+import pytest
+
+from paper_2111_01524_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+EPS_F64 = 1e-12
+EPS_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def vof():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_01524_gb300 import build, vof as V
+    build.build()
+    return V
+
+
+def _case(name):
+    if name == "hex12":
+        m = I.hex_mesh(12)
+        body = I.sphere((0.35, 0.35, 0.35), 0.15)
+    elif name == "hex7":  # ragged: no size is a multiple of a block or warp
+        m = I.hex_mesh(7)
+        body = I.sphere((0.45, 0.5, 0.52), 0.3)
+    elif name == "tet4":
+        m = I.kuhn_tet_mesh(4, seed=3)
+        body = I.sphere((0.5, 0.55, 0.5), 0.27)
+    elif name == "hex32":
+        m = I.hex_mesh(32)
+        body = I.sphere((0.35, 0.35, 0.35), 0.15)
+    else:
+        raise KeyError(name)
+    F0 = I.init_fraction(m, body, levels=3)
+    return m, F0
+
+
+CASES = ["hex12", "hex7", "tet4"]
+
+
+@pytest.fixture(scope="module")
+def cases(orc):
+    out = {}
+    for n in CASES + ["hex32"]:
+        m, F0 = _case(n)
+        out[n] = (m, F0, orc.Mesh(m))
+    return out
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_geometry_parity(vof, cases, name):
+    m, F0, om = cases[name]
+    ctx = vof.Context(m)
+    g, go = ctx.geometry(), om.geometry()
+    assert np.allclose(g["cell_vol"], go["cell_vol"], rtol=1e-14, atol=0)
+    for k in ("cell_cen", "face_cen", "face_nrm"):
+        assert np.abs(g[k] - go[k]).max() < 1e-15, k
+    assert np.allclose(g["face_area"], go["face_area"], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_connectivity_bit_exact(vof, cases, name):
+    m, F0, om = cases[name]
+    ctx = vof.Context(m)
+    p, i = ctx.neighbors()
+    po, io = om.neighbors()
+    assert np.array_equal(p, po) and np.array_equal(i, io)
+    faces = np.arange(om.n_face, dtype=np.int32)
+    got = ctx.candidates(faces)
+    for f in faces:
+        assert np.array_equal(got[f], om.candidates(f)), f
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_reconstruct_parity_fp64(vof, cases, name):
+    m, F0, om = cases[name]
+    ctx = vof.Context(m, precision=vof.PREC_FP64)
+    ctx.set_fraction(F0)
+    ctx.reconstruct()
+    st = om.reconstruct(F0)
+    tv, tf, tc = ctx.tags()
+    assert np.array_equal(tc, st["tag_c"])
+    assert np.array_equal(tv, st["tag_v"])
+    assert np.array_equal(ctx.get_fraction(), st["F"])  # cut-off is exact
+    P = ctx.planes()
+    band = st["tag_c"] == 0
+    assert band.sum() > 10
+    h = np.cbrt(om.geometry()["cell_vol"])
+    assert np.abs(P[band, :3] - st["nrm"][band]).max() < 1e-12
+    assert (np.abs(P[band, 3] - st["C"][band]) / h[band]).max() < 1e-12
+    assert np.all(P[~band] == 0)
+
+
+@pytest.mark.parametrize("name", ["hex12", "tet4"])
+def test_flux_polyhedra_parity(vof, cases, name):
+    m, F0, om = cases[name]
+    ctx = vof.Context(m)
+    vel = I.deformation(3.0)
+    dt = om.suggest_dt(vel, 0.2, 0.5, 3.0)
+    faces = np.arange(0, om.n_face, 3, dtype=np.int32)
+    got = ctx.flux_polyhedra(vel, 0.2, dt, faces)
+    for f, P in zip(faces, got):
+        Po, vd, fl = om.fmfpa(int(f), vel, 0.2 + 0.5 * dt, dt)
+        assert P.shape == Po.shape
+        if fl & 2:
+            continue  # edge-on loop: apex placement is undefined
+        assert np.abs(P - Po).max() < 1e-13, f
+
+
+def _one_step(vof, m, F0, om, vel, precision, t=0.0, cfl=0.5):
+    ctx = vof.Context(m, precision=precision)
+    ctx.set_fraction(F0)
+    ctx.reconstruct()
+    st = om.reconstruct(F0)
+    dt = om.suggest_dt(vel, t, cfl, 1e9)
+    assert abs(ctx.suggest_dt(vel, t, cfl, 1e9) - dt) <= 1e-14 * dt
+    ctx.advect(vel, t, dt)
+    Vd, VF = ctx.face_flux()
+    Vdo, VFo, stats = om.faceflux(vel, t, dt, st)
+    Fadv = ctx.get_fraction()
+    Fo = om.vofadv(st["F"], Vdo, VFo)
+    return ctx, st, (Vd, VF, Fadv), (Vdo, VFo, Fo)
+
+
+VELS = {"deformation": I.deformation(3.0), "rotation": I.rotation(2 * np.pi),
+        "translation": I.translation((0.7, -0.4, 0.25))}
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("vname", sorted(VELS))
+def test_advect_parity_fp64(vof, cases, name, vname):
+    m, F0, om = cases[name]
+    vel = VELS[vname]
+    ctx, st, (Vd, VF, F), (Vdo, VFo, Fo) = _one_step(vof, m, F0, om, vel, vof.PREC_FP64)
+    V = om.geometry()["cell_vol"]
+    assert np.abs(Vd - Vdo).max() <= 1e-14 * np.abs(Vdo).max() + 1e-30
+    assert np.abs(VF - VFo).max() < EPS_F64 * V.min()
+    assert np.abs(F - Fo).max() < EPS_F64
+    tv, tf, tc = ctx.tags()
+    assert np.array_equal(tf, st["tag_f"])
+    s = ctx.stats()
+    assert s["n_overflow"] == 0
+    assert s["n_active_faces"] == int((st["tag_f"] == 0).sum())
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_advect_parity_mixed(vof, cases, name):
+    m, F0, om = cases[name]
+    vel = VELS["deformation"]
+    ctx, st, (Vd, VF, F), (Vdo, VFo, Fo) = _one_step(vof, m, F0, om, vel, vof.PREC_MIXED)
+    V = om.geometry()["cell_vol"]
+    assert np.abs(F - Fo).max() < EPS_MIXED
+    assert np.abs(VF - VFo).max() < EPS_MIXED * V.min()
+    assert ctx.stats()["n_overflow"] == 0
+
+
+def test_multistep_parity_config1(vof, cases):
+    """32^3 deformation, 10 steps at CFL 0.5: the GPU and the oracle each
+    run the whole loop on their own; F agrees to 1e-12 after every step."""
+    m, F0, om = cases["hex32"]
+    vel = I.deformation(3.0)
+    ctx = vof.Context(m, precision=vof.PREC_FP64)
+    ctx.set_fraction(F0)
+    ctx.reconstruct()
+    st = om.reconstruct(F0)
+    t = 0.0
+    V = om.geometry()["cell_vol"]
+    vol0 = (V * st["F"]).sum()
+    for k in range(10):
+        dt = om.suggest_dt(vel, t, 0.5, 3.0)
+        ctx.step(vel, t, dt)
+        st = om.step(vel, t, dt, st)
+        t += dt
+        F = ctx.get_fraction()
+        assert np.abs(F - st["F"]).max() < EPS_F64, k
+    s = ctx.stats()
+    assert abs(s["volume"] - vol0) < 1e-12 * vol0
+    assert s["n_overflow"] == 0
+
+
+def test_cfl1_translation_exact_shift_gpu(vof):
+    n = 8
+    m = I.hex_mesh(n)
+    F0 = I.init_fraction(m, I.sphere((0.45, 0.52, 0.48), 0.3), levels=3)
+    for prec in (vof.PREC_FP64,):
+        ctx = vof.Context(m, precision=prec)
+        ctx.set_fraction(F0)
+        ctx.reconstruct()
+        F = ctx.get_fraction().reshape(n, n, n)
+        ctx.advect(I.translation((1.0, 0.0, 0.0)), 0.0, 1.0 / n)
+        G = ctx.get_fraction().reshape(n, n, n)
+        assert np.abs(G[:, :, 1:] - F[:, :, :-1]).max() < 4e-15
+        assert np.abs(G[:, :, 0]).max() == 0.0
+
+
+def test_edge_cases(vof):
+    m = I.hex_mesh(5)
+    vel = I.deformation(3.0)
+    for value in (0.0, 1.0):
+        ctx = vof.Context(m)
+        ctx.set_fraction(np.full(125, value))
+        ctx.reconstruct()
+        ctx.step(vel, 0.0, 0.02)
+        s = ctx.stats()
+        assert s["n_active_faces"] == 0 and s["n_interfacial"] == 0
+        assert np.all(ctx.get_fraction() == value)
+    # a single interfacial cell in an empty grid
+    F = np.zeros(125)
+    F[62] = 0.3
+    ctx = vof.Context(m)
+    ctx.set_fraction(F)
+    ctx.reconstruct()
+    ctx.step(I.translation((0.3, 0.2, -0.1)), 0.0, 0.05)
+    G = ctx.get_fraction()
+    V = ctx.geometry()["cell_vol"]
+    assert abs((V * G).sum() - 0.3 * V[62]) < 1e-17
+    assert G.min() >= 0 and G.max() <= 1
+
+
+def test_invalid_inputs_are_rejected(vof):
+    with pytest.raises(vof.VofError) as e:
+        vof.Context(I.trihex_mesh(2, seed=1))  # non-convex cells
+    assert e.value.status == vof.VOF_EINVAL
+    ctx = vof.Context(I.hex_mesh(3))
+    ctx.set_fraction(np.full(27, 0.5))
+    with pytest.raises(vof.VofError) as e:
+        ctx.advect(I.deformation(3.0), 0.0, 0.01)  # needs a reconstruction
+    assert e.value.status == vof.VOF_ESTATE
+    with pytest.raises(vof.VofError):
+        ctx.candidates([10 ** 6])
+    bad = I.hex_mesh(2)
+    bad = dict(bad)
+    bad["owner"] = bad["owner"].copy()
+    bad["owner"][0] = 99
+    with pytest.raises(vof.VofError):
+        vof.Context(bad)

@@ -97,16 +97,16 @@ def test_unstructured_geometry(orc, gen):
     assert (g["cell_vol"] > 0).all()
     if gen == "tet":
         # centroid of a tetrahedron = average of its 4 vertices (closed form)
-        T = m["cell_tets"]
+        T, _ = m["cell_tets"](np.arange(om.n_cell))
         assert np.allclose(g["cell_cen"], T.mean(axis=1), atol=1e-15)
         assert g["cell_convex"].all()
     else:
         # distorted cells: centroid from the independent tet decomposition
-        T = m["cell_tets"]
+        T, cot = m["cell_tets"](np.arange(om.n_cell))
         v = np.einsum("ij,ij->i", T[:, 1] - T[:, 0], np.cross(T[:, 2] - T[:, 0], T[:, 3] - T[:, 0])) / 6
         cen = np.zeros((om.n_cell, 3))
-        np.add.at(cen, m["cell_of_tet"], v[:, None] * T.mean(axis=1))
-        vol = np.bincount(m["cell_of_tet"], weights=v)
+        np.add.at(cen, cot, v[:, None] * T.mean(axis=1))
+        vol = np.bincount(cot, weights=v)
         assert np.allclose(g["cell_cen"], cen / vol[:, None], atol=1e-15)
         assert not g["cell_convex"].all()
 
