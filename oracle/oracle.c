@@ -615,10 +615,16 @@ int orc_fmfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
     double e0[3], e1[3];
     sub3(x[(i + 1) % I], x[i], e0);
     sub3(x[i], x[im], e1);
-    double ok_s = norm3(s[i]) > 1e-10 * norm3(e0) * norm3(ue[i]) &&
-                  norm3(s[im]) > 1e-10 * norm3(e1) * norm3(ue[im]);
+    /* a side plane is undefined when its edge is (nearly) parallel to the
+     * edge-centre velocity, and the line is undefined when the two side
+     * planes are (nearly) parallel; the back-traced point then has a
+     * relative error of order eps/sin(angle), so below sin = 1e-3 the
+     * streak-line point is used instead */
+    const double tol = 1e-3;
+    int ok_s = norm3(s[i]) > tol * norm3(e0) * norm3(ue[i]) &&
+               norm3(s[im]) > tol * norm3(e1) * norm3(ue[im]);
     double dd = dot3(d, d);
-    if (ok_s && sqrt(dd) > 1e-10 * norm3(s[im]) * norm3(s[i])) {
+    if (ok_s && sqrt(dd) > tol * norm3(s[im]) * norm3(s[i])) {
       /* back-trace along the line of intersection of the two side planes:
        * orthogonal projection of the streak-line displacement on the line */
       double k = dt * dot3(uv[i], d) / dd;

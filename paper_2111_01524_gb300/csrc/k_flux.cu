@@ -342,7 +342,9 @@ __device__ bool build_fmfpa(const DevMesh& M, const FluxParams& p, int j, double
   const G nue = sqrt(ex_u * ex_u + ey_u * ey_u + ez_u * ez_u);
   const G nep = __shfl_sync(GVOF_FULL, ne, prv), nuep = __shfl_sync(GVOF_FULL, nue, prv);
   const G dd = dx * dx + dy * dy + dz * dz;
-  const G tol = (G)1e-10;
+  // below sin(angle) = 1e-3 the side plane or the line is ill-conditioned
+  // (relative error eps/sin) and the streak-line point is used instead
+  const G tol = (G)1e-3;
   const bool ok = ns > tol * ne * nue && nsp > tol * nep * nuep && sqrt(dd) > tol * nsp * ns;
   G bxl, byl, bzl;
   if (ok) {
