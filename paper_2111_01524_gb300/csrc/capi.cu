@@ -40,7 +40,9 @@ void free_all(vof_ctx* c) {
                   c->fnx, c->fny, c->fnz, c->fa, c->cf_ptr, c->cf, c->cv_ptr, c->cv, c->vc_ptr,
                   c->vc, c->nb_ptr, c->nb, c->ccx, c->ccy, c->ccz, c->cvol, c->bb, c->convex,
                   c->F, c->nx, c->ny, c->nz, c->C, c->tv, c->tf, c->tc, c->Vd, c->VF, c->srate,
-                  c->icells, c->afaces, c->cnt, c->red};
+                  c->icells, c->afaces, c->cnt, c->red, c->vx2, c->vy2, c->vz2, c->fcx2,
+                  c->fcy2, c->fcz2, c->ccx2, c->ccy2, c->ccz2, c->bb2, c->fnx32, c->fny32,
+                  c->fnz32, c->fa32, c->cvol32, c->nx32, c->ny32, c->nz32, c->C32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -221,6 +223,16 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
   CKI(dalloc(c, &c->Vd, nf)); CKI(dalloc(c, &c->VF, nf)); CKI(dalloc(c, &c->srate, nf));
   CKI(dalloc(c, &c->icells, nc)); CKI(dalloc(c, &c->afaces, nf));
   CKI(dalloc(c, &c->cnt, kNCnt)); CKI(dalloc(c, &c->red, kRedSlots));
+  if (o.precision == VOF_PREC_MIXED) {
+    CKI(dalloc(c, &c->vx2, nv)); CKI(dalloc(c, &c->vy2, nv)); CKI(dalloc(c, &c->vz2, nv));
+    CKI(dalloc(c, &c->fcx2, nf)); CKI(dalloc(c, &c->fcy2, nf)); CKI(dalloc(c, &c->fcz2, nf));
+    CKI(dalloc(c, &c->fnx32, nf)); CKI(dalloc(c, &c->fny32, nf)); CKI(dalloc(c, &c->fnz32, nf));
+    CKI(dalloc(c, &c->fa32, nf));
+    CKI(dalloc(c, &c->ccx2, nc)); CKI(dalloc(c, &c->ccy2, nc)); CKI(dalloc(c, &c->ccz2, nc));
+    CKI(dalloc(c, &c->bb2, 6 * nc)); CKI(dalloc(c, &c->cvol32, nc));
+    CKI(dalloc(c, &c->nx32, nc)); CKI(dalloc(c, &c->ny32, nc)); CKI(dalloc(c, &c->nz32, nc));
+    CKI(dalloc(c, &c->C32, nc));
+  }
   CKI(cudaMallocHost(&c->pinned, 4096));
 
   // SoA vertex coordinates
@@ -256,6 +268,7 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
   CKI(cudaMemset(c->VF, 0, sizeof(double) * nf));
   CKI(launch_face_geometry(c, 0));
   CKI(launch_cell_geometry(c, 0));
+  if (o.precision == VOF_PREC_MIXED) CKI(launch_mixed_copies(c, 0));
   CKI(cudaDeviceSynchronize());
   {
     std::vector<uint8_t> cvx(nc);

@@ -155,6 +155,34 @@ __global__ void k_velocity_setup(DevMesh M, Vel v, double* srate, unsigned long 
   }
 }
 
+__device__ __forceinline__ float2 split(double x) {
+  float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// (hi, lo) float pairs of the absolute positions and FP32 copies of the
+// directions, areas and volumes used by the mixed-precision band kernels
+__global__ void k_mixed_copies(DevMesh M, float2* vx2, float2* vy2, float2* vz2, float2* fcx2,
+                               float2* fcy2, float2* fcz2, float* fnx32, float* fny32,
+                               float* fnz32, float* fa32, float2* ccx2, float2* ccy2,
+                               float2* ccz2, float2* bb2, float* cvol32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t v = t0; v < M.nv; v += stride) {
+    vx2[v] = split(M.x[v]); vy2[v] = split(M.y[v]); vz2[v] = split(M.z[v]);
+  }
+  for (int64_t f = t0; f < M.nf; f += stride) {
+    fcx2[f] = split(M.fcx[f]); fcy2[f] = split(M.fcy[f]); fcz2[f] = split(M.fcz[f]);
+    fnx32[f] = (float)M.fnx[f]; fny32[f] = (float)M.fny[f]; fnz32[f] = (float)M.fnz[f];
+    fa32[f] = (float)M.fa[f];
+  }
+  for (int64_t c = t0; c < M.nc; c += stride) {
+    ccx2[c] = split(M.ccx[c]); ccy2[c] = split(M.ccy[c]); ccz2[c] = split(M.ccz[c]);
+    cvol32[c] = (float)M.cvol[c];
+    for (int d = 0; d < 6; ++d) bb2[d * M.nc + c] = split(M.bb[d * M.nc + c]);
+  }
+}
+
 inline int grid_for(int64_t n, int bs) {
   int64_t g = (n + bs - 1) / bs;
   int64_t cap = (int64_t)kSMs * 16;
@@ -172,6 +200,16 @@ cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s) {
 cudaError_t launch_cell_geometry(const vof_ctx* c, cudaStream_t s) {
   k_cell_geometry<<<grid_for(c->nc, 256), 256, 0, s>>>(mesh_view(c), c->ccx, c->ccy, c->ccz,
                                                        c->cvol, c->bb, c->convex);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_copies(const vof_ctx* c, cudaStream_t s) {
+  int64_t n = c->nf > c->nv ? c->nf : c->nv;
+  if (c->nc > n) n = c->nc;
+  k_mixed_copies<<<grid_for(n, 256), 256, 0, s>>>(mesh_view(c), c->vx2, c->vy2, c->vz2, c->fcx2,
+                                                 c->fcy2, c->fcz2, c->fnx32, c->fny32, c->fnz32,
+                                                 c->fa32, c->ccx2, c->ccy2, c->ccz2, c->bb2,
+                                                 c->cvol32);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,8 @@
 // cell update of Eq. fnext with the final clip (Sec. 2.2). These kernels
 // are HBM-bound: one thread per cell / node / face, coalesced SoA loads,
 // warp-aggregated compaction of the band work lists.
+#include <cstring>
+
 #include "vof_common.cuh"
 
 namespace gvof {
@@ -27,19 +29,27 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t item, int32_t* li
   if (pred) list[base + __popc(m & ((1u << lane) - 1))] = item;
 }
 
+// FP64 comparisons run on the (narrow) FP64 pipe of the GPU; the sweeps
+// compare the bit patterns instead: for doubles, x < y <=> bits(x) < bits(y)
+// whenever y > 0 (negative x have negative bit patterns as int64)
+constexpr long long kOneBits = 0x3FF0000000000000LL;
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+__device__ __forceinline__ bool is_one(double x) { return dbits(x) == kOneBits; }
+
 // cut-off of uniform cells and cell tags (Sec. 2.1, Sec. 3.3); interfacial
 // cells are appended to the band list
-__global__ void k_cell_tags(int64_t nc, double eps, double* F, int8_t* tc, int32_t* icells,
-                            unsigned long long* cnt) {
+__global__ void k_cell_tags(int64_t nc, long long eps_bits, long long ome_bits, double* F,
+                            int8_t* tc, int32_t* icells, unsigned long long* cnt) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += stride) {
     int64_t c = base + threadIdx.x;
     bool in = c < nc;
     int8_t t = -1;
     if (in) {
-      double f = F[c];
-      if (f < eps) { t = -1; if (f != 0.0) F[c] = 0.0; }
-      else if (f > 1.0 - eps) { t = 1; if (f != 1.0) F[c] = 1.0; }
+      const long long b = dbits(F[c]);
+      if (b < eps_bits) { t = -1; if (b != 0) F[c] = 0.0; }             // F < eps
+      else if (b > ome_bits) { t = 1; if (b != kOneBits) F[c] = 1.0; }  // F > 1 - eps
       else t = 0;
       tc[c] = t;
     }
@@ -57,9 +67,9 @@ __global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv) 
     int64_t q0 = M.vc_ptr[v], q1 = M.vc_ptr[v + 1];
     bool allz = true, allo = true;
     for (int64_t q = q0; q < q1; ++q) {
-      double f = F[M.vc[q]];
-      allz &= (f == 0.0);
-      allo &= (f == 1.0);
+      const double f = F[M.vc[q]];
+      allz &= is_zero(f);
+      allo &= is_one(f);
     }
     int8_t t;
     if (allz) t = -1;
@@ -119,15 +129,27 @@ __global__ void k_update(DevMesh M, double* F, const double* Vd, const double* V
   double eb = 0.0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
        c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
+    const double F0 = F[c];
+    // an empty cell that no fluid enters stays exactly empty: Eq. fnext
+    // gives 0 for F = 0 and V_FT = 0 whatever V_dT (no FP64 work needed)
+    if (is_zero(F0)) {
+      bool none = true;
+      for (int64_t q = q0; q < q1 && none; ++q) {
+        const int fs = M.cf[q];
+        none = is_zero(VF[fs >= 0 ? fs : ~fs]);
+      }
+      if (none) continue;
+    }
     double vdt = 0.0, vft = 0.0;
-    for (int64_t q = M.cf_ptr[c]; q < M.cf_ptr[c + 1]; ++q) {
+    for (int64_t q = q0; q < q1; ++q) {
       int fs = M.cf[q];
       if (fs >= 0) { vdt += Vd[fs]; vft += VF[fs]; }
       else { vdt -= Vd[~fs]; vft -= VF[~fs]; }
     }
     double V = M.cvol[c];
     double h = vdt / (2.0 * V);
-    double fn = (F[c] * (1.0 + h) - vft / V) / (1.0 - h);
+    double fn = (F0 * (1.0 + h) - vft / V) / (1.0 - h);
     eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
     F[c] = fmax(fmin(fn, 1.0), 0.0);
   }
@@ -178,8 +200,11 @@ constexpr int kUpdBlocks = kSMs * 4;  // fixed, <= kRedSlots/2 - 2
 cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(c->cnt + kNIcells, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_cell_tags<<<grid_for(c->nc, 256), 256, 0, s>>>(c->nc, c->opt.eps, c->F, c->tc, c->icells,
-                                                   c->cnt);
+  const double eps = c->opt.eps, ome = 1.0 - c->opt.eps;
+  long long eb, ob;
+  std::memcpy(&eb, &eps, sizeof eb);
+  std::memcpy(&ob, &ome, sizeof ob);
+  k_cell_tags<<<grid_for(c->nc, 256), 256, 0, s>>>(c->nc, eb, ob, c->F, c->tc, c->icells, c->cnt);
   return cudaGetLastError();
 }
 

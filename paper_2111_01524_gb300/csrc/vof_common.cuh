@@ -38,6 +38,16 @@ struct DevMesh {
   const double *ccx, *ccy, *ccz;  // cell centroid
   const double* cvol;
   const double* bb;               // bounding boxes, SoA: bb[d*nc + c], d = 0..5 (lo xyz, hi xyz)
+  // mixed-precision copies (allocated for VOF_PREC_MIXED only): absolute
+  // positions as (hi, lo) float pairs, hi = fl(x), lo = fl(x - hi), so that
+  // differences of nearby points are formed in FP32 without losing the
+  // digits an FP32 absolute coordinate would drop; directions in FP32
+  const float2 *vx2, *vy2, *vz2;
+  const float2 *fcx2, *fcy2, *fcz2;
+  const float *fnx32, *fny32, *fnz32, *fa32;
+  const float2 *ccx2, *ccy2, *ccz2;
+  const float2* bb2;
+  const float* cvol32;
 };
 
 struct DevState {
@@ -50,6 +60,7 @@ struct DevState {
   int32_t* afaces;           // compacted active faces
   unsigned long long* cnt;   // counters, see Cnt
   double* red;               // reduction scratch [kRedSlots]
+  float *nx32, *ny32, *nz32, *C32;  // FP32 copies of the planes (mixed only)
 };
 
 enum Cnt {
@@ -119,6 +130,36 @@ __device__ __forceinline__ void vel0<float>(const Vel& v, float x, float y, floa
   }
 }
 
+// absolute coordinates in the two precisions: double, or a (hi, lo) float
+// pair whose difference with another pair is formed in FP32 as
+// (a.hi - b.hi) + (a.lo - b.lo)
+template <typename G>
+struct Prec;
+template <>
+struct Prec<double> {
+  using A = double;
+};
+template <>
+struct Prec<float> {
+  using A = float2;
+};
+__device__ __forceinline__ double rel(double a, double b) { return a - b; }
+__device__ __forceinline__ float rel(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+
+// mesh and plane arrays as seen by the band kernels of precision G
+template <typename G>
+struct GeoView {
+  using A = typename Prec<G>::A;
+  const A *vx, *vy, *vz;      // vertices
+  const A *fcx, *fcy, *fcz;   // face centroids
+  const G *fnx, *fny, *fnz;   // face unit normals (out of the owner)
+  const G* fa;                // face areas
+  const A *ccx, *ccy, *ccz;   // cell centroids
+  const A* bb;                // cell bounding boxes [6 * nc]
+  const G* cvol;              // cell volumes
+  const G *pnx, *pny, *pnz, *pC;  // PLIC planes (read)
+};
+
 }  // namespace gvof
 
 struct vof_ctx {
@@ -143,6 +184,9 @@ struct vof_ctx {
   double *ccx, *ccy, *ccz, *cvol;
   double* bb;
   uint8_t* convex;
+  float2 *vx2, *vy2, *vz2, *fcx2, *fcy2, *fcz2, *ccx2, *ccy2, *ccz2, *bb2;
+  float *fnx32, *fny32, *fnz32, *fa32, *cvol32;
+  float *nx32, *ny32, *nz32, *C32;
   // state (device)
   double* F;
   double *nx, *ny, *nz, *C;
@@ -183,6 +227,10 @@ inline DevMesh mesh_view(const vof_ctx* c) {
   m.cf_ptr = c->cf_ptr; m.cf = c->cf; m.cv_ptr = c->cv_ptr; m.cv = c->cv;
   m.vc_ptr = c->vc_ptr; m.vc = c->vc; m.nb_ptr = c->nb_ptr; m.nb = c->nb;
   m.ccx = c->ccx; m.ccy = c->ccy; m.ccz = c->ccz; m.cvol = c->cvol; m.bb = c->bb;
+  m.vx2 = c->vx2; m.vy2 = c->vy2; m.vz2 = c->vz2;
+  m.fcx2 = c->fcx2; m.fcy2 = c->fcy2; m.fcz2 = c->fcz2;
+  m.fnx32 = c->fnx32; m.fny32 = c->fny32; m.fnz32 = c->fnz32; m.fa32 = c->fa32;
+  m.ccx2 = c->ccx2; m.ccy2 = c->ccy2; m.ccz2 = c->ccz2; m.bb2 = c->bb2; m.cvol32 = c->cvol32;
   return m;
 }
 
@@ -191,7 +239,33 @@ inline DevState state_view(const vof_ctx* c) {
   s.F = c->F; s.nx = c->nx; s.ny = c->ny; s.nz = c->nz; s.C = c->C;
   s.tv = c->tv; s.tf = c->tf; s.tc = c->tc; s.Vd = c->Vd; s.VF = c->VF; s.srate = c->srate;
   s.icells = c->icells; s.afaces = c->afaces; s.cnt = c->cnt; s.red = c->red;
+  s.nx32 = c->nx32; s.ny32 = c->ny32; s.nz32 = c->nz32; s.C32 = c->C32;
   return s;
+}
+
+template <typename G>
+GeoView<G> geo_view(const vof_ctx* c);
+
+template <>
+inline GeoView<double> geo_view<double>(const vof_ctx* c) {
+  GeoView<double> g;
+  g.vx = c->x; g.vy = c->y; g.vz = c->z;
+  g.fcx = c->fcx; g.fcy = c->fcy; g.fcz = c->fcz;
+  g.fnx = c->fnx; g.fny = c->fny; g.fnz = c->fnz; g.fa = c->fa;
+  g.ccx = c->ccx; g.ccy = c->ccy; g.ccz = c->ccz; g.bb = c->bb; g.cvol = c->cvol;
+  g.pnx = c->nx; g.pny = c->ny; g.pnz = c->nz; g.pC = c->C;
+  return g;
+}
+
+template <>
+inline GeoView<float> geo_view<float>(const vof_ctx* c) {
+  GeoView<float> g;
+  g.vx = c->vx2; g.vy = c->vy2; g.vz = c->vz2;
+  g.fcx = c->fcx2; g.fcy = c->fcy2; g.fcz = c->fcz2;
+  g.fnx = c->fnx32; g.fny = c->fny32; g.fnz = c->fnz32; g.fa = c->fa32;
+  g.ccx = c->ccx2; g.ccy = c->ccy2; g.ccz = c->ccz2; g.bb = c->bb2; g.cvol = c->cvol32;
+  g.pnx = c->nx32; g.pny = c->ny32; g.pnz = c->nz32; g.pC = c->C32;
+  return g;
 }
 
 inline Vel to_vel(const vof_velocity& v) {
@@ -213,6 +287,7 @@ inline double time_factor(const Vel& v, double t) {
 cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_cell_geometry(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_velocity_setup(const vof_ctx* c, const Vel& v, cudaStream_t s);
+cudaError_t launch_mixed_copies(const vof_ctx* c, cudaStream_t s);
 // sweeps (k_sweep.cu)
 cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s);
