@@ -35,7 +35,9 @@ struct ReconSmem {
     LoopSmem<double> d;
     LoopSmem<float> f;
   };
+  int vid[kMaxCellEntries];  // vertex id of each loop entry
   int fs[kMaxCellFaces + 1];
+  int corner[4];             // neighbours of the extreme vertex
 };
 
 template <typename T>
@@ -130,6 +132,79 @@ __device__ P plane_constant(const ReconSmem& S, int nfc, int ncv, P s_lane, P nx
   return Ca + (s / P(3)) * (Cb - Ca);
 }
 
+// Closed-form plane constant when the fluid (or, for F > 1/2, the empty)
+// region is the corner of an extreme vertex with three edges: between that
+// vertex and the next breakpoint the region is the tetrahedron cut off the
+// three edges e_i, of volume D^3 |det(e1,e2,e3)| / (6 |n.e1 n.e2 n.e3|) at
+// plane distance D from the vertex, so D = cbrt(6 T |n.e1 n.e2 n.e3| / |det|).
+// FP64; returns false when the corner does not apply (the bracketing method
+// is used then). Needs the loops' vertex ids in smem and s_lane = n.(x_v-xc).
+__device__ bool corner_constant(const DevMesh& M, ReconSmem& Sm, int c, int ncv, int vl,
+                                double s_lane, double nx, double ny, double nz, double F,
+                                double Vc, int lane, double* Cout) {
+  const bool low = F <= 0.5;  // fluid corner at the top vertex, else empty corner at the bottom
+  const double key = lane < ncv ? (low ? s_lane : -s_lane) : -1e300;
+  // extreme vertex (largest key) and the next breakpoint
+  double k1 = key, k2 = -1e300;
+  int v1 = vl;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ok1 = __shfl_xor_sync(GVOF_FULL, k1, o), ok2 = __shfl_xor_sync(GVOF_FULL, k2, o);
+    const int ov1 = __shfl_xor_sync(GVOF_FULL, v1, o);
+    if (ok1 > k1 || (ok1 == k1 && ov1 < v1)) {
+      k2 = fmax(k1, ok2);
+      k1 = ok1;
+      v1 = ov1;
+    } else {
+      k2 = fmax(k2, ok1);
+    }
+  }
+  // neighbours of v1: the entry after v1 in every outward loop
+  const int nent = Sm.fs[M.cf_ptr[c + 1] - M.cf_ptr[c]];
+  int found = 0;
+  for (int base = 0; base < nent; base += 32) {
+    const int e = base + lane;
+    int nb = -1;
+    if (e < nent && Sm.vid[e] == v1) {
+      // loop that holds entry e
+      int f = 0;
+      while (Sm.fs[f + 1] <= e) ++f;
+      const int nxt = (e + 1 == Sm.fs[f + 1]) ? Sm.fs[f] : e + 1;
+      nb = Sm.vid[nxt];
+    }
+    const unsigned bal = __ballot_sync(GVOF_FULL, nb >= 0);
+    if (nb >= 0) {
+      const int pos = found + __popc(bal & ((1u << lane) - 1u));
+      if (pos < 4) Sm.corner[pos] = nb;
+    }
+    found += __popc(bal);
+  }
+  __syncwarp();
+  if (found != 3) return false;
+  const double sgn = low ? 1.0 : -1.0;
+  double e[3][3], a[3];
+  for (int i = 0; i < 3; ++i) {
+    const int w = Sm.corner[i];
+    e[i][0] = M.x[w] - M.x[v1]; e[i][1] = M.y[w] - M.y[v1]; e[i][2] = M.z[w] - M.z[v1];
+    a[i] = -sgn * (nx * e[i][0] + ny * e[i][1] + nz * e[i][2]);  // > 0 along the edges
+  }
+  const double det = fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                          e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                          e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]));
+  const double hs = cbrt(Vc);
+  if (!(a[0] > 1e-9 * hs && a[1] > 1e-9 * hs && a[2] > 1e-9 * hs) || !(det > 0.0)) return false;
+  const double prod = a[0] * a[1] * a[2];
+  const double T = (low ? F : 1.0 - F) * Vc;
+  const double hsc = 1.0 / cbrt(Vc);
+  // breakpoint distance in absolute units (s was formed in scaled units)
+  const double D2 = (k1 - k2) / hsc;
+  if (!(T <= D2 * D2 * D2 * det / (6.0 * prod))) return false;
+  const double D = cbrt(6.0 * T * prod / det);
+  const double s_top = k1 / hsc;  // key of the extreme vertex, absolute units
+  // low: fluid = {s >= s_top - D}, C = D - s_top; high: empty = {s <= s_bot + D}
+  *Cout = low ? (D - s_top) : (s_top - D);
+  return true;
+}
+
 // load the cell's outward face loops (cell-local, scaled) in precision P
 template <typename P, typename G>
 __device__ void load_loops(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm, int c,
@@ -157,6 +232,7 @@ __device__ void load_loops(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm
     const int64_t b = M.fptr[fid];
     for (int i = 0; i < len; ++i) {
       const int v = M.fvert[b + (out ? i : len - 1 - i)];
+      Sm.vid[off + i] = v;
       if (sizeof(P) == sizeof(G)) {
         Lp.x[off + i] = (P)(rel(Gv.vx[v], xc) * (G)sc);
         Lp.y[off + i] = (P)(rel(Gv.vy[v], yc) * (G)sc);
@@ -228,7 +304,26 @@ __global__ void __launch_bounds__(kWarps * 32) k_reconstruct(DevMesh M, GeoView<
     const int ncv = (int)(M.cv_ptr[c + 1] - v0);
     const int vl = lane < ncv ? M.cv[v0 + lane] : M.cv[v0];
     double Cout;
-    if (kMixed && (Fc < kNear01 || Fc > 1.0 - kNear01)) {
+    const bool near01 = Fc < kNear01 || Fc > 1.0 - kNear01;
+    if (!kMixed || near01) {
+      // FP64 closed form when the fluid / empty region is a vertex corner
+      const double hcd = cbrt(M.cvol[c]), scd = 1.0 / hcd;
+      load_loops<double, G>(M, Gv, Sm, c, xc, yc, zc, scd, nfc, lane);
+      const double nxd = nx, nyd = ny, nzd = nz;
+      const double s = nxd * (M.x[vl] - M.ccx[c]) * scd + nyd * (M.y[vl] - M.ccy[c]) * scd +
+                       nzd * (M.z[vl] - M.ccz[c]) * scd;
+      if (corner_constant(M, Sm, c, ncv, vl, s, nxd, nyd, nzd, Fc, M.cvol[c], lane, &Cout)) {
+        if (lane == 0) {
+          S.nx[c] = nxd; S.ny[c] = nyd; S.nz[c] = nzd; S.C[c] = Cout;
+          if (kMixed) {
+            S.nx32[c] = (float)nx; S.ny32[c] = (float)ny; S.nz32[c] = (float)nz; S.C32[c] = (float)Cout;
+          }
+        }
+        __syncwarp();
+        continue;
+      }
+    }
+    if (kMixed && near01) {
       const double hcd = cbrt(M.cvol[c]), scd = 1.0 / hcd;
       load_loops<double, G>(M, Gv, Sm, c, xc, yc, zc, scd, nfc, lane);
       const double nxd = nx, nyd = ny, nzd = nz;
