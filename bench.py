@@ -399,7 +399,7 @@ def main():
             "phases_ms": {k: v[0] for k, v in phases.items()},
             "band": {"interfacial_cells": stats["n_interfacial"],
                      "active_faces": stats["n_active_faces"],
-                     "truncations_per_step": stats["n_truncations"] / max(1, a.steps + a.warmup),
+                     "truncations_last_step": stats["n_truncations"],
                      "overflow": stats["n_overflow"]},
             "volume_rel_change": vol_rel,
             "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,

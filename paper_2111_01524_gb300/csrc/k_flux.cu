@@ -77,10 +77,14 @@ struct PolyState {
 };
 
 // restore the FMFPA polyhedron: x_0..x_{I-1}, back-traced I..2I-1, apex 2I;
-// faces: the cell face, I side quads, I bottom triangles (Sec. 2.2.2)
+// faces: the cell face, I side quads, I bottom triangles (Sec. 2.2.2). A
+// side quad whose back-traced vertices do not both lie on its side plane
+// (streak-line fallback) is not planar; it is split into the triangles
+// (x_{i+1}, x_i, x_{I+i}) and (x_{i+1}, x_{I+i}, x_{I+i+1}), bit i of split.
 template <typename G>
-__device__ void restore_base(Poly<G>& P, PolyState& st, int I, int lane) {
+__device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, int lane) {
   const int nvb = 2 * I + 1;
+  const int nsplit = __popc(split);
   if (lane < nvb) {
     P.vx[lane] = P.bx[lane]; P.vy[lane] = P.by[lane]; P.vz[lane] = P.bz[lane];
     if (lane == 0) {
@@ -88,21 +92,34 @@ __device__ void restore_base(Poly<G>& P, PolyState& st, int I, int lane) {
       P.flen[0][0] = (uint8_t)I;
     } else if (lane <= I) {
       const int i = lane - 1, ip = (i + 1 == I) ? 0 : i + 1;
-      P.fv[0][0][lane] = (uint8_t)ip;
-      P.fv[0][1][lane] = (uint8_t)i;
-      P.fv[0][2][lane] = (uint8_t)(I + i);
-      P.fv[0][3][lane] = (uint8_t)(I + ip);
-      P.flen[0][lane] = 4;
+      const int slot = 1 + i + __popc(split & ((1u << i) - 1u));
+      if ((split >> i) & 1u) {
+        P.fv[0][0][slot] = (uint8_t)ip;
+        P.fv[0][1][slot] = (uint8_t)i;
+        P.fv[0][2][slot] = (uint8_t)(I + i);
+        P.flen[0][slot] = 3;
+        P.fv[0][0][slot + 1] = (uint8_t)ip;
+        P.fv[0][1][slot + 1] = (uint8_t)(I + i);
+        P.fv[0][2][slot + 1] = (uint8_t)(I + ip);
+        P.flen[0][slot + 1] = 3;
+      } else {
+        P.fv[0][0][slot] = (uint8_t)ip;
+        P.fv[0][1][slot] = (uint8_t)i;
+        P.fv[0][2][slot] = (uint8_t)(I + i);
+        P.fv[0][3][slot] = (uint8_t)(I + ip);
+        P.flen[0][slot] = 4;
+      }
     } else {
       const int i = lane - 1 - I, ip = (i + 1 == I) ? 0 : i + 1;
-      P.fv[0][0][lane] = (uint8_t)(I + ip);
-      P.fv[0][1][lane] = (uint8_t)(I + i);
-      P.fv[0][2][lane] = (uint8_t)(2 * I);
-      P.flen[0][lane] = 3;
+      const int slot = lane + nsplit;
+      P.fv[0][0][slot] = (uint8_t)(I + ip);
+      P.fv[0][1][slot] = (uint8_t)(I + i);
+      P.fv[0][2][slot] = (uint8_t)(2 * I);
+      P.flen[0][slot] = 3;
     }
   }
   st.nv = nvb;
-  st.nf = nvb;
+  st.nf = nvb + nsplit;
   st.cur = 0;
   __syncwarp();
 }
@@ -159,7 +176,13 @@ __device__ void compact(Poly<G>& P, PolyState& st, int lane) {
 template <typename G>
 __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, unsigned& err) {
   if (st.nv > NV - NR) compact(P, st, lane);
-  for (int v = lane; v < st.nv; v += 32) P.phi[v] = a0 * P.vx[v] + a1 * P.vy[v] + a2 * P.vz[v] + b;
+  bool vout = false;
+  for (int v = lane; v < st.nv; v += 32) {
+    const G ph = a0 * P.vx[v] + a1 * P.vy[v] + a2 * P.vz[v] + b;
+    P.phi[v] = ph;
+    vout |= !(ph >= G(0));
+  }
+  if (!__any_sync(GVOF_FULL, vout)) return 0;  // no vertex outside: unchanged
   __syncwarp();
   const int cur = st.cur, nf = st.nf, nv = st.nv;
   const int fl = lane < NF ? lane : 0;
@@ -309,6 +332,7 @@ struct FaceFrame {
   int I;
   G lo[3], hi[3];                  // local bounding box of the polyhedron
   int degenerate, edgeon;
+  unsigned split;                  // non-planar side quads (bit i: side i)
 };
 
 // FMFPA construction (Sec. 2.2.2) into P.b*: side plane i contains edge i
@@ -368,7 +392,12 @@ __device__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv, const FluxPa
   } else {
     bxl = lx - ux; byl = ly - uy; bzl = lz - uz;
   }
-  fr.degenerate = __popc(__ballot_sync(GVOF_FULL, act && !ok));
+  const unsigned bad = __ballot_sync(GVOF_FULL, act && !ok);
+  fr.degenerate = __popc(bad);
+  // side i joins back-traced vertices i and i+1: planar only if both lie
+  // on its side plane
+  const unsigned full_mask = (I >= 32) ? 0xffffffffu : ((1u << I) - 1u);
+  fr.split = (bad | (((bad >> 1) | (bad << (I - 1))) & full_mask)) & full_mask;
   // centroid of the back-traced loop and its vector area B
   const G bxn = __shfl_sync(GVOF_FULL, bxl, nxt), byn = __shfl_sync(GVOF_FULL, byl, nxt),
           bzn = __shfl_sync(GVOF_FULL, bzl, nxt);
@@ -430,10 +459,19 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
   return lo < n && a[lo] == key;
 }
 
-// vol(P ∩ cell k ∩ fluid_k) in face-local units
+// vol(P ∩ cell k ∩ fluid_k) in face-local units.
+// The cell's planes are first tested against the base polyhedron's vertices
+// (one ballot per plane): a plane with every vertex outside empties the
+// intersection, a plane with none outside is skipped, and only the planes
+// that cut are clipped. A polyhedron inside the cell needs no clipping at
+// all for a full cell (its volume is V_d) and one clip for an interfacial
+// cell. Vertices within tol of a plane count as on its inner side; tol is
+// a few ulps of the face-local unit, so the volume this neglects is of the
+// order of the rounding of the plane itself.
 template <typename G>
 __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int k,
-                              const FaceFrame<G>& fr, Poly<G>& P, int lane, unsigned& err) {
+                              const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err) {
+  const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
   // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
   // frame a = -n_out, b = -n_out.(c - p_g) / L
   const int64_t c0 = M.cf_ptr[k];
@@ -447,21 +485,48 @@ __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevS
     pa0 = -ox; pa1 = -oy; pa2 = -oz;
     pb = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) + oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
   }
+  const int nvb = 2 * fr.I + 1;
+  const bool hv = lane < nvb;
+  const G bx = hv ? P.bx[lane] : G(0), by = hv ? P.by[lane] : G(0), bz = hv ? P.bz[lane] : G(0);
+  const unsigned vmask = (1u << nvb) - 1u;
+  unsigned cut = 0u;
+  for (int g = 0; g < nfk; ++g) {
+    const G a0 = __shfl_sync(GVOF_FULL, pa0, g), a1 = __shfl_sync(GVOF_FULL, pa1, g),
+            a2 = __shfl_sync(GVOF_FULL, pa2, g), b = __shfl_sync(GVOF_FULL, pb, g);
+    const G ph = a0 * bx + a1 * by + a2 * bz + b;
+    const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
+    const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
+    if (in == 0u && out != 0u) return G(0);  // P on the outer side of a face plane
+    if (out) cut |= 1u << g;
+    (void)vmask;
+  }
+  const bool tag0 = S.tc[k] == 0;
+  G pn0 = G(0), pn1 = G(0), pn2 = G(0), pnb = G(0);
+  if (tag0) {
+    // fluid half-space of the PLIC plane: n.(x - x_k) + C >= 0
+    pn0 = Gv.pnx[k]; pn1 = Gv.pny[k]; pn2 = Gv.pnz[k];
+    pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
+           Gv.pC[k]) * fr.sc;
+  }
+  if (cut == 0u) {
+    if (!tag0) return Vl;  // P inside a full cell
+    const G ph = pn0 * bx + pn1 * by + pn2 * bz + pnb;
+    const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
+    const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
+    if (out == 0u) return Vl;          // P inside the fluid of the cell
+    if (in == 0u) return G(0);         // P inside the empty part
+  }
   PolyState st;
-  restore_base(P, st, fr.I, lane);
+  restore_base(P, st, fr.I, fr.split, lane);
   int res = 0;
-  for (int g = 0; g < nfk && res != 2; ++g) {
+  while (cut && res != 2) {
+    const int g = __ffs(cut) - 1;
+    cut &= cut - 1u;
     const G a0 = __shfl_sync(GVOF_FULL, pa0, g), a1 = __shfl_sync(GVOF_FULL, pa1, g),
             a2 = __shfl_sync(GVOF_FULL, pa2, g), b = __shfl_sync(GVOF_FULL, pb, g);
     res = clip(P, st, a0, a1, a2, b, lane, err);
   }
-  if (res != 2 && S.tc[k] == 0) {
-    // fluid half-space of the PLIC plane: n.(x - x_k) + C >= 0
-    const G nx = Gv.pnx[k], ny = Gv.pny[k], nz = Gv.pnz[k];
-    const G b = (nx * rel(fr.cx, Gv.ccx[k]) + ny * rel(fr.cy, Gv.ccy[k]) +
-                 nz * rel(fr.cz, Gv.ccz[k]) + Gv.pC[k]) * fr.sc;
-    res = clip(P, st, nx, ny, nz, b, lane, err);
-  }
+  if (res != 2 && tag0) res = clip(P, st, pn0, pn1, pn2, pnb, lane, err);
   return res == 2 ? G(0) : volume(P, st, lane);
 }
 
@@ -486,6 +551,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_flux(DevMesh M, GeoView<G> Gv, 
     n_edge += fr.edgeon;
     unsigned err = 0u;
     G vf = G(0);
+    const G Vl = (G)S.Vd[j] * (fr.sc * fr.sc * fr.sc);  // volume of P, local units
     // candidates: owner, its node neighbours, then the neighbour and its
     // node neighbours not seen yet (Sec. 2.2: donating regions of several
     // cells), filtered by tag and by the local bounding box of the polyhedron
@@ -516,7 +582,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_flux(DevMesh M, GeoView<G> Gv, 
           const int src = __ffs(bal) - 1;
           bal &= bal - 1u;
           const int kk = __shfl_sync(GVOF_FULL, k, src);
-          vf += truncate_in_cell<G>(M, Gv, S, kk, fr, P, lane, err);
+          vf += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err);
           ++n_trunc;
         }
       }
