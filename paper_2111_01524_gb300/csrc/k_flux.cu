@@ -31,6 +31,10 @@
 namespace gvof {
 namespace {
 
+#ifndef GVOF_FLUX_MINB
+#define GVOF_FLUX_MINB 4
+#endif
+
 constexpr int kWarps = 4;
 constexpr int MAXI = kMaxFaceVerts;   // face vertices
 constexpr int NB = 2 * MAXI + 1;      // base polyhedron vertices / faces
@@ -48,7 +52,10 @@ struct __align__(16) Poly {
   uint8_t flen[2][NF];
   uint8_t ra[NR], rb[NR];    // cut-edge records: inside vertex, outside vertex
   int8_t capnext[NR];
+  int8_t rnext[NR];          // next record of the same inside vertex
+  int rfirst[NV];            // first record of each inside vertex (-1: none)
   uint8_t newid[NV];
+  G pl[NF][4];               // half-spaces of the current candidate cell
 };
 
 template <typename T>
@@ -180,6 +187,7 @@ __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, 
   for (int v = lane; v < st.nv; v += 32) {
     const G ph = a0 * P.vx[v] + a1 * P.vy[v] + a2 * P.vz[v] + b;
     P.phi[v] = ph;
+    P.rfirst[v] = -1;
     vout |= !(ph >= G(0));
   }
   if (!__any_sync(GVOF_FULL, vout)) return 0;  // no vertex outside: unchanged
@@ -188,16 +196,17 @@ __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, 
   const int fl = lane < NF ? lane : 0;
   bool has_in = false, has_out = false;
   int nexit = 0, L = 0;
+  unsigned inmask = 0u;  // bit k: loop vertex k inside
   if (lane < nf) {
     L = P.flen[cur][lane];
-    bool prev = P.phi[P.fv[cur][L - 1][fl]] >= G(0);
-    for (int k = 0; k < L; ++k) {
-      const bool in = P.phi[P.fv[cur][k][fl]] >= G(0);
-      has_in |= in;
-      has_out |= !in;
-      nexit += (prev && !in);
-      prev = in;
-    }
+    for (int k = 0; k < L; ++k)
+      if (P.phi[P.fv[cur][k][fl]] >= G(0)) inmask |= 1u << k;
+    const unsigned full = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+    has_in = inmask != 0u;
+    has_out = inmask != full;
+    // exit edges k -> k+1: k inside, k+1 outside
+    const unsigned nxt_in = ((inmask >> 1) | (inmask << (L - 1))) & full;
+    nexit = __popc(inmask & ~nxt_in);
   }
   const unsigned bin = __ballot_sync(GVOF_FULL, has_in);
   const unsigned bout = __ballot_sync(GVOF_FULL, has_out);
@@ -215,9 +224,10 @@ __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, 
   if (lane < nf && nexit) {
     int r = off;
     for (int k = 0; k < L; ++k) {
-      const int va = P.fv[cur][k][fl], vb = P.fv[cur][(k + 1 == L) ? 0 : k + 1][fl];
-      const G pa = P.phi[va], pb = P.phi[vb];
-      if (pa >= G(0) && !(pb >= G(0))) {
+      const int k1 = (k + 1 == L) ? 0 : k + 1;
+      if (((inmask >> k) & 1u) && !((inmask >> k1) & 1u)) {
+        const int va = P.fv[cur][k][fl], vb = P.fv[cur][k1][fl];
+        const G pa = P.phi[va], pb = P.phi[vb];
         const G t = pa / (pa - pb);
         const int id = nv + r;
         P.vx[id] = P.vx[va] + t * (P.vx[vb] - P.vx[va]);
@@ -226,6 +236,7 @@ __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, 
         P.ra[r] = (uint8_t)va;
         P.rb[r] = (uint8_t)vb;
         P.capnext[r] = -1;
+        P.rnext[r] = (int8_t)atomicExch(&P.rfirst[va], r);  // chain by inside vertex
         ++r;
       }
     }
@@ -235,35 +246,29 @@ __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, 
   const int slot = __popc(bin & ((1u << lane) - 1u));
   bool bad = false;
   if (lane < nf && has_in) {
-    int k0 = 0;
-    while (!(P.phi[P.fv[cur][k0][fl]] >= G(0))) ++k0;
+    const int k0 = __ffs(inmask) - 1;
     int n = 0, pend = -1;
     for (int s = 0; s < L; ++s) {
       int k = k0 + s;
       if (k >= L) k -= L;
       const int k1 = (k + 1 == L) ? 0 : k + 1;
-      const int va = P.fv[cur][k][fl], vb = P.fv[cur][k1][fl];
-      const bool ia = P.phi[va] >= G(0), ib = P.phi[vb] >= G(0);
+      const int va = P.fv[cur][k][fl];
+      const bool ia = (inmask >> k) & 1u, ib = (inmask >> k1) & 1u;
       if (ia) {
         if (n < LM) P.fv[nxt][n][slot] = (uint8_t)va;
         ++n;
       }
-      if (ia && !ib) {
-        int r = -1;
-        for (int q = off; q < off + nexit; ++q)
-          if (P.ra[q] == va && P.rb[q] == vb) { r = q; break; }
-        if (r < 0) { bad = true; break; }
+      if (ia != ib) {
+        const int vb = P.fv[cur][k1][fl];
+        // record of the cut edge (inside vertex, outside vertex)
+        const int vin = ia ? va : vb, vout2 = ia ? vb : va;
+        int r = P.rfirst[vin];
+        while (r >= 0 && P.rb[r] != vout2) r = P.rnext[r];
+        if (r < 0 || (!ia && pend < 0)) { bad = true; break; }
         if (n < LM) P.fv[nxt][n][slot] = (uint8_t)(nv + r);
         ++n;
-        pend = r;
-      } else if (!ia && ib) {
-        int r = -1;
-        for (int q = 0; q < total; ++q)
-          if (P.ra[q] == vb && P.rb[q] == va) { r = q; break; }
-        if (r < 0 || pend < 0) { bad = true; break; }
-        if (n < LM) P.fv[nxt][n][slot] = (uint8_t)(nv + r);
-        ++n;
-        P.capnext[r] = (int8_t)pend;  // cap edge: entry -> preceding exit
+        if (ia) pend = r;
+        else P.capnext[r] = (int8_t)pend;  // cap edge: entry -> preceding exit
       }
     }
     if (n > LM) bad = true;
@@ -476,29 +481,26 @@ __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevS
   // frame a = -n_out, b = -n_out.(c - p_g) / L
   const int64_t c0 = M.cf_ptr[k];
   const int nfk = (int)(M.cf_ptr[k + 1] - c0);
-  G pa0 = G(0), pa1 = G(0), pa2 = G(0), pb = G(0);
   if (lane < nfk) {
     const int fs = M.cf[c0 + lane];
     const int f = fs >= 0 ? fs : ~fs;
     const G sg = fs >= 0 ? G(1) : G(-1);
     const G ox = sg * Gv.fnx[f], oy = sg * Gv.fny[f], oz = sg * Gv.fnz[f];
-    pa0 = -ox; pa1 = -oy; pa2 = -oz;
-    pb = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) + oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
+    P.pl[lane][0] = -ox; P.pl[lane][1] = -oy; P.pl[lane][2] = -oz;
+    P.pl[lane][3] = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) +
+                      oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
   }
+  __syncwarp();
   const int nvb = 2 * fr.I + 1;
   const bool hv = lane < nvb;
   const G bx = hv ? P.bx[lane] : G(0), by = hv ? P.by[lane] : G(0), bz = hv ? P.bz[lane] : G(0);
-  const unsigned vmask = (1u << nvb) - 1u;
   unsigned cut = 0u;
   for (int g = 0; g < nfk; ++g) {
-    const G a0 = __shfl_sync(GVOF_FULL, pa0, g), a1 = __shfl_sync(GVOF_FULL, pa1, g),
-            a2 = __shfl_sync(GVOF_FULL, pa2, g), b = __shfl_sync(GVOF_FULL, pb, g);
-    const G ph = a0 * bx + a1 * by + a2 * bz + b;
+    const G ph = P.pl[g][0] * bx + P.pl[g][1] * by + P.pl[g][2] * bz + P.pl[g][3];
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
     if (in == 0u && out != 0u) return G(0);  // P on the outer side of a face plane
     if (out) cut |= 1u << g;
-    (void)vmask;
   }
   const bool tag0 = S.tc[k] == 0;
   G pn0 = G(0), pn1 = G(0), pn2 = G(0), pnb = G(0);
@@ -522,16 +524,14 @@ __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevS
   while (cut && res != 2) {
     const int g = __ffs(cut) - 1;
     cut &= cut - 1u;
-    const G a0 = __shfl_sync(GVOF_FULL, pa0, g), a1 = __shfl_sync(GVOF_FULL, pa1, g),
-            a2 = __shfl_sync(GVOF_FULL, pa2, g), b = __shfl_sync(GVOF_FULL, pb, g);
-    res = clip(P, st, a0, a1, a2, b, lane, err);
+    res = clip(P, st, P.pl[g][0], P.pl[g][1], P.pl[g][2], P.pl[g][3], lane, err);
   }
   if (res != 2 && tag0) res = clip(P, st, pn0, pn1, pn2, pnb, lane, err);
   return res == 2 ? G(0) : volume(P, st, lane);
 }
 
 template <typename G>
-__global__ void __launch_bounds__(kWarps * 32) k_flux(DevMesh M, GeoView<G> Gv, DevState S,
+__global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S,
                                                       FluxParams p) {
   __shared__ Poly<G> polys[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
