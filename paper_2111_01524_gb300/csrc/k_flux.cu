@@ -32,7 +32,7 @@ namespace gvof {
 namespace {
 
 #ifndef GVOF_FLUX_MINB
-#define GVOF_FLUX_MINB 4
+#define GVOF_FLUX_MINB 8
 #endif
 
 constexpr int kWarps = 4;
@@ -464,19 +464,25 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
   return lo < n && a[lo] == key;
 }
 
-// vol(P ∩ cell k ∩ fluid_k) in face-local units.
+// vol(P ∩ cell k ∩ X_k) in face-local units, X_k the fluid of cell k
+// (empty_side = false: all of a full cell, the PLIC half-space of an
+// interfacial cell) or its empty part (empty_side = true: all of an empty
+// cell, the complementary half-space of an interfacial cell).
 // The cell's planes are first tested against the base polyhedron's vertices
 // (one ballot per plane): a plane with every vertex outside empties the
 // intersection, a plane with none outside is skipped, and only the planes
-// that cut are clipped. A polyhedron inside the cell needs no clipping at
-// all for a full cell (its volume is V_d) and one clip for an interfacial
-// cell. Vertices within tol of a plane count as on its inner side; tol is
-// a few ulps of the face-local unit, so the volume this neglects is of the
-// order of the rounding of the plane itself.
+// that cut are clipped. *whole is set when P lies inside X_k (the result is
+// then the volume of P itself). Vertices within tol of a plane count as on
+// its inner side; tol is a few ulps of the face-local unit, so the volume
+// this neglects is of the order of the rounding of the plane itself.
 template <typename G>
 __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int k,
-                              const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err) {
+                              const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
+                              bool empty_side, bool* whole) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
+  *whole = false;
+  const int8_t tk = S.tc[k];
+  if (tk == (empty_side ? 1 : -1)) return G(0);
   // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
   // frame a = -n_out, b = -n_out.(c - p_g) / L
   const int64_t c0 = M.cf_ptr[k];
@@ -502,21 +508,22 @@ __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevS
     if (in == 0u && out != 0u) return G(0);  // P on the outer side of a face plane
     if (out) cut |= 1u << g;
   }
-  const bool tag0 = S.tc[k] == 0;
+  const bool tag0 = tk == 0;
   G pn0 = G(0), pn1 = G(0), pn2 = G(0), pnb = G(0);
   if (tag0) {
     // fluid half-space of the PLIC plane: n.(x - x_k) + C >= 0
     pn0 = Gv.pnx[k]; pn1 = Gv.pny[k]; pn2 = Gv.pnz[k];
     pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
            Gv.pC[k]) * fr.sc;
+    if (empty_side) { pn0 = -pn0; pn1 = -pn1; pn2 = -pn2; pnb = -pnb; }
   }
   if (cut == 0u) {
-    if (!tag0) return Vl;  // P inside a full cell
+    if (!tag0) { *whole = true; return Vl; }  // P inside the cell
     const G ph = pn0 * bx + pn1 * by + pn2 * bz + pnb;
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
-    if (out == 0u) return Vl;          // P inside the fluid of the cell
-    if (in == 0u) return G(0);         // P inside the empty part
+    if (out == 0u) { *whole = true; return Vl; }  // P inside X_k
+    if (in == 0u) return G(0);
   }
   PolyState st;
   restore_base(P, st, fr.I, fr.split, lane);
@@ -528,6 +535,56 @@ __device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevS
   }
   if (res != 2 && tag0) res = clip(P, st, pn0, pn1, pn2, pnb, lane, err);
   return res == 2 ? G(0) : volume(P, st, lane);
+}
+
+// sum of vol(P ∩ cell k ∩ X_k) over the candidate cells: owner, its node
+// neighbours, then the neighbour and its node neighbours not seen yet
+// (Sec. 2.2: donating regions of several cells), filtered by the local
+// bounding box of the polyhedron. Returns the sum in face-local units and
+// sets *whole when P lies inside one X_k.
+template <typename G>
+__device__ G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
+                              const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
+                              bool empty_side, bool* whole, unsigned long long& n_trunc) {
+  const int64_t nc = M.nc;
+  const int own = M.own[j], nbr = M.nbr[j];
+  const int64_t a0 = M.nb_ptr[own];
+  const int na = (int)(M.nb_ptr[own + 1] - a0);
+  const int8_t skip_tag = empty_side ? 1 : -1;
+  G v = G(0);
+  *whole = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int c0 = pass == 0 ? own : nbr;
+    if (c0 < 0) break;
+    const int64_t b0 = M.nb_ptr[c0];
+    const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
+    for (int base = 0; base < nb; base += 32) {
+      const int idx = base + lane;
+      int k = -1;
+      if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
+      bool keep = k >= 0;
+      if (keep && pass == 1) keep = !(k == own || sorted_contains(M.nb + a0, na, k));
+      if (keep) keep = S.tc[k] != skip_tag;
+      if (keep) {
+        const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
+        const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
+        const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
+        keep = fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy &&
+               fr.hi[2] > lz && fr.lo[2] < hz;
+      }
+      unsigned bal = __ballot_sync(GVOF_FULL, keep);
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const int kk = __shfl_sync(GVOF_FULL, k, src);
+        bool w = false;
+        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, empty_side, &w);
+        ++n_trunc;
+        if (w) { *whole = true; return Vl; }  // no other cell meets P
+      }
+    }
+  }
+  return v;
 }
 
 template <typename G>
@@ -550,45 +607,25 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     n_deg += fr.degenerate;
     n_edge += fr.edgeon;
     unsigned err = 0u;
-    G vf = G(0);
     const G Vl = (G)S.Vd[j] * (fr.sc * fr.sc * fr.sc);  // volume of P, local units
-    // candidates: owner, its node neighbours, then the neighbour and its
-    // node neighbours not seen yet (Sec. 2.2: donating regions of several
-    // cells), filtered by tag and by the local bounding box of the polyhedron
-    const int own = M.own[j], nbr = M.nbr[j];
-    const int64_t a0 = M.nb_ptr[own];
-    const int na = (int)(M.nb_ptr[own + 1] - a0);
-    for (int pass = 0; pass < 2; ++pass) {
-      const int c0 = pass == 0 ? own : nbr;
-      if (c0 < 0) break;
-      const int64_t b0 = M.nb_ptr[c0];
-      const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
-      for (int base = 0; base < nb; base += 32) {
-        const int idx = base + lane;
-        int k = -1;
-        if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
-        bool keep = k >= 0;
-        if (keep && pass == 1) keep = !(k == own || sorted_contains(M.nb + a0, na, k));
-        if (keep) keep = S.tc[k] != -1;
-        if (keep) {
-          const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
-          const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
-          const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
-          keep = fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy &&
-                 fr.hi[2] > lz && fr.lo[2] < hz;
-        }
-        unsigned bal = __ballot_sync(GVOF_FULL, keep);
-        while (bal) {
-          const int src = __ffs(bal) - 1;
-          bal &= bal - 1u;
-          const int kk = __shfl_sync(GVOF_FULL, k, src);
-          vf += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err);
-          ++n_trunc;
-        }
-      }
+    const G L3 = fr.L * fr.L * fr.L;
+    bool whole = false;
+    const G vf = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, false, &whole, n_trunc);
+    double VFj;
+    if (whole) {
+      VFj = S.Vd[j];  // P inside the fluid of one cell: exactly V_d
+    } else if (sizeof(G) == 4 && M.nbr[j] >= 0 && fabs(vf) > G(0.5) * fabs(Vl)) {
+      // mostly fluid: V_F = V_d - (empty part of P), so that the FP32 error
+      // scales with the empty part (P lies in the candidate cells for an
+      // interior face at CFL <= 1, so fluid + empty = V_d)
+      bool we = false;
+      const G ve = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, true, &we, n_trunc);
+      VFj = we ? 0.0 : S.Vd[j] - (double)(ve * L3);
+    } else {
+      VFj = (double)(vf * L3);
     }
     if (err) ++n_over;
-    if (lane == 0) S.VF[j] = (double)(vf * (fr.L * fr.L * fr.L));
+    if (lane == 0) S.VF[j] = VFj;
   }
   if (lane == 0) {
     if (n_trunc) atomicAdd(S.cnt + kNTrunc, n_trunc);
