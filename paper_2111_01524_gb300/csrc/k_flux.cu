@@ -133,7 +133,7 @@ __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, i
 
 // drop unreferenced vertices and renumber (keeps room for a clip)
 template <typename G>
-__device__ void compact(Poly<G>& P, PolyState& st, int lane) {
+__device__ __noinline__ void compact(Poly<G>& P, PolyState& st, int lane) {
   for (int v = lane; v < NV; v += 32) P.newid[v] = 0;
   __syncwarp();
   if (lane < st.nf) {
@@ -181,7 +181,8 @@ __device__ void compact(Poly<G>& P, PolyState& st, int lane) {
 // returns 0: unchanged, 1: clipped, 2: empty. err bit0: capacity overflow
 // or inconsistent topology (the face's V_F is then unreliable and counted).
 template <typename G>
-__device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, unsigned& err) {
+__device__ __noinline__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane,
+                                 unsigned& err) {
   if (st.nv > NV - NR) compact(P, st, lane);
   bool vout = false;
   for (int v = lane; v < st.nv; v += 32) {
@@ -303,7 +304,7 @@ __device__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane, 
 
 // signed volume of the surface: each lane fans one face loop
 template <typename G>
-__device__ G volume(const Poly<G>& P, const PolyState& st, int lane) {
+__device__ __noinline__ G volume(const Poly<G>& P, const PolyState& st, int lane) {
   G acc = G(0);
   if (st.nf > 0) {
     const int o = P.fv[st.cur][0][0];
@@ -476,7 +477,7 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
 // its inner side; tol is a few ulps of the face-local unit, so the volume
 // this neglects is of the order of the rounding of the plane itself.
 template <typename G>
-__device__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int k,
+__device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int k,
                               const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
                               bool empty_side, bool* whole) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
