@@ -174,6 +174,24 @@ enum { VOF_PHASE_CELL_TAGS = 0, VOF_PHASE_NODE_TAGS = 1, VOF_PHASE_RECONSTRUCT =
        VOF_PHASE_FACE_SWEEP = 3, VOF_PHASE_FLUX = 4, VOF_PHASE_UPDATE = 5, VOF_NUM_PHASES = 6 };
 vof_status vof_set_timing(vof_ctx* ctx, int on);
 vof_status vof_get_timing(vof_ctx* ctx, double* ms, int64_t* launches, int n);
+/* Allocation-free weighted sum: *out = sum over i < n of w[i] * F[i] (the
+ * global fluid volume when w holds the cell volumes), in the same fixed
+ * order on every call. The paper has no counterpart; this entry point
+ * exists for callers that cannot allocate device memory where they need the
+ * sum, e.g. a solver that reserved its whole device budget up front, or a
+ * time loop that must not pay the device-wide synchronisation or the
+ * failure modes of cudaMalloc. w, F and out are DEVICE pointers owned by the
+ * caller; the result is written to out[0] asynchronously on `stream`.
+ * It allocates nothing: its only scratch is a file-scope device array of
+ * 65536 doubles (512 KiB) that every GPU loading the library holds until
+ * the process exits, so n is limited to 65536 * 4096 = 268,435,456;
+ * larger (or negative) n returns VOF_EINVAL with a message. The first call
+ * on a device looks up that array's device address (set-up, once per
+ * device); make that first call before any stream capture. All calls share
+ * the array: calls that overlap on the GPU (different streams, or different
+ * host threads using one device) race, so serialise them. */
+vof_status vof_volume_sum_noalloc(const double* w, const double* F, int64_t n, double* out,
+                                  void* stream);
 /* bytes of device memory held by the context */
 int64_t vof_device_bytes(const vof_ctx* ctx);
 

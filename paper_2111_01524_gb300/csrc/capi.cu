@@ -131,6 +131,10 @@ double dt_from(const double hmin[3], const double um[3], double cfl) {
 
 }  // namespace
 
+namespace gvof {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace gvof
+
 extern "C" {
 
 const char* vof_last_error(void) { return g_err.c_str(); }

@@ -282,6 +282,9 @@ inline double time_factor(const Vel& v, double t) {
   return 1.0;
 }
 
+// message returned by vof_last_error() on this thread
+void set_last_error(const char* msg);
+
 // ------------------------------------------------------------ launchers
 // set-up (k_setup.cu)
 cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s);

@@ -89,6 +89,8 @@ def lib():
         L.vof_get_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.vof_set_timing.argtypes = [vp, C.c_int]
         L.vof_get_timing.argtypes = [vp, vp, vp, C.c_int]
+        L.vof_volume_sum_noalloc.argtypes = [vp, vp, i64, vp, vp]
+        L.vof_volume_sum_noalloc.restype = C.c_int
         L.vof_device_bytes.restype = i64
         L.vof_device_bytes.argtypes = [vp]
         for name in ("vof_init", "vof_set_fraction", "vof_get_fraction", "vof_reconstruct",
@@ -130,6 +132,17 @@ def _stream(stream):
     if hasattr(stream, "cuda_stream"):
         return C.c_void_p(stream.cuda_stream)
     return C.c_void_p(int(stream))
+
+
+def volume_sum_noalloc(w, F, out, n=None, stream=None):
+    """sum_i w[i] * F[i] into out[0] through the allocation-free entry point.
+
+    w, F, out are CUDA tensors (float64) owned by the caller; nothing is
+    allocated by the library. Returns the raw status (VOF_OK on success).
+    """
+    if n is None:
+        n = w.numel()
+    return lib().vof_volume_sum_noalloc(_ptr(w), _ptr(F), int(n), _ptr(out), _stream(stream))
 
 
 def velocity_struct(v):
