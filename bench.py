@@ -182,8 +182,9 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_bytes_per_launch": b, "peak_source": peak_kind}
     # band kernels: plain ALU arithmetic
+    # the counters describe the last advect (one launch of each band kernel)
     fl = (ctx_counts["n_active_faces"] * FLOPS_PER_ACTIVE_FACE
-          + ctx_counts["n_truncations"] * FLOPS_PER_TRUNCATION) / max(launches, 1)
+          + ctx_counts["n_truncations"] * FLOPS_PER_TRUNCATION)
     mhz = clocks.get("sm_mhz") or 1900.0
     lanes = FP32_LANES_PER_SM if precision == "mixed" else FP64_LANES_PER_SM
     peak = N_SM * lanes * 2 * mhz * 1e6 / 1e12

@@ -55,7 +55,7 @@ struct __align__(16) Poly {
   int8_t rnext[NR];          // next record of the same inside vertex
   int rfirst[NV];            // first record of each inside vertex (-1: none)
   uint8_t newid[NV];
-  G pl[NF][4];               // half-spaces of the current candidate cell
+  G pl[NF + 1][4];           // half-spaces of the current candidate cell; [NF]: PLIC
 };
 
 template <typename T>
@@ -325,6 +325,50 @@ __device__ __noinline__ G volume(const Poly<G>& P, const PolyState& st, int lane
   return wsum(acc) / G(6);
 }
 
+// volume of the part of the surface on the inner side a.x + b >= 0 of a
+// plane, without building the cut: each lane clips its face loop on the fly
+// (Sutherland-Hodgman) and fans it with the origin ON the plane, so the cap
+// the cut would close contributes nothing to the divergence sum
+template <typename G>
+__device__ __noinline__ G volume_cut(const Poly<G>& P, const PolyState& st, G a0, G a1, G a2, G b,
+                                     int lane) {
+  G acc = G(0);
+  if (lane < st.nf) {
+    const G aa = a0 * a0 + a1 * a1 + a2 * a2;
+    const G ox = -b * a0 / aa, oy = -b * a1 / aa, oz = -b * a2 / aa;
+    const int L = P.flen[st.cur][lane];
+    int v = P.fv[st.cur][L - 1][lane];
+    G ax = P.vx[v] - ox, ay = P.vy[v] - oy, az = P.vz[v] - oz;
+    G pa = a0 * ax + a1 * ay + a2 * az;
+    int ne = 0;
+    G q0x = 0, q0y = 0, q0z = 0, qpx = 0, qpy = 0, qpz = 0;
+    for (int k = 0; k < L; ++k) {
+      v = P.fv[st.cur][k][lane];
+      const G bx = P.vx[v] - ox, by = P.vy[v] - oy, bz = P.vz[v] - oz;
+      const G pb = a0 * bx + a1 * by + a2 * bz;
+      const bool ia = pa >= G(0), ib = pb >= G(0);
+      for (int e = 0; e < 2; ++e) {
+        G px, py, pz;
+        if (e == 0) {
+          if (ia == ib) continue;
+          const G t = pa / (pa - pb);
+          px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
+        } else {
+          if (!ib) continue;
+          px = bx; py = by; pz = bz;
+        }
+        if (ne == 0) { q0x = px; q0y = py; q0z = pz; }
+        else if (ne >= 2)
+          acc += q0x * (qpy * pz - qpz * py) + q0y * (qpz * px - qpx * pz) + q0z * (qpx * py - qpy * px);
+        qpx = px; qpy = py; qpz = pz;
+        ++ne;
+      }
+      ax = bx; ay = by; az = bz; pa = pb;
+    }
+  }
+  return wsum(acc) / G(6);
+}
+
 struct FluxParams {
   Vel vel;
   double g;    // time factor at t + dt/2
@@ -510,21 +554,32 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
     if (out) cut |= 1u << g;
   }
   const bool tag0 = tk == 0;
-  G pn0 = G(0), pn1 = G(0), pn2 = G(0), pnb = G(0);
+  bool plic = false;
   if (tag0) {
     // fluid half-space of the PLIC plane: n.(x - x_k) + C >= 0
-    pn0 = Gv.pnx[k]; pn1 = Gv.pny[k]; pn2 = Gv.pnz[k];
-    pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
-           Gv.pC[k]) * fr.sc;
+    G pn0 = Gv.pnx[k], pn1 = Gv.pny[k], pn2 = Gv.pnz[k];
+    G pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
+             Gv.pC[k]) * fr.sc;
     if (empty_side) { pn0 = -pn0; pn1 = -pn1; pn2 = -pn2; pnb = -pnb; }
-  }
-  if (cut == 0u) {
-    if (!tag0) { *whole = true; return Vl; }  // P inside the cell
     const G ph = pn0 * bx + pn1 * by + pn2 * bz + pnb;
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
-    if (out == 0u) { *whole = true; return Vl; }  // P inside X_k
-    if (in == 0u) return G(0);
+    if (in == 0u && out != 0u) return G(0);  // P inside the other side
+    plic = out != 0u;
+    if (plic && lane == 0) {
+      P.pl[NF][0] = pn0; P.pl[NF][1] = pn1; P.pl[NF][2] = pn2; P.pl[NF][3] = pnb;
+    }
+  }
+  if (cut == 0u && !plic) { *whole = true; return Vl; }  // P inside X_k
+  // the planes that cut, the PLIC plane last; all but the last are clipped
+  // topologically, the last one only inside the volume sum
+  __syncwarp();
+  int last;
+  if (plic) {
+    last = NF;
+  } else {
+    last = 31 - __clz(cut);
+    cut &= ~(1u << last);
   }
   PolyState st;
   restore_base(P, st, fr.I, fr.split, lane);
@@ -534,8 +589,8 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
     cut &= cut - 1u;
     res = clip(P, st, P.pl[g][0], P.pl[g][1], P.pl[g][2], P.pl[g][3], lane, err);
   }
-  if (res != 2 && tag0) res = clip(P, st, pn0, pn1, pn2, pnb, lane, err);
-  return res == 2 ? G(0) : volume(P, st, lane);
+  if (res == 2) return G(0);
+  return volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
 }
 
 // sum of vol(P ∩ cell k ∩ X_k) over the candidate cells: owner, its node
