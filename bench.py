@@ -333,6 +333,8 @@ def main():
         Fm = ctxm.get_fraction()
         F64 = ctx64.get_fraction()
         fp64 = {"value": v64, "unit": UNIT, "steps": fsteps, "ms_per_step": ms64 / fsteps,
+                "band": {"interfacial_cells": st64["n_interfacial"],
+                         "active_faces": st64["n_active_faces"]},
                 "mixed_over_fp64": value / v64,
                 "max_abs_F_diff_mixed_vs_fp64": float(np.abs(Fm - F64).max()),
                 "after_steps": fsteps + a.warmup}

@@ -333,9 +333,13 @@ template <typename G>
 __device__ __noinline__ G volume_cut(const Poly<G>& P, const PolyState& st, G a0, G a1, G a2, G b,
                                      int lane) {
   G acc = G(0);
-  if (lane < st.nf) {
+  if (st.nf > 0 && lane < st.nf) {
+    // origin: projection of a vertex of the surface onto the plane, so that
+    // the fan terms stay of the size of the polyhedron
+    const int v0 = P.fv[st.cur][0][0];
     const G aa = a0 * a0 + a1 * a1 + a2 * a2;
-    const G ox = -b * a0 / aa, oy = -b * a1 / aa, oz = -b * a2 / aa;
+    const G d0 = (a0 * P.vx[v0] + a1 * P.vy[v0] + a2 * P.vz[v0] + b) / aa;
+    const G ox = P.vx[v0] - d0 * a0, oy = P.vy[v0] - d0 * a1, oz = P.vz[v0] - d0 * a2;
     const int L = P.flen[st.cur][lane];
     int v = P.fv[st.cur][L - 1][lane];
     G ax = P.vx[v] - ox, ay = P.vy[v] - oy, az = P.vz[v] - oz;
