@@ -355,8 +355,15 @@ __device__ __noinline__ G volume_cut(const Poly<G>& P, const PolyState& st, G a0
         G px, py, pz;
         if (e == 0) {
           if (ia == ib) continue;
-          const G t = pa / (pa - pb);
-          px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
+          // interpolate from the inside end, as the face on the other side of
+          // this edge does, so both compute the same point bit for bit
+          if (ia) {
+            const G t = pa / (pa - pb);
+            px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
+          } else {
+            const G t = pb / (pb - pa);
+            px = bx + t * (ax - bx); py = by + t * (ay - by); pz = bz + t * (az - bz);
+          }
         } else {
           if (!ib) continue;
           px = bx; py = by; pz = bz;

@@ -72,8 +72,15 @@ __device__ P cut_volume(const ReconSmem& S, int nfc, P nx, P ny, P nz, P C) {
         P px, py, pz;
         if (e == 0) {
           if (ia == ib) continue;
-          const P t = pa / (pa - pb);
-          px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
+          // interpolate from the inside end, as the face on the other side of
+          // this edge does, so both compute the same point bit for bit
+          if (ia) {
+            const P t = pa / (pa - pb);
+            px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
+          } else {
+            const P t = pb / (pb - pa);
+            px = bx + t * (ax - bx); py = by + t * (ay - by); pz = bz + t * (az - bz);
+          }
         } else {
           if (!ib) continue;
           px = bx; py = by; pz = bz;
