@@ -332,11 +332,22 @@ __device__ __noinline__ G volume(const Poly<G>& P, const PolyState& st, int lane
 template <typename G>
 __device__ __noinline__ G volume_cut(const Poly<G>& P, const PolyState& st, G a0, G a1, G a2, G b,
                                      int lane) {
+  // origin: projection onto the plane of a vertex on the inner side, so that
+  // the fan terms are of the size of the part that is kept (which may be a
+  // thin sliver of the polyhedron) and the FP32 error scales with it
+  int myv = -1;
+  if (lane < st.nf) {
+    const int L = P.flen[st.cur][lane];
+    for (int k = 0; k < L; ++k) {
+      const int v = P.fv[st.cur][k][lane];
+      if (a0 * P.vx[v] + a1 * P.vy[v] + a2 * P.vz[v] + b >= G(0)) { myv = v; break; }
+    }
+  }
+  const unsigned have = __ballot_sync(GVOF_FULL, myv >= 0);
+  if (have == 0u) return G(0);  // no vertex on the inner side: nothing is kept
+  const int v0 = __shfl_sync(GVOF_FULL, myv, __ffs(have) - 1);
   G acc = G(0);
-  if (st.nf > 0 && lane < st.nf) {
-    // origin: projection of a vertex of the surface onto the plane, so that
-    // the fan terms stay of the size of the polyhedron
-    const int v0 = P.fv[st.cur][0][0];
+  if (lane < st.nf) {
     const G aa = a0 * a0 + a1 * a1 + a2 * a2;
     const G d0 = (a0 * P.vx[v0] + a1 * P.vy[v0] + a2 * P.vz[v0] + b) / aa;
     const G ox = P.vx[v0] - d0 * a0, oy = P.vy[v0] - d0 * a1, oz = P.vz[v0] - d0 * a2;
