@@ -612,6 +612,12 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
     res = clip(P, st, P.pl[g][0], P.pl[g][1], P.pl[g][2], P.pl[g][3], lane, err);
   }
   if (res == 2) return G(0);
+  if (sizeof(G) == 8) {
+    // FP64: the streaming cut recomputes every cut point twice, and FP64
+    // divisions are costly on this GPU; clip topologically instead
+    res = clip(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane, err);
+    return res == 2 ? G(0) : volume(P, st, lane);
+  }
   return volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
 }
 
