@@ -10,9 +10,9 @@
  *  - Mesh: OpenFOAM-like face-based polyhedral mesh (Sec. 3.1). Faces are
  *    planar polygons; their nodes run counter-clockwise seen from outside
  *    the owner cell, so the right-hand normal leaves the owner. A boundary
- *    face has neighbour = -1. Cells must be convex (uniform hexahedra,
- *    tetrahedra, any convex polyhedra); a non-convex cell is rejected by
- *    vof_init with VOF_EINVAL.
+ *    face has neighbour = -1. Cells may be convex or non-convex (e.g. the
+ *    distorted cubic cells with triangulated faces of Sec. 4); a cell has
+ *    at most 32 faces, 32 nodes and 128 face-node entries.
  *  - PLIC plane of an interfacial cell (Eq. plic-eq):  n.(x - xc) + C = 0,
  *    xc = cell centroid, n = unit normal pointing into the fluid; the fluid
  *    is the part of the cell where n.(x - xc) + C >= 0.

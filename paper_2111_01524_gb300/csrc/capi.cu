@@ -275,10 +275,6 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
   if (o.precision == VOF_PREC_MIXED) CKI(launch_mixed_copies(c, 0));
   CKI(cudaDeviceSynchronize());
   {
-    std::vector<uint8_t> cvx(nc);
-    CKI(cudaMemcpy(cvx.data(), c->convex, nc, cudaMemcpyDeviceToHost));
-    for (int64_t k = 0; k < nc; ++k)
-      if (!cvx[k]) return cleanup(VOF_EINVAL, "cell " + std::to_string(k) + " is not convex");
     std::vector<double> bb(6 * nc);
     CKI(cudaMemcpy(bb.data(), c->bb, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost));
     for (int d = 0; d < 3; ++d) {

@@ -531,71 +531,43 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
   return lo < n && a[lo] == key;
 }
 
-// vol(P ∩ cell k ∩ X_k) in face-local units, X_k the fluid of cell k
-// (empty_side = false: all of a full cell, the PLIC half-space of an
-// interfacial cell) or its empty part (empty_side = true: all of an empty
-// cell, the complementary half-space of an interfacial cell).
-// The cell's planes are first tested against the base polyhedron's vertices
-// (one ballot per plane): a plane with every vertex outside empties the
+// vol(P ∩ K ∩ X) in face-local units, K the convex region of the np
+// half-spaces P.pl[0..np) (inner side a.x + b >= 0) and X either all space
+// (plic = false) or the half-space P.pl[NF] (the PLIC plane, oriented to
+// the side that is wanted).
+// The planes are first tested against the base polyhedron's vertices (one
+// ballot per plane): a plane with every vertex outside empties the
 // intersection, a plane with none outside is skipped, and only the planes
-// that cut are clipped. *whole is set when P lies inside X_k (the result is
-// then the volume of P itself). Vertices within tol of a plane count as on
-// its inner side; tol is a few ulps of the face-local unit, so the volume
-// this neglects is of the order of the rounding of the plane itself.
+// that cut are clipped: all but the last topologically, the last one inside
+// the volume sum. *whole is set when P lies inside K ∩ X (the result is then
+// the volume of P itself). Vertices within tol of a plane count as on its
+// inner side; tol is a few ulps of the face-local unit, so the volume this
+// neglects is of the order of the rounding of the plane itself.
 template <typename G>
-__device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int k,
-                              const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
-                              bool empty_side, bool* whole) {
+__device__ __noinline__ G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
+                                          G Vl, int lane, unsigned& err, bool* whole) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
   *whole = false;
-  const int8_t tk = S.tc[k];
-  if (tk == (empty_side ? 1 : -1)) return G(0);
-  // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
-  // frame a = -n_out, b = -n_out.(c - p_g) / L
-  const int64_t c0 = M.cf_ptr[k];
-  const int nfk = (int)(M.cf_ptr[k + 1] - c0);
-  if (lane < nfk) {
-    const int fs = M.cf[c0 + lane];
-    const int f = fs >= 0 ? fs : ~fs;
-    const G sg = fs >= 0 ? G(1) : G(-1);
-    const G ox = sg * Gv.fnx[f], oy = sg * Gv.fny[f], oz = sg * Gv.fnz[f];
-    P.pl[lane][0] = -ox; P.pl[lane][1] = -oy; P.pl[lane][2] = -oz;
-    P.pl[lane][3] = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) +
-                      oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
-  }
-  __syncwarp();
   const int nvb = 2 * fr.I + 1;
   const bool hv = lane < nvb;
   const G bx = hv ? P.bx[lane] : G(0), by = hv ? P.by[lane] : G(0), bz = hv ? P.bz[lane] : G(0);
   unsigned cut = 0u;
-  for (int g = 0; g < nfk; ++g) {
+  for (int g = 0; g < np; ++g) {
     const G ph = P.pl[g][0] * bx + P.pl[g][1] * by + P.pl[g][2] * bz + P.pl[g][3];
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
-    if (in == 0u && out != 0u) return G(0);  // P on the outer side of a face plane
+    if (in == 0u && out != 0u) return G(0);  // P on the outer side of a plane
     if (out) cut |= 1u << g;
   }
-  const bool tag0 = tk == 0;
   bool plic = false;
-  if (tag0) {
-    // fluid half-space of the PLIC plane: n.(x - x_k) + C >= 0
-    G pn0 = Gv.pnx[k], pn1 = Gv.pny[k], pn2 = Gv.pnz[k];
-    G pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
-             Gv.pC[k]) * fr.sc;
-    if (empty_side) { pn0 = -pn0; pn1 = -pn1; pn2 = -pn2; pnb = -pnb; }
-    const G ph = pn0 * bx + pn1 * by + pn2 * bz + pnb;
+  if (has_plic) {
+    const G ph = P.pl[NF][0] * bx + P.pl[NF][1] * by + P.pl[NF][2] * bz + P.pl[NF][3];
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
-    if (in == 0u && out != 0u) return G(0);  // P inside the other side
+    if (in == 0u && out != 0u) return G(0);  // P on the other side of the interface
     plic = out != 0u;
-    if (plic && lane == 0) {
-      P.pl[NF][0] = pn0; P.pl[NF][1] = pn1; P.pl[NF][2] = pn2; P.pl[NF][3] = pnb;
-    }
   }
-  if (cut == 0u && !plic) { *whole = true; return Vl; }  // P inside X_k
-  // the planes that cut, the PLIC plane last; all but the last are clipped
-  // topologically, the last one only inside the volume sum
-  __syncwarp();
+  if (cut == 0u && !plic) { *whole = true; return Vl; }  // P inside K ∩ X
   int last;
   if (plic) {
     last = NF;
@@ -619,6 +591,106 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
     return res == 2 ? G(0) : volume(P, st, lane);
   }
   return volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
+}
+
+// vol(P ∩ cell k ∩ X_k) in face-local units, X_k the fluid of cell k
+// (empty_side = false: all of a full cell, the PLIC half-space of an
+// interfacial cell) or its empty part (empty_side = true: all of an empty
+// cell, the complementary half-space of an interfacial cell). A convex cell
+// is the intersection of its face half-spaces; a non-convex cell is the
+// signed sum of the tetrahedra that join its centroid to the fan triangles of
+// its faces (winding-number decomposition, valid for any closed cell).
+template <typename G>
+__device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
+                                           const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
+                                           Poly<G>& P, int lane, unsigned& err, bool empty_side,
+                                           bool* whole) {
+  *whole = false;
+  const int8_t tk = S.tc[k];
+  if (tk == (empty_side ? 1 : -1)) return G(0);
+  const bool tag0 = tk == 0;
+  if (tag0 && lane == 0) {
+    // half-space of the PLIC plane on the wanted side: n.(x - x_k) + C >= 0
+    G pn0 = Gv.pnx[k], pn1 = Gv.pny[k], pn2 = Gv.pnz[k];
+    G pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
+             Gv.pC[k]) * fr.sc;
+    if (empty_side) { pn0 = -pn0; pn1 = -pn1; pn2 = -pn2; pnb = -pnb; }
+    P.pl[NF][0] = pn0; P.pl[NF][1] = pn1; P.pl[NF][2] = pn2; P.pl[NF][3] = pnb;
+  }
+  const int64_t c0 = M.cf_ptr[k];
+  const int nfk = (int)(M.cf_ptr[k + 1] - c0);
+  if (M.convex[k]) {
+    // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
+    // frame a = -n_out, b = -n_out.(c - p_g) / L
+    if (lane < nfk) {
+      const int fs = M.cf[c0 + lane];
+      const int f = fs >= 0 ? fs : ~fs;
+      const G sg = fs >= 0 ? G(1) : G(-1);
+      const G ox = sg * Gv.fnx[f], oy = sg * Gv.fny[f], oz = sg * Gv.fnz[f];
+      P.pl[lane][0] = -ox; P.pl[lane][1] = -oy; P.pl[lane][2] = -oz;
+      P.pl[lane][3] = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) +
+                        oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
+    }
+    __syncwarp();
+    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole);
+  }
+  // non-convex cell: signed tetrahedra (centroid, fan triangle of a face)
+  const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
+          rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
+  G v = G(0);
+  for (int q = 0; q < nfk; ++q) {
+    const int fs = M.cf[c0 + q];
+    const int f = fs >= 0 ? fs : ~fs;
+    const int64_t fb = M.fptr[f];
+    const int L = (int)(M.fptr[f + 1] - fb);
+    for (int t = 1; t + 1 < L; ++t) {
+      // triangle (v0, v_t, v_t+1) of the face, outward from cell k
+      int ia = M.fvert[fb], ib = M.fvert[fb + t], ic = M.fvert[fb + t + 1];
+      if (fs < 0) { const int tmp = ib; ib = ic; ic = tmp; }
+      G T[4][3];
+      T[0][0] = rx; T[0][1] = ry; T[0][2] = rz;
+      const int ids[3] = {ia, ib, ic};
+      for (int e = 0; e < 3; ++e) {
+        T[e + 1][0] = rel(Gv.vx[ids[e]], fr.cx) * fr.sc;
+        T[e + 1][1] = rel(Gv.vy[ids[e]], fr.cy) * fr.sc;
+        T[e + 1][2] = rel(Gv.vz[ids[e]], fr.cz) * fr.sc;
+      }
+      const G ux = T[1][0] - T[0][0], uy = T[1][1] - T[0][1], uz = T[1][2] - T[0][2];
+      const G wx = T[2][0] - T[0][0], wy = T[2][1] - T[0][1], wz = T[2][2] - T[0][2];
+      const G zx = T[3][0] - T[0][0], zy = T[3][1] - T[0][1], zz = T[3][2] - T[0][2];
+      const G det = ux * (wy * zz - wz * zy) + uy * (wz * zx - wx * zz) + uz * (wx * zy - wy * zx);
+      if (det == G(0)) continue;
+      const G sgn = det > G(0) ? G(1) : G(-1);
+      // bounding-box rejection of the tetrahedron
+      G lo0 = T[0][0], hi0 = T[0][0], lo1 = T[0][1], hi1 = T[0][1], lo2 = T[0][2], hi2 = T[0][2];
+      for (int e = 1; e < 4; ++e) {
+        lo0 = min(lo0, T[e][0]); hi0 = max(hi0, T[e][0]);
+        lo1 = min(lo1, T[e][1]); hi1 = max(hi1, T[e][1]);
+        lo2 = min(lo2, T[e][2]); hi2 = max(hi2, T[e][2]);
+      }
+      if (!(fr.hi[0] > lo0 && fr.lo[0] < hi0 && fr.hi[1] > lo1 && fr.lo[1] < hi1 &&
+            fr.hi[2] > lo2 && fr.lo[2] < hi2))
+        continue;
+      // inward planes of the tetrahedron: face opposite vertex a, outward
+      // normal (q1 - q0) x (q2 - q0) for a positive tetrahedron
+      if (lane < 4) {
+        const int o0 = lane == 0 ? 1 : 0;
+        const int o1 = lane == 0 ? 2 : (lane == 1 ? 3 : (lane == 2 ? 1 : 2));
+        const int o2 = lane == 0 ? 3 : (lane == 1 ? 2 : (lane == 2 ? 3 : 1));
+        const G ax = T[o1][0] - T[o0][0], ay = T[o1][1] - T[o0][1], az = T[o1][2] - T[o0][2];
+        const G cx = T[o2][0] - T[o0][0], cy = T[o2][1] - T[o0][1], cz = T[o2][2] - T[o0][2];
+        G nx = (ay * cz - az * cy) * sgn, ny = (az * cx - ax * cz) * sgn, nz = (ax * cy - ay * cx) * sgn;
+        const G nn = G(1) / sqrt(nx * nx + ny * ny + nz * nz);
+        nx *= nn; ny *= nn; nz *= nn;
+        P.pl[lane][0] = -nx; P.pl[lane][1] = -ny; P.pl[lane][2] = -nz;
+        P.pl[lane][3] = nx * T[o0][0] + ny * T[o0][1] + nz * T[o0][2];
+      }
+      __syncwarp();
+      bool w = false;
+      v += sgn * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w);
+    }
+  }
+  return v;
 }
 
 // sum of vol(P ∩ cell k ∩ X_k) over the candidate cells: owner, its node

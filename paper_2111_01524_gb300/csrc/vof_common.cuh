@@ -38,6 +38,7 @@ struct DevMesh {
   const double *ccx, *ccy, *ccz;  // cell centroid
   const double* cvol;
   const double* bb;               // bounding boxes, SoA: bb[d*nc + c], d = 0..5 (lo xyz, hi xyz)
+  const uint8_t* convex;          // 1 if the cell is convex
   // mixed-precision copies (allocated for VOF_PREC_MIXED only): absolute
   // positions as (hi, lo) float pairs, hi = fl(x), lo = fl(x - hi), so that
   // differences of nearby points are formed in FP32 without losing the
@@ -227,6 +228,7 @@ inline DevMesh mesh_view(const vof_ctx* c) {
   m.cf_ptr = c->cf_ptr; m.cf = c->cf; m.cv_ptr = c->cv_ptr; m.cv = c->cv;
   m.vc_ptr = c->vc_ptr; m.vc = c->vc; m.nb_ptr = c->nb_ptr; m.nb = c->nb;
   m.ccx = c->ccx; m.ccy = c->ccy; m.ccz = c->ccz; m.cvol = c->cvol; m.bb = c->bb;
+  m.convex = c->convex;
   m.vx2 = c->vx2; m.vy2 = c->vy2; m.vz2 = c->vz2;
   m.fcx2 = c->fcx2; m.fcy2 = c->fcy2; m.fcz2 = c->fcz2;
   m.fnx32 = c->fnx32; m.fny32 = c->fny32; m.fnz32 = c->fnz32; m.fa32 = c->fa32;

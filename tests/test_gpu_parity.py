@@ -35,6 +35,9 @@ def _case(name):
     elif name == "tet4":
         m = I.kuhn_tet_mesh(4, seed=3)
         body = I.sphere((0.5, 0.55, 0.5), 0.27)
+    elif name == "trihex3":  # distorted cubic cells, triangulated faces, non-convex
+        m = I.trihex_mesh(3, seed=2)
+        body = I.sphere((0.5, 0.48, 0.52), 0.3)
     elif name == "hex32":
         m = I.hex_mesh(32)
         body = I.sphere((0.35, 0.35, 0.35), 0.15)
@@ -44,7 +47,7 @@ def _case(name):
     return m, F0
 
 
-CASES = ["hex12", "hex7", "tet4"]
+CASES = ["hex12", "hex7", "tet4", "trihex3"]
 
 
 @pytest.fixture(scope="module")
@@ -228,9 +231,6 @@ def test_edge_cases(vof):
 
 
 def test_invalid_inputs_are_rejected(vof):
-    with pytest.raises(vof.VofError) as e:
-        vof.Context(I.trihex_mesh(2, seed=1))  # non-convex cells
-    assert e.value.status == vof.VOF_EINVAL
     ctx = vof.Context(I.hex_mesh(3))
     ctx.set_fraction(np.full(27, 0.5))
     with pytest.raises(vof.VofError) as e:
@@ -238,9 +238,15 @@ def test_invalid_inputs_are_rejected(vof):
     assert e.value.status == vof.VOF_ESTATE
     with pytest.raises(vof.VofError):
         ctx.candidates([10 ** 6])
-    bad = I.hex_mesh(2)
-    bad = dict(bad)
+    bad = dict(I.hex_mesh(2))
     bad["owner"] = bad["owner"].copy()
     bad["owner"][0] = 99
+    with pytest.raises(vof.VofError) as e:
+        vof.Context(bad)
+    assert e.value.status == vof.VOF_EINVAL
+    bad = dict(I.hex_mesh(2))
+    bad["neighbour"] = bad["neighbour"].copy()
+    inner = int(np.nonzero(bad["neighbour"] >= 0)[0][0])
+    bad["neighbour"][inner] = bad["owner"][inner]
     with pytest.raises(vof.VofError):
         vof.Context(bad)
