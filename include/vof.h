@@ -109,6 +109,18 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
 void vof_destroy(vof_ctx* ctx);
 const char* vof_last_error(void);
 
+/* Batching: n_grids independent meshes joined into one context. Cells,
+ * faces and nodes of grid g follow those of grid g-1 (offsets from
+ * vof_batch_offsets), so every kernel of a step processes all grids in one
+ * launch; each grid keeps its own velocity field and time step (the
+ * *_batch calls take arrays of n_grids velocities, times and steps). A
+ * context made by vof_init is a batch of one grid. */
+vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                          vof_ctx** out);
+/* offsets [n_grids+1] of each grid's cells, faces, nodes (any may be NULL) */
+vof_status vof_batch_offsets(vof_ctx* ctx, int* n_grids, int64_t* cell_off, int64_t* face_off,
+                             int64_t* vert_off);
+
 /* Volume fraction F [n_cell] (host or device pointer, see `mem`). Setting F
  * invalidates the reconstruction: call vof_reconstruct next. */
 vof_status vof_set_fraction(vof_ctx* ctx, const double* F, int mem, void* stream);
@@ -136,6 +148,32 @@ vof_status vof_step(vof_ctx* ctx, const vof_velocity* vel, double t, double dt, 
  * Host result; the first call for a velocity field runs a device sweep. */
 vof_status vof_suggest_dt(vof_ctx* ctx, const vof_velocity* vel, double t, double cfl,
                           double t_end, double* dt);
+
+/* Batched forms: vels, t, dt, t_end, dt_out are HOST arrays of n_grids. */
+vof_status vof_advect_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
+                            const double* dt, void* stream);
+vof_status vof_step_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
+                          const double* dt, void* stream);
+vof_status vof_suggest_dt_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
+                                double cfl, const double* t_end, double* dt_out);
+
+/* CUDA graph of one step: vof_graph_capture records the launches of one
+ * vof_advect (with_reconstruct = 0) or vof_step (1) on `stream` (not the
+ * legacy default stream) into a graph; vof_graph_launch writes the step's
+ * per-grid parameters into device memory (an asynchronous copy from a pinned
+ * ring) and replays the graph. The kernels read every per-step value from
+ * that device table, so one graph serves all steps. Re-capture after
+ * vof_autotune. */
+vof_status vof_graph_capture(vof_ctx* ctx, int with_reconstruct, void* stream);
+vof_status vof_graph_launch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
+                            const double* dt, void* stream);
+
+/* Launch-shape autotuner: times the flux and reconstruction kernels on the
+ * current state for 2..16 blocks per SM and keeps the fastest grid sizes
+ * (returned when the pointers are not NULL). F and the reconstruction are
+ * left unchanged; the face volumes are those of a step (t, dt). */
+vof_status vof_autotune(vof_ctx* ctx, const vof_velocity* vels, const double* t, const double* dt,
+                        void* stream, int* flux_blocks, int* recon_blocks);
 
 /* planes [4*n_cell]: nx, ny, nz, C per cell (zeros for non-interfacial). */
 vof_status vof_get_planes(vof_ctx* ctx, double* planes, int mem, void* stream);

@@ -1,6 +1,7 @@
 // C-ABI entry points of the gvof library (declared in include/vof.h).
 #include <stdio.h>
 
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -13,6 +14,7 @@ using namespace gvof;
 namespace {
 
 thread_local std::string g_err;
+constexpr int kRing = 16;  // pinned slots for per-step grid parameters
 
 vof_status fail(vof_status s, const std::string& msg) {
   g_err = msg;
@@ -45,7 +47,17 @@ void free_all(vof_ctx* c) {
                   c->fnz32, c->fa32, c->cvol32, c->nx32, c->ny32, c->nz32, c->C32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  void* ptrs2[] = {c->face_off_d, c->gp_d, c->umax_d};
+  for (void* p : ptrs2)
+    if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->gp_ring) cudaFreeHost(c->gp_ring);
+  for (int i = 0; i < kRing; ++i)
+    if (c->ring_ev[i]) cudaEventDestroy(c->ring_ev[i]);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  delete c->cell_off; delete c->face_off; delete c->vert_off;
+  delete c->hmin_g; delete c->umax_g; delete c->vel_g;
 }
 
 cudaMemcpyKind kind_to_dev(int mem) {
@@ -72,25 +84,63 @@ bool same_vel(const Vel& a, const Vel& b) {
          a.cy == b.cy && a.cz == b.cz && a.ux == b.ux && a.uy == b.uy && a.uz == b.uz;
 }
 
-vof_status ensure_velocity(vof_ctx* c, const vof_velocity* vel, cudaStream_t s) {
-  if (!vel) return fail(VOF_EINVAL, "velocity is NULL");
-  if (vel->kind < VOF_VEL_DEFORMATION || vel->kind > VOF_VEL_TRANSLATION)
+vof_status check_velocity(const vof_velocity& v) {
+  if (v.kind < VOF_VEL_DEFORMATION || v.kind > VOF_VEL_TRANSLATION)
     return fail(VOF_EINVAL, "unknown velocity kind");
-  if (vel->kind == VOF_VEL_DEFORMATION && !(vel->period > 0))
+  if (v.kind == VOF_VEL_DEFORMATION && !(v.period > 0))
     return fail(VOF_EINVAL, "deformation period must be > 0");
-  Vel v = to_vel(*vel);
-  if (c->vel_valid && same_vel(v, c->vel_cached)) return VOF_OK;
-  CK(launch_velocity_setup(c, v, s));
-  unsigned long long* h = (unsigned long long*)c->pinned;
-  CK(cudaMemcpyAsync(h, c->cnt + kUmax, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  return VOF_OK;
+}
+
+// write the per-grid parameters of one step into the device table (through a
+// pinned ring slot, so the host may prepare the next step while this copy is
+// in flight)
+vof_status upload_params(vof_ctx* c, const double* t, const double* dt, cudaStream_t s) {
+  const int n = c->n_grids;
+  const int slot = c->ring_pos;
+  c->ring_pos = (c->ring_pos + 1) % kRing;
+  CK(cudaEventSynchronize(c->ring_ev[slot]));  // previous use of this slot done
+  GridParam* h = c->gp_ring + (size_t)slot * n;
+  for (int g = 0; g < n; ++g) {
+    const Vel& v = (*c->vel_g)[g];
+    const double tt = t ? t[g] : 0.0, d = dt ? dt[g] : 0.0;
+    h[g].vel = v;
+    h[g].g = time_factor(v, tt + 0.5 * d);
+    h[g].dt = d;
+    h[g].gdt = h[g].g * d;
+    h[g].pad = 0.0;
+  }
+  CK(cudaMemcpyAsync(c->gp_d, h, sizeof(GridParam) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(c->ring_ev[slot], s));
+  return VOF_OK;
+}
+
+// per-face flux rates and per-grid speed maxima of the velocity fields
+// (recomputed only when a field changes)
+vof_status ensure_velocity(vof_ctx* c, const vof_velocity* vels, cudaStream_t s) {
+  if (!vels) return fail(VOF_EINVAL, "velocity is NULL");
+  const int n = c->n_grids;
+  bool same = c->vel_valid;
+  for (int g = 0; g < n; ++g) {
+    vof_status st = check_velocity(vels[g]);
+    if (st != VOF_OK) return st;
+    if (same && !same_vel(to_vel(vels[g]), (*c->vel_g)[g])) same = false;
+  }
+  if (same) return VOF_OK;
+  for (int g = 0; g < n; ++g) (*c->vel_g)[g] = to_vel(vels[g]);
+  vof_status st = upload_params(c, nullptr, nullptr, s);
+  if (st != VOF_OK) return st;
+  CK(launch_velocity_setup(c, s));
+  std::vector<unsigned long long> h(3 * n);
+  CK(cudaMemcpyAsync(h.data(), c->umax_d, sizeof(unsigned long long) * 3 * n,
+                     cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  for (int d = 0; d < 3; ++d) {
-    long long bits = (long long)h[d];
+  for (int i = 0; i < 3 * n; ++i) {
+    long long bits = (long long)h[i];
     double x;
     std::memcpy(&x, &bits, sizeof x);
-    c->umax0[d] = x;
+    (*c->umax_g)[i] = x;
   }
-  c->vel_cached = v;
   c->vel_valid = true;
   return VOF_OK;
 }
@@ -137,13 +187,17 @@ void set_last_error(const char* msg) { g_err = msg; }
 
 extern "C" {
 
+static vof_status advect_launches(vof_ctx* c, cudaStream_t s);
+static vof_status reconstruct_launches(vof_ctx* c, cudaStream_t s);
+
 const char* vof_last_error(void) { return g_err.c_str(); }
 
 int64_t vof_device_bytes(const vof_ctx* c) { return c ? c->bytes : 0; }
 
-vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out) {
-  if (!mesh || !out) return fail(VOF_EINVAL, "mesh or out is NULL");
-  *out = nullptr;
+static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out,
+                            const std::vector<int64_t>& cell_off,
+                            const std::vector<int64_t>& face_off,
+                            const std::vector<int64_t>& vert_off) {
   const int64_t nv = mesh->n_vert, nf = mesh->n_face, nc = mesh->n_cell;
   if (nv <= 0 || nf <= 0 || nc <= 0) return fail(VOF_EINVAL, "empty mesh");
   if (nv >= (1LL << 31) || nf >= (1LL << 31) || nc >= (1LL << 31))
@@ -195,6 +249,14 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
   c->max_cell_faces = hc.max_cell_faces;
   c->max_cell_verts = hc.max_cell_verts;
   cudaGetDevice(&c->device);
+  const int ng = (int)cell_off.size() - 1;
+  c->n_grids = ng;
+  c->cell_off = new std::vector<int64_t>(cell_off);
+  c->face_off = new std::vector<int64_t>(face_off);
+  c->vert_off = new std::vector<int64_t>(vert_off);
+  c->hmin_g = new std::vector<double>(3 * ng, 0.0);
+  c->umax_g = new std::vector<double>(3 * ng, 0.0);
+  c->vel_g = new std::vector<Vel>(ng);
   auto cleanup = [&](vof_status s, const std::string& m) {
     free_all(c);
     delete c;
@@ -238,6 +300,13 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
     CKI(dalloc(c, &c->C32, nc));
   }
   CKI(cudaMallocHost(&c->pinned, 4096));
+  CKI(dalloc(c, &c->face_off_d, ng + 1));
+  CKI(dalloc(c, &c->gp_d, ng));
+  CKI(dalloc(c, &c->umax_d, 3 * ng));
+  CKI(cudaMallocHost(&c->gp_ring, sizeof(GridParam) * kRing * ng));
+  for (int i = 0; i < kRing; ++i) CKI(cudaEventCreateWithFlags(&c->ring_ev[i], cudaEventDisableTiming));
+  CKI(cudaMemcpy(c->face_off_d, face_off.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice));
+  CKI(cudaMemset(c->gp_d, 0, sizeof(GridParam) * ng));
 
   // SoA vertex coordinates
   {
@@ -277,14 +346,74 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx**
   {
     std::vector<double> bb(6 * nc);
     CKI(cudaMemcpy(bb.data(), c->bb, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost));
-    for (int d = 0; d < 3; ++d) {
-      double h = 1e300;
-      for (int64_t k = 0; k < nc; ++k) h = std::min(h, bb[(3 + d) * nc + k] - bb[d * nc + k]);
-      c->hmin[d] = h;
-    }
+    for (int g = 0; g < ng; ++g)
+      for (int d = 0; d < 3; ++d) {
+        double h = 1e300;
+        for (int64_t k = cell_off[g]; k < cell_off[g + 1]; ++k)
+          h = std::min(h, bb[(3 + d) * nc + k] - bb[d * nc + k]);
+        (*c->hmin_g)[3 * g + d] = h;
+      }
   }
 #undef CKI
   *out = c;
+  return VOF_OK;
+}
+
+vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out) {
+  if (!mesh || !out) return fail(VOF_EINVAL, "mesh or out is NULL");
+  *out = nullptr;
+  std::vector<int64_t> co = {0, mesh->n_cell}, fo = {0, mesh->n_face}, vo = {0, mesh->n_vert};
+  return init_impl(mesh, opt, out, co, fo, vo);
+}
+
+vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                          vof_ctx** out) {
+  if (!meshes || !out || n_grids < 1) return fail(VOF_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  if (n_grids == 1) return vof_init(meshes, opt, out);
+  std::vector<int64_t> co(n_grids + 1, 0), fo(n_grids + 1, 0), vo(n_grids + 1, 0), po(n_grids + 1, 0);
+  for (int g = 0; g < n_grids; ++g) {
+    const vof_mesh_desc& m = meshes[g];
+    if (m.n_vert <= 0 || m.n_face <= 0 || m.n_cell <= 0 || !m.X || !m.face_ptr || !m.face_vert ||
+        !m.owner || !m.neighbour)
+      return fail(VOF_EINVAL, "grid " + std::to_string(g) + ": empty or NULL mesh");
+    co[g + 1] = co[g] + m.n_cell;
+    fo[g + 1] = fo[g] + m.n_face;
+    vo[g + 1] = vo[g] + m.n_vert;
+    po[g + 1] = po[g] + m.face_ptr[m.n_face];
+  }
+  // join the grids: ids of grid g are shifted by the sizes of grids < g
+  std::vector<double> X(3 * vo[n_grids]);
+  std::vector<int64_t> fp(fo[n_grids] + 1);
+  std::vector<int32_t> fv(po[n_grids]), own(fo[n_grids]), nbr(fo[n_grids]);
+  for (int g = 0; g < n_grids; ++g) {
+    const vof_mesh_desc& m = meshes[g];
+    std::memcpy(X.data() + 3 * vo[g], m.X, sizeof(double) * 3 * m.n_vert);
+    for (int64_t f = 0; f < m.n_face; ++f) {
+      fp[fo[g] + f] = po[g] + m.face_ptr[f];
+      own[fo[g] + f] = (int32_t)(m.owner[f] + co[g]);
+      nbr[fo[g] + f] = m.neighbour[f] >= 0 ? (int32_t)(m.neighbour[f] + co[g]) : -1;
+    }
+    for (int64_t k = 0; k < m.face_ptr[m.n_face]; ++k)
+      fv[po[g] + k] = (int32_t)(m.face_vert[k] + vo[g]);
+  }
+  fp[fo[n_grids]] = po[n_grids];
+  vof_mesh_desc j;
+  j.n_vert = vo[n_grids]; j.n_face = fo[n_grids]; j.n_cell = co[n_grids];
+  j.X = X.data(); j.face_ptr = fp.data(); j.face_vert = fv.data(); j.owner = own.data();
+  j.neighbour = nbr.data();
+  return init_impl(&j, opt, out, co, fo, vo);
+}
+
+vof_status vof_batch_offsets(vof_ctx* c, int* n_grids, int64_t* cell_off, int64_t* face_off,
+                             int64_t* vert_off) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (n_grids) *n_grids = c->n_grids;
+  for (int g = 0; g <= c->n_grids; ++g) {
+    if (cell_off) cell_off[g] = (*c->cell_off)[g];
+    if (face_off) face_off[g] = (*c->face_off)[g];
+    if (vert_off) vert_off[g] = (*c->vert_off)[g];
+  }
   return VOF_OK;
 }
 
@@ -343,26 +472,61 @@ vof_status vof_get_fraction(vof_ctx* c, double* F, int mem, void* stream) {
 vof_status vof_reconstruct(vof_ctx* c, void* stream) {
   if (!c) return fail(VOF_EINVAL, "NULL context");
   cudaStream_t s = (cudaStream_t)stream;
-  { PhaseTimer t(c, VOF_PHASE_CELL_TAGS, s); CK(launch_cell_tags(c, s)); }
-  { PhaseTimer t(c, VOF_PHASE_NODE_TAGS, s); CK(launch_node_tags(c, s)); }
-  { PhaseTimer t(c, VOF_PHASE_RECONSTRUCT, s); CK(launch_reconstruct(c, s)); }
+  vof_status st = reconstruct_launches(c, s);
+  if (st != VOF_OK) return st;
   c->recon_valid = true;
   return VOF_OK;
 }
 
-vof_status vof_advect(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
+static vof_status advect_launches(vof_ctx* c, cudaStream_t s) {
+  { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s); CK(launch_face_sweep(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_UPDATE, s); CK(launch_update(c, s)); }
+  return VOF_OK;
+}
+
+static vof_status reconstruct_launches(vof_ctx* c, cudaStream_t s) {
+  { PhaseTimer t(c, VOF_PHASE_CELL_TAGS, s); CK(launch_cell_tags(c, s)); }
+  { PhaseTimer t(c, VOF_PHASE_NODE_TAGS, s); CK(launch_node_tags(c, s)); }
+  { PhaseTimer t(c, VOF_PHASE_RECONSTRUCT, s); CK(launch_reconstruct(c, s)); }
+  return VOF_OK;
+}
+
+static vof_status check_steps(const vof_ctx* c, const double* t, const double* dt) {
+  if (!t || !dt) return fail(VOF_EINVAL, "t or dt is NULL");
+  for (int g = 0; g < c->n_grids; ++g)
+    if (!(dt[g] >= 0) || !std::isfinite(t[g])) return fail(VOF_EINVAL, "dt must be >= 0 and t finite");
+  return VOF_OK;
+}
+
+vof_status vof_advect_batch(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
+                            void* stream) {
   if (!c) return fail(VOF_EINVAL, "NULL context");
   if (!c->recon_valid) return fail(VOF_ESTATE, "advect needs a reconstruction of the current F");
-  if (!(dt >= 0)) return fail(VOF_EINVAL, "dt must be >= 0");
-  cudaStream_t s = (cudaStream_t)stream;
-  vof_status st = ensure_velocity(c, vel, s);
+  vof_status st = check_steps(c, t, dt);
   if (st != VOF_OK) return st;
-  const double g = time_factor(c->vel_cached, t + 0.5 * dt);
-  { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s); CK(launch_face_sweep(c, g, dt, s)); }
-  { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, c->vel_cached, g, dt, s)); }
-  { PhaseTimer tm(c, VOF_PHASE_UPDATE, s); CK(launch_update(c, s)); }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_velocity(c, vels, s);
+  if (st != VOF_OK) return st;
+  st = upload_params(c, t, dt, s);
+  if (st != VOF_OK) return st;
+  st = advect_launches(c, s);
+  if (st != VOF_OK) return st;
   c->recon_valid = false;
   return VOF_OK;
+}
+
+vof_status vof_step_batch(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
+                          void* stream) {
+  vof_status st = vof_advect_batch(c, vels, t, dt, stream);
+  if (st != VOF_OK) return st;
+  return vof_reconstruct(c, stream);
+}
+
+vof_status vof_advect(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (c->n_grids != 1) return fail(VOF_EINVAL, "batch context: use vof_advect_batch");
+  return vof_advect_batch(c, vel, &t, &dt, stream);
 }
 
 vof_status vof_step(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
@@ -371,24 +535,118 @@ vof_status vof_step(vof_ctx* c, const vof_velocity* vel, double t, double dt, vo
   return vof_reconstruct(c, stream);
 }
 
+vof_status vof_suggest_dt_batch(vof_ctx* c, const vof_velocity* vels, const double* t, double cfl,
+                                const double* t_end, double* dt_out) {
+  if (!c || !t || !t_end || !dt_out) return fail(VOF_EINVAL, "NULL argument");
+  if (!(cfl > 0)) return fail(VOF_EINVAL, "cfl must be > 0");
+  vof_status st = ensure_velocity(c, vels, 0);
+  if (st != VOF_OK) return st;
+  for (int gi = 0; gi < c->n_grids; ++gi) {
+    const Vel& v = (*c->vel_g)[gi];
+    const double* hmin = c->hmin_g->data() + 3 * gi;
+    const double* u0 = c->umax_g->data() + 3 * gi;
+    double um[3];
+    const double g0 = std::fabs(time_factor(v, t[gi]));
+    for (int d = 0; d < 3; ++d) um[d] = g0 * u0[d];
+    double d1 = dt_from(hmin, um, cfl);
+    if (t[gi] + d1 > t_end[gi]) d1 = t_end[gi] - t[gi];
+    const double g1 = std::fabs(time_factor(v, t[gi] + d1));
+    for (int d = 0; d < 3; ++d) um[d] = std::max(um[d], g1 * u0[d]);
+    const double d2 = dt_from(hmin, um, cfl);
+    double r = std::min(d1, d2);
+    if (t[gi] + r > t_end[gi]) r = t_end[gi] - t[gi];
+    dt_out[gi] = r;
+  }
+  return VOF_OK;
+}
+
 vof_status vof_suggest_dt(vof_ctx* c, const vof_velocity* vel, double t, double cfl,
                           double t_end, double* dt) {
   if (!c || !dt) return fail(VOF_EINVAL, "NULL argument");
-  if (!(cfl > 0)) return fail(VOF_EINVAL, "cfl must be > 0");
-  vof_status st = ensure_velocity(c, vel, 0);
+  if (c->n_grids != 1) return fail(VOF_EINVAL, "batch context: use vof_suggest_dt_batch");
+  return vof_suggest_dt_batch(c, vel, &t, cfl, &t_end, dt);
+}
+
+vof_status vof_graph_capture(vof_ctx* c, int with_reconstruct, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (c->timing) return fail(VOF_ESTATE, "switch timing off before capturing a graph");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (s == 0) return fail(VOF_EINVAL, "graph capture needs a non-default stream");
+  if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  vof_status st = advect_launches(c, s);
+  if (st == VOF_OK && with_reconstruct) st = reconstruct_launches(c, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != VOF_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return fail(VOF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  c->graph = g;
+  CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+  c->graph_step = with_reconstruct ? 1 : 0;
+  return VOF_OK;
+}
+
+vof_status vof_graph_launch(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
+                            void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (!c->graph_exec) return fail(VOF_ESTATE, "no captured graph (vof_graph_capture)");
+  if (!c->recon_valid) return fail(VOF_ESTATE, "advect needs a reconstruction of the current F");
+  vof_status st = check_steps(c, t, dt);
   if (st != VOF_OK) return st;
-  const Vel& v = c->vel_cached;
-  double um[3];
-  double g0 = std::fabs(time_factor(v, t));
-  for (int d = 0; d < 3; ++d) um[d] = g0 * c->umax0[d];
-  double d1 = dt_from(c->hmin, um, cfl);
-  if (t + d1 > t_end) d1 = t_end - t;
-  double g1 = std::fabs(time_factor(v, t + d1));
-  for (int d = 0; d < 3; ++d) um[d] = std::max(um[d], g1 * c->umax0[d]);
-  double d2 = dt_from(c->hmin, um, cfl);
-  double r = std::min(d1, d2);
-  if (t + r > t_end) r = t_end - t;
-  *dt = r;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_velocity(c, vels, s);
+  if (st != VOF_OK) return st;
+  st = upload_params(c, t, dt, s);
+  if (st != VOF_OK) return st;
+  CK(cudaGraphLaunch(c->graph_exec, s));
+  c->recon_valid = c->graph_step == 1;
+  return VOF_OK;
+}
+
+vof_status vof_autotune(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
+                        void* stream, int* flux_blocks, int* recon_blocks) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  if (!c->recon_valid) return fail(VOF_ESTATE, "autotune needs a reconstruction of the current F");
+  vof_status st = check_steps(c, t, dt);
+  if (st != VOF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_velocity(c, vels, s);
+  if (st != VOF_OK) return st;
+  st = upload_params(c, t, dt, s);
+  if (st != VOF_OK) return st;
+  const bool timing = c->timing;
+  c->timing = false;
+  CK(launch_face_sweep(c, s));  // active faces of the current state (F is not changed)
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cand[] = {kSMs * 2, kSMs * 4, kSMs * 6, kSMs * 8, kSMs * 12, kSMs * 16};
+  float best_f = 1e30f, best_r = 1e30f;
+  int bf = kSMs * 8, br = kSMs * 8;
+  for (int which = 0; which < 2; ++which)
+    for (int g : cand) {
+      float tot = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        if (which == 0) c->flux_blocks = g; else c->recon_blocks = g;
+        CK(cudaEventRecord(e0, s));
+        CK(which == 0 ? launch_flux(c, s) : launch_reconstruct(c, s));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;  // first launch warms caches
+      }
+      if (which == 0 && tot < best_f) { best_f = tot; bf = g; }
+      if (which == 1 && tot < best_r) { best_r = tot; br = g; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->flux_blocks = bf;
+  c->recon_blocks = br;
+  c->timing = timing;
+  if (flux_blocks) *flux_blocks = bf;
+  if (recon_blocks) *recon_blocks = br;
   return VOF_OK;
 }
 
@@ -493,7 +751,12 @@ vof_status vof_get_flux_polyhedra(vof_ctx* c, const vof_velocity* vel, double t,
   if (!c || !faces || !verts || !counts || n < 0) return fail(VOF_EINVAL, "bad argument");
   for (int i = 0; i < n; ++i)
     if (faces[i] < 0 || faces[i] >= c->nf) return fail(VOF_EINVAL, "face index out of range");
-  vof_status st = ensure_velocity(c, vel, 0);
+  if (!vel) return fail(VOF_EINVAL, "velocity is NULL");
+  std::vector<vof_velocity> vv(c->n_grids, *vel);
+  std::vector<double> tt(c->n_grids, t), dd(c->n_grids, dt);
+  vof_status st = ensure_velocity(c, vv.data(), 0);
+  if (st != VOF_OK) return st;
+  st = upload_params(c, tt.data(), dd.data(), 0);
   if (st != VOF_OK) return st;
   if (n == 0) return VOF_OK;
   const int NBV = 2 * kMaxFaceVerts + 1;
@@ -504,8 +767,7 @@ vof_status vof_get_flux_polyhedra(vof_ctx* c, const vof_velocity* vel, double t,
   CK(cudaMalloc(&dv, sizeof(double) * n * NBV * 3));
   CK(cudaMemset(dv, 0, sizeof(double) * n * NBV * 3));
   CK(cudaMemcpy(df, faces, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-  const double g = time_factor(c->vel_cached, t + 0.5 * dt);
-  CK(launch_polyhedra(c, c->vel_cached, g, dt, df, n, dv, dcnt, 0));
+  CK(launch_polyhedra(c, df, n, dv, dcnt, 0));
   CK(cudaMemcpy(verts, dv, sizeof(double) * n * NBV * 3, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(counts, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
   cudaFree(df); cudaFree(dcnt); cudaFree(dv);

@@ -744,8 +744,7 @@ __device__ G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevS
 }
 
 template <typename G>
-__global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S,
-                                                      FluxParams p) {
+__global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S) {
   __shared__ Poly<G> polys[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Poly<G>& P = polys[wib];
@@ -754,6 +753,8 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
   unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0;
   for (unsigned w = blockIdx.x * kWarps + wib; w < n_af; w += gridDim.x * kWarps) {
     const int j = S.afaces[w];
+    const GridParam& gq = S.gp[M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j)];
+    const FluxParams p{gq.vel, gq.g, gq.dt};
     FaceFrame<G> fr;
     if (!build_fmfpa<G>(M, Gv, p, j, S.Vd[j], P, fr, lane)) {
       if (lane == 0) S.VF[j] = 0.0;
@@ -845,13 +846,15 @@ __global__ void k_candidates(DevMesh M, const int32_t* faces, int n, int64_t cap
 }
 
 template <typename G>
-__global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, FluxParams p, const double* srate,
+__global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const double* srate,
                             const int32_t* faces, int n, double* verts, int32_t* counts) {
   __shared__ Poly<G> polys[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Poly<G>& P = polys[wib];
   for (int w = blockIdx.x * kWarps + wib; w < n; w += gridDim.x * kWarps) {
     const int j = faces[w];
+    const GridParam& gq = gp[grid_of(M.face_off, M.n_grids, j)];
+    const FluxParams p{gq.vel, gq.g, gq.dt};
     FaceFrame<G> fr;
     const double Vd = srate[j] * p.g * p.dt;
     const bool ok = build_fmfpa<G>(M, Gv, p, j, Vd, P, fr, lane);
@@ -868,13 +871,12 @@ __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, FluxParams p, const double
 
 }  // namespace
 
-cudaError_t launch_flux(const vof_ctx* c, const Vel& v, double g_half, double dt, cudaStream_t s) {
-  FluxParams p{v, g_half, dt};
-  const int grid = kSMs * 8;
+cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s) {
+  const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * 8;
   if (c->opt.precision == VOF_PREC_MIXED)
-    k_flux<float><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c), p);
+    k_flux<float><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c));
   else
-    k_flux<double><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c), p);
+    k_flux<double><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c));
   return cudaGetLastError();
 }
 
@@ -884,15 +886,13 @@ cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_polyhedra(const vof_ctx* c, const Vel& v, double g_half, double dt,
-                             const int32_t* faces, int n, double* verts, int32_t* counts,
-                             cudaStream_t s) {
-  FluxParams p{v, g_half, dt};
+cudaError_t launch_polyhedra(const vof_ctx* c, const int32_t* faces, int n, double* verts,
+                             int32_t* counts, cudaStream_t s) {
   if (c->opt.precision == VOF_PREC_MIXED)
-    k_polyhedra<float><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), p, c->srate,
-                                                     faces, n, verts, counts);
+    k_polyhedra<float><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), c->gp_d,
+                                                     c->srate, faces, n, verts, counts);
   else
-    k_polyhedra<double><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), p,
+    k_polyhedra<double><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), c->gp_d,
                                                       c->srate, faces, n, verts, counts);
   return cudaGetLastError();
 }

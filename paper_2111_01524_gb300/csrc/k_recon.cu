@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_reconstruct(DevMesh M, GeoView<
 }  // namespace
 
 cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s) {
-  const int grid = kSMs * 8;
+  const int grid = c->recon_blocks > 0 ? c->recon_blocks : kSMs * 8;
   if (c->opt.precision == VOF_PREC_MIXED)
     k_reconstruct<float, true><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c),
                                                             state_view(c), c->opt.beta);

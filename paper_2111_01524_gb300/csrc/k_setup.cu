@@ -132,26 +132,35 @@ __global__ void k_cell_geometry(DevMesh M, double* ccx, double* ccy, double* ccz
 }
 
 // flux rate (u0(x_f).n_f) A_f of every face and max |u0| per axis over the
-// face centres (for Eq. eq:cfl)
-__global__ void k_velocity_setup(DevMesh M, Vel v, double* srate, unsigned long long* umax) {
-  double m0 = 0, m1 = 0, m2 = 0;
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M.nf;
-       f += (int64_t)gridDim.x * blockDim.x) {
-    double u, w, s;
-    vel0<double>(v, M.fcx[f], M.fcy[f], M.fcz[f], u, w, s);
-    srate[f] = (u * M.fnx[f] + w * M.fny[f] + s * M.fnz[f]) * M.fa[f];
-    m0 = fmax(m0, fabs(u)); m1 = fmax(m1, fabs(w)); m2 = fmax(m2, fabs(s));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    m0 = fmax(m0, __shfl_xor_sync(GVOF_FULL, m0, o));
-    m1 = fmax(m1, __shfl_xor_sync(GVOF_FULL, m1, o));
-    m2 = fmax(m2, __shfl_xor_sync(GVOF_FULL, m2, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    // non-negative doubles order like their bit patterns
-    atomicMax(umax + 0, (unsigned long long)__double_as_longlong(m0));
-    atomicMax(umax + 1, (unsigned long long)__double_as_longlong(m1));
-    atomicMax(umax + 2, (unsigned long long)__double_as_longlong(m2));
+// face centres of each grid (for Eq. eq:cfl); the velocity of a face is the
+// one of its grid
+__global__ void k_velocity_setup(DevMesh M, const GridParam* gp, double* srate,
+                                 unsigned long long* umax) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < M.nf; base += stride) {
+    const int64_t f = base + threadIdx.x;
+    const bool in = f < M.nf;
+    const int g = grid_of(M.face_off, M.n_grids, in ? f : M.nf - 1);
+    double m[3] = {0.0, 0.0, 0.0};
+    if (in) {
+      double u, w, s;
+      vel0<double>(gp[g].vel, M.fcx[f], M.fcy[f], M.fcz[f], u, w, s);
+      srate[f] = (u * M.fnx[f] + w * M.fny[f] + s * M.fnz[f]) * M.fa[f];
+      m[0] = fabs(u); m[1] = fabs(w); m[2] = fabs(s);
+    }
+    // non-negative doubles order like their bit patterns; one atomic per
+    // warp when the warp lies in one grid
+    const int g0 = __shfl_sync(GVOF_FULL, g, 0);
+    if (__all_sync(GVOF_FULL, g == g0)) {
+      for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) m[d] = fmax(m[d], __shfl_xor_sync(GVOF_FULL, m[d], o));
+      if ((threadIdx.x & 31) == 0)
+        for (int d = 0; d < 3; ++d)
+          atomicMax(umax + 3 * g + d, (unsigned long long)__double_as_longlong(m[d]));
+    } else if (in) {
+      for (int d = 0; d < 3; ++d)
+        atomicMax(umax + 3 * g + d, (unsigned long long)__double_as_longlong(m[d]));
+    }
   }
 }
 
@@ -213,11 +222,10 @@ cudaError_t launch_mixed_copies(const vof_ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_velocity_setup(const vof_ctx* c, const Vel& v, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(c->cnt + kUmax, 0, 3 * sizeof(unsigned long long), s);
+cudaError_t launch_velocity_setup(const vof_ctx* c, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->umax_d, 0, 3 * sizeof(unsigned long long) * c->n_grids, s);
   if (e != cudaSuccess) return e;
-  k_velocity_setup<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), v, c->srate,
-                                                        c->cnt + kUmax);
+  k_velocity_setup<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->gp_d, c->srate, c->umax_d);
   return cudaGetLastError();
 }
 

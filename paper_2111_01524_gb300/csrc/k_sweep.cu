@@ -95,9 +95,10 @@ __global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv) 
 // face sweep: face tags from node tags, V_d = g(t+dt/2) (u0.n) A dt,
 // V_F = 0 on tag -1 faces, V_F = V_d on tag 1 faces (no geometry, Sec. 3.3);
 // tag 0 faces are appended to the active list for the flux kernel
-__global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate, double gdt,
-                             int8_t* tf, double* Vd, double* VF, int32_t* afaces,
-                             unsigned long long* cnt) {
+__global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate,
+                             const GridParam* gp, int8_t* tf, double* Vd, double* VF,
+                             int32_t* afaces, unsigned long long* cnt) {
+  const double gdt1 = gp[0].gdt;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < M.nf; base += stride) {
     int64_t f = base + threadIdx.x;
@@ -112,6 +113,7 @@ __global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate, d
         allp &= (x == 1);
       }
       t = allm ? -1 : (allp ? 1 : 0);
+      const double gdt = M.n_grids == 1 ? gdt1 : gp[grid_of(M.face_off, M.n_grids, f)].gdt;
       double vd = srate[f] * gdt;
       tf[f] = t;
       Vd[f] = vd;
@@ -216,12 +218,12 @@ cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_face_sweep(const vof_ctx* c, double g_half, double dt, cudaStream_t s) {
+cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s) {
   // counters of this advect: active faces, truncations, overflow, fallbacks
   static_assert(kNAfaces + 1 == kNTrunc && kNTrunc + 3 == kNEdgeOn, "counter layout");
   cudaError_t e = cudaMemsetAsync(c->cnt + kNAfaces, 0, 5 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->srate, g_half * dt,
+  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->srate, c->gp_d,
                                                     c->tf, c->Vd, c->VF, c->afaces, c->cnt);
   return cudaGetLastError();
 }

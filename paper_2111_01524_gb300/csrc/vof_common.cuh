@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <vector>
 
 #include "../../include/vof.h"
 
@@ -14,6 +15,31 @@ namespace gvof {
 
 constexpr int kSMs = 152;  // GB300
 constexpr int kMaxFaceVerts = 8;
+
+struct Vel {
+  int kind;
+  double period, omega, cx, cy, cz, ux, uy, uz;
+};
+
+// per-grid parameters of one step, in device memory so that the launches of
+// a step take no per-step argument (and can be replayed as a CUDA graph)
+struct GridParam {
+  Vel vel;
+  double g;    // time factor of the field at t + dt/2
+  double dt;
+  double gdt;  // g * dt
+  double pad;
+};
+
+// grid of face f: faces of grid i are [face_off[i], face_off[i+1])
+__device__ __forceinline__ int grid_of(const int64_t* face_off, int n_grids, int64_t f) {
+  int lo = 0, hi = n_grids;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (face_off[mid] <= f) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 // device view of the mesh: every array is SoA so that per-face and
 // per-cell sweeps load coalesced
@@ -39,6 +65,8 @@ struct DevMesh {
   const double* cvol;
   const double* bb;               // bounding boxes, SoA: bb[d*nc + c], d = 0..5 (lo xyz, hi xyz)
   const uint8_t* convex;          // 1 if the cell is convex
+  const int64_t* face_off;        // [n_grids + 1] first face of each grid
+  int n_grids;
   // mixed-precision copies (allocated for VOF_PREC_MIXED only): absolute
   // positions as (hi, lo) float pairs, hi = fl(x), lo = fl(x - hi), so that
   // differences of nearby points are formed in FP32 without losing the
@@ -62,6 +90,7 @@ struct DevState {
   unsigned long long* cnt;   // counters, see Cnt
   double* red;               // reduction scratch [kRedSlots]
   float *nx32, *ny32, *nz32, *C32;  // FP32 copies of the planes (mixed only)
+  const GridParam* gp;              // [n_grids] parameters of the current step
 };
 
 enum Cnt {
@@ -75,11 +104,6 @@ enum Cnt {
   kNCnt = 16
 };
 constexpr int kRedSlots = 2 * 1024;
-
-struct Vel {
-  int kind;
-  double period, omega, cx, cy, cz, ux, uy, uz;
-};
 
 // velocity of the test problems without its time factor: u(x, t) = g(t) u0(x)
 template <typename T>
@@ -197,9 +221,6 @@ struct vof_ctx {
   unsigned long long* cnt;
   double* red;
   // host-side caches
-  double hmin[3];
-  double umax0[3];
-  gvof::Vel vel_cached;
   bool vel_valid;
   bool recon_valid;
   int max_face_verts;
@@ -207,6 +228,24 @@ struct vof_ctx {
   int max_cell_verts;
   int64_t bytes;
   void* pinned;  // small pinned host buffer for counters / sums
+  // batching: grids joined into this context
+  int n_grids;
+  int64_t* face_off_d;                      // device copy of face offsets
+  std::vector<int64_t>* cell_off, *face_off, *vert_off;  // host offsets [n_grids + 1]
+  std::vector<double>* hmin_g;              // [3 * n_grids]
+  std::vector<double>* umax_g;              // [3 * n_grids]
+  std::vector<gvof::Vel>* vel_g;            // cached velocity per grid
+  gvof::GridParam* gp_d;                    // [n_grids] device table
+  gvof::GridParam* gp_ring;                 // pinned ring [kRing * n_grids]
+  cudaEvent_t ring_ev[16];  // one per ring slot
+  int ring_pos;
+  unsigned long long* umax_d;               // [3 * n_grids]
+  // CUDA graph of one step (optional)
+  cudaGraph_t graph;
+  cudaGraphExec_t graph_exec;
+  int graph_step;                           // 1: advect + reconstruct, 0: advect only
+  // launch shapes (autotuned)
+  int flux_blocks, recon_blocks;
   // optional per-phase timing (events recorded around each launch)
   bool timing;
   int n_ev_pairs;
@@ -229,6 +268,8 @@ inline DevMesh mesh_view(const vof_ctx* c) {
   m.vc_ptr = c->vc_ptr; m.vc = c->vc; m.nb_ptr = c->nb_ptr; m.nb = c->nb;
   m.ccx = c->ccx; m.ccy = c->ccy; m.ccz = c->ccz; m.cvol = c->cvol; m.bb = c->bb;
   m.convex = c->convex;
+  m.face_off = c->face_off_d;
+  m.n_grids = c->n_grids;
   m.vx2 = c->vx2; m.vy2 = c->vy2; m.vz2 = c->vz2;
   m.fcx2 = c->fcx2; m.fcy2 = c->fcy2; m.fcz2 = c->fcz2;
   m.fnx32 = c->fnx32; m.fny32 = c->fny32; m.fnz32 = c->fnz32; m.fa32 = c->fa32;
@@ -242,6 +283,7 @@ inline DevState state_view(const vof_ctx* c) {
   s.tv = c->tv; s.tf = c->tf; s.tc = c->tc; s.Vd = c->Vd; s.VF = c->VF; s.srate = c->srate;
   s.icells = c->icells; s.afaces = c->afaces; s.cnt = c->cnt; s.red = c->red;
   s.nx32 = c->nx32; s.ny32 = c->ny32; s.nz32 = c->nz32; s.C32 = c->C32;
+  s.gp = c->gp_d;
   return s;
 }
 
@@ -291,22 +333,21 @@ void set_last_error(const char* msg);
 // set-up (k_setup.cu)
 cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_cell_geometry(const vof_ctx* c, cudaStream_t s);
-cudaError_t launch_velocity_setup(const vof_ctx* c, const Vel& v, cudaStream_t s);
+cudaError_t launch_velocity_setup(const vof_ctx* c, cudaStream_t s);  // velocities in gp_d
 cudaError_t launch_mixed_copies(const vof_ctx* c, cudaStream_t s);
 // sweeps (k_sweep.cu)
 cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s);
-cudaError_t launch_face_sweep(const vof_ctx* c, double g_half, double dt, cudaStream_t s);
+cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s);  // writes red[0], red[1]
 // reconstruction (k_recon.cu)
 cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);
 // flux (k_flux.cu)
-cudaError_t launch_flux(const vof_ctx* c, const Vel& v, double g_half, double dt, cudaStream_t s);
+cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int64_t cap_per_face,
                               int32_t* out, int32_t* counts, cudaStream_t s);
-cudaError_t launch_polyhedra(const vof_ctx* c, const Vel& v, double g_half, double dt,
-                             const int32_t* faces, int n, double* verts, int32_t* counts,
-                             cudaStream_t s);
+cudaError_t launch_polyhedra(const vof_ctx* c, const int32_t* faces, int n, double* verts,
+                             int32_t* counts, cudaStream_t s);
 
 }  // namespace gvof

@@ -89,6 +89,18 @@ def lib():
         L.vof_get_stats.argtypes = [vp, C.POINTER(Stats), vp]
         L.vof_set_timing.argtypes = [vp, C.c_int]
         L.vof_get_timing.argtypes = [vp, vp, vp, C.c_int]
+        L.vof_init_batch.argtypes = [vp, C.c_int, vp, C.POINTER(vp)]
+        L.vof_batch_offsets.argtypes = [vp, vp, vp, vp, vp]
+        L.vof_advect_batch.argtypes = [vp, vp, vp, vp, vp]
+        L.vof_step_batch.argtypes = [vp, vp, vp, vp, vp]
+        L.vof_suggest_dt_batch.argtypes = [vp, vp, vp, dbl, vp, vp]
+        L.vof_graph_capture.argtypes = [vp, C.c_int, vp]
+        L.vof_graph_launch.argtypes = [vp, vp, vp, vp, vp]
+        L.vof_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        for name in ("vof_init_batch", "vof_batch_offsets", "vof_advect_batch", "vof_step_batch",
+                     "vof_suggest_dt_batch", "vof_graph_capture", "vof_graph_launch",
+                     "vof_autotune"):
+            getattr(L, name).restype = C.c_int
         L.vof_volume_sum_noalloc.argtypes = [vp, vp, i64, vp, vp]
         L.vof_volume_sum_noalloc.restype = C.c_int
         L.vof_device_bytes.restype = i64
@@ -156,28 +168,46 @@ def velocity_struct(v):
     return s
 
 
+def _mesh_desc(mesh, keep):
+    X = np.ascontiguousarray(mesh["X"], np.float64)
+    fp = np.ascontiguousarray(mesh["face_ptr"], np.int64)
+    fv = np.ascontiguousarray(mesh["face_vert"], np.int32)
+    own = np.ascontiguousarray(mesh["owner"], np.int32)
+    nbr = np.ascontiguousarray(mesh["neighbour"], np.int32)
+    keep.extend([X, fp, fv, own, nbr])
+    return _Mesh(X.shape[0], own.shape[0], int(mesh["n_cell"]), _ptr(X).value, _ptr(fp).value,
+                 _ptr(fv).value, _ptr(own).value, _ptr(nbr).value)
+
+
 class Context:
-    """A mesh resident on the device with its VOF state (one vof_ctx)."""
+    """Meshes resident on the device with their VOF state (one vof_ctx).
+
+    ``mesh`` is one mesh dict, or a list of them for a batch: the grids are
+    joined into one context and advanced together, each with its own
+    velocity and time step (the ``*_batch`` methods).
+    """
 
     def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5):
         L = lib()
-        self._X = np.ascontiguousarray(mesh["X"], np.float64)
-        self._fp = np.ascontiguousarray(mesh["face_ptr"], np.int64)
-        self._fv = np.ascontiguousarray(mesh["face_vert"], np.int32)
-        self._own = np.ascontiguousarray(mesh["owner"], np.int32)
-        self._nbr = np.ascontiguousarray(mesh["neighbour"], np.int32)
-        md = _Mesh(self._X.shape[0], self._own.shape[0], int(mesh["n_cell"]), _ptr(self._X).value,
-                   _ptr(self._fp).value, _ptr(self._fv).value, _ptr(self._own).value,
-                   _ptr(self._nbr).value)
+        meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
+        keep = []
+        descs = (_Mesh * len(meshes))(*[_mesh_desc(m, keep) for m in meshes])
         opt = _Opt()
         opt.eps, opt.beta, opt.precision = eps, beta, precision
         h = C.c_void_p()
-        _check(L.vof_init(C.byref(md), C.byref(opt), C.byref(h)))
+        _check(L.vof_init_batch(descs, len(meshes), C.byref(opt), C.byref(h)))
         self._h = h
-        self.n_vert, self.n_face, self.n_cell = md.n_vert, md.n_face, md.n_cell
+        self.n_grids = len(meshes)
+        self.n_vert = sum(d.n_vert for d in descs)
+        self.n_face = sum(d.n_face for d in descs)
+        self.n_cell = sum(d.n_cell for d in descs)
         self.precision = precision
-        # the host copies are not needed after init
-        del self._X, self._fp, self._fv, self._own, self._nbr
+        co = np.empty(self.n_grids + 1, np.int64)
+        fo = np.empty(self.n_grids + 1, np.int64)
+        vo = np.empty(self.n_grids + 1, np.int64)
+        _check(L.vof_batch_offsets(h, None, _ptr(co), _ptr(fo), _ptr(vo)))
+        self.cell_off, self.face_off, self.vert_off = co, fo, vo
+        del keep  # the host copies are not needed after init
 
     def close(self):
         if getattr(self, "_h", None):
@@ -217,6 +247,42 @@ class Context:
     def step(self, vel, t, dt, stream=None):
         v = velocity_struct(vel)
         _check(lib().vof_step(self._h, C.byref(v), t, dt, _stream(stream)))
+
+    # --- batched forms (one velocity, time and step per grid)
+    def _batch_args(self, vels, t, dt):
+        vels = list(vels) if isinstance(vels, (list, tuple)) else [vels] * self.n_grids
+        va = (_Vel * self.n_grids)(*[velocity_struct(v) for v in vels])
+        ta = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (self.n_grids,)))
+        da = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (self.n_grids,)))
+        return va, ta, da
+
+    def advect_batch(self, vels, t, dt, stream=None):
+        va, ta, da = self._batch_args(vels, t, dt)
+        _check(lib().vof_advect_batch(self._h, va, _ptr(ta), _ptr(da), _stream(stream)))
+
+    def step_batch(self, vels, t, dt, stream=None):
+        va, ta, da = self._batch_args(vels, t, dt)
+        _check(lib().vof_step_batch(self._h, va, _ptr(ta), _ptr(da), _stream(stream)))
+
+    def suggest_dt_batch(self, vels, t, cfl, t_end):
+        va, ta, te = self._batch_args(vels, t, t_end)
+        out = np.empty(self.n_grids)
+        _check(lib().vof_suggest_dt_batch(self._h, va, _ptr(ta), cfl, _ptr(te), _ptr(out)))
+        return out
+
+    def graph_capture(self, with_reconstruct=True, stream=None):
+        _check(lib().vof_graph_capture(self._h, 1 if with_reconstruct else 0, _stream(stream)))
+
+    def graph_launch(self, vels, t, dt, stream=None):
+        va, ta, da = self._batch_args(vels, t, dt)
+        _check(lib().vof_graph_launch(self._h, va, _ptr(ta), _ptr(da), _stream(stream)))
+
+    def autotune(self, vels, t, dt, stream=None):
+        va, ta, da = self._batch_args(vels, t, dt)
+        fb, rb = C.c_int(), C.c_int()
+        _check(lib().vof_autotune(self._h, va, _ptr(ta), _ptr(da), _stream(stream), C.byref(fb),
+                                  C.byref(rb)))
+        return fb.value, rb.value
 
     def suggest_dt(self, vel, t, cfl, t_end):
         v = velocity_struct(vel)
