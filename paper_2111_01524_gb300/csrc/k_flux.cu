@@ -391,12 +391,6 @@ __device__ __noinline__ G volume_cut(const Poly<G>& P, const PolyState& st, G a0
   return wsum(acc) / G(6);
 }
 
-struct FluxParams {
-  Vel vel;
-  double g;    // time factor at t + dt/2
-  double dt;
-};
-
 template <typename G>
 struct FaceFrame {
   typename Prec<G>::A cx, cy, cz;  // face centroid (absolute)
@@ -414,12 +408,18 @@ struct FaceFrame {
 // of the back-traced loop moves along the face normal by the closed-form
 // amount that makes the signed volume equal V_d.
 template <typename G>
-__device__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv, const FluxParams& p, int j,
-                            double Vd, Poly<G>& P, FaceFrame<G>& fr, int lane) {
+__device__ __noinline__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv,
+                                         const GridParam& p, int j, double Vd, Poly<G>& P,
+                                         FaceFrame<G>& frs, int lane) {
+  FaceFrame<G> fr;  // built in registers, published to shared memory at the end
   const int64_t fb = M.fptr[j];
   const int I = (int)(M.fptr[j + 1] - fb);
   fr.I = I;
-  if (I > MAXI || I < 3) return false;
+  if (I > MAXI || I < 3) {
+    if (lane == 0) frs.I = I;
+    __syncwarp();
+    return false;
+  }
   fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
   fr.L = sqrt(Gv.fa[j]);
   fr.sc = G(1) / fr.L;
@@ -519,6 +519,8 @@ __device__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv, const FluxPa
   }
   fr.lo[0] = wmin(x0); fr.lo[1] = wmin(y0); fr.lo[2] = wmin(z0);
   fr.hi[0] = wmax(x1); fr.hi[1] = wmax(y1); fr.hi[2] = wmax(z1);
+  if (lane == 0) frs = fr;
+  __syncwarp();
   return true;
 }
 
@@ -593,48 +595,14 @@ __device__ __noinline__ G truncate_planes(Poly<G>& P, int np, bool has_plic, con
   return volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
 }
 
-// vol(P ∩ cell k ∩ X_k) in face-local units, X_k the fluid of cell k
-// (empty_side = false: all of a full cell, the PLIC half-space of an
-// interfacial cell) or its empty part (empty_side = true: all of an empty
-// cell, the complementary half-space of an interfacial cell). A convex cell
-// is the intersection of its face half-spaces; a non-convex cell is the
-// signed sum of the tetrahedra that join its centroid to the fan triangles of
-// its faces (winding-number decomposition, valid for any closed cell).
+// vol(P ∩ K ∩ X) for a non-convex cell K: signed sum over the tetrahedra
+// that join its centroid to the fan triangles of its faces (winding-number
+// decomposition, valid for any closed cell); the PLIC half-space, if any, is
+// already in P.pl[NF]
 template <typename G>
-__device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
-                                           const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
-                                           Poly<G>& P, int lane, unsigned& err, bool empty_side,
-                                           bool* whole) {
-  *whole = false;
-  const int8_t tk = S.tc[k];
-  if (tk == (empty_side ? 1 : -1)) return G(0);
-  const bool tag0 = tk == 0;
-  if (tag0 && lane == 0) {
-    // half-space of the PLIC plane on the wanted side: n.(x - x_k) + C >= 0
-    G pn0 = Gv.pnx[k], pn1 = Gv.pny[k], pn2 = Gv.pnz[k];
-    G pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
-             Gv.pC[k]) * fr.sc;
-    if (empty_side) { pn0 = -pn0; pn1 = -pn1; pn2 = -pn2; pnb = -pnb; }
-    P.pl[NF][0] = pn0; P.pl[NF][1] = pn1; P.pl[NF][2] = pn2; P.pl[NF][3] = pnb;
-  }
-  const int64_t c0 = M.cf_ptr[k];
-  const int nfk = (int)(M.cf_ptr[k + 1] - c0);
-  if (M.convex[k]) {
-    // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
-    // frame a = -n_out, b = -n_out.(c - p_g) / L
-    if (lane < nfk) {
-      const int fs = M.cf[c0 + lane];
-      const int f = fs >= 0 ? fs : ~fs;
-      const G sg = fs >= 0 ? G(1) : G(-1);
-      const G ox = sg * Gv.fnx[f], oy = sg * Gv.fny[f], oz = sg * Gv.fnz[f];
-      P.pl[lane][0] = -ox; P.pl[lane][1] = -oy; P.pl[lane][2] = -oz;
-      P.pl[lane][3] = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) +
-                        oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
-    }
-    __syncwarp();
-    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole);
-  }
-  // non-convex cell: signed tetrahedra (centroid, fan triangle of a face)
+__device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>& Gv, int k,
+                                             int64_t c0, int nfk, bool tag0, const FaceFrame<G>& fr,
+                                             G Vl, Poly<G>& P, int lane, unsigned& err) {
   const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
           rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
   G v = G(0);
@@ -693,13 +661,58 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
   return v;
 }
 
+
+// vol(P ∩ cell k ∩ X_k) in face-local units, X_k the fluid of cell k
+// (empty_side = false: all of a full cell, the PLIC half-space of an
+// interfacial cell) or its empty part (empty_side = true: all of an empty
+// cell, the complementary half-space of an interfacial cell). A convex cell
+// is the intersection of its face half-spaces; a non-convex cell is the
+// signed sum of the tetrahedra that join its centroid to the fan triangles of
+// its faces (winding-number decomposition, valid for any closed cell).
+template <typename G>
+__device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
+                                           const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
+                                           Poly<G>& P, int lane, unsigned& err, bool empty_side,
+                                           bool* whole) {
+  *whole = false;
+  const int8_t tk = S.tc[k];
+  if (tk == (empty_side ? 1 : -1)) return G(0);
+  const bool tag0 = tk == 0;
+  if (tag0 && lane == 0) {
+    // half-space of the PLIC plane on the wanted side: n.(x - x_k) + C >= 0
+    G pn0 = Gv.pnx[k], pn1 = Gv.pny[k], pn2 = Gv.pnz[k];
+    G pnb = (pn0 * rel(fr.cx, Gv.ccx[k]) + pn1 * rel(fr.cy, Gv.ccy[k]) + pn2 * rel(fr.cz, Gv.ccz[k]) +
+             Gv.pC[k]) * fr.sc;
+    if (empty_side) { pn0 = -pn0; pn1 = -pn1; pn2 = -pn2; pnb = -pnb; }
+    P.pl[NF][0] = pn0; P.pl[NF][1] = pn1; P.pl[NF][2] = pn2; P.pl[NF][3] = pnb;
+  }
+  const int64_t c0 = M.cf_ptr[k];
+  const int nfk = (int)(M.cf_ptr[k + 1] - c0);
+  if (M.convex[k]) {
+    // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
+    // frame a = -n_out, b = -n_out.(c - p_g) / L
+    if (lane < nfk) {
+      const int fs = M.cf[c0 + lane];
+      const int f = fs >= 0 ? fs : ~fs;
+      const G sg = fs >= 0 ? G(1) : G(-1);
+      const G ox = sg * Gv.fnx[f], oy = sg * Gv.fny[f], oz = sg * Gv.fnz[f];
+      P.pl[lane][0] = -ox; P.pl[lane][1] = -oy; P.pl[lane][2] = -oz;
+      P.pl[lane][3] = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) +
+                        oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
+    }
+    __syncwarp();
+    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole);
+  }
+  return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
+}
+
 // sum of vol(P ∩ cell k ∩ X_k) over the candidate cells: owner, its node
 // neighbours, then the neighbour and its node neighbours not seen yet
 // (Sec. 2.2: donating regions of several cells), filtered by the local
 // bounding box of the polyhedron. Returns the sum in face-local units and
 // sets *whole when P lies inside one X_k.
 template <typename G>
-__device__ G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
+__device__ __noinline__ G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
                               bool empty_side, bool* whole, unsigned long long& n_trunc) {
   const int64_t nc = M.nc;
@@ -746,17 +759,23 @@ __device__ G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevS
 template <typename G>
 __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S) {
   __shared__ Poly<G> polys[kWarps];
+  __shared__ GridParam wgp[kWarps];
+  __shared__ FaceFrame<G> wfr[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Poly<G>& P = polys[wib];
-  const int64_t nc = M.nc;
+  FaceFrame<G>& fr = wfr[wib];
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
   unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0;
   for (unsigned w = blockIdx.x * kWarps + wib; w < n_af; w += gridDim.x * kWarps) {
     const int j = S.afaces[w];
-    const GridParam& gq = S.gp[M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j)];
-    const FluxParams p{gq.vel, gq.g, gq.dt};
-    FaceFrame<G> fr;
-    if (!build_fmfpa<G>(M, Gv, p, j, S.Vd[j], P, fr, lane)) {
+    // the face's grid parameters, staged in shared memory (read at use)
+    {
+      const int gi = M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j);
+      constexpr int nw = (int)(sizeof(GridParam) / sizeof(double));
+      if (lane < nw) ((double*)&wgp[wib])[lane] = ((const double*)&S.gp[gi])[lane];
+      __syncwarp();
+    }
+    if (!build_fmfpa<G>(M, Gv, wgp[wib], j, S.Vd[j], P, fr, lane)) {
       if (lane == 0) S.VF[j] = 0.0;
       ++n_over;
       continue;
@@ -849,15 +868,15 @@ template <typename G>
 __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const double* srate,
                             const int32_t* faces, int n, double* verts, int32_t* counts) {
   __shared__ Poly<G> polys[kWarps];
+  __shared__ FaceFrame<G> wfr[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Poly<G>& P = polys[wib];
+  FaceFrame<G>& fr = wfr[wib];
   for (int w = blockIdx.x * kWarps + wib; w < n; w += gridDim.x * kWarps) {
     const int j = faces[w];
     const GridParam& gq = gp[grid_of(M.face_off, M.n_grids, j)];
-    const FluxParams p{gq.vel, gq.g, gq.dt};
-    FaceFrame<G> fr;
-    const double Vd = srate[j] * p.g * p.dt;
-    const bool ok = build_fmfpa<G>(M, Gv, p, j, Vd, P, fr, lane);
+    const double Vd = srate[j] * gq.g * gq.dt;
+    const bool ok = build_fmfpa<G>(M, Gv, gq, j, Vd, P, fr, lane);
     if (lane == 0) counts[w] = ok ? fr.I : -1;
     if (ok && lane < 2 * fr.I + 1) {
       const double L = (double)fr.L;
