@@ -34,6 +34,18 @@ namespace {
 #ifndef GVOF_FLUX_MINB
 #define GVOF_FLUX_MINB 8
 #endif
+// call structure of the flux kernel (inlining trades instruction-cache
+// footprint against call overhead); chosen by measurement
+#ifdef GVOF_INLINE_PLANES
+#define GVOF_PLANES_ATTR __forceinline__
+#else
+#define GVOF_PLANES_ATTR __noinline__
+#endif
+#ifdef GVOF_INLINE_OUTER
+#define GVOF_OUTER_ATTR __forceinline__
+#else
+#define GVOF_OUTER_ATTR __noinline__
+#endif
 
 constexpr int kWarps = 4;
 constexpr int MAXI = kMaxFaceVerts;   // face vertices
@@ -408,7 +420,7 @@ struct FaceFrame {
 // of the back-traced loop moves along the face normal by the closed-form
 // amount that makes the signed volume equal V_d.
 template <typename G>
-__device__ __noinline__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv,
+__device__ GVOF_OUTER_ATTR bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv,
                                          const GridParam& p, int j, double Vd, Poly<G>& P,
                                          FaceFrame<G>& frs, int lane) {
   FaceFrame<G> fr;  // built in registers, published to shared memory at the end
@@ -546,7 +558,7 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
 // inner side; tol is a few ulps of the face-local unit, so the volume this
 // neglects is of the order of the rounding of the plane itself.
 template <typename G>
-__device__ __noinline__ G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
+__device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
                                           G Vl, int lane, unsigned& err, bool* whole) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
   *whole = false;
@@ -712,7 +724,7 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
 // bounding box of the polyhedron. Returns the sum in face-local units and
 // sets *whole when P lies inside one X_k.
 template <typename G>
-__device__ __noinline__ G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
+__device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
                               bool empty_side, bool* whole, unsigned long long& n_trunc) {
   const int64_t nc = M.nc;
