@@ -35,7 +35,15 @@ namespace {
 #define GVOF_FLUX_MINB 8
 #endif
 // call structure of the flux kernel (inlining trades instruction-cache
-// footprint against call overhead); chosen by measurement
+// footprint against call overhead); chosen by measurement: inlining the plane
+// truncation and the per-face routines while clip, volume and the per-cell
+// truncation stay real calls was fastest (256^3 deformation, mixed)
+#ifndef GVOF_OUTLINE_PLANES
+#define GVOF_INLINE_PLANES
+#endif
+#ifndef GVOF_OUTLINE_OUTER
+#define GVOF_INLINE_OUTER
+#endif
 #ifdef GVOF_INLINE_PLANES
 #define GVOF_PLANES_ATTR __forceinline__
 #else
