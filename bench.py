@@ -60,6 +60,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=1)
+    p.add_argument("--workload", default="deformation",
+                   choices=["deformation", "tets", "batch", "serve"],
+                   help="deformation: hex grid, Enright field (default line); tets: jittered Kuhn "
+                        "tets in rotation; batch: 64 distorted grids advanced together; serve: "
+                        "Poisson request stream")
+    p.add_argument("--requests", type=int, default=48)
     return p.parse_args()
 
 
@@ -254,10 +260,209 @@ def main_reference(a):
     return 0
 
 
+# ---------------------------------------------------------------- other workloads
+def _make_trihex(args):
+    side, seed, axes, jitter = args
+    m = I.trihex_mesh(side, jitter=jitter, seed=seed)
+    F = I.init_fraction(m, I.ellipsoid((0.5, 0.5, 0.5), axes), levels=3)
+    keep = {k: m[k] for k in ("X", "face_ptr", "face_vert", "owner", "neighbour", "n_cell", "kind")}
+    return keep, F
+
+
+def batch_inputs(n_grids=64, seed=20211106, procs=16):
+    """64 distorted triangulated-hex grids of side log-uniform in 16..96,
+    interior vertices jittered by U[-0.3h, 0.3h]^3, each with a seeded
+    axis-aligned ellipsoid (semi-axes U[0.1, 0.25]) and a uniform velocity
+    U[-1, 1]^3 (generated in a spawn process pool, before any CUDA call)."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(np.log(16), np.log(96), n_grids))).astype(int)
+    axes = rng.uniform(0.1, 0.25, (n_grids, 3))
+    vels = rng.uniform(-1.0, 1.0, (n_grids, 3))
+    jobs = [(int(sides[g]), seed + g, tuple(axes[g]), 0.3) for g in range(n_grids)]
+    with mp.get_context("spawn").Pool(min(procs, os.cpu_count() or 1)) as pool:
+        out = pool.map(_make_trihex, jobs)
+    return [o[0] for o in out], [o[1] for o in out], [I.translation(tuple(v)) for v in vels], sides
+
+
+def main_batch(a):
+    meshes, Fs, vels, sides = batch_inputs()
+    import torch
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import vof as V
+    B.build()
+    torch.cuda.set_device(0)
+    n = len(meshes)
+    ctx = V.Context(meshes, precision=V.PREC_MIXED)
+    stream = torch.cuda.Stream()
+    cells = int(ctx.n_cell)
+    umax = np.array([np.abs(v.u0).max() for v in vels])
+    h = np.array([1.0 / s for s in sides])
+    # READING d4b: dt_g = min(CFL 0.5 step, 0.2 / (100 |U|_inf)) so that 100
+    # steps keep every body inside its domain
+    with torch.cuda.stream(stream):
+        ctx.set_fraction(np.concatenate(Fs))
+        ctx.reconstruct()
+        t = np.zeros(n)
+        dt_cfl = ctx.suggest_dt_batch(vels, t, 0.5, np.full(n, 1e9))
+        dt = np.minimum(dt_cfl, 0.2 / (100.0 * umax))
+        tuned = ctx.autotune(vels, t, dt)
+        ctx.graph_capture(with_reconstruct=True)
+        for _ in range(a.warmup):
+            ctx.graph_launch(vels, t, dt)
+            t = t + dt
+        torch.cuda.synchronize()
+        clk = ClockSampler(0)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            ctx.graph_launch(vels, t, dt)
+            t = t + dt
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        st = ctx.stats()
+    line = {"metric": METRIC, "value": cells * a.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {n} distorted triangulated-hex grids (side log-uniform "
+                                   "16..96, jitter 0.3h, non-convex cells), ellipsoids, uniform "
+                                   "translation, one CUDA graph per step",
+                       "cells": cells, "faces": int(ctx.n_face), "grids": n,
+                       "sides": [int(x) for x in sides], "autotuned_blocks": list(tuned)},
+            "gpu_launches": 6 * a.steps,
+            "band": {"interfacial_cells": st["n_interfacial"], "active_faces": st["n_active_faces"],
+                     "truncations_last_step": st["n_truncations"], "overflow": st["n_overflow"]},
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
+def main_tets(a):
+    """64^3 cubes x 6 jittered Kuhn tets (1.57 M cells), sphere r = 0.15 at
+    (0.5, 0.75, 0.5), rigid rotation, CFL 0.4; mixed beside FP64."""
+    import torch
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import vof as V
+    B.build()
+    m = I.kuhn_tet_mesh(64, jitter=0.2, seed=20211105)
+    F0 = I.init_fraction(m, I.sphere((0.5, 0.75, 0.5), 0.15), levels=3)
+    vel = I.rotation(2 * np.pi)
+    res = {}
+    for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
+        ctx = V.Context(m, precision=prec)
+        ctx.set_fraction(F0)
+        ctx.reconstruct()
+        t = 0.0
+        for _ in range(a.warmup):
+            dt = ctx.suggest_dt(vel, t, 0.4, 1.0)
+            ctx.step(vel, t, dt)
+            t += dt
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            dt = ctx.suggest_dt(vel, t, 0.4, 1.0)
+            ctx.step(vel, t, dt)
+            t += dt
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": m["n_cell"] * a.steps / (ms * 1e-3), "ms_per_step": ms / a.steps,
+                     "F": ctx.get_fraction(), "stats": ctx.stats()}
+    line = {"metric": METRIC, "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["mixed"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "64^3 x 6 jittered Kuhn tets, sphere r=0.15 at (0.5,0.75,0.5), "
+                                   "rigid rotation, CFL 0.4", "cells": int(m["n_cell"])},
+            "fp64_path": {"value": res["fp64"]["value"],
+                          "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+                          "max_abs_F_diff_mixed_vs_fp64":
+                              float(np.abs(res["mixed"]["F"] - res["fp64"]["F"]).max())},
+            "band": {k: res["mixed"]["stats"][k] for k in ("n_interfacial", "n_active_faces",
+                                                           "n_truncations", "n_overflow")}}
+    print(json.dumps(line))
+    return 0
+
+
+def _make_request_inputs(args):
+    kind, side, seed, body, axes = args
+    if kind == "hex":
+        m = I.hex_mesh(side)
+    else:
+        m = I.kuhn_tet_mesh(side, jitter=0.2, seed=seed)
+    b = I.sphere((0.5, 0.5, 0.5), 0.15) if body == "sphere" else I.ellipsoid((0.5, 0.5, 0.5), axes)
+    F = I.init_fraction(m, b, levels=3)
+    keep = {k: m[k] for k in ("X", "face_ptr", "face_vert", "owner", "neighbour", "n_cell", "kind")}
+    return keep, F
+
+
+def main_serve(a):
+    """Poisson stream (mean 200 req/s) of requests on hex or jittered-tet grids
+    of side log-uniform in 24..64, sphere or ellipsoid, field deformation /
+    rotation / translation, N ~ U{10..200} steps; admission by 80% of free
+    device memory; mixed precision."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(20211107)
+    n = a.requests
+    specs = []
+    for rid in range(n):
+        kind = "hex" if rng.random() < 0.5 else "tet"
+        side = int(np.rint(np.exp(rng.uniform(np.log(24), np.log(64)))))
+        if kind == "tet":
+            side = max(8, side // 2)  # 6 tets per cube: comparable cell counts
+        body = "sphere" if rng.random() < 0.5 else "ellipsoid"
+        specs.append((kind, side, 20211107 + rid, body, tuple(rng.uniform(0.1, 0.25, 3))))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        inputs = pool.map(_make_request_inputs, specs)
+    import torch
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import serve as S
+    B.build()
+    torch.cuda.set_device(0)
+    fields = [I.deformation(3.0), I.rotation(2 * np.pi)]
+
+    def make(rid, r):
+        m, F = inputs[rid]
+        which = r.integers(3)
+        vel = fields[which] if which < 2 else I.translation(tuple(r.uniform(-1, 1, 3)))
+        cfl = 0.4 if specs[rid][0] == "tet" else 0.5
+        return S.Request(rid=rid, mesh=m, F0=F, vel=vel, n_steps=int(r.integers(10, 201)), cfl=cfl)
+
+    reqs = S.poisson_trace(n, 200.0, 20211108, make)
+    backend = S.DeviceBackend(precision_mixed=True, use_graphs=True)
+    srv = S.Server(backend, budget_fraction=0.8)
+    st = srv.run(reqs)
+    sm = st.summary()
+    line = {"metric": METRIC, "value": sm["cell_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": int(sum(r.n_steps for r in reqs)), "warmup": 0,
+            "p50_ms": sm["p50_s"] * 1e3, "p99_ms": sm["p99_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"Poisson stream, {n} requests at 200 req/s, hex/jittered-tet "
+                                   "grids of side log-uniform 24..64, N ~ U{10..200} steps",
+                       "requests": n, "budget_bytes": srv.budget},
+            "serve": sm}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return main_reference(a)
+    if a.workload == "batch":
+        return main_batch(a)
+    if a.workload == "tets":
+        return main_tets(a)
+    if a.workload == "serve":
+        return main_serve(a)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)

@@ -344,19 +344,24 @@ def trihex_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.3, seed=0):
     ptr, fv = _csr(tri.astype(np.int32))
 
     def tets(cells):
+        # every cell has 24 tetrahedra, stored contiguously after the sort
         cells = np.asarray(cells, np.int64)
         if len(cells) == 0:
             return P[:0], cot[:0]
-        idx = np.concatenate([np.arange(start[c], start[c + 1]) for c in cells])
+        idx = (start[cells][:, None] + np.arange(24)[None, :]).reshape(-1)
         return P[idx], cot[idx]
 
-    def points(cells):
-        T, _ = tets(cells)
-        return T.reshape(len(cells), -1, 3)
+    def corners(cells):
+        # the 8 grid corners of the cell; its face centres are averages of
+        # them, so the corners' bounding ball contains the whole cell
+        cells = np.asarray(cells, np.int64)
+        i, j, k = cells % n, (cells // n) % n, cells // (n * n)
+        ids = [_vid(n, i + (b & 1), j + ((b >> 1) & 1), k + ((b >> 2) & 1)) for b in range(8)]
+        return np.stack(ids, axis=1)
 
     return dict(X=Xall, face_ptr=ptr, face_vert=fv, owner=t_owner.astype(np.int32),
-                neighbour=t_nbr.astype(np.int32), n_cell=nc, cell_corners=None,
-                cell_tets=tets, cell_points=points, kind="trihex", n=n, h=h)
+                neighbour=t_nbr.astype(np.int32), n_cell=nc, cell_corners=corners,
+                cell_tets=tets, kind="trihex", n=n, h=h)
 
 
 def mesh_counts(mesh):
