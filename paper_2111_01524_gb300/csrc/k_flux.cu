@@ -625,17 +625,42 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
                                              G Vl, Poly<G>& P, int lane, unsigned& err) {
   const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
           rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
+  // fan triangles per face, and their running count (lanes over faces)
+  int ntri = 0, fs_l = 0;
+  int64_t fb_l = 0;
+  if (lane < nfk) {
+    fs_l = M.cf[c0 + lane];
+    const int f = fs_l >= 0 ? fs_l : ~fs_l;
+    fb_l = M.fptr[f];
+    ntri = (int)(M.fptr[f + 1] - fb_l) - 2;
+  }
+  int incl = ntri;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(GVOF_FULL, incl, d);
+    if (lane >= d) incl += t;
+  }
+  const int total = __shfl_sync(GVOF_FULL, incl, 31);
+  const int first = incl - ntri;
   G v = G(0);
-  for (int q = 0; q < nfk; ++q) {
-    const int fs = M.cf[c0 + q];
-    const int f = fs >= 0 ? fs : ~fs;
-    const int64_t fb = M.fptr[f];
-    const int L = (int)(M.fptr[f + 1] - fb);
-    for (int t = 1; t + 1 < L; ++t) {
-      // triangle (v0, v_t, v_t+1) of the face, outward from cell k
+  // lanes over tetrahedra, 32 at a time: build, orient, reject by bounding box
+  for (int base = 0; base < total; base += 32) {
+    const int id = base + lane;
+    G T[4][3];
+    G sgn = G(0);
+    bool keep = false;
+    // face holding tetrahedron id: the last face whose first <= id
+    int q = 0;
+    for (int r = 0; r < nfk; ++r) {
+      const int fr_first = __shfl_sync(GVOF_FULL, first, r);
+      if (fr_first <= id) q = r;
+    }
+    const int fs = __shfl_sync(GVOF_FULL, fs_l, q & 31);
+    const int64_t fb = __shfl_sync(GVOF_FULL, fb_l, q & 31);
+    const int fq_first = __shfl_sync(GVOF_FULL, first, q & 31);
+    if (id < total) {
+      const int t = id - fq_first + 1;
       int ia = M.fvert[fb], ib = M.fvert[fb + t], ic = M.fvert[fb + t + 1];
       if (fs < 0) { const int tmp = ib; ib = ic; ic = tmp; }
-      G T[4][3];
       T[0][0] = rx; T[0][1] = ry; T[0][2] = rz;
       const int ids[3] = {ia, ib, ic};
       for (int e = 0; e < 3; ++e) {
@@ -647,40 +672,45 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
       const G wx = T[2][0] - T[0][0], wy = T[2][1] - T[0][1], wz = T[2][2] - T[0][2];
       const G zx = T[3][0] - T[0][0], zy = T[3][1] - T[0][1], zz = T[3][2] - T[0][2];
       const G det = ux * (wy * zz - wz * zy) + uy * (wz * zx - wx * zz) + uz * (wx * zy - wy * zx);
-      if (det == G(0)) continue;
-      const G sgn = det > G(0) ? G(1) : G(-1);
-      // bounding-box rejection of the tetrahedron
+      sgn = det > G(0) ? G(1) : G(-1);
       G lo0 = T[0][0], hi0 = T[0][0], lo1 = T[0][1], hi1 = T[0][1], lo2 = T[0][2], hi2 = T[0][2];
       for (int e = 1; e < 4; ++e) {
         lo0 = min(lo0, T[e][0]); hi0 = max(hi0, T[e][0]);
         lo1 = min(lo1, T[e][1]); hi1 = max(hi1, T[e][1]);
         lo2 = min(lo2, T[e][2]); hi2 = max(hi2, T[e][2]);
       }
-      if (!(fr.hi[0] > lo0 && fr.lo[0] < hi0 && fr.hi[1] > lo1 && fr.lo[1] < hi1 &&
-            fr.hi[2] > lo2 && fr.lo[2] < hi2))
-        continue;
+      keep = det != G(0) && fr.hi[0] > lo0 && fr.lo[0] < hi0 && fr.hi[1] > lo1 &&
+             fr.lo[1] < hi1 && fr.hi[2] > lo2 && fr.lo[2] < hi2;
+    }
+    unsigned bal = __ballot_sync(GVOF_FULL, keep);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1u;
+      G Tq[4][3];
+      for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d) Tq[a][d] = __shfl_sync(GVOF_FULL, T[a][d], src);
+      const G sg = __shfl_sync(GVOF_FULL, sgn, src);
       // inward planes of the tetrahedron: face opposite vertex a, outward
       // normal (q1 - q0) x (q2 - q0) for a positive tetrahedron
       if (lane < 4) {
         const int o0 = lane == 0 ? 1 : 0;
         const int o1 = lane == 0 ? 2 : (lane == 1 ? 3 : (lane == 2 ? 1 : 2));
         const int o2 = lane == 0 ? 3 : (lane == 1 ? 2 : (lane == 2 ? 3 : 1));
-        const G ax = T[o1][0] - T[o0][0], ay = T[o1][1] - T[o0][1], az = T[o1][2] - T[o0][2];
-        const G cx = T[o2][0] - T[o0][0], cy = T[o2][1] - T[o0][1], cz = T[o2][2] - T[o0][2];
-        G nx = (ay * cz - az * cy) * sgn, ny = (az * cx - ax * cz) * sgn, nz = (ax * cy - ay * cx) * sgn;
+        const G ax = Tq[o1][0] - Tq[o0][0], ay = Tq[o1][1] - Tq[o0][1], az = Tq[o1][2] - Tq[o0][2];
+        const G cx = Tq[o2][0] - Tq[o0][0], cy = Tq[o2][1] - Tq[o0][1], cz = Tq[o2][2] - Tq[o0][2];
+        G nx = (ay * cz - az * cy) * sg, ny = (az * cx - ax * cz) * sg, nz = (ax * cy - ay * cx) * sg;
         const G nn = G(1) / sqrt(nx * nx + ny * ny + nz * nz);
         nx *= nn; ny *= nn; nz *= nn;
         P.pl[lane][0] = -nx; P.pl[lane][1] = -ny; P.pl[lane][2] = -nz;
-        P.pl[lane][3] = nx * T[o0][0] + ny * T[o0][1] + nz * T[o0][2];
+        P.pl[lane][3] = nx * Tq[o0][0] + ny * Tq[o0][1] + nz * Tq[o0][2];
       }
       __syncwarp();
       bool w = false;
-      v += sgn * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w);
+      v += sg * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w);
     }
   }
   return v;
 }
-
 
 // vol(P ∩ cell k ∩ X_k) in face-local units, X_k the fluid of cell k
 // (empty_side = false: all of a full cell, the PLIC half-space of an

@@ -61,9 +61,10 @@ def test_results_alone_and_in_the_mix(env, graphs):
 def test_budget_limits_residency(env):
     vof, serve = env
     reqs = _requests(serve)
-    # a budget that holds one request at a time still serves all, in order
+    # a budget that holds the largest request alone: requests wait for room,
+    # the resident set never exceeds the budget, and every result is right
     big = max(serve.estimate_device_bytes(r.mesh) for r in reqs)
     st = serve.Server(serve.DeviceBackend(), budget_bytes=big).run(reqs)
-    assert st.summary()["max_active"] == 1
+    assert st.max_bytes <= big and st.summary()["max_active"] < len(reqs)
     for r in reqs:
         assert np.array_equal(r.result, _alone(vof, r, vof.PREC_MIXED))
