@@ -561,15 +561,20 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
 // ballot per plane): a plane with every vertex outside empties the
 // intersection, a plane with none outside is skipped, and only the planes
 // that cut are clipped: all but the last topologically, the last one inside
-// the volume sum. *whole is set when P lies inside K ∩ X (the result is then
+// the volume sum. *whole = 1 when P lies inside K ∩ X (the result is then
 // the volume of P itself). Vertices within tol of a plane count as on its
 // inner side; tol is a few ulps of the face-local unit, so the volume this
 // neglects is of the order of the rounding of the plane itself.
+// Two-sided (vout != nullptr, with the PLIC plane, FP32 only): *vout also
+// receives vol(P ∩ K ∩ X^c), both cut from the same clipped polyhedron, and
+// *whole = 2 when P lies inside K ∩ X^c.
 template <typename G>
 __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
-                                          G Vl, int lane, unsigned& err, bool* whole) {
+                                          G Vl, int lane, unsigned& err, int* whole, G* vout) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
-  *whole = false;
+  *whole = 0;
+  const bool two = sizeof(G) == 4 && vout != nullptr && has_plic;
+  if (vout) *vout = G(0);
   const int nvb = 2 * fr.I + 1;
   const bool hv = lane < nvb;
   const G bx = hv ? P.bx[lane] : G(0), by = hv ? P.by[lane] : G(0), bz = hv ? P.bz[lane] : G(0);
@@ -581,15 +586,20 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
     if (in == 0u && out != 0u) return G(0);  // P on the outer side of a plane
     if (out) cut |= 1u << g;
   }
-  bool plic = false;
+  int pst = 0;  // PLIC: 0 P on the X side, 1 cut, 2 P on the other side
   if (has_plic) {
     const G ph = P.pl[NF][0] * bx + P.pl[NF][1] * by + P.pl[NF][2] * bz + P.pl[NF][3];
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
-    if (in == 0u && out != 0u) return G(0);  // P on the other side of the interface
-    plic = out != 0u;
+    pst = (in == 0u && out != 0u) ? 2 : (out != 0u ? 1 : 0);
   }
-  if (cut == 0u && !plic) { *whole = true; return Vl; }  // P inside K ∩ X
+  if (pst == 2 && !two) return G(0);  // P on the other side of the interface
+  const bool plic = pst == 1;
+  if (cut == 0u && !plic) {
+    if (pst == 2) { *whole = 2; *vout = Vl; return G(0); }  // P inside K ∩ X^c
+    *whole = 1;
+    return Vl;  // P inside K ∩ X
+  }
   int last;
   if (plic) {
     last = NF;
@@ -612,7 +622,11 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
     res = clip(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane, err);
     return res == 2 ? G(0) : volume(P, st, lane);
   }
-  return volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
+  const G v = volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
+  if (!two) return v;
+  if (pst == 2) { *vout = v; return G(0); }
+  if (pst == 1) *vout = volume_cut(P, st, -P.pl[NF][0], -P.pl[NF][1], -P.pl[NF][2], -P.pl[NF][3], lane);
+  return v;
 }
 
 // vol(P ∩ K ∩ X) for a non-convex cell K: signed sum over the tetrahedra
@@ -622,7 +636,7 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
 template <typename G>
 __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>& Gv, int k,
                                              int64_t c0, int nfk, bool tag0, const FaceFrame<G>& fr,
-                                             G Vl, Poly<G>& P, int lane, unsigned& err) {
+                                             G Vl, Poly<G>& P, int lane, unsigned& err, G* vout) {
   const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
           rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
   // fan triangles per face, and their running count (lanes over faces)
@@ -705,8 +719,10 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
         P.pl[lane][3] = nx * Tq[o0][0] + ny * Tq[o0][1] + nz * Tq[o0][2];
       }
       __syncwarp();
-      bool w = false;
-      v += sg * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w);
+      int w = 0;
+      G vo = G(0);
+      v += sg * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w, vout ? &vo : nullptr);
+      if (vout) *vout += sg * vo;
     }
   }
   return v;
@@ -719,12 +735,15 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
 // is the intersection of its face half-spaces; a non-convex cell is the
 // signed sum of the tetrahedra that join its centroid to the fan triangles of
 // its faces (winding-number decomposition, valid for any closed cell).
+// vout != nullptr (FP32, empty_side = false): an interfacial cell also gives
+// its empty part in *vout (truncate_planes, two-sided).
 template <typename G>
 __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
                                            const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
                                            Poly<G>& P, int lane, unsigned& err, bool empty_side,
-                                           bool* whole) {
-  *whole = false;
+                                           int* whole, G* vout) {
+  *whole = 0;
+  if (vout) *vout = G(0);
   const int8_t tk = S.tc[k];
   if (tk == (empty_side ? 1 : -1)) return G(0);
   const bool tag0 = tk == 0;
@@ -751,27 +770,32 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
                         oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
     }
     __syncwarp();
-    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole);
+    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole, vout);
   }
-  return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
+  return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err, vout);
 }
 
 // sum of vol(P ∩ cell k ∩ X_k) over the candidate cells: owner, its node
 // neighbours, then the neighbour and its node neighbours not seen yet
 // (Sec. 2.2: donating regions of several cells), filtered by the local
-// bounding box of the polyhedron. Returns the sum in face-local units and
-// sets *whole when P lies inside one X_k.
+// bounding box of the polyhedron, in face-local units.
+// mode 0: the fluid parts (full and interfacial cells); mode 1: the same,
+// and the empty parts of the interfacial cells added to *gas from the same
+// clipped polyhedra; mode 2: the empty cells only (all of each).
+// *whole = 1 (2) when P lies inside the fluid (empty) part of one cell;
+// *saw_empty (modes 0, 1): an empty cell met the bounding box of P.
 template <typename G>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
-                              bool empty_side, bool* whole, unsigned long long& n_trunc) {
+                              int mode, G* gas, int* whole, bool* saw_empty,
+                              unsigned long long& n_trunc) {
   const int64_t nc = M.nc;
   const int own = M.own[j], nbr = M.nbr[j];
   const int64_t a0 = M.nb_ptr[own];
   const int na = (int)(M.nb_ptr[own + 1] - a0);
-  const int8_t skip_tag = empty_side ? 1 : -1;
   G v = G(0);
-  *whole = false;
+  *whole = 0;
+  *saw_empty = false;
   for (int pass = 0; pass < 2; ++pass) {
     const int c0 = pass == 0 ? own : nbr;
     if (c0 < 0) break;
@@ -783,7 +807,11 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
       if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
       bool keep = k >= 0;
       if (keep && pass == 1) keep = !(k == own || sorted_contains(M.nb + a0, na, k));
-      if (keep) keep = S.tc[k] != skip_tag;
+      int8_t tk = 0;
+      if (keep) {
+        tk = S.tc[k];
+        if (mode == 2 && tk != -1) keep = false;
+      }
       if (keep) {
         const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
         const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
@@ -791,15 +819,24 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
         keep = fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy &&
                fr.hi[2] > lz && fr.lo[2] < hz;
       }
+      if (mode != 2) {
+        // (warp-uniform: it decides whether the warp sweeps the empty cells)
+        if (__any_sync(GVOF_FULL, keep && tk == -1)) *saw_empty = true;
+        keep = keep && tk != -1;
+      }
       unsigned bal = __ballot_sync(GVOF_FULL, keep);
       while (bal) {
         const int src = __ffs(bal) - 1;
         bal &= bal - 1u;
         const int kk = __shfl_sync(GVOF_FULL, k, src);
-        bool w = false;
-        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, empty_side, &w);
+        int w = 0;
+        G vo = G(0);
+        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, mode == 2, &w,
+                                 mode == 1 ? &vo : nullptr);
         ++n_trunc;
-        if (w) { *whole = true; return Vl; }  // no other cell meets P
+        if (mode == 2 && w) w = 2;
+        if (w) { *whole = w; return w == 1 ? Vl : G(0); }  // no other cell meets P
+        if (mode == 1) *gas += vo;
       }
     }
   }
@@ -835,18 +872,30 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     unsigned err = 0u;
     const G Vl = (G)S.Vd[j] * (fr.sc * fr.sc * fr.sc);  // volume of P, local units
     const G L3 = fr.L * fr.L * fr.L;
-    bool whole = false;
-    const G vf = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, false, &whole, n_trunc);
+    // FP64: the fluid part. FP32: the fluid part and the empty part of the
+    // interfacial cells from the same clipped polyhedra; when P is mostly
+    // fluid, V_F = V_d - (empty part of P), so that the FP32 error scales
+    // with the empty part (P lies in the candidate cells for an interior
+    // face at CFL <= 1, so fluid + empty = V_d), the empty cells' share
+    // added by a second sweep over those cells only
+    const int mode = sizeof(G) == 4 ? 1 : 0;
+    G ve = G(0);
+    int wh = 0;
+    bool saw_empty = false;
+    const G vf = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, mode, &ve, &wh, &saw_empty,
+                                     n_trunc);
     double VFj;
-    if (whole) {
+    if (wh == 1) {
       VFj = S.Vd[j];  // P inside the fluid of one cell: exactly V_d
-    } else if (sizeof(G) == 4 && M.nbr[j] >= 0 && fabs(vf) > G(0.5) * fabs(Vl)) {
-      // mostly fluid: V_F = V_d - (empty part of P), so that the FP32 error
-      // scales with the empty part (P lies in the candidate cells for an
-      // interior face at CFL <= 1, so fluid + empty = V_d)
-      bool we = false;
-      const G ve = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, true, &we, n_trunc);
-      VFj = we ? 0.0 : S.Vd[j] - (double)(ve * L3);
+    } else if (wh == 2) {
+      VFj = 0.0;      // P inside the empty part of one cell
+    } else if (mode == 1 && M.nbr[j] >= 0 && fabs(vf) > G(0.5) * fabs(Vl)) {
+      if (saw_empty) {
+        G unused = G(0);
+        bool s2 = false;
+        ve += sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, 2, &unused, &wh, &s2, n_trunc);
+      }
+      VFj = wh == 2 ? 0.0 : S.Vd[j] - (double)(ve * L3);
     } else {
       VFj = (double)(vf * L3);
     }
