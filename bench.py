@@ -13,9 +13,11 @@ LSGIR + plane constant, i.e. every kernel of the hot path. Inputs (mesh,
 F, planes) are resident in HBM and far larger than L2 (the mesh arrays
 alone are ~10 GB at 256^3), so no L2 flush is needed between steps.
 
-Multi-GPU: the path runs one independent replica of the workload per rank
-(no data-path collective); value = total cell-steps of all ranks / the
-slowest rank's time.
+Multi-GPU (no data-path collective anywhere): the single-grid workloads run
+one independent replica per rank; the batched and served workloads shard
+their independent units (grids, requests) across ranks by estimated work
+(cells x steps). value = total cell-steps of all ranks / the slowest rank's
+time.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on the
 host cores on the same workload, one full step per timed step.
@@ -40,9 +42,17 @@ from paper_2111_01524_gb300 import inputs as I  # noqa: E402
 
 METRIC = "VOF cell-steps/s (recon+advect) mixed vs FP64 at stated F error; p50/p99 latency"
 UNIT = "cell-steps/s"
-# algorithmic work per unit (stated and derived in the design doc)
+# algorithmic work per unit of the band kernels: flops of one FMFPA
+# construction and of one (face, cell) truncation with its divergence sum
 FLOPS_PER_ACTIVE_FACE = 350.0      # FMFPA construction
 FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
+# ncu capture of one flux launch (128^3 deformation step, mixed: 56,810 active
+# faces): dram__bytes_read.sum + dram__bytes_write.sum = 26.96 + 4.23 MB, i.e.
+# 549 B per active face, issue active 45.9%, FMA pipe 13.4%; valid for the
+# kernel source it was taken on (traffic is null for any other source)
+FLUX_NCU = {"source_sha256": "02d54c614f34f2be4499adfe2813d19349f4bf2fa2638a9fdb2838e55212e466",
+            "dram_bytes_per_active_face": 549.0, "issue_active": 0.459, "fma_pipe_active": 0.134,
+            "capture": "profiles/k_flux_deformation128_mixed.md"}
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
 N_SM = 152
@@ -150,6 +160,29 @@ def dist_env():
     return ws, rank, local
 
 
+def dist_init():
+    """One rank per GPU; the process group carries only the barrier and the
+    measurement bookkeeping."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local, dist
+
+
+def over_ranks(dist, value, op):
+    """max / sum of a host float over ranks (identity on one rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def run_steps(ctx, vel, cfl, t_end, t, n, stream, timing=False):
     """n steps of the advection loop; returns new t and per-step ms (events)."""
     import torch
@@ -169,7 +202,8 @@ def run_steps(ctx, vel, cfl, t_end, t, n, stream, timing=False):
 
 
 def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision):
-    """Roofline of the dominant kernel (see the design doc for the per-unit work)."""
+    """Roofline of the dominant kernel: algorithmic HBM bytes per launch for the
+    sweeps, algorithmic flops per launch for the band kernels."""
     ms, launches = phase["ms"], phase["launches"]
     per_launch_ms = ms / max(launches, 1)
     nc, nf, nv = grid_counts["n_cell"], grid_counts["n_face"], grid_counts["n_vert"]
@@ -191,12 +225,19 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
     # the counters describe the last advect (one launch of each band kernel)
     fl = (ctx_counts["n_active_faces"] * FLOPS_PER_ACTIVE_FACE
           + ctx_counts["n_truncations"] * FLOPS_PER_TRUNCATION)
+    traffic, ncu = None, None
+    if name == "flux" and precision == "mixed":
+        import hashlib
+        src = os.path.join(ROOT, "paper_2111_01524_gb300", "csrc", "k_flux.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() == FLUX_NCU["source_sha256"]:
+            traffic = FLUX_NCU["dram_bytes_per_active_face"] * ctx_counts["n_active_faces"]
+            ncu = {k: FLUX_NCU[k] for k in ("issue_active", "fma_pipe_active", "capture")}
     mhz = clocks.get("sm_mhz") or 1900.0
     lanes = FP32_LANES_PER_SM if precision == "mixed" else FP64_LANES_PER_SM
     peak = N_SM * lanes * 2 * mhz * 1e6 / 1e12
     achieved = fl / (per_launch_ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "ncu": ncu,
             "algorithmic_flops_per_launch": fl,
             "peak_source": f"{'FP32' if precision == 'mixed' else 'FP64'} FMA lanes x SMs x "
                            f"median SM clock {mhz:.0f} MHz"}
@@ -269,29 +310,42 @@ def _make_trihex(args):
     return keep, F
 
 
-def batch_inputs(n_grids=64, seed=20211106, procs=16):
+def batch_spec(n_grids=64, seed=20211106):
     """64 distorted triangulated-hex grids of side log-uniform in 16..96,
     interior vertices jittered by U[-0.3h, 0.3h]^3, each with a seeded
     axis-aligned ellipsoid (semi-axes U[0.1, 0.25]) and a uniform velocity
-    U[-1, 1]^3 (generated in a spawn process pool, before any CUDA call)."""
-    import multiprocessing as mp
+    U[-1, 1]^3."""
     rng = np.random.default_rng(seed)
     sides = np.rint(np.exp(rng.uniform(np.log(16), np.log(96), n_grids))).astype(int)
     axes = rng.uniform(0.1, 0.25, (n_grids, 3))
     vels = rng.uniform(-1.0, 1.0, (n_grids, 3))
-    jobs = [(int(sides[g]), seed + g, tuple(axes[g]), 0.3) for g in range(n_grids)]
-    with mp.get_context("spawn").Pool(min(procs, os.cpu_count() or 1)) as pool:
+    return sides, axes, vels, seed
+
+
+def batch_inputs(select, procs=16):
+    """Meshes and F0 of the selected grids of batch_spec() (generated in a
+    spawn process pool, before any CUDA call)."""
+    import multiprocessing as mp
+    sides, axes, vels, seed = batch_spec()
+    jobs = [(int(sides[g]), seed + g, tuple(axes[g]), 0.3) for g in select]
+    with mp.get_context("spawn").Pool(max(1, min(procs, os.cpu_count() or 1, len(jobs)))) as pool:
         out = pool.map(_make_trihex, jobs)
-    return [o[0] for o in out], [o[1] for o in out], [I.translation(tuple(v)) for v in vels], sides
+    return ([o[0] for o in out], [o[1] for o in out],
+            [I.translation(tuple(vels[g])) for g in select], sides[list(select)])
 
 
 def main_batch(a):
-    meshes, Fs, vels, sides = batch_inputs()
+    from paper_2111_01524_gb300 import shard
+    ws, rank, local = dist_env()
+    all_sides = batch_spec()[0]
+    # the grids are independent: each rank takes a share balanced by cells
+    parts = shard.balance([float(s) ** 3 for s in all_sides], ws)
+    meshes, Fs, vels, sides = batch_inputs(parts[rank])
     import torch
+    ws, rank, local, dist = dist_init()
     from paper_2111_01524_gb300 import build as B
     from paper_2111_01524_gb300 import vof as V
     B.build()
-    torch.cuda.set_device(0)
     n = len(meshes)
     ctx = V.Context(meshes, precision=V.PREC_MIXED)
     stream = torch.cuda.Stream()
@@ -312,7 +366,9 @@ def main_batch(a):
             ctx.graph_launch(vels, t, dt)
             t = t + dt
         torch.cuda.synchronize()
-        clk = ClockSampler(0)
+        if dist is not None:
+            dist.barrier()
+        clk = ClockSampler(local)
         clk.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -322,18 +378,28 @@ def main_batch(a):
             t = t + dt
         e1.record(stream)
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1)
+        ms = over_ranks(dist, e0.elapsed_time(e1), "max")
         st = ctx.stats()
-    line = {"metric": METRIC, "value": cells * a.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+    total_cells = over_ranks(dist, cells, "sum")
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": total_cells * a.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"batch of {n} distorted triangulated-hex grids (side log-uniform "
-                                   "16..96, jitter 0.3h, non-convex cells), ellipsoids, uniform "
-                                   "translation, one CUDA graph per step",
-                       "cells": cells, "faces": int(ctx.n_face), "grids": n,
-                       "sides": [int(x) for x in sides], "autotuned_blocks": list(tuned)},
+            "config": {"workload": f"batch of {len(all_sides)} distorted triangulated-hex grids (side "
+                                   "log-uniform 16..96, jitter 0.3h, non-convex cells), ellipsoids, "
+                                   "uniform translation, one CUDA graph per step",
+                       "cells": int(total_cells), "grids": len(all_sides),
+                       "rank0": {"grids": n, "cells": cells, "faces": int(ctx.n_face),
+                                 "sides": [int(x) for x in sides], "autotuned_blocks": list(tuned)},
+                       "parallelism": f"grids sharded over {ws} rank(s) by cells"},
             "gpu_launches": 6 * a.steps,
             "band": {"interfacial_cells": st["n_interfacial"], "active_faces": st["n_active_faces"],
                      "truncations_last_step": st["n_truncations"], "overflow": st["n_overflow"]},
@@ -344,8 +410,10 @@ def main_batch(a):
 
 def main_tets(a):
     """64^3 cubes x 6 jittered Kuhn tets (1.57 M cells), sphere r = 0.15 at
-    (0.5, 0.75, 0.5), rigid rotation, CFL 0.4; mixed beside FP64."""
+    (0.5, 0.75, 0.5), rigid rotation, CFL 0.4; mixed beside FP64. One
+    replica per rank."""
     import torch
+    ws, rank, local, dist = dist_init()
     from paper_2111_01524_gb300 import build as B
     from paper_2111_01524_gb300 import vof as V
     B.build()
@@ -363,6 +431,10 @@ def main_tets(a):
             ctx.step(vel, t, dt)
             t += dt
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clk = ClockSampler(local)
+        clk.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -372,15 +444,24 @@ def main_tets(a):
             t += dt
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        res[name] = {"value": m["n_cell"] * a.steps / (ms * 1e-3), "ms_per_step": ms / a.steps,
-                     "F": ctx.get_fraction(), "stats": ctx.stats()}
-    line = {"metric": METRIC, "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": 1,
+        if dist is not None:
+            dist.barrier()
+        clocks = clk.stop()
+        ms = over_ranks(dist, e0.elapsed_time(e1), "max")
+        res[name] = {"value": ws * m["n_cell"] * a.steps / (ms * 1e-3), "ms_per_step": ms / a.steps,
+                     "F": ctx.get_fraction(), "stats": ctx.stats(), "clocks": clocks}
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["mixed"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": "64^3 x 6 jittered Kuhn tets, sphere r=0.15 at (0.5,0.75,0.5), "
-                                   "rigid rotation, CFL 0.4", "cells": int(m["n_cell"])},
+                                   "rigid rotation, CFL 0.4", "cells": int(m["n_cell"]),
+                       "parallelism": f"replicas x{ws}"},
+            "gpu_launches": 6 * a.steps, "clocks": res["mixed"]["clocks"],
             "fp64_path": {"value": res["fp64"]["value"],
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
                           "max_abs_F_diff_mixed_vs_fp64":
@@ -409,6 +490,8 @@ def main_serve(a):
     rotation / translation, N ~ U{10..200} steps; admission by 80% of free
     device memory; mixed precision."""
     import multiprocessing as mp
+    from paper_2111_01524_gb300 import shard
+    ws, rank, local = dist_env()
     rng = np.random.default_rng(20211107)
     n = a.requests
     specs = []
@@ -419,35 +502,69 @@ def main_serve(a):
             side = max(8, side // 2)  # 6 tets per cube: comparable cell counts
         body = "sphere" if rng.random() < 0.5 else "ellipsoid"
         specs.append((kind, side, 20211107 + rid, body, tuple(rng.uniform(0.1, 0.25, 3))))
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        inputs = pool.map(_make_request_inputs, specs)
-    import torch
-    from paper_2111_01524_gb300 import build as B
     from paper_2111_01524_gb300 import serve as S
-    B.build()
-    torch.cuda.set_device(0)
     fields = [I.deformation(3.0), I.rotation(2 * np.pi)]
 
-    def make(rid, r):
-        m, F = inputs[rid]
+    # the trace (arrival times, fields, step counts) first, without meshes
+    def make_stub(rid, r):
         which = r.integers(3)
         vel = fields[which] if which < 2 else I.translation(tuple(r.uniform(-1, 1, 3)))
         cfl = 0.4 if specs[rid][0] == "tet" else 0.5
-        return S.Request(rid=rid, mesh=m, F0=F, vel=vel, n_steps=int(r.integers(10, 201)), cfl=cfl)
+        return S.Request(rid=rid, mesh=None, F0=None, vel=vel, n_steps=int(r.integers(10, 201)),
+                         cfl=cfl)
 
-    reqs = S.poisson_trace(n, 200.0, 20211108, make)
+    trace = S.poisson_trace(n, 200.0, 20211108, make_stub)
+    # requests are independent: each rank serves a share balanced by
+    # estimated cell-steps (cells: side^3 for hex, 6 side^3 for tets)
+    est = [(specs[r.rid][1] ** 3) * (6 if specs[r.rid][0] == "tet" else 1) * r.n_steps
+           for r in trace]
+    mine = shard.balance(est, ws)[rank]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1, len(mine)))) as pool:
+        built = pool.map(_make_request_inputs, [specs[i] for i in mine])
+    reqs = []
+    for i, (m, F) in zip(mine, built):
+        r = trace[i]
+        r.mesh, r.F0 = m, F
+        reqs.append(r)
+    import torch
+    ws, rank, local, dist = dist_init()
+    from paper_2111_01524_gb300 import build as B
+    B.build()
     backend = S.DeviceBackend(precision_mixed=True, use_graphs=True)
     srv = S.Server(backend, budget_fraction=0.8)
+    if dist is not None:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
     st = srv.run(reqs)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clk.stop()
     sm = st.summary()
-    line = {"metric": METRIC, "value": sm["cell_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": int(sum(r.n_steps for r in reqs)), "warmup": 0,
-            "p50_ms": sm["p50_s"] * 1e3, "p99_ms": sm["p99_s"] * 1e3,
+    wall = over_ranks(dist, st.wall, "max")
+    cell_steps = over_ranks(dist, st.cell_steps, "sum")
+    lat = list(st.latencies)
+    if dist is not None:
+        allat = [None] * ws
+        dist.all_gather_object(allat, lat)
+        lat = [x for part in allat for x in part]
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    lat = np.asarray(lat) if lat else np.zeros(1)
+    line = {"metric": METRIC, "value": cell_steps / wall, "unit": UNIT, "n_gpus": ws,
+            "steps": int(sum(r.n_steps for r in trace)), "warmup": 0,
+            "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+            "p99_ms": float(np.percentile(lat, 99)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": f"Poisson stream, {n} requests at 200 req/s, hex/jittered-tet "
                                    "grids of side log-uniform 24..64, N ~ U{10..200} steps",
-                       "requests": n, "budget_bytes": srv.budget},
+                       "requests": n, "budget_bytes": srv.budget,
+                       "parallelism": f"requests sharded over {ws} rank(s) by cell-steps"},
+            # per request: the first reconstruction (3 kernels), then 6 per step
+            "gpu_launches": int(sum(3 + 6 * r.n_steps for r in reqs)), "clocks": clocks,
             "serve": sm}
     print(json.dumps(line))
     return 0

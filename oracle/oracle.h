@@ -3,7 +3,7 @@
  * INFRASTRUCTURE ONLY.
  *
  * A plain, slow FP64 CPU implementation of what one time step computes, used
- * by the tests, the smoke check and the CPU-baseline timing to judge the CUDA
+ * by the tests, the smoke check and the CPU-baseline timing to check the CUDA
  * library. Nothing in the product path may call it. It shares no code with
  * the CUDA path. Every function names the passage of the paper it follows.
  *

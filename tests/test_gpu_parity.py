@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
 
 Tolerances: connectivity, candidate lists and tags bit-exact; FP64 path F
-within 1e-12 absolute (spec bound), per-face volumes within 1e-12 of
-the cell volume; mixed path F within 1e-6 (spec bound).
+within 1e-12 absolute, per-face volumes within 1e-12 of the cell volume;
+mixed path F within 1e-6 absolute.
 """
 import numpy as np
 import pytest
