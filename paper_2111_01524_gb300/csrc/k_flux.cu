@@ -76,7 +76,10 @@ struct __align__(16) Poly {
   int rfirst[NV];            // first record of each inside vertex (-1: none)
   uint8_t newid[NV];
   G pl[NF + 1][4];           // half-spaces of the current candidate cell; [NF]: PLIC
+  int32_t cand[sizeof(G) == 4 ? 128 : 1];  // candidate cells met by the box of P (FP32)
 };
+template <typename G>
+__host__ __device__ constexpr int cand_cap() { return sizeof(G) == 4 ? 128 : 0; }
 
 template <typename T>
 __device__ __forceinline__ T wsum(T v) {
@@ -775,68 +778,113 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
   return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err, vout);
 }
 
-// sum of vol(P ∩ cell k ∩ X_k) over the candidate cells: owner, its node
-// neighbours, then the neighbour and its node neighbours not seen yet
-// (Sec. 2.2: donating regions of several cells), filtered by the local
-// bounding box of the polyhedron, in face-local units.
-// mode 0: the fluid parts (full and interfacial cells); mode 1: the same,
-// and the empty parts of the interfacial cells added to *gas from the same
-// clipped polyhedra; mode 2: the empty cells only (all of each).
-// *whole = 1 (2) when P lies inside the fluid (empty) part of one cell;
-// *saw_empty (modes 0, 1): an empty cell met the bounding box of P.
+// one chunk of up to 32 candidate cells of face j (pass 0: the owner's node
+// neighbours and the owner; pass 1: the neighbour's and the neighbour, minus
+// those already seen), filtered by the local bounding box of the
+// polyhedron; returns the lane's cell (-1: none) and its tag
+template <typename G>
+__device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
+                                         const FaceFrame<G>& fr, int own, int64_t a0, int na, int pass,
+                                         int c0, int64_t b0, int nb, int idx, int8_t& tk) {
+  const int64_t nc = M.nc;
+  int k = -1;
+  if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
+  if (k >= 0 && pass == 1 && (k == own || sorted_contains(M.nb + a0, na, k))) k = -1;
+  tk = 0;
+  if (k >= 0) {
+    const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
+    const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
+    const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
+    if (!(fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy && fr.hi[2] > lz &&
+          fr.lo[2] < hz))
+      k = -1;
+    else
+      tk = S.tc[k];
+  }
+  return k;
+}
+
+// V_F of face j in face-local units (Sec. 2.2): the candidate cells (owner,
+// its node neighbours, then the neighbour and its node neighbours not seen
+// yet: donating regions of several cells) met by the bounding box of P are
+// listed first, with their tags. The fluid form sums vol(P ∩ cell ∩ fluid)
+// over the full and interfacial cells. The complement form (FP32 only, an
+// interior face, where P lies in the candidate cells at CFL <= 1 so that
+// fluid + empty = V_d) gives V_d minus the sum of the empty parts over the
+// interfacial and empty cells, so that the FP32 error scales with the empty
+// part. The form is chosen from the tags so that a polyhedron that lies
+// only in fluid gives exactly V_d and one that lies only in empty space
+// exactly 0: complement when no empty cell is met, fluid when no full cell
+// is, otherwise by the donating cell's F. Returns V_F / L^3; *whole: P lies
+// in the fluid (1) or empty (2) part of one cell (V_F = V_d or 0 exactly).
 template <typename G>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
-                              int mode, G* gas, int* whole, bool* saw_empty,
-                              unsigned long long& n_trunc) {
-  const int64_t nc = M.nc;
+                              int* whole, bool* complement, unsigned long long& n_trunc) {
   const int own = M.own[j], nbr = M.nbr[j];
   const int64_t a0 = M.nb_ptr[own];
   const int na = (int)(M.nb_ptr[own + 1] - a0);
-  G v = G(0);
+  constexpr int cap = cand_cap<G>();
+  int n = cap + 1;  // FP64: the fluid form, no list (the cells are scanned once)
+  bool neg = false, pos = false;
+  if (sizeof(G) == 4) n = 0;
+  for (int pass = 0; sizeof(G) == 4 && pass < 2; ++pass) {
+    const int c0 = pass == 0 ? own : nbr;
+    if (c0 < 0) break;
+    const int64_t b0 = M.nb_ptr[c0];
+    const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
+    for (int base = 0; base < nb; base += 32) {
+      int8_t tk;
+      const int k = candidate(M, Gv, S, fr, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
+      if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
+      if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
+      const int at = n + __popc(bal & ((1u << lane) - 1u));
+      if (k >= 0 && at < cap) P.cand[at] = k;
+      n += __popc(bal);
+    }
+  }
+  __syncwarp();
+  bool comp = false;
+  if (sizeof(G) == 4 && nbr >= 0) {
+    if (!neg && pos) comp = true;
+    else if (neg && !pos) comp = false;
+    else comp = S.F[S.Vd[j] > 0.0 ? own : nbr] > 0.5;
+  }
+  *complement = comp;
   *whole = 0;
-  *saw_empty = false;
+  // the cells the form needs: fluid form tags 1 and 0, complement 0 and -1
+  const int8_t skip = comp ? 1 : -1;
+  G v = G(0);
+  if (n <= cap) {
+    for (int i = 0; i < n; ++i) {
+      const int kk = P.cand[i];
+      if (S.tc[kk] == skip) continue;
+      int w = 0;
+      v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w, nullptr);
+      ++n_trunc;
+      if (w) { *whole = comp ? 2 : 1; return G(0); }  // no other cell meets P
+    }
+    return v;
+  }
+  // more candidates than the list holds: the same cells, scanned again
   for (int pass = 0; pass < 2; ++pass) {
     const int c0 = pass == 0 ? own : nbr;
     if (c0 < 0) break;
     const int64_t b0 = M.nb_ptr[c0];
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
     for (int base = 0; base < nb; base += 32) {
-      const int idx = base + lane;
-      int k = -1;
-      if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
-      bool keep = k >= 0;
-      if (keep && pass == 1) keep = !(k == own || sorted_contains(M.nb + a0, na, k));
-      int8_t tk = 0;
-      if (keep) {
-        tk = S.tc[k];
-        if (mode == 2 && tk != -1) keep = false;
-      }
-      if (keep) {
-        const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
-        const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
-        const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
-        keep = fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy &&
-               fr.hi[2] > lz && fr.lo[2] < hz;
-      }
-      if (mode != 2) {
-        // (warp-uniform: it decides whether the warp sweeps the empty cells)
-        if (__any_sync(GVOF_FULL, keep && tk == -1)) *saw_empty = true;
-        keep = keep && tk != -1;
-      }
-      unsigned bal = __ballot_sync(GVOF_FULL, keep);
+      int8_t tk;
+      const int k = candidate(M, Gv, S, fr, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      unsigned bal = __ballot_sync(GVOF_FULL, k >= 0 && tk != skip);
       while (bal) {
         const int src = __ffs(bal) - 1;
         bal &= bal - 1u;
         const int kk = __shfl_sync(GVOF_FULL, k, src);
         int w = 0;
-        G vo = G(0);
-        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, mode == 2, &w,
-                                 mode == 1 ? &vo : nullptr);
+        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w, nullptr);
         ++n_trunc;
-        if (mode == 2 && w) w = 2;
-        if (w) { *whole = w; return w == 1 ? Vl : G(0); }  // no other cell meets P
-        if (mode == 1) *gas += vo;
+        if (w) { *whole = comp ? 2 : 1; return G(0); }
       }
     }
   }
@@ -872,33 +920,13 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     unsigned err = 0u;
     const G Vl = (G)S.Vd[j] * (fr.sc * fr.sc * fr.sc);  // volume of P, local units
     const G L3 = fr.L * fr.L * fr.L;
-    // FP64: the fluid part. FP32: the fluid part and the empty part of the
-    // interfacial cells from the same clipped polyhedra; when P is mostly
-    // fluid, V_F = V_d - (empty part of P), so that the FP32 error scales
-    // with the empty part (P lies in the candidate cells for an interior
-    // face at CFL <= 1, so fluid + empty = V_d), the empty cells' share
-    // added by a second sweep over those cells only
-    const int mode = sizeof(G) == 4 ? 1 : 0;
-    G ve = G(0);
     int wh = 0;
-    bool saw_empty = false;
-    const G vf = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, mode, &ve, &wh, &saw_empty,
-                                     n_trunc);
+    bool comp = false;
+    const G v = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, &wh, &comp, n_trunc);
     double VFj;
-    if (wh == 1) {
-      VFj = S.Vd[j];  // P inside the fluid of one cell: exactly V_d
-    } else if (wh == 2) {
-      VFj = 0.0;      // P inside the empty part of one cell
-    } else if (mode == 1 && M.nbr[j] >= 0 && fabs(vf) > G(0.5) * fabs(Vl)) {
-      if (saw_empty) {
-        G unused = G(0);
-        bool s2 = false;
-        ve += sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, 2, &unused, &wh, &s2, n_trunc);
-      }
-      VFj = wh == 2 ? 0.0 : S.Vd[j] - (double)(ve * L3);
-    } else {
-      VFj = (double)(vf * L3);
-    }
+    if (wh == 1) VFj = S.Vd[j];  // P inside the fluid of one cell: exactly V_d
+    else if (wh == 2) VFj = 0.0;  // P inside the empty part of one cell
+    else VFj = comp ? S.Vd[j] - (double)(v * L3) : (double)(v * L3);
     if (err) ++n_over;
     if (lane == 0) S.VF[j] = VFj;
   }
