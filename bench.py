@@ -211,8 +211,8 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
     hbm_bytes = {
         "cell_tags": nc * (8 + 1),
         "node_tags": nv * (8 + 1) + 8 * nc * 4 + nc * 8,
-        "face_sweep": nf * (8 + 16 + 8 + 1 + 8 + 8) + nv,
-        "update": nc * (8 + 24 + 16 + 8) + nf * 16,
+        "face_sweep": nf * (8 + 16 + 1) + nv,
+        "update": nc * (8 + 24 + 16 + 8) + nf * (8 + 1),
     }
     if name in hbm_bytes:
         b = hbm_bytes[name]

@@ -678,6 +678,7 @@ vof_status vof_get_tags(vof_ctx* c, int8_t* tv, int8_t* tf, int8_t* tc, int mem,
 vof_status vof_get_face_flux(vof_ctx* c, double* Vd, double* VF, int mem, void* stream) {
   if (!c) return fail(VOF_EINVAL, "NULL context");
   cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_face_flux_export(c, s));
   if (Vd) CK(cudaMemcpyAsync(Vd, c->Vd, sizeof(double) * c->nf, kind_from_dev(mem), s));
   if (VF) CK(cudaMemcpyAsync(VF, c->VF, sizeof(double) * c->nf, kind_from_dev(mem), s));
   if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));

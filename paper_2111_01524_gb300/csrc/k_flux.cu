@@ -568,16 +568,11 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
 // the volume of P itself). Vertices within tol of a plane count as on its
 // inner side; tol is a few ulps of the face-local unit, so the volume this
 // neglects is of the order of the rounding of the plane itself.
-// Two-sided (vout != nullptr, with the PLIC plane, FP32 only): *vout also
-// receives vol(P ∩ K ∩ X^c), both cut from the same clipped polyhedron, and
-// *whole = 2 when P lies inside K ∩ X^c.
 template <typename G>
 __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
-                                          G Vl, int lane, unsigned& err, int* whole, G* vout) {
+                                          G Vl, int lane, unsigned& err, int* whole) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
   *whole = 0;
-  const bool two = sizeof(G) == 4 && vout != nullptr && has_plic;
-  if (vout) *vout = G(0);
   const int nvb = 2 * fr.I + 1;
   const bool hv = lane < nvb;
   const G bx = hv ? P.bx[lane] : G(0), by = hv ? P.by[lane] : G(0), bz = hv ? P.bz[lane] : G(0);
@@ -589,20 +584,15 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
     if (in == 0u && out != 0u) return G(0);  // P on the outer side of a plane
     if (out) cut |= 1u << g;
   }
-  int pst = 0;  // PLIC: 0 P on the X side, 1 cut, 2 P on the other side
+  bool plic = false;
   if (has_plic) {
     const G ph = P.pl[NF][0] * bx + P.pl[NF][1] * by + P.pl[NF][2] * bz + P.pl[NF][3];
     const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
     const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
-    pst = (in == 0u && out != 0u) ? 2 : (out != 0u ? 1 : 0);
+    if (in == 0u && out != 0u) return G(0);  // P on the other side of the interface
+    plic = out != 0u;
   }
-  if (pst == 2 && !two) return G(0);  // P on the other side of the interface
-  const bool plic = pst == 1;
-  if (cut == 0u && !plic) {
-    if (pst == 2) { *whole = 2; *vout = Vl; return G(0); }  // P inside K ∩ X^c
-    *whole = 1;
-    return Vl;  // P inside K ∩ X
-  }
+  if (cut == 0u && !plic) { *whole = 1; return Vl; }  // P inside K ∩ X
   int last;
   if (plic) {
     last = NF;
@@ -625,11 +615,7 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
     res = clip(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane, err);
     return res == 2 ? G(0) : volume(P, st, lane);
   }
-  const G v = volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
-  if (!two) return v;
-  if (pst == 2) { *vout = v; return G(0); }
-  if (pst == 1) *vout = volume_cut(P, st, -P.pl[NF][0], -P.pl[NF][1], -P.pl[NF][2], -P.pl[NF][3], lane);
-  return v;
+  return volume_cut(P, st, P.pl[last][0], P.pl[last][1], P.pl[last][2], P.pl[last][3], lane);
 }
 
 // vol(P ∩ K ∩ X) for a non-convex cell K: signed sum over the tetrahedra
@@ -639,7 +625,7 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
 template <typename G>
 __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>& Gv, int k,
                                              int64_t c0, int nfk, bool tag0, const FaceFrame<G>& fr,
-                                             G Vl, Poly<G>& P, int lane, unsigned& err, G* vout) {
+                                             G Vl, Poly<G>& P, int lane, unsigned& err) {
   const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
           rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
   // fan triangles per face, and their running count (lanes over faces)
@@ -723,9 +709,7 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
       }
       __syncwarp();
       int w = 0;
-      G vo = G(0);
-      v += sg * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w, vout ? &vo : nullptr);
-      if (vout) *vout += sg * vo;
+      v += sg * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w);
     }
   }
   return v;
@@ -738,15 +722,12 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
 // is the intersection of its face half-spaces; a non-convex cell is the
 // signed sum of the tetrahedra that join its centroid to the fan triangles of
 // its faces (winding-number decomposition, valid for any closed cell).
-// vout != nullptr (FP32, empty_side = false): an interfacial cell also gives
-// its empty part in *vout (truncate_planes, two-sided).
 template <typename G>
 __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
                                            const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
                                            Poly<G>& P, int lane, unsigned& err, bool empty_side,
-                                           int* whole, G* vout) {
+                                           int* whole) {
   *whole = 0;
-  if (vout) *vout = G(0);
   const int8_t tk = S.tc[k];
   if (tk == (empty_side ? 1 : -1)) return G(0);
   const bool tag0 = tk == 0;
@@ -773,9 +754,9 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
                         oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
     }
     __syncwarp();
-    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole, vout);
+    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole);
   }
-  return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err, vout);
+  return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
 }
 
 // one chunk of up to 32 candidate cells of face j (pass 0: the owner's node
@@ -819,8 +800,9 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
 // in the fluid (1) or empty (2) part of one cell (V_F = V_d or 0 exactly).
 template <typename G>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
-                              const FaceFrame<G>& fr, G Vl, Poly<G>& P, int lane, unsigned& err,
-                              int* whole, bool* complement, unsigned long long& n_trunc) {
+                              const FaceFrame<G>& fr, double Vd, G Vl, Poly<G>& P, int lane,
+                              unsigned& err, int* whole, bool* complement,
+                              unsigned long long& n_trunc) {
   const int own = M.own[j], nbr = M.nbr[j];
   const int64_t a0 = M.nb_ptr[own];
   const int na = (int)(M.nb_ptr[own + 1] - a0);
@@ -849,7 +831,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
   if (sizeof(G) == 4 && nbr >= 0) {
     if (!neg && pos) comp = true;
     else if (neg && !pos) comp = false;
-    else comp = S.F[S.Vd[j] > 0.0 ? own : nbr] > 0.5;
+    else comp = S.F[Vd > 0.0 ? own : nbr] > 0.5;
   }
   *complement = comp;
   *whole = 0;
@@ -861,7 +843,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
       const int kk = P.cand[i];
       if (S.tc[kk] == skip) continue;
       int w = 0;
-      v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w, nullptr);
+      v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
       ++n_trunc;
       if (w) { *whole = comp ? 2 : 1; return G(0); }  // no other cell meets P
     }
@@ -882,7 +864,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
         bal &= bal - 1u;
         const int kk = __shfl_sync(GVOF_FULL, k, src);
         int w = 0;
-        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w, nullptr);
+        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
         ++n_trunc;
         if (w) { *whole = comp ? 2 : 1; return G(0); }
       }
@@ -910,7 +892,8 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
       if (lane < nw) ((double*)&wgp[wib])[lane] = ((const double*)&S.gp[gi])[lane];
       __syncwarp();
     }
-    if (!build_fmfpa<G>(M, Gv, wgp[wib], j, S.Vd[j], P, fr, lane)) {
+    const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
+    if (!build_fmfpa<G>(M, Gv, wgp[wib], j, Vd, P, fr, lane)) {
       if (lane == 0) S.VF[j] = 0.0;
       ++n_over;
       continue;
@@ -918,15 +901,15 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     n_deg += fr.degenerate;
     n_edge += fr.edgeon;
     unsigned err = 0u;
-    const G Vl = (G)S.Vd[j] * (fr.sc * fr.sc * fr.sc);  // volume of P, local units
+    const G Vl = (G)Vd * (fr.sc * fr.sc * fr.sc);  // volume of P, local units
     const G L3 = fr.L * fr.L * fr.L;
     int wh = 0;
     bool comp = false;
-    const G v = sweep_candidates<G>(M, Gv, S, j, fr, Vl, P, lane, err, &wh, &comp, n_trunc);
+    const G v = sweep_candidates<G>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp, n_trunc);
     double VFj;
-    if (wh == 1) VFj = S.Vd[j];  // P inside the fluid of one cell: exactly V_d
+    if (wh == 1) VFj = Vd;  // P inside the fluid of one cell: exactly V_d
     else if (wh == 2) VFj = 0.0;  // P inside the empty part of one cell
-    else VFj = comp ? S.Vd[j] - (double)(v * L3) : (double)(v * L3);
+    else VFj = comp ? Vd - (double)(v * L3) : (double)(v * L3);
     if (err) ++n_over;
     if (lane == 0) S.VF[j] = VFj;
   }

@@ -95,10 +95,8 @@ __global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv) 
 // face sweep: face tags from node tags, V_d = g(t+dt/2) (u0.n) A dt,
 // V_F = 0 on tag -1 faces, V_F = V_d on tag 1 faces (no geometry, Sec. 3.3);
 // tag 0 faces are appended to the active list for the flux kernel
-__global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate,
-                             const GridParam* gp, int8_t* tf, double* Vd, double* VF,
-                             int32_t* afaces, unsigned long long* cnt) {
-  const double gdt1 = gp[0].gdt;
+__global__ void k_face_sweep(DevMesh M, const int8_t* tv, int8_t* tf, int32_t* afaces,
+                             unsigned long long* cnt) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < M.nf; base += stride) {
     int64_t f = base + threadIdx.x;
@@ -113,12 +111,7 @@ __global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate,
         allp &= (x == 1);
       }
       t = allm ? -1 : (allp ? 1 : 0);
-      const double gdt = M.n_grids == 1 ? gdt1 : gp[grid_of(M.face_off, M.n_grids, f)].gdt;
-      double vd = srate[f] * gdt;
       tf[f] = t;
-      Vd[f] = vd;
-      if (t == -1) VF[f] = 0.0;
-      else if (t == 1) VF[f] = vd;
     }
     warp_append(in && t == 0, (int32_t)f, afaces, cnt + kNAfaces);
   }
@@ -126,28 +119,64 @@ __global__ void k_face_sweep(DevMesh M, const int8_t* tv, const double* srate,
 
 // Eq. fnext and the clip of Sec. 2.2; red[] receives per-block partial
 // E_bound maxima (before the clip)
-__global__ void k_update(DevMesh M, double* F, const double* Vd, const double* VF,
-                         double* red) {
+// V_F of face f: the shortcut of its tag (Sec. 3.3: 0 for tag -1, V_d for
+// tag 1), else the flux kernel's value
+__device__ __forceinline__ double face_vf(int8_t t, double vd, const double* VF, int f) {
+  return t == 0 ? VF[f] : (t == 1 ? vd : 0.0);
+}
+
+__device__ __forceinline__ double grid_gdt(const DevMesh& M, const GridParam* gp, int f) {
+  return M.n_grids == 1 ? gp[0].gdt : gp[grid_of(M.face_off, M.n_grids, f)].gdt;
+}
+
+// V_d = (u0.n) A g dt of each face and V_F from the face tags, written in
+// place of the flux kernel's per-face array (read-back of the face volumes)
+__global__ void k_face_flux_export(DevMesh M, const int8_t* tf, const double* srate,
+                                   const GridParam* gp, double* Vd, double* VF) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M.nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const double vd = srate[f] * grid_gdt(M, gp, (int)f);
+    Vd[f] = vd;
+    const int8_t t = tf[f];
+    if (t != 0) VF[f] = t == 1 ? vd : 0.0;
+  }
+}
+
+// Eq. fnext per cell; V_d of a face is formed here from its rate and the
+// grid's g dt, V_F from its tag (so the face sweep stores neither)
+__global__ void k_update(DevMesh M, double* F, const int8_t* tf, const double* srate,
+                         const GridParam* gp, const double* VF, double* red) {
   double eb = 0.0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
     const double F0 = F[c];
+    // the faces of a cell belong to its grid
+    double gdt = gp[0].gdt;
+    if (M.n_grids > 1 && q1 > q0) {
+      const int fs0 = M.cf[q0];
+      gdt = gp[grid_of(M.face_off, M.n_grids, fs0 >= 0 ? fs0 : ~fs0)].gdt;
+    }
     // an empty cell that no fluid enters stays exactly empty: Eq. fnext
     // gives 0 for F = 0 and V_FT = 0 whatever V_dT (no FP64 work needed)
     if (is_zero(F0)) {
       bool none = true;
       for (int64_t q = q0; q < q1 && none; ++q) {
         const int fs = M.cf[q];
-        none = is_zero(VF[fs >= 0 ? fs : ~fs]);
+        const int f = fs >= 0 ? fs : ~fs;
+        const int8_t t = tf[f];
+        none = t == -1 || is_zero(t == 0 ? VF[f] : srate[f] * gdt);
       }
       if (none) continue;
     }
     double vdt = 0.0, vft = 0.0;
     for (int64_t q = q0; q < q1; ++q) {
-      int fs = M.cf[q];
-      if (fs >= 0) { vdt += Vd[fs]; vft += VF[fs]; }
-      else { vdt -= Vd[~fs]; vft -= VF[~fs]; }
+      const int fs = M.cf[q];
+      const int f = fs >= 0 ? fs : ~fs;
+      const double vd = srate[f] * gdt;
+      const double vf = face_vf(tf[f], vd, VF, f);
+      if (fs >= 0) { vdt += vd; vft += vf; }
+      else { vdt -= vd; vft -= vf; }
     }
     double V = M.cvol[c];
     double h = vdt / (2.0 * V);
@@ -223,13 +252,17 @@ cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s) {
   static_assert(kNAfaces + 1 == kNTrunc && kNTrunc + 3 == kNEdgeOn, "counter layout");
   cudaError_t e = cudaMemsetAsync(c->cnt + kNAfaces, 0, 5 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->srate, c->gp_d,
-                                                    c->tf, c->Vd, c->VF, c->afaces, c->cnt);
+  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->tf, c->afaces, c->cnt);
+  return cudaGetLastError();
+}
+cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s) {
+  k_face_flux_export<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tf, c->srate, c->gp_d,
+                                                          c->Vd, c->VF);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s) {
-  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->Vd, c->VF, c->red);
+  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->tf, c->srate, c->gp_d, c->VF, c->red);
   return cudaGetLastError();
 }
 

@@ -340,6 +340,7 @@ cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s);
+cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s);  // writes red[0], red[1]
 // reconstruction (k_recon.cu)
 cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);
