@@ -640,6 +640,9 @@ def main():
     g = ctx.geometry()
     vol0 = float((g["cell_vol"] * F0).sum())
     vol_rel = abs(stats["volume"] - vol0) / vol0
+    # the library's bookkeeping: what clip, cut-off and boundary removed
+    book_rel = abs(stats["volume"] - (vol0 - stats["clip_loss"] - stats["cutoff_loss"]
+                                      - stats["boundary_outflow"])) / vol0
 
     fp64 = None
     if not a.no_fp64 and prec == V.PREC_MIXED:
@@ -727,6 +730,8 @@ def main():
                      "truncations_last_step": stats["n_truncations"],
                      "overflow": stats["n_overflow"]},
             "volume_rel_change": vol_rel,
+            "volume_bookkeeping_rel_residual": book_rel,
+            "clip_loss_rel": stats["clip_loss"] / vol0,
             "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
             "cpu_baseline": cpu,
         }

@@ -100,6 +100,14 @@ typedef struct {
   int64_t n_edgeon;       /* FMFPA faces whose back-traced loop was edge-on */
   double volume;          /* sum over cells of V F (FP64, fixed-order) */
   double ebound;          /* E_bound^Linf of Sec. 4.2 before the clip of the last advect */
+  /* Volume bookkeeping since the last vof_set_fraction (Sec. 2.2, Eq. fnext
+   * and the final clip; Sec. 2.1 cut-off), each summed in a fixed order:
+   * volume == V_0 - clip_loss - cutoff_loss - boundary_outflow, V_0 the
+   * volume of the F that was set, up to rounding (the update conserves the
+   * fluid that the face volumes move; only these three terms change it). */
+  double clip_loss;         /* sum over cells and steps of V (F_unclipped - F) */
+  double cutoff_loss;       /* sum of V (F - F_cut) removed by the cut-off to 0 / 1 */
+  double boundary_outflow;  /* sum of V_F over boundary faces (fluid leaving the domain) */
 } vof_stats;
 
 /* Create a context: copies the mesh to the device and builds its derived

@@ -47,7 +47,7 @@ void free_all(vof_ctx* c) {
                   c->fnz32, c->fa32, c->cvol32, c->nx32, c->ny32, c->nz32, c->C32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* ptrs2[] = {c->face_off_d, c->gp_d, c->umax_d};
+  void* ptrs2[] = {c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -289,6 +289,16 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
   CKI(dalloc(c, &c->Vd, nf)); CKI(dalloc(c, &c->VF, nf)); CKI(dalloc(c, &c->srate, nf));
   CKI(dalloc(c, &c->icells, nc)); CKI(dalloc(c, &c->afaces, nf));
   CKI(dalloc(c, &c->cnt, kNCnt)); CKI(dalloc(c, &c->red, kRedSlots));
+  CKI(dalloc(c, &c->acc, kNAcc * kAccSlots));
+  {
+    std::vector<int32_t> bf;
+    for (int64_t f = 0; f < nf; ++f)
+      if (mesh->neighbour[f] < 0) bf.push_back((int32_t)f);
+    c->nbf = (int64_t)bf.size();
+    CKI(dalloc(c, &c->bfaces, c->nbf > 0 ? c->nbf : 1));
+    if (c->nbf > 0)
+      CKI(cudaMemcpy(c->bfaces, bf.data(), sizeof(int32_t) * c->nbf, cudaMemcpyHostToDevice));
+  }
   if (o.precision == VOF_PREC_MIXED) {
     CKI(dalloc(c, &c->vx2, nv)); CKI(dalloc(c, &c->vy2, nv)); CKI(dalloc(c, &c->vz2, nv));
     CKI(dalloc(c, &c->fcx2, nf)); CKI(dalloc(c, &c->fcy2, nf)); CKI(dalloc(c, &c->fcz2, nf));
@@ -331,6 +341,7 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
   CKI(cudaMemcpy(c->nb, hc.nb.data(), sizeof(int32_t) * c->nnb, cudaMemcpyHostToDevice));
   CKI(cudaMemset(c->cnt, 0, sizeof(unsigned long long) * kNCnt));
   CKI(cudaMemset(c->red, 0, sizeof(double) * kRedSlots));
+  CKI(cudaMemset(c->acc, 0, sizeof(double) * kNAcc * kAccSlots));
   CKI(cudaMemset(c->F, 0, sizeof(double) * nc));
   CKI(cudaMemset(c->nx, 0, sizeof(double) * nc));
   CKI(cudaMemset(c->ny, 0, sizeof(double) * nc));
@@ -456,6 +467,8 @@ vof_status vof_set_fraction(vof_ctx* c, const double* F, int mem, void* stream) 
   if (!c || !F) return fail(VOF_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(c->F, F, sizeof(double) * c->nc, kind_to_dev(mem), s));
+  // the volume bookkeeping starts from this F
+  CK(cudaMemsetAsync(c->acc, 0, sizeof(double) * kNAcc * kAccSlots, s));
   if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
   c->recon_valid = false;
   return VOF_OK;
@@ -782,7 +795,7 @@ vof_status vof_get_stats(vof_ctx* c, vof_stats* out, void* stream) {
   unsigned long long* h = (unsigned long long*)c->pinned;
   double* hd = (double*)((char*)c->pinned + 1024);
   CK(cudaMemcpyAsync(h, c->cnt, sizeof(unsigned long long) * kNCnt, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hd, c->red + kRedSlots - 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hd, c->red + kRedSlots - 5, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out->n_interfacial = (int64_t)h[kNIcells];
   out->n_active_faces = (int64_t)h[kNAfaces];
@@ -790,8 +803,11 @@ vof_status vof_get_stats(vof_ctx* c, vof_stats* out, void* stream) {
   out->n_overflow = (int64_t)h[kNOverflow];
   out->n_degenerate = (int64_t)h[kNDegen];
   out->n_edgeon = (int64_t)h[kNEdgeOn];
-  out->volume = hd[0];
-  out->ebound = hd[1];
+  out->clip_loss = hd[kAccClip];
+  out->boundary_outflow = hd[kAccBoundary];
+  out->cutoff_loss = hd[kAccCutoff];
+  out->volume = hd[3];
+  out->ebound = hd[4];
   return VOF_OK;
 }
 

@@ -35,26 +35,51 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t item, int32_t* li
 constexpr long long kOneBits = 0x3FF0000000000000LL;
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+
+// sum over the block in a fixed order (valid in thread 0); every thread of the
+// block must call it
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sb[32];
+  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GVOF_FULL, v, o);
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sb[i];
+  return t;
+}
 __device__ __forceinline__ bool is_one(double x) { return dbits(x) == kOneBits; }
 
 // cut-off of uniform cells and cell tags (Sec. 2.1, Sec. 3.3); interfacial
 // cells are appended to the band list
 __global__ void k_cell_tags(int64_t nc, long long eps_bits, long long ome_bits, double* F,
-                            int8_t* tc, int32_t* icells, unsigned long long* cnt) {
+                            const double* cvol, int8_t* tc, int32_t* icells,
+                            unsigned long long* cnt, double* acc_cut) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double cut = 0.0;  // volume the cut-off removes (Sec. 2.1)
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += stride) {
     int64_t c = base + threadIdx.x;
     bool in = c < nc;
     int8_t t = -1;
     if (in) {
-      const long long b = dbits(F[c]);
-      if (b < eps_bits) { t = -1; if (b != 0) F[c] = 0.0; }             // F < eps
-      else if (b > ome_bits) { t = 1; if (b != kOneBits) F[c] = 1.0; }  // F > 1 - eps
-      else t = 0;
+      const double f = F[c];
+      const long long b = dbits(f);
+      if (b < eps_bits) {  // F < eps
+        t = -1;
+        if (b != 0) { F[c] = 0.0; cut += cvol[c] * f; }
+      } else if (b > ome_bits) {  // F > 1 - eps
+        t = 1;
+        if (b != kOneBits) { F[c] = 1.0; cut += cvol[c] * (f - 1.0); }
+      } else {
+        t = 0;
+      }
       tc[c] = t;
     }
     warp_append(in && t == 0, (int32_t)c, icells, cnt + kNIcells);
   }
+  const double s = block_sum(cut);
+  if (threadIdx.x == 0) acc_cut[blockIdx.x] += s;
 }
 
 // node value F* by inverse-distance weighting of the cells sharing the node
@@ -145,8 +170,11 @@ __global__ void k_face_flux_export(DevMesh M, const int8_t* tf, const double* sr
 // Eq. fnext per cell; V_d of a face is formed here from its rate and the
 // grid's g dt, V_F from its tag (so the face sweep stores neither)
 __global__ void k_update(DevMesh M, double* F, const int8_t* tf, const double* srate,
-                         const GridParam* gp, const double* VF, double* red) {
+                         const GridParam* gp, const double* VF, double* red,
+                         const int32_t* bfaces, int64_t nbf, double* acc) {
   double eb = 0.0;
+  double clip = 0.0;  // volume the clip to [0, 1] removes
+  double bnd = 0.0;   // fluid that leaves through the domain boundary (R11)
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
@@ -182,7 +210,24 @@ __global__ void k_update(DevMesh M, double* F, const int8_t* tf, const double* s
     double h = vdt / (2.0 * V);
     double fn = (F0 * (1.0 + h) - vft / V) / (1.0 - h);
     eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
-    F[c] = fmax(fmin(fn, 1.0), 0.0);
+    const double fc = fmax(fmin(fn, 1.0), 0.0);
+    clip += V * (fn - fc);
+    F[c] = fc;
+  }
+  // boundary faces (owner side only), each once
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = bfaces[i];
+    const int8_t t = tf[f];
+    if (t == -1) continue;
+    const double vd = srate[f] * grid_gdt(M, gp, f);
+    bnd += face_vf(t, vd, VF, f);
+  }
+  {
+    const double s1 = block_sum(clip);
+    if (threadIdx.x == 0) acc[kAccClip * kAccSlots + blockIdx.x] += s1;
+    const double s2 = block_sum(bnd);
+    if (threadIdx.x == 0) acc[kAccBoundary * kAccSlots + blockIdx.x] += s2;
   }
   for (int o = 16; o > 0; o >>= 1) eb = fmax(eb, __shfl_xor_sync(GVOF_FULL, eb, o));
   __shared__ double s[32];
@@ -214,7 +259,7 @@ __global__ void k_volume_partial(DevMesh M, const double* F, double* red) {
   }
 }
 
-__global__ void k_volume_final(double* red, int nblocks, int neb) {
+__global__ void k_volume_final(double* red, int nblocks, int neb, const double* acc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double t = 0.0;
   for (int i = 0; i < nblocks; ++i) t += red[i];
@@ -222,6 +267,11 @@ __global__ void k_volume_final(double* red, int nblocks, int neb) {
   for (int i = 0; i < neb; ++i) eb = fmax(eb, red[kRedSlots / 2 + i]);
   red[kRedSlots - 2] = t;
   red[kRedSlots - 1] = eb;
+  for (int a = 0; a < kNAcc; ++a) {
+    double s = 0.0;
+    for (int i = 0; i < kAccSlots; ++i) s += acc[a * kAccSlots + i];
+    red[kRedSlots - 5 + a] = s;
+  }
 }
 
 constexpr int kUpdBlocks = kSMs * 4;  // fixed, <= kRedSlots/2 - 2
@@ -235,7 +285,8 @@ cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s) {
   long long eb, ob;
   std::memcpy(&eb, &eps, sizeof eb);
   std::memcpy(&ob, &ome, sizeof ob);
-  k_cell_tags<<<grid_for(c->nc, 256), 256, 0, s>>>(c->nc, eb, ob, c->F, c->tc, c->icells, c->cnt);
+  k_cell_tags<<<grid_for(c->nc, 256), 256, 0, s>>>(c->nc, eb, ob, c->F, c->cvol, c->tc, c->icells,
+                                                   c->cnt, c->acc + kAccCutoff * kAccSlots);
   return cudaGetLastError();
 }
 
@@ -262,13 +313,14 @@ cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s) {
 }
 
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s) {
-  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->tf, c->srate, c->gp_d, c->VF, c->red);
+  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->tf, c->srate, c->gp_d, c->VF, c->red,
+                                      c->bfaces, c->nbf, c->acc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s) {
   k_volume_partial<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->red);
-  k_volume_final<<<1, 32, 0, s>>>(c->red, kUpdBlocks, kUpdBlocks);
+  k_volume_final<<<1, 32, 0, s>>>(c->red, kUpdBlocks, kUpdBlocks, c->acc);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,10 @@ enum Cnt {
   kNCnt = 16
 };
 constexpr int kRedSlots = 2 * 1024;
+// volume bookkeeping: per-block running sums, one region each (fixed block
+// counts, so every sum is formed in the same order every step)
+constexpr int kAccSlots = kSMs * 16;
+enum Acc { kAccClip = 0, kAccBoundary = 1, kAccCutoff = 2, kNAcc = 3 };
 
 // velocity of the test problems without its time factor: u(x, t) = g(t) u0(x)
 template <typename T>
@@ -220,6 +224,9 @@ struct vof_ctx {
   int32_t *icells, *afaces;
   unsigned long long* cnt;
   double* red;
+  double* acc;  // [kNAcc * kAccSlots] volume bookkeeping since the last set_fraction
+  int32_t* bfaces;  // boundary faces (no neighbour)
+  int64_t nbf;
   // host-side caches
   bool vel_valid;
   bool recon_valid;

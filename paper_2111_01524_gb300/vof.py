@@ -49,7 +49,8 @@ class Stats(C.Structure):
     _fields_ = [("n_interfacial", C.c_int64), ("n_active_faces", C.c_int64),
                 ("n_truncations", C.c_int64), ("n_overflow", C.c_int64),
                 ("n_degenerate", C.c_int64), ("n_edgeon", C.c_int64),
-                ("volume", C.c_double), ("ebound", C.c_double)]
+                ("volume", C.c_double), ("ebound", C.c_double), ("clip_loss", C.c_double),
+                ("cutoff_loss", C.c_double), ("boundary_outflow", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

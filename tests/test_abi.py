@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -49,4 +51,34 @@ def test_struct_layouts():
     assert ctypes.sizeof(vof._Mesh) == 3 * 8 + 5 * 8
     assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 7 * 4
     assert ctypes.sizeof(vof._Vel) == 4 + 4 + 8 + 8 + 24 + 24
-    assert ctypes.sizeof(vof.Stats) == 6 * 8 + 2 * 8
+    assert ctypes.sizeof(vof.Stats) == 6 * 8 + 5 * 8
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and field offsets of the binding's structs equal the C header's
+    (compiled here with the host compiler)."""
+    import shutil
+    import subprocess
+    from paper_2111_01524_gb300 import vof
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"vof_mesh_desc": vof._Mesh, "vof_options": vof._Opt, "vof_velocity": vof._Vel,
+               "vof_stats": vof.Stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vof.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
