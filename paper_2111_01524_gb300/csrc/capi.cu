@@ -47,7 +47,8 @@ void free_all(vof_ctx* c) {
                   c->fnz32, c->fa32, c->cvol32, c->nx32, c->ny32, c->nz32, c->C32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* ptrs2[] = {c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces};
+  void* ptrs2[] = {c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces, c->vf_ptr, c->vf,
+                   c->stamp_c, c->stamp_v, c->stamp_f, c->bcells, c->bnodes};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -291,6 +292,26 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
   CKI(dalloc(c, &c->cnt, kNCnt)); CKI(dalloc(c, &c->red, kRedSlots));
   CKI(dalloc(c, &c->acc, kNAcc * kAccSlots));
   {
+    // node -> faces CSR for the band-limited face sweep
+    std::vector<int64_t> vp(nv + 1, 0);
+    for (int64_t k = 0; k < nfv; ++k) ++vp[mesh->face_vert[k] + 1];
+    for (int64_t v = 0; v < nv; ++v) vp[v + 1] += vp[v];
+    std::vector<int32_t> vfl(nfv);
+    std::vector<int64_t> pos(vp.begin(), vp.end() - 1);
+    for (int64_t f = 0; f < nf; ++f)
+      for (int64_t k = mesh->face_ptr[f]; k < mesh->face_ptr[f + 1]; ++k)
+        vfl[pos[mesh->face_vert[k]]++] = (int32_t)f;
+    CKI(dalloc(c, &c->vf_ptr, nv + 1));
+    CKI(dalloc(c, &c->vf, nfv));
+    CKI(cudaMemcpy(c->vf_ptr, vp.data(), sizeof(int64_t) * (nv + 1), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(c->vf, vfl.data(), sizeof(int32_t) * nfv, cudaMemcpyHostToDevice));
+    CKI(dalloc(c, &c->stamp_c, nc)); CKI(dalloc(c, &c->stamp_v, nv)); CKI(dalloc(c, &c->stamp_f, nf));
+    CKI(dalloc(c, &c->bcells, nc)); CKI(dalloc(c, &c->bnodes, nv));
+    CKI(cudaMemset(c->stamp_c, 0, sizeof(int32_t) * nc));
+    CKI(cudaMemset(c->stamp_v, 0, sizeof(int32_t) * nv));
+    CKI(cudaMemset(c->stamp_f, 0, sizeof(int32_t) * nf));
+  }
+  {
     std::vector<int32_t> bf;
     for (int64_t f = 0; f < nf; ++f)
       if (mesh->neighbour[f] < 0) bf.push_back((int32_t)f);
@@ -467,8 +488,9 @@ vof_status vof_set_fraction(vof_ctx* c, const double* F, int mem, void* stream) 
   if (!c || !F) return fail(VOF_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(c->F, F, sizeof(double) * c->nc, kind_to_dev(mem), s));
-  // the volume bookkeeping starts from this F
+  // the volume bookkeeping starts from this F, and the next sweeps are full
   CK(cudaMemsetAsync(c->acc, 0, sizeof(double) * kNAcc * kAccSlots, s));
+  CK(cudaMemsetAsync(c->cnt + kBandCellsOk, 0, 2 * sizeof(unsigned long long), s));
   if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
   c->recon_valid = false;
   return VOF_OK;

@@ -1,8 +1,26 @@
-// Full-grid sweeps of one step: tags (Sec. 3.3), the face sweep that forms
-// V_d (Eq. a-donacion) and the shortcut fluxes of tag -1/1 faces, and the
-// cell update of Eq. fnext with the final clip (Sec. 2.2). These kernels
-// are HBM-bound: one thread per cell / node / face, coalesced SoA loads,
-// warp-aggregated compaction of the band work lists.
+// Sweeps of one step: tags (Sec. 3.3), the face sweep that finds the faces
+// with geometric fluxes, and the cell update of Eq. fnext with the final clip
+// (Sec. 2.2). One thread per cell / node / face, coalesced SoA loads,
+// warp-aggregated compaction of the work lists.
+//
+// Band-limited sweeps. The paper's sweeps visit every cell, node and face;
+// on a large grid almost all of them are uniform (F = 0 or 1) and stay so.
+// A cell's F can change in a step only if one of its faces carries a
+// geometric flux (tag 0) or it is interfacial: a cell whose faces all carry
+// shortcut fluxes keeps F = 0 exactly, and F = 1 up to the last bit that the
+// cut-off restores. So after the first, full, sweeps:
+//  - the update visits the band cells: owner and neighbour of every active
+//    face, and the interfacial cells (de-duplicated by per-step stamps);
+//  - the cut-off and cell tags visit the band cells (every interfacial cell
+//    is one of them);
+//  - node tags visit the band nodes, the nodes of the band cells (no other
+//    node has a cell whose F changed);
+//  - the next face sweep visits the faces of the band nodes: a face whose
+//    tag changes has a band node, and every face active in the last step
+//    lies on a band cell.
+// F and every tag are those of the full sweeps. Device flags (counter slots
+// kBandCellsOk, kBandNodesOk) select band or full work inside the kernels,
+// so a captured CUDA graph stays valid for every replay.
 #include <cstring>
 
 #include "vof_common.cuh"
@@ -51,16 +69,25 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 __device__ __forceinline__ bool is_one(double x) { return dbits(x) == kOneBits; }
 
+// de-duplicating claim of an entity for this step's list
+__device__ __forceinline__ bool claim(int32_t* stamp, int64_t i, int32_t epoch) {
+  return atomicExch(stamp + i, epoch) != epoch;
+}
+
 // cut-off of uniform cells and cell tags (Sec. 2.1, Sec. 3.3); interfacial
-// cells are appended to the band list
+// cells are appended to their list. Visits all cells, or the band cells when
+// the last update produced them.
 __global__ void k_cell_tags(int64_t nc, long long eps_bits, long long ome_bits, double* F,
                             const double* cvol, int8_t* tc, int32_t* icells,
-                            unsigned long long* cnt, double* acc_cut) {
+                            unsigned long long* cnt, double* acc_cut, const int32_t* bcells) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double cut = 0.0;  // volume the cut-off removes (Sec. 2.1)
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += stride) {
-    int64_t c = base + threadIdx.x;
-    bool in = c < nc;
+  const bool band = cnt[kBandCellsOk] != 0;
+  const int64_t n = band ? (int64_t)cnt[kNBandCells] : nc;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < n;
+    const int64_t c = in ? (band ? bcells[i] : i) : 0;
     int8_t t = -1;
     if (in) {
       const double f = F[c];
@@ -86,9 +113,13 @@ __global__ void k_cell_tags(int64_t nc, long long eps_bits, long long ome_bits, 
 // and node tags (Sec. 3.3). Nodes whose cells are all empty or all full take
 // F* = 0 or 1 exactly without forming the weights.
 template <typename G>
-__global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < M.nv;
-       v += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv,
+                            const unsigned long long* cnt, const int32_t* bnodes) {
+  const bool band = cnt[kBandCellsOk] != 0;
+  const int64_t n = band ? (int64_t)cnt[kNBandNodes] : M.nv;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = band ? bnodes[i] : i;
     int64_t q0 = M.vc_ptr[v], q1 = M.vc_ptr[v + 1];
     bool allz = true, allo = true;
     for (int64_t q = q0; q < q1; ++q) {
@@ -120,25 +151,124 @@ __global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv) 
 // face sweep: face tags from node tags, V_d = g(t+dt/2) (u0.n) A dt,
 // V_F = 0 on tag -1 faces, V_F = V_d on tag 1 faces (no geometry, Sec. 3.3);
 // tag 0 faces are appended to the active list for the flux kernel
+__device__ __forceinline__ int8_t face_tag(const DevMesh& M, const int8_t* tv, int64_t f) {
+  const int64_t b = M.fptr[f], e = M.fptr[f + 1];
+  bool allm = true, allp = true;
+  for (int64_t k = b; k < e; ++k) {
+    const int8_t x = tv[M.fvert[k]];
+    allm &= (x == -1);
+    allp &= (x == 1);
+  }
+  return allm ? -1 : (allp ? 1 : 0);
+}
+
+// start of a step: new stamp epoch, empty band cell list
+__global__ void k_band_begin(unsigned long long* cnt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    cnt[kEpoch] += 1;
+    cnt[kNBandCells] = 0;
+  }
+}
+
+// face tags and the active list: all faces, or (band nodes valid) one warp
+// per band node over the faces that contain it
 __global__ void k_face_sweep(DevMesh M, const int8_t* tv, int8_t* tf, int32_t* afaces,
-                             unsigned long long* cnt) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < M.nf; base += stride) {
-    int64_t f = base + threadIdx.x;
-    bool in = f < M.nf;
-    int8_t t = 0;
-    if (in) {
-      int64_t b = M.fptr[f], e = M.fptr[f + 1];
-      bool allm = true, allp = true;
-      for (int64_t k = b; k < e; ++k) {
-        int8_t x = tv[M.fvert[k]];
-        allm &= (x == -1);
-        allp &= (x == 1);
+                             unsigned long long* cnt, const int64_t* vf_ptr, const int32_t* vf,
+                             const int32_t* bnodes, int32_t* stamp_f) {
+  if (cnt[kBandNodesOk] == 0) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < M.nf; base += stride) {
+      int64_t f = base + threadIdx.x;
+      bool in = f < M.nf;
+      int8_t t = 0;
+      if (in) {
+        t = face_tag(M, tv, f);
+        tf[f] = t;
       }
-      t = allm ? -1 : (allp ? 1 : 0);
-      tf[f] = t;
+      warp_append(in && t == 0, (int32_t)f, afaces, cnt + kNAfaces);
     }
-    warp_append(in && t == 0, (int32_t)f, afaces, cnt + kNAfaces);
+    return;
+  }
+  const int32_t epoch = (int32_t)cnt[kEpoch];
+  const int64_t nb = (int64_t)cnt[kNBandNodes];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < nb; i += nw) {
+    const int v = bnodes[i];
+    const int64_t q0 = vf_ptr[v], q1 = vf_ptr[v + 1];
+    for (int64_t base = q0; base < q1; base += 32) {
+      const int64_t q = base + lane;
+      bool act = false;
+      int f = 0;
+      if (q < q1) {
+        f = vf[q];
+        const int8_t t = face_tag(M, tv, f);
+        tf[f] = t;  // every warp that meets f writes the same tag
+        act = t == 0 && claim(stamp_f, f, epoch);
+      }
+      warp_append(act, f, afaces, cnt + kNAfaces);
+    }
+  }
+}
+
+// band cells: owner and neighbour of each active face, and the interfacial
+// cells, each once
+__global__ void k_band_cells(DevMesh M, const int32_t* afaces, const int32_t* icells,
+                             unsigned long long* cnt, int32_t* stamp_c, int32_t* bcells) {
+  const int32_t epoch = (int32_t)cnt[kEpoch];
+  const int64_t na = (int64_t)cnt[kNAfaces], ni = (int64_t)cnt[kNIcells];
+  const int64_t n = na + ni;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int c0 = -1, c1 = -1;
+    if (i < na) {
+      const int f = afaces[i];
+      c0 = M.own[f];
+      c1 = M.nbr[f];
+    } else if (i < n) {
+      c0 = icells[i - na];
+    }
+    const bool p0 = c0 >= 0 && claim(stamp_c, c0, epoch);
+    warp_append(p0, c0, bcells, cnt + kNBandCells);
+    const bool p1 = c1 >= 0 && claim(stamp_c, c1, epoch);
+    warp_append(p1, c1, bcells, cnt + kNBandCells);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[kBandCellsOk] = 1;
+}
+
+// band nodes: the nodes of the band cells, each once (one warp per cell)
+__global__ void k_band_nodes(DevMesh M, const int32_t* bcells, unsigned long long* cnt,
+                             int32_t* stamp_v, int32_t* bnodes) {
+  if (cnt[kBandCellsOk] == 0) return;
+  const int32_t epoch = (int32_t)cnt[kEpoch];
+  const int64_t n = (int64_t)cnt[kNBandCells];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < n; i += nw) {
+    const int c = bcells[i];
+    const int64_t q0 = M.cv_ptr[c], q1 = M.cv_ptr[c + 1];
+    for (int64_t base = q0; base < q1; base += 32) {
+      const int64_t q = base + lane;
+      int v = 0;
+      bool p = false;
+      if (q < q1) {
+        v = M.cv[q];
+        p = claim(stamp_v, v, epoch);
+      }
+      warp_append(p, v, bnodes, cnt + kNBandNodes);
+    }
+  }
+}
+
+// end of a reconstruction: the band node list is valid for the next face
+// sweep only if this reconstruction was band-limited
+__global__ void k_band_end(unsigned long long* cnt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    cnt[kBandNodesOk] = cnt[kBandCellsOk];
+    cnt[kBandCellsOk] = 0;
   }
 }
 
@@ -171,12 +301,15 @@ __global__ void k_face_flux_export(DevMesh M, const int8_t* tf, const double* sr
 // grid's g dt, V_F from its tag (so the face sweep stores neither)
 __global__ void k_update(DevMesh M, double* F, const int8_t* tf, const double* srate,
                          const GridParam* gp, const double* VF, double* red,
-                         const int32_t* bfaces, int64_t nbf, double* acc) {
+                         const int32_t* bfaces, int64_t nbf, double* acc,
+                         const unsigned long long* cnt, const int32_t* bcells) {
   double eb = 0.0;
   double clip = 0.0;  // volume the clip to [0, 1] removes
   double bnd = 0.0;   // fluid that leaves through the domain boundary (R11)
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t n = (int64_t)cnt[kNBandCells];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = bcells[i];
     const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
     const double F0 = F[c];
     // the faces of a cell belong to its grid
@@ -286,15 +419,22 @@ cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s) {
   std::memcpy(&eb, &eps, sizeof eb);
   std::memcpy(&ob, &ome, sizeof ob);
   k_cell_tags<<<grid_for(c->nc, 256), 256, 0, s>>>(c->nc, eb, ob, c->F, c->cvol, c->tc, c->icells,
-                                                   c->cnt, c->acc + kAccCutoff * kAccSlots);
+                                                   c->cnt, c->acc + kAccCutoff * kAccSlots,
+                                                   c->bcells);
   return cudaGetLastError();
 }
 
 cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->cnt + kNBandNodes, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_band_nodes<<<kSMs * 4, 256, 0, s>>>(mesh_view(c), c->bcells, c->cnt, c->stamp_v, c->bnodes);
   if (c->opt.precision == VOF_PREC_MIXED)
-    k_node_tags<float><<<grid_for(c->nv, 256), 256, 0, s>>>(mesh_view(c), c->F, c->opt.eps, c->tv);
+    k_node_tags<float><<<grid_for(c->nv, 256), 256, 0, s>>>(mesh_view(c), c->F, c->opt.eps, c->tv,
+                                                            c->cnt, c->bnodes);
   else
-    k_node_tags<double><<<grid_for(c->nv, 256), 256, 0, s>>>(mesh_view(c), c->F, c->opt.eps, c->tv);
+    k_node_tags<double><<<grid_for(c->nv, 256), 256, 0, s>>>(mesh_view(c), c->F, c->opt.eps, c->tv,
+                                                             c->cnt, c->bnodes);
+  k_band_end<<<1, 32, 0, s>>>(c->cnt);
   return cudaGetLastError();
 }
 
@@ -303,7 +443,9 @@ cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s) {
   static_assert(kNAfaces + 1 == kNTrunc && kNTrunc + 3 == kNEdgeOn, "counter layout");
   cudaError_t e = cudaMemsetAsync(c->cnt + kNAfaces, 0, 5 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->tf, c->afaces, c->cnt);
+  k_band_begin<<<1, 32, 0, s>>>(c->cnt);
+  k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->tf, c->afaces, c->cnt,
+                                                    c->vf_ptr, c->vf, c->bnodes, c->stamp_f);
   return cudaGetLastError();
 }
 cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s) {
@@ -313,8 +455,10 @@ cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s) {
 }
 
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s) {
+  k_band_cells<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->afaces, c->icells, c->cnt, c->stamp_c,
+                                          c->bcells);
   k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->tf, c->srate, c->gp_d, c->VF, c->red,
-                                      c->bfaces, c->nbf, c->acc);
+                                      c->bfaces, c->nbf, c->acc, c->cnt, c->bcells);
   return cudaGetLastError();
 }
 

@@ -101,6 +101,12 @@ enum Cnt {
   kNDegen = 4,
   kNEdgeOn = 5,
   kUmax = 6,  // 3 slots: max |u0| per axis (bit pattern of non-negative doubles)
+  // band-limited sweeps (see k_sweep.cu)
+  kNBandCells = 9,   // cells whose F the update may change this step
+  kNBandNodes = 10,  // nodes of those cells
+  kEpoch = 11,       // step counter for the de-duplication stamps
+  kBandCellsOk = 12, // the band cell list of the last advect is valid
+  kBandNodesOk = 13, // the band node list of the last reconstruction is valid
   kNCnt = 16
 };
 constexpr int kRedSlots = 2 * 1024;
@@ -227,6 +233,11 @@ struct vof_ctx {
   double* acc;  // [kNAcc * kAccSlots] volume bookkeeping since the last set_fraction
   int32_t* bfaces;  // boundary faces (no neighbour)
   int64_t nbf;
+  // band-limited sweeps: node -> faces CSR, per-entity stamps, band lists
+  int64_t* vf_ptr;
+  int32_t* vf;
+  int32_t *stamp_c, *stamp_v, *stamp_f;
+  int32_t *bcells, *bnodes;
   // host-side caches
   bool vel_valid;
   bool recon_valid;

@@ -167,6 +167,34 @@ def test_advect_parity_mixed(vof, cases, name):
     assert ctx.stats()["n_overflow"] == 0
 
 
+@pytest.mark.parametrize("name", CASES)
+def test_multistep_tags_and_band_sweeps(vof, cases, name):
+    """After the first step the sweeps are band-limited (only the cells, nodes
+    and faces the step can change are visited): over 8 coupled steps the node
+    and cell tags equal the oracle's full sweeps bit for bit, the face tags
+    each advect uses equal the oracle's of the state it advects, and F stays
+    within 1e-12."""
+    m, F0, om = cases[name]
+    vel = VELS["rotation"] if name.startswith("tet") else VELS["deformation"]
+    ctx = vof.Context(m, precision=vof.PREC_FP64)
+    ctx.set_fraction(F0)
+    ctx.reconstruct()
+    st = om.reconstruct(F0)
+    t = 0.0
+    for k in range(8):
+        dt = om.suggest_dt(vel, t, 0.5, 10.0)
+        prev = st
+        ctx.step(vel, t, dt)
+        st = om.step(vel, t, dt, st)
+        t += dt
+        tv, tf, tc = ctx.tags()
+        assert np.array_equal(tv, st["tag_v"]), (name, k)
+        assert np.array_equal(tc, st["tag_c"]), (name, k)
+        assert np.array_equal(tf, prev["tag_f"]), (name, k)
+        assert np.abs(ctx.get_fraction() - st["F"]).max() < EPS_F64, (name, k)
+    assert ctx.stats()["n_interfacial"] == int((st["tag_c"] == 0).sum())
+
+
 def test_multistep_parity_config1(vof, cases):
     """32^3 deformation, 10 steps at CFL 0.5: the GPU and the oracle each
     run the whole loop on their own; F agrees to 1e-12 after every step."""
@@ -189,6 +217,45 @@ def test_multistep_parity_config1(vof, cases):
     s = ctx.stats()
     assert abs(s["volume"] - vol0) < 1e-12 * vol0
     assert s["n_overflow"] == 0
+
+
+def test_full_cycle_config1(vof, cases):
+    """32^3 deformation over the whole cycle (t = 0 -> T = 3, 250 steps at
+    CFL 0.5): the FP64 path stays within 1e-12 of the oracle at every step
+    although each side feeds back its own results; the mixed path's shape
+    error E_shape = sum V |F(T) - F(0)| (Sec. 4.2) agrees with the oracle's to
+    1e-5 relative and both conserve volume to 1e-12 in the bookkeeping."""
+    m, F0, om = cases["hex32"]
+    vel = I.deformation(3.0)
+    c64 = vof.Context(m, precision=vof.PREC_FP64)
+    cmx = vof.Context(m, precision=vof.PREC_MIXED)
+    for c in (c64, cmx):
+        c.set_fraction(F0)
+        c.reconstruct()
+    st = om.reconstruct(F0)
+    V = om.geometry()["cell_vol"]
+    vol0 = float((V * F0).sum())
+    t, k = 0.0, 0
+    while t < 3.0 - 1e-14:
+        dt = om.suggest_dt(vel, t, 0.5, 3.0)
+        assert dt == c64.suggest_dt(vel, t, 0.5, 3.0)
+        st = om.step(vel, t, dt, st)
+        c64.step(vel, t, dt)
+        cmx.step(vel, t, dt)
+        t += dt
+        k += 1
+        if k % 10 == 0:
+            assert np.abs(c64.get_fraction() - st["F"]).max() < EPS_F64, k
+    assert k == 250
+    Fo, F64, Fm = st["F"], c64.get_fraction(), cmx.get_fraction()
+    assert np.abs(F64 - Fo).max() < EPS_F64
+    es_o = float((V * np.abs(Fo - F0)).sum())
+    es_m = float((V * np.abs(Fm - F0)).sum())
+    assert abs(es_m - es_o) < 1e-5 * es_o, (es_m, es_o)
+    for c in (c64, cmx):
+        s = c.stats()
+        resid = s["volume"] - (vol0 - s["clip_loss"] - s["cutoff_loss"] - s["boundary_outflow"])
+        assert abs(resid) < 1e-12 * vol0
 
 
 def test_cfl1_translation_exact_shift_gpu(vof):
