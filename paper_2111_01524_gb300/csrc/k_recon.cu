@@ -9,7 +9,8 @@
 // the breakpoint C_v = -n.x_v of vertex v; warp max/min reductions give the
 // bracket between consecutive breakpoints, where V is exactly a cubic in C.
 // Two more evaluations inside the bracket fix the cubic, whose root is found
-// by safeguarded Newton iteration.
+// by safeguarded Newton iteration. Each round of evaluations spreads its
+// (sample, face) pairs over the lanes.
 // Precision: the FP64 path works in double. The mixed path works in FP32 in
 // cell-local coordinates scaled by V^(-1/3) (absolute positions as (hi, lo)
 // float pairs) and switches to FP64 for the plane constant of cells with F
@@ -19,6 +20,12 @@
 
 namespace gvof {
 namespace {
+
+// blocks per SM the register allocation must allow (64 registers a thread
+// at 8: twice the resident warps of an unbounded allocation, measured faster)
+#ifndef GVOF_RECON_MINB
+#define GVOF_RECON_MINB 8
+#endif
 
 constexpr int kWarps = 4;
 constexpr int kMaxCellFaces = 32;
@@ -51,50 +58,66 @@ __device__ __forceinline__ const LoopSmem<float>& loops(const ReconSmem& S, floa
 __device__ __forceinline__ LoopSmem<double>& loops_w(ReconSmem& S, double) { return S.d; }
 __device__ __forceinline__ LoopSmem<float>& loops_w(ReconSmem& S, float) { return S.f; }
 
-// volume of the part of the cell where n.x + C >= 0 (scaled cell-local frame)
+// adds to vol six times the contribution of face f to the volume of the
+// part of the cell where n.x + C >= 0 (scaled cell-local frame): the face
+// loop clipped to the half-space and fanned from a point of the plane, so
+// that the cap the cut would close contributes nothing
 template <typename P>
-__device__ P cut_volume(const ReconSmem& S, int nfc, P nx, P ny, P nz, P C) {
+__device__ void face_cut(const ReconSmem& S, int f, P nx, P ny, P nz, P C, P& vol) {
   const LoopSmem<P>& Lp = loops(S, P(0));
   const P ox = -C * nx, oy = -C * ny, oz = -C * nz;  // a point of the plane
-  P vol = P(0);
-  for (int f = 0; f < nfc; ++f) {
-    const int b = S.fs[f], L = S.fs[f + 1] - b;
-    P ax = Lp.x[b + L - 1] - ox, ay = Lp.y[b + L - 1] - oy, az = Lp.z[b + L - 1] - oz;
-    P pa = nx * ax + ny * ay + nz * az;
-    int ne = 0;
-    P q0x = 0, q0y = 0, q0z = 0, qpx = 0, qpy = 0, qpz = 0;
-    for (int k = 0; k < L; ++k) {
-      const P bx = Lp.x[b + k] - ox, by = Lp.y[b + k] - oy, bz = Lp.z[b + k] - oz;
-      const P pb = nx * bx + ny * by + nz * bz;
-      const bool ia = pa >= P(0), ib = pb >= P(0);
-      // emit the clipped polygon's points in order; fan from the first
-      for (int e = 0; e < 2; ++e) {
-        P px, py, pz;
-        if (e == 0) {
-          if (ia == ib) continue;
-          // interpolate from the inside end, as the face on the other side of
-          // this edge does, so both compute the same point bit for bit
-          if (ia) {
-            const P t = pa / (pa - pb);
-            px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
-          } else {
-            const P t = pb / (pb - pa);
-            px = bx + t * (ax - bx); py = by + t * (ay - by); pz = bz + t * (az - bz);
-          }
+  const int b = S.fs[f], L = S.fs[f + 1] - b;
+  P ax = Lp.x[b + L - 1] - ox, ay = Lp.y[b + L - 1] - oy, az = Lp.z[b + L - 1] - oz;
+  P pa = nx * ax + ny * ay + nz * az;
+  int ne = 0;
+  P q0x = 0, q0y = 0, q0z = 0, qpx = 0, qpy = 0, qpz = 0;
+  for (int k = 0; k < L; ++k) {
+    const P bx = Lp.x[b + k] - ox, by = Lp.y[b + k] - oy, bz = Lp.z[b + k] - oz;
+    const P pb = nx * bx + ny * by + nz * bz;
+    const bool ia = pa >= P(0), ib = pb >= P(0);
+    // emit the clipped polygon's points in order; fan from the first
+    for (int e = 0; e < 2; ++e) {
+      P px, py, pz;
+      if (e == 0) {
+        if (ia == ib) continue;
+        // interpolate from the inside end, as the face on the other side of
+        // this edge does, so both compute the same point bit for bit
+        if (ia) {
+          const P t = pa / (pa - pb);
+          px = ax + t * (bx - ax); py = ay + t * (by - ay); pz = az + t * (bz - az);
         } else {
-          if (!ib) continue;
-          px = bx; py = by; pz = bz;
+          const P t = pb / (pb - pa);
+          px = bx + t * (ax - bx); py = by + t * (ay - by); pz = bz + t * (az - bz);
         }
-        if (ne == 0) { q0x = px; q0y = py; q0z = pz; }
-        else if (ne >= 2)
-          vol += q0x * (qpy * pz - qpz * py) + q0y * (qpz * px - qpx * pz) + q0z * (qpx * py - qpy * px);
-        qpx = px; qpy = py; qpz = pz;
-        ++ne;
+      } else {
+        if (!ib) continue;
+        px = bx; py = by; pz = bz;
       }
-      ax = bx; ay = by; az = bz; pa = pb;
+      if (ne == 0) { q0x = px; q0y = py; q0z = pz; }
+      else if (ne >= 2)
+        vol += q0x * (qpy * pz - qpz * py) + q0y * (qpz * px - qpx * pz) + q0z * (qpx * py - qpy * px);
+      qpx = px; qpy = py; qpz = pz;
+      ++ne;
     }
+    ax = bx; ay = by; az = bz; pa = pb;
   }
-  return vol / P(6);
+}
+
+// V(C_s) for ns samples at once: lane (s, g), s = lane % ns, clips the faces
+// g, g + G, ... (G = 32 / ns groups) at the lane's C (that of its sample s),
+// and the groups' partial sums are added in a fixed order; every lane returns
+// the volume of its sample. FP64 keeps one lane per sample (G = 1), so that
+// its sums are formed in the order of the plain face-by-face evaluation.
+template <typename P>
+__device__ P cut_volumes(const ReconSmem& S, int nfc, P nx, P ny, P nz, P C, int ns, int lane) {
+  const int G = sizeof(P) == 8 ? 1 : 32 / ns;
+  const int s = lane % ns, g = lane / ns;
+  P part = P(0);
+  if (g < G)
+    for (int f = g; f < nfc; f += G) face_cut<P>(S, f, nx, ny, nz, C, part);
+  P tot = P(0);
+  for (int gg = 0; gg < G; ++gg) tot += __shfl_sync(GVOF_FULL, part, s + ns * gg);
+  return tot / P(6);
 }
 
 // plane constant (cell-local, scaled) for target volume T; lane v < ncv
@@ -104,7 +127,9 @@ __device__ P plane_constant(const ReconSmem& S, int nfc, int ncv, P s_lane, P nx
                             int lane) {
   const bool has = lane < ncv;
   const P Cv = has ? -s_lane : P(0);
-  const P Vv = has ? cut_volume<P>(S, nfc, nx, ny, nz, Cv) : P(0);
+  // V at the breakpoint of every vertex, lanes (vertex, face group)
+  const P Vall = cut_volumes<P>(S, nfc, nx, ny, nz, __shfl_sync(GVOF_FULL, Cv, lane % ncv), ncv, lane);
+  const P Vv = has ? Vall : P(0);
   // bracket [Ca, Cb]: largest breakpoint with V <= T, smallest with V >= T
   P Ca = (has && Vv <= T) ? Cv : P(-1e30), Va = Vv;
   P Cb = (has && Vv >= T) ? Cv : P(1e30), Vb = Vv;
@@ -116,9 +141,9 @@ __device__ P plane_constant(const ReconSmem& S, int nfc, int ncv, P s_lane, P nx
   }
   if (Va == T || !(Cb > Ca)) return Ca;
   if (Vb == T) return Cb;
-  // V is a cubic on [Ca, Cb]: sample at 1/3 and 2/3
-  const P Cm = Ca + (Cb - Ca) * (lane == 0 ? P(1) / P(3) : P(2) / P(3));
-  const P Vm = (lane < 2) ? cut_volume<P>(S, nfc, nx, ny, nz, Cm) : P(0);
+  // V is a cubic on [Ca, Cb]: sample at 1/3 (even lanes) and 2/3 (odd lanes)
+  const P Cm = Ca + (Cb - Ca) * ((lane & 1) == 0 ? P(1) / P(3) : P(2) / P(3));
+  const P Vm = cut_volumes<P>(S, nfc, nx, ny, nz, Cm, 2, lane);
   const P y0 = Va, y3 = Vb;
   const P y1 = __shfl_sync(GVOF_FULL, Vm, 0), y2 = __shfl_sync(GVOF_FULL, Vm, 1);
   // Newton forward form in s = 3 (C - Ca) / (Cb - Ca), s in [0, 3]
@@ -255,7 +280,7 @@ __device__ void load_loops(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm
 }
 
 template <typename G, bool kMixed>
-__global__ void __launch_bounds__(kWarps * 32) k_reconstruct(DevMesh M, GeoView<G> Gv, DevState S,
+__global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(DevMesh M, GeoView<G> Gv, DevState S,
                                                              double beta) {
   __shared__ ReconSmem smem[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
