@@ -46,12 +46,12 @@ UNIT = "cell-steps/s"
 # construction and of one (face, cell) truncation with its divergence sum
 FLOPS_PER_ACTIVE_FACE = 350.0      # FMFPA construction
 FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
-# ncu capture of one flux launch (128^3 deformation step, mixed: 56,810 active
-# faces): dram__bytes_read.sum + dram__bytes_write.sum = 26.96 + 4.23 MB, i.e.
-# 549 B per active face, issue active 45.9%, FMA pipe 13.4%; valid for the
+# ncu capture of one flux launch (128^3 deformation step, mixed: ~57,300 active
+# faces): dram__bytes_read.sum + dram__bytes_write.sum = 26.94 + 1.91 MB, i.e.
+# 504 B per active face, issue active 38.2%, FMA pipe 10.9%; valid for the
 # kernel source it was taken on (traffic is null for any other source)
-FLUX_NCU = {"source_sha256": "02d54c614f34f2be4499adfe2813d19349f4bf2fa2638a9fdb2838e55212e466",
-            "dram_bytes_per_active_face": 549.0, "issue_active": 0.459, "fma_pipe_active": 0.134,
+FLUX_NCU = {"source_sha256": "5f7825894673ab28cd57465c2d6fd2bd6e6be737c9b3f3685b04317821ae35ea",
+            "dram_bytes_per_active_face": 504.0, "issue_active": 0.382, "fma_pipe_active": 0.109,
             "capture": "profiles/k_flux_deformation128_mixed.md"}
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
