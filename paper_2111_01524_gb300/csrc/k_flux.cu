@@ -86,6 +86,17 @@ __device__ __forceinline__ T wsum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GVOF_FULL, v, o);
   return v;
 }
+// warp min / max of a float by the integer reduction unit: the map
+// i -> i ^ ((i >> 31) & 0x7fffffff) of its bit pattern is monotonic
+__device__ __forceinline__ int fkey(float v) {
+  const int i = __float_as_int(v);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float fkey_inv(int k) {
+  return __int_as_float(k ^ ((k >> 31) & 0x7fffffff));
+}
+__device__ __forceinline__ float wmin(float v) { return fkey_inv(__reduce_min_sync(GVOF_FULL, fkey(v))); }
+__device__ __forceinline__ float wmax(float v) { return fkey_inv(__reduce_max_sync(GVOF_FULL, fkey(v))); }
 template <typename T>
 __device__ __forceinline__ T wmin(T v) {
   for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(GVOF_FULL, v, o));

@@ -237,6 +237,71 @@ __device__ bool corner_constant(const DevMesh& M, ReconSmem& Sm, int c, int ncv,
   return true;
 }
 
+// FP32 form of corner_constant for the mixed path: the same closed form in
+// the scaled cell-local frame, edges from the (hi, lo) positions. The mixed
+// path stores its plane constants in FP32, whose rounding (a few 1e-8 of the
+// cell size) bounds what an FP64 root would add. Returns the scaled C.
+template <typename G>
+__device__ bool corner_constant32(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm, int c, int ncv,
+                                  int vl, float s_lane, float nx, float ny, float nz, double F, float Vs,
+                                  float sc, int lane, float* Cout) {
+  const bool low = F <= 0.5;  // fluid corner at the top vertex, else empty corner at the bottom
+  const float key = lane < ncv ? (low ? s_lane : -s_lane) : -1e30f;
+  float k1 = key, k2 = -1e30f;
+  int v1 = vl;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ok1 = __shfl_xor_sync(GVOF_FULL, k1, o), ok2 = __shfl_xor_sync(GVOF_FULL, k2, o);
+    const int ov1 = __shfl_xor_sync(GVOF_FULL, v1, o);
+    if (ok1 > k1 || (ok1 == k1 && ov1 < v1)) {
+      k2 = fmaxf(k1, ok2);
+      k1 = ok1;
+      v1 = ov1;
+    } else {
+      k2 = fmaxf(k2, ok1);
+    }
+  }
+  const int nent = Sm.fs[M.cf_ptr[c + 1] - M.cf_ptr[c]];
+  int found = 0;
+  for (int base = 0; base < nent; base += 32) {
+    const int e = base + lane;
+    int nb = -1;
+    if (e < nent && Sm.vid[e] == v1) {
+      int f = 0;
+      while (Sm.fs[f + 1] <= e) ++f;
+      const int nxt = (e + 1 == Sm.fs[f + 1]) ? Sm.fs[f] : e + 1;
+      nb = Sm.vid[nxt];
+    }
+    const unsigned bal = __ballot_sync(GVOF_FULL, nb >= 0);
+    if (nb >= 0) {
+      const int pos = found + __popc(bal & ((1u << lane) - 1u));
+      if (pos < 4) Sm.corner[pos] = nb;
+    }
+    found += __popc(bal);
+  }
+  __syncwarp();
+  if (found != 3) return false;
+  const float sgn = low ? 1.f : -1.f;
+  float e[3][3], a[3];
+  for (int i = 0; i < 3; ++i) {
+    const int w = Sm.corner[i];
+    e[i][0] = rel(Gv.vx[w], Gv.vx[v1]) * sc;
+    e[i][1] = rel(Gv.vy[w], Gv.vy[v1]) * sc;
+    e[i][2] = rel(Gv.vz[w], Gv.vz[v1]) * sc;
+    a[i] = -sgn * (nx * e[i][0] + ny * e[i][1] + nz * e[i][2]);  // > 0 along the edges
+  }
+  const float det = fabsf(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                          e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                          e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]));
+  if (!(a[0] > 1e-6f && a[1] > 1e-6f && a[2] > 1e-6f) || !(det > 0.f)) return false;
+  const float prod = a[0] * a[1] * a[2];
+  const float T = (float)((low ? F : 1.0 - F) * (double)Vs);
+  const float D2 = k1 - k2;
+  if (!(T <= D2 * D2 * D2 * det / (6.f * prod))) return false;
+  const float D = cbrtf(6.f * T * prod / det);
+  *Cout = low ? (D - k1) : (k1 - D);
+  return true;
+}
+
 // load the cell's outward face loops (cell-local, scaled) in precision P
 template <typename P, typename G>
 __device__ void load_loops(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm, int c,
@@ -337,7 +402,24 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
     const int vl = lane < ncv ? M.cv[v0 + lane] : M.cv[v0];
     double Cout;
     const bool near01 = Fc < kNear01 || Fc > 1.0 - kNear01;
-    if (!kMixed || near01) {
+    if (kMixed && near01) {
+      // FP32 corner closed form
+      load_loops<G, G>(M, Gv, Sm, c, xc, yc, zc, (double)sc, nfc, lane);
+      const G s = nx * rel(Gv.vx[vl], xc) * sc + ny * rel(Gv.vy[vl], yc) * sc +
+                  nz * rel(Gv.vz[vl], zc) * sc;
+      float C32c;
+      if (corner_constant32(M, Gv, Sm, c, ncv, vl, (float)s, (float)nx, (float)ny, (float)nz, Fc,
+                            (float)(V * sc * sc * sc), (float)sc, lane, &C32c)) {
+        Cout = (double)(C32c * (float)hc);
+        if (lane == 0) {
+          S.nx[c] = (double)nx; S.ny[c] = (double)ny; S.nz[c] = (double)nz; S.C[c] = Cout;
+          S.nx32[c] = (float)nx; S.ny32[c] = (float)ny; S.nz32[c] = (float)nz; S.C32[c] = (float)Cout;
+        }
+        __syncwarp();
+        continue;
+      }
+    }
+    if (!kMixed) {
       // FP64 closed form when the fluid / empty region is a vertex corner
       const double hcd = cbrt(M.cvol[c]), scd = 1.0 / hcd;
       load_loops<double, G>(M, Gv, Sm, c, xc, yc, zc, scd, nfc, lane);
