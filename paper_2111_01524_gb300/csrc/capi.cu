@@ -47,7 +47,7 @@ void free_all(vof_ctx* c) {
                   c->fnz32, c->fa32, c->cvol32, c->nx32, c->ny32, c->nz32, c->C32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* ptrs2[] = {c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces, c->vf_ptr, c->vf,
+  void* ptrs2[] = {c->cpl32, c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces, c->vf_ptr, c->vf,
                    c->stamp_c, c->stamp_v, c->stamp_f, c->bcells, c->bnodes};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
@@ -329,6 +329,7 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     CKI(dalloc(c, &c->bb2, 6 * nc)); CKI(dalloc(c, &c->cvol32, nc));
     CKI(dalloc(c, &c->nx32, nc)); CKI(dalloc(c, &c->ny32, nc)); CKI(dalloc(c, &c->nz32, nc));
     CKI(dalloc(c, &c->C32, nc));
+    CKI(dalloc(c, &c->cpl32, c->ncf));
   }
   CKI(cudaMallocHost(&c->pinned, 4096));
   CKI(dalloc(c, &c->face_off_d, ng + 1));

@@ -755,7 +755,15 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
   if (M.convex[k]) {
     // inward half-spaces of cell k: -n_out.(x - p_g) >= 0, i.e. in the local
     // frame a = -n_out, b = -n_out.(c - p_g) / L
-    if (lane < nfk) {
+    if constexpr (sizeof(G) == 4) {
+      // FP32: from the cell's plane table, n.(x - x_k) >= d in the face-local frame
+      if (lane < nfk) {
+        const G rx = rel(fr.cx, Gv.ccx[k]), ry = rel(fr.cy, Gv.ccy[k]), rz = rel(fr.cz, Gv.ccz[k]);
+        const float4 q = M.cpl32[c0 + lane];
+        P.pl[lane][0] = q.x; P.pl[lane][1] = q.y; P.pl[lane][2] = q.z;
+        P.pl[lane][3] = (q.x * rx + q.y * ry + q.z * rz - q.w) * fr.sc;
+      }
+    } else if (lane < nfk) {
       const int fs = M.cf[c0 + lane];
       const int f = fs >= 0 ? fs : ~fs;
       const G sg = fs >= 0 ? G(1) : G(-1);
@@ -773,11 +781,14 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
 // one chunk of up to 32 candidate cells of face j (pass 0: the owner's node
 // neighbours and the owner; pass 1: the neighbour's and the neighbour, minus
 // those already seen), filtered by the local bounding box of the
-// polyhedron; returns the lane's cell (-1: none) and its tag
+// polyhedron and (FP32, convex cells) by the cell's face planes: a cell with
+// a plane that has every vertex of P strictly outside cannot meet P; returns
+// the lane's cell (-1: none) and its tag
 template <typename G>
 __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
-                                         const FaceFrame<G>& fr, int own, int64_t a0, int na, int pass,
-                                         int c0, int64_t b0, int nb, int idx, int8_t& tk) {
+                                         const FaceFrame<G>& fr, const Poly<G>& P, int own, int64_t a0,
+                                         int na, int pass, int c0, int64_t b0, int nb, int idx,
+                                         int8_t& tk) {
   const int64_t nc = M.nc;
   int k = -1;
   if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
@@ -790,9 +801,24 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
     if (!(fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy && fr.hi[2] > lz &&
           fr.lo[2] < hz))
       k = -1;
-    else
-      tk = S.tc[k];
   }
+  if constexpr (sizeof(G) == 4) {
+    if (k >= 0 && M.convex[k]) {
+      const int64_t q0 = M.cf_ptr[k];
+      const int nfk = (int)(M.cf_ptr[k + 1] - q0);
+      const int nvb = 2 * fr.I + 1;
+      const G rx = rel(fr.cx, Gv.ccx[k]), ry = rel(fr.cy, Gv.ccy[k]), rz = rel(fr.cz, Gv.ccz[k]);
+      for (int g = 0; g < nfk; ++g) {
+        const float4 q = M.cpl32[q0 + g];
+        const G b = (q.x * rx + q.y * ry + q.z * rz - q.w) * fr.sc;
+        bool out = true;
+        for (int v = 0; v < nvb && out; ++v)
+          out = q.x * P.bx[v] + q.y * P.by[v] + q.z * P.bz[v] + b < G(-2e-7);
+        if (out) { k = -1; break; }
+      }
+    }
+  }
+  if (k >= 0) tk = S.tc[k];
   return k;
 }
 
@@ -828,7 +854,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
-      const int k = candidate(M, Gv, S, fr, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      const int k = candidate(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
       const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
       if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
       if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
@@ -868,7 +894,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
-      const int k = candidate(M, Gv, S, fr, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      const int k = candidate(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
       unsigned bal = __ballot_sync(GVOF_FULL, k >= 0 && tk != skip);
       while (bal) {
         const int src = __ffs(bal) - 1;

@@ -192,6 +192,21 @@ __global__ void k_mixed_copies(DevMesh M, float2* vx2, float2* vy2, float2* vz2,
   }
 }
 
+// per cell face entry: inward unit normal and its offset from the centroid
+__global__ void k_cell_planes(DevMesh M, float4* cpl) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = M.cf_ptr[c]; q < M.cf_ptr[c + 1]; ++q) {
+      const int fs = M.cf[q];
+      const int f = fs >= 0 ? fs : ~fs;
+      const double s = fs >= 0 ? -1.0 : 1.0;  // inward = -(outward of this cell)
+      const double nx = s * M.fnx[f], ny = s * M.fny[f], nz = s * M.fnz[f];
+      const double d = nx * (M.fcx[f] - M.ccx[c]) + ny * (M.fcy[f] - M.ccy[c]) + nz * (M.fcz[f] - M.ccz[c]);
+      cpl[q] = make_float4((float)nx, (float)ny, (float)nz, (float)d);
+    }
+  }
+}
+
 inline int grid_for(int64_t n, int bs) {
   int64_t g = (n + bs - 1) / bs;
   int64_t cap = (int64_t)kSMs * 16;
@@ -219,6 +234,7 @@ cudaError_t launch_mixed_copies(const vof_ctx* c, cudaStream_t s) {
                                                  c->fcy2, c->fcz2, c->fnx32, c->fny32, c->fnz32,
                                                  c->fa32, c->ccx2, c->ccy2, c->ccz2, c->bb2,
                                                  c->cvol32);
+  k_cell_planes<<<grid_for(c->nc, 256), 256, 0, s>>>(mesh_view(c), c->cpl32);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,10 @@ struct DevMesh {
   const float2 *ccx2, *ccy2, *ccz2;
   const float2* bb2;
   const float* cvol32;
+  // per cell face entry (cell -> faces CSR order): inward unit normal n and
+  // d = n.(p_face - x_cell), so that the cell is n.(x - x_cell) >= d on
+  // every face plane (convex cells; FP32, mixed only)
+  const float4* cpl32;
 };
 
 struct DevState {
@@ -221,6 +225,7 @@ struct vof_ctx {
   uint8_t* convex;
   float2 *vx2, *vy2, *vz2, *fcx2, *fcy2, *fcz2, *ccx2, *ccy2, *ccz2, *bb2;
   float *fnx32, *fny32, *fnz32, *fa32, *cvol32;
+  float4* cpl32;
   float *nx32, *ny32, *nz32, *C32;
   // state (device)
   double* F;
@@ -292,6 +297,7 @@ inline DevMesh mesh_view(const vof_ctx* c) {
   m.fcx2 = c->fcx2; m.fcy2 = c->fcy2; m.fcz2 = c->fcz2;
   m.fnx32 = c->fnx32; m.fny32 = c->fny32; m.fnz32 = c->fnz32; m.fa32 = c->fa32;
   m.ccx2 = c->ccx2; m.ccy2 = c->ccy2; m.ccz2 = c->ccz2; m.bb2 = c->bb2; m.cvol32 = c->cvol32;
+  m.cpl32 = c->cpl32;
   return m;
 }
 
