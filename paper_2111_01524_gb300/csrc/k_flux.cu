@@ -781,9 +781,10 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
 // one chunk of up to 32 candidate cells of face j (pass 0: the owner's node
 // neighbours and the owner; pass 1: the neighbour's and the neighbour, minus
 // those already seen), filtered by the local bounding box of the
-// polyhedron and (FP32, convex cells) by the cell's face planes: a cell with
-// a plane that has every vertex of P strictly outside cannot meet P; returns
-// the lane's cell (-1: none) and its tag
+// polyhedron and (FP32, convex cells other than axis-aligned boxes, whose box
+// test is already this one) by the cell's face planes: a cell with a plane
+// that has every vertex of P strictly outside cannot meet P; returns the
+// lane's cell (-1: none) and its tag
 template <typename G>
 __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
                                          const FaceFrame<G>& fr, const Poly<G>& P, int own, int64_t a0,
@@ -803,7 +804,7 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
       k = -1;
   }
   if constexpr (sizeof(G) == 4) {
-    if (k >= 0 && M.convex[k]) {
+    if (k >= 0 && M.convex[k] == 1) {
       const int64_t q0 = M.cf_ptr[k];
       const int nfk = (int)(M.cf_ptr[k + 1] - q0);
       const int nvb = 2 * fr.I + 1;

@@ -99,9 +99,11 @@ __global__ void k_cell_geometry(DevMesh M, double* ccx, double* ccy, double* ccz
       bb[d * M.nc + c] = lo[d];
       bb[(3 + d) * M.nc + c] = hi[d];
     }
-    // convex: no vertex lies outside the plane of any of its faces
+    // convex: no vertex lies outside the plane of any of its faces; 2: convex
+    // and every face normal along an axis (a box: its bounding box is itself)
     double h = cbrt(fabs(vol));
     uint8_t cvx = 1;
+    bool axes = true;
     for (int64_t q = M.cf_ptr[c]; q < M.cf_ptr[c + 1] && cvx; ++q) {
       int fs = M.cf[q];
       int f = fs >= 0 ? fs : ~fs;
@@ -120,6 +122,8 @@ __global__ void k_cell_geometry(DevMesh M, double* ccx, double* ccy, double* ccz
         }
         double l = sqrt(nx * nx + ny * ny + nz * nz);
         nx /= l; ny /= l; nz /= l;
+        const int small = (fabs(nx) < 1e-12) + (fabs(ny) < 1e-12) + (fabs(nz) < 1e-12);
+        axes = axes && small == 2;
       }
       for (int64_t p = v0; p < v1; ++p) {
         int v = M.cv[p];
@@ -127,7 +131,7 @@ __global__ void k_cell_geometry(DevMesh M, double* ccx, double* ccy, double* ccz
         if (d > 1e-10 * h) { cvx = 0; break; }
       }
     }
-    convex[c] = cvx;
+    convex[c] = cvx && axes ? 2 : cvx;
   }
 }
 

@@ -64,7 +64,7 @@ struct DevMesh {
   const double *ccx, *ccy, *ccz;  // cell centroid
   const double* cvol;
   const double* bb;               // bounding boxes, SoA: bb[d*nc + c], d = 0..5 (lo xyz, hi xyz)
-  const uint8_t* convex;          // 1 if the cell is convex
+  const uint8_t* convex;          // 0: not convex, 1: convex, 2: convex box with axis-aligned faces
   const int64_t* face_off;        // [n_grids + 1] first face of each grid
   int n_grids;
   // mixed-precision copies (allocated for VOF_PREC_MIXED only): absolute
