@@ -18,6 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+
+# flux polyhedron constructions of faceflux / step
+FMFPA = 0  # face-matched (Sec. 2.2.2)
+EMFPA = 1  # edge-matched (Sec. 2.2.1)
 _lib = None
 
 
@@ -78,7 +82,9 @@ def lib():
         L.orc_velocity_eval.argtypes = [vp, vp, dbl, vp]
         L.orc_fmfpa.restype = i32
         L.orc_fmfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
-        L.orc_faceflux.argtypes = [vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_emfpa.restype = i32
+        L.orc_emfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
+        L.orc_faceflux.argtypes = [vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp, vp, i32]
         L.orc_vofadv.argtypes = [vp, vp, vp, vp]
         L.orc_suggest_dt.restype = dbl
         L.orc_suggest_dt.argtypes = [vp, vp, dbl, dbl, dbl]
@@ -196,14 +202,25 @@ class Mesh:
             raise ValueError("face too large")
         return out[:2 * I + 1].copy(), float(vd[0]), int(fl[0])
 
-    def faceflux(self, vel, t, dt, st):
+    def emfpa(self, face, vel, t_half, dt):
+        """EMFPA flux polyhedron (Sec. 2.2.1): 3I+1 points."""
+        out = np.empty((97, 3))
+        vd = np.zeros(1)
+        fl = np.zeros(1, np.int32)
+        v = _vel(vel)
+        I = lib().orc_emfpa(self._m, int(face), C.byref(v), t_half, dt, _p(out), 32, _p(vd), _p(fl))
+        if I < 0:
+            raise ValueError("face too large")
+        return out[:3 * I + 1].copy(), float(vd[0]), int(fl[0])
+
+    def faceflux(self, vel, t, dt, st, method=FMFPA):
         Vd = np.empty(self.n_face)
         VF = np.empty(self.n_face)
         stats = np.zeros(4, np.int64)
         v = _vel(vel)
         lib().orc_faceflux(self._m, C.byref(v), t, dt, _p(st["F"]), _p(st["tag_f"]),
                            _p(st["tag_c"]), _p(st["nrm"]), _p(st["C"]), _p(Vd), _p(VF),
-                           _p(stats))
+                           _p(stats), int(method))
         return Vd, VF, stats
 
     def vofadv(self, F, Vd, VF):
@@ -222,10 +239,11 @@ class Mesh:
         lib().orc_velocity_eval(C.byref(v), _p(x), t, _p(u))
         return u
 
-    def step(self, vel, t, dt, st, eps=1e-12, beta=1.5):
+    def step(self, vel, t, dt, st, eps=1e-12, beta=1.5, method=FMFPA):
         """One time step of the advection test loop (Algorithm alg:adv):
-        faceflux -> vofadv -> taggrid -> lsgir -> volume enforcement."""
-        Vd, VF, stats = self.faceflux(vel, t, dt, st)
+        faceflux -> vofadv -> taggrid -> lsgir -> volume enforcement.
+        method: the flux polyhedron, FMFPA (Sec. 2.2.2) or EMFPA (Sec. 2.2.1)."""
+        Vd, VF, stats = self.faceflux(vel, t, dt, st, method)
         F = self.vofadv(st["F"], Vd, VF)
         new = self.reconstruct(F, eps, beta)
         new["Vd"], new["VF"], new["stats"] = Vd, VF, stats

@@ -1,10 +1,10 @@
 /*
- * Oracle for the unsplit geometric VOF step (LSGIR + FMFPA) -- TEST
+ * Oracle for the unsplit geometric VOF step (LSGIR + FMFPA / EMFPA) -- TEST
  * INFRASTRUCTURE ONLY: called by tests/, the smoke check and the CPU-baseline
  * timing; never by the product path. Plain FP64 C, written from the paper
  * (arXiv 2111.01524): Sec. 2.1 (cut-off, PLIC, volume enforcement), Sec.
- * 2.1.1 (LSGIR), Sec. 2.2 (flux volumes, Eq. fnext, clip), Sec. 2.2.2
- * (FMFPA), Sec. 3 (grid, taggrid), Sec. 4.2 (Eq. eq:cfl, velocity fields).
+ * 2.1.1 (LSGIR), Sec. 2.2 (flux volumes, Eq. fnext, clip), Sec. 2.2.1
+ * (EMFPA), Sec. 2.2.2 (FMFPA), Sec. 3 (grid, taggrid), Sec. 4.2 (Eq. eq:cfl, velocity fields).
  *
  * Numerics are deliberately simple and independent of the CUDA library:
  *   - every volume is a sum of signed tetrahedra;
@@ -18,7 +18,8 @@
  * centre" is the volume centroid; back-traced FMFPA vertices are the
  * orthogonal projection of the streak-line point onto the side-plane
  * intersection line; the apex of the bottom triangulation moves along the
- * face normal by the closed-form amount that makes the signed volume V_d;
+ * face normal by the closed-form amount that makes the signed volume V_d
+ * (both constructions); the EMFPA side-face centre is the vertex average;
  * overlap candidates are the owner, the neighbour and their node neighbours;
  * face tag 1 carries V_F = V_d and face tag -1 carries V_F = 0.
  */
@@ -579,6 +580,109 @@ void orc_velocity_eval(const orc_velocity* v, const double x[3], double t, doubl
 /* --------------------------------------------------------- FMFPA (Sec 2.2.2) */
 static double poly_volume_loops(int nv, const double* V, int nf, const int* fp, const int* fi);
 
+/* face loops of a flux polyhedron over its vertex list (outward orientation
+ * for V_d > 0); returns the number of loops.
+ * method 0, FMFPA (Sec. 2.2.2): vertices x_0..x_{I-1}, back-traced
+ *   x_I..x_{2I-1}, apex 2I; loops: the cell face, I side quads, I bottom
+ *   triangles (2I+1 faces).
+ * method 1, EMFPA (Sec. 2.2.1): vertices as above, then the side-face
+ *   centres s_0..s_{I-1} at 2I..3I-1 and the apex at 3I; each side face
+ *   (x_{i+1}, x_i, x_{I+i}, x_{I+i+1}) is replaced by the four triangles
+ *   that join its edges to s_i (5I+1 faces). */
+static int flux_loops(int method, int I, int* fp, int* fi) {
+  int nfp = 0, k = 0;
+  fp[0] = 0;
+  for (int i = 0; i < I; ++i) fi[k++] = i;
+  fp[++nfp] = k;
+  for (int i = 0; i < I; ++i) {
+    int ip = (i + 1) % I;
+    int q[4] = {ip, i, I + i, I + ip};
+    if (method == 1) {
+      for (int e = 0; e < 4; ++e) {
+        fi[k++] = q[e]; fi[k++] = q[(e + 1) % 4]; fi[k++] = 2 * I + i;
+        fp[++nfp] = k;
+      }
+    } else {
+      for (int e = 0; e < 4; ++e) fi[k++] = q[e];
+      fp[++nfp] = k;
+    }
+  }
+  int apex = method == 1 ? 3 * I : 2 * I;
+  for (int i = 0; i < I; ++i) {
+    int ip = (i + 1) % I;
+    fi[k++] = I + ip; fi[k++] = I + i; fi[k++] = apex;
+    fp[++nfp] = k;
+  }
+  return nfp;
+}
+
+/* apex of the bottom triangulation: the centroid xc of the back-traced loop
+ * xb moved along the face normal n so that the closed surface has signed
+ * volume Vd (Sec. 2.2.1). Moving the apex by lam n changes the volume by
+ * -lam n.B/3, B the vector area of the back-traced loop, so lam = 3(V0 -
+ * Vd)/(n.B) with V0 the volume at lam = 0. Returns 0, or 2 if the loop is
+ * edge-on (|n.B| <= 1e-8 A) and the apex stays at xc. */
+static int place_apex(int nvp, double (*P)[3], int nfp, const int* fp, const int* fi,
+                      double (*xb)[3], int I, const double* n, double A, double Vd,
+                      int apex) {
+  double xc[3] = {0, 0, 0};
+  for (int i = 0; i < I; ++i)
+    for (int q = 0; q < 3; ++q) xc[q] += xb[i][q] / I;
+  for (int q = 0; q < 3; ++q) P[apex][q] = xc[q];
+  double V0 = poly_volume_loops(nvp, &P[0][0], nfp, fp, fi);
+  double B[3] = {0, 0, 0};
+  for (int i = 0; i < I; ++i) {
+    double w[3];
+    cross3(xb[i], xb[(i + 1) % I], w);
+    for (int q = 0; q < 3; ++q) B[q] += 0.5 * w[q];
+  }
+  double nB = dot3(n, B);
+  double lam = 0.0;
+  int fl = 0;
+  if (fabs(nB) > 1e-8 * A) lam = 3.0 * (V0 - Vd) / nB;
+  else fl = 2;
+  for (int q = 0; q < 3; ++q) P[apex][q] = xc[q] + lam * n[q];
+  return fl;
+}
+
+/* --------------------------------------------------------- EMFPA (Sec 2.2.1) */
+int orc_emfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
+              double dt, double* out, int capI, double* Vd, int* flags) {
+  int64_t b = m->fptr[f];
+  int I = (int)(m->fptr[f + 1] - b);
+  if (I > capI || I > 32) return -1;
+  const double* c = m->fc + 3 * f;
+  const double* n = m->fn + 3 * f;
+  double uc[3];
+  orc_velocity_eval(vel, c, th, uc);
+  *Vd = dot3(uc, n) * m->fa[f] * dt; /* Eq. a-donacion */
+  /* frame with origin at the face centroid; every vertex goes back along
+   * its own streak line with the velocity at t^{n+1/2} (Eq. streak-line2) */
+  double P[97][3], xb[32][3];
+  for (int i = 0; i < I; ++i) {
+    const double* xa = m->X + 3 * m->fvert[b + i];
+    double u[3];
+    orc_velocity_eval(vel, xa, th, u);
+    sub3(xa, c, P[i]);
+    for (int q = 0; q < 3; ++q) xb[i][q] = P[i][q] - dt * u[q];
+  }
+  for (int i = 0; i < I; ++i) {
+    int ip = (i + 1) % I;
+    for (int q = 0; q < 3; ++q) {
+      P[I + i][q] = xb[i][q];
+      /* geometric centre of side face i: plain vertex average */
+      P[2 * I + i][q] = 0.25 * (P[i][q] + P[ip][q] + xb[i][q] + xb[ip][q]);
+    }
+  }
+  int nvp = 3 * I + 1;
+  int fp[5 * 32 + 2], fi[16 * 32];
+  int nfp = flux_loops(1, I, fp, fi);
+  *flags = place_apex(nvp, P, nfp, fp, fi, xb, I, n, m->fa[f], *Vd, 3 * I);
+  for (int i = 0; i < nvp; ++i)
+    for (int q = 0; q < 3; ++q) out[3 * i + q] = P[i][q] + c[q];
+  return I;
+}
+
 int orc_fmfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
               double dt, double* out, int capI, double* Vd, int* flags) {
   int64_t b = m->fptr[f];
@@ -639,37 +743,9 @@ int orc_fmfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
   double P[65][3];
   for (int i = 0; i < I; ++i)
     for (int q = 0; q < 3; ++q) { P[i][q] = x[i][q]; P[I + i][q] = xb[i][q]; }
-  double xc[3] = {0, 0, 0};
-  for (int i = 0; i < I; ++i)
-    for (int q = 0; q < 3; ++q) xc[q] += xb[i][q] / I;
-  for (int q = 0; q < 3; ++q) P[2 * I][q] = xc[q];
   int fp[66], fi[66 * 4];
-  int nfp = 0, k = 0;
-  fp[0] = 0;
-  for (int i = 0; i < I; ++i) fi[k++] = i;
-  fp[++nfp] = k;
-  for (int i = 0; i < I; ++i) {
-    int ip = (i + 1) % I;
-    fi[k++] = ip; fi[k++] = i; fi[k++] = I + i; fi[k++] = I + ip;
-    fp[++nfp] = k;
-  }
-  for (int i = 0; i < I; ++i) {
-    int ip = (i + 1) % I;
-    fi[k++] = I + ip; fi[k++] = I + i; fi[k++] = 2 * I;
-    fp[++nfp] = k;
-  }
-  double V0 = poly_volume_loops(nvp, &P[0][0], nfp, fp, fi);
-  double B[3] = {0, 0, 0};
-  for (int i = 0; i < I; ++i) {
-    double w[3];
-    cross3(xb[i], xb[(i + 1) % I], w);
-    for (int q = 0; q < 3; ++q) B[q] += 0.5 * w[q];
-  }
-  double nB = dot3(n, B);
-  double lam = 0.0;
-  if (fabs(nB) > 1e-8 * m->fa[f]) lam = 3.0 * (V0 - *Vd) / nB;
-  else *flags |= 2;
-  for (int q = 0; q < 3; ++q) P[2 * I][q] = xc[q] + lam * n[q];
+  int nfp = flux_loops(0, I, fp, fi);
+  *flags |= place_apex(nvp, P, nfp, fp, fi, xb, I, n, m->fa[f], *Vd, 2 * I);
   for (int i = 0; i < nvp; ++i)
     for (int q = 0; q < 3; ++q) out[3 * i + q] = P[i][q] + c[q];
   return I;
@@ -868,7 +944,7 @@ static double truncate_in_cell(const orc_mesh* m, int nv, const double* V, int n
 void orc_faceflux(const orc_mesh* m, const orc_velocity* vel, double t, double dt,
                   const double* F, const int8_t* tag_f, const int8_t* tag_c,
                   const double* nrm, const double* Cp, double* Vd, double* VF,
-                  int64_t* stats) {
+                  int64_t* stats, int method) {
   (void)F;
   double th = t + 0.5 * dt;
   int64_t n_geo = 0, n_deg = 0, n_edge = 0, n_trunc = 0;
@@ -883,13 +959,14 @@ void orc_faceflux(const orc_mesh* m, const orc_velocity* vel, double t, double d
     if (tag_f[f] == -1) { VF[f] = 0.0; continue; }
     if (tag_f[f] == 1) { VF[f] = vd; continue; }
     ++n_geo;
-    double P[65 * 3];
+    double P[97 * 3];
     double vdd;
     int flags;
-    int I = orc_fmfpa(m, f, vel, th, dt, P, 32, &vdd, &flags);
+    int I = method == 1 ? orc_emfpa(m, f, vel, th, dt, P, 32, &vdd, &flags)
+                        : orc_fmfpa(m, f, vel, th, dt, P, 32, &vdd, &flags);
     if (flags & 1) ++n_deg;
     if (flags & 2) ++n_edge;
-    int nvp = 2 * I + 1;
+    int nvp = method == 1 ? 3 * I + 1 : 2 * I + 1;
     /* local frame at the face centroid */
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < nvp; ++i)
@@ -899,20 +976,8 @@ void orc_faceflux(const orc_mesh* m, const orc_velocity* vel, double t, double d
         if (xv > hi[d]) hi[d] = xv;
         P[3 * i + d] = xv - c[d];
       }
-    int fp[66], fi[66 * 4], nfp = 0, k = 0;
-    fp[0] = 0;
-    for (int i = 0; i < I; ++i) fi[k++] = i;
-    fp[++nfp] = k;
-    for (int i = 0; i < I; ++i) {
-      int ip = (i + 1) % I;
-      fi[k++] = ip; fi[k++] = i; fi[k++] = I + i; fi[k++] = I + ip;
-      fp[++nfp] = k;
-    }
-    for (int i = 0; i < I; ++i) {
-      int ip = (i + 1) % I;
-      fi[k++] = I + ip; fi[k++] = I + i; fi[k++] = 2 * I;
-      fp[++nfp] = k;
-    }
+    int fp[5 * 32 + 2], fi[16 * 32];
+    int nfp = flux_loops(method, I, fp, fi);
     int32_t cand[4096];
     int nc = orc_candidates(m, f, cand, 4096);
     if (nc > 4096) nc = 4096;

@@ -1,5 +1,5 @@
 /*
- * Oracle for the unsplit geometric VOF step (LSGIR + FMFPA) -- TEST
+ * Oracle for the unsplit geometric VOF step (LSGIR + FMFPA / EMFPA) -- TEST
  * INFRASTRUCTURE ONLY.
  *
  * A plain, slow FP64 CPU implementation of what one time step computes, used
@@ -86,13 +86,24 @@ int orc_fmfpa(const orc_mesh* m, int64_t face, const orc_velocity* v,
               double t_half, double dt, double* verts, int cap_I, double* Vd,
               int* flags);
 
-/* faceflux (Sec. 3.5 with Sec. 2.2): V_d and V_F for every face. stats[0]
- * = geometric faces, [1] = degenerate-line fallbacks, [2] = edge-on faces,
- * [3] = (face, cell) truncations evaluated. Threads: OpenMP over faces. */
+/* EMFPA flux polyhedron of one face (Sec. 2.2.1). verts receives 3I+1
+ * points: x_1..x_I, the back-traced x_{I+1}..x_{2I} (Eq. streak-line2 with
+ * the vertex velocity at t_half), the side-face centres s_1..s_I (vertex
+ * average of x_i, x_{i+1}, x_{I+i}, x_{I+i+1}) and the apex. Returns I, or
+ * -1 if I > cap_I. *Vd = (u_c.n) A dt. flags bit1: the back-traced loop was
+ * edge-on and the apex could not be placed (lambda = 0). */
+int orc_emfpa(const orc_mesh* m, int64_t face, const orc_velocity* v,
+              double t_half, double dt, double* verts, int cap_I, double* Vd,
+              int* flags);
+
+/* faceflux (Sec. 3.5 with Sec. 2.2): V_d and V_F for every face, with the
+ * flux polyhedra of `method` (0: FMFPA, 1: EMFPA). stats[0] = geometric
+ * faces, [1] = degenerate-line fallbacks, [2] = edge-on faces, [3] =
+ * (face, cell) truncations evaluated. Threads: OpenMP over faces. */
 void orc_faceflux(const orc_mesh* m, const orc_velocity* v, double t,
                   double dt, const double* F, const int8_t* tag_f,
                   const int8_t* tag_c, const double* nrm, const double* C,
-                  double* Vd, double* VF, int64_t* stats);
+                  double* Vd, double* VF, int64_t* stats, int method);
 
 /* vofadv (Eq. fnext + the final clip): F updated in place. */
 void orc_vofadv(const orc_mesh* m, const double* Vd, const double* VF,

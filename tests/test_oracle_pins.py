@@ -397,6 +397,238 @@ def test_fmfpa_face_matching(orc):
     assert checked > 10
 
 
+# ---------------------------------------------------------------- EMFPA
+def _emfpa_faces(nI):
+    """Faces of the edge-matched polyhedron as Sec. 2.2.1 states them: the
+    cell face; each side face (edge i, the two streak lines, the back-traced
+    edge) as four triangles around its centre s_i; the back-traced loop as a
+    fan of I triangles around the apex."""
+    faces = [list(range(nI))]
+    for i in range(nI):
+        ip = (i + 1) % nI
+        side = [ip, i, nI + i, nI + ip]
+        faces += [[side[e], side[(e + 1) % 4], 2 * nI + i] for e in range(4)]
+    faces += [[nI + (i + 1) % nI, nI + i, 3 * nI] for i in range(nI)]
+    return faces
+
+
+def _face_nodes(m, f):
+    return m["X"][m["face_vert"][m["face_ptr"][f]:m["face_ptr"][f + 1]]]
+
+
+def _rot_u(x, omega, c):
+    """rigid rotation about the z-parallel axis through c, written out"""
+    return np.stack([-omega * (x[:, 1] - c[1]), omega * (x[:, 0] - c[0]), 0.0 * x[:, 2]], 1)
+
+
+def test_emfpa_uniform_velocity_is_prism(orc):
+    m = I.kuhn_tet_mesh(3, seed=2)
+    om = orc.Mesh(m)
+    u = np.array((0.3, -0.2, 0.5))
+    vel = I.translation(u)
+    dt = 0.01
+    g = om.geometry()
+    for f in range(0, len(m["owner"]), 5):
+        P, vd, fl = om.emfpa(f, vel, 0.0, dt)
+        X = _face_nodes(m, f)
+        nI = len(X)
+        assert P.shape[0] == 3 * nI + 1  # 3I+1 vertices (Sec. 2.2.1)
+        assert np.allclose(P[:nI], X, atol=1e-15)
+        assert np.allclose(P[nI:2 * nI], X - dt * u, atol=1e-15)
+        # a uniform field makes every side face a planar parallelogram and
+        # the polyhedron the exact prism: the apex needs no correction
+        assert np.allclose(P[3 * nI], (X - dt * u).mean(0), atol=1e-14)
+        assert abs(vd - u @ g["face_nrm"][f] * g["face_area"][f] * dt) < 1e-18
+        assert len(_emfpa_faces(nI)) == 5 * nI + 1
+
+
+@pytest.mark.parametrize("gen", ["hex", "tet"])
+def test_emfpa_rotation_backtrace_and_volume(orc, gen):
+    """Rigid rotation: each vertex goes back along its own streak line with
+    its own velocity (Eq. streak-line2), the side centres are vertex
+    averages, and the apex lies on the normal through the centroid of the
+    back-traced loop at the height that makes the volume V_d."""
+    m = I.hex_mesh(5, jitter=0.2, seed=4) if gen == "hex" else I.kuhn_tet_mesh(4, seed=5)
+    om = orc.Mesh(m)
+    g = om.geometry()
+    omega, c = 2.0 * np.pi, (0.5, 0.5, 0.5)
+    vel = I.rotation(omega, c)
+    dt = 0.02
+    n_checked = 0
+    for f in range(0, len(m["owner"]), 3):
+        P, vd, fl = om.emfpa(f, vel, 0.1, dt)
+        X = _face_nodes(m, f)
+        nI = len(X)
+        xb = X - dt * _rot_u(X, omega, c)
+        assert np.allclose(P[nI:2 * nI], xb, atol=1e-15)
+        for i in range(nI):
+            ip = (i + 1) % nI
+            ctr = 0.25 * (X[i] + X[ip] + xb[i] + xb[ip])
+            assert np.allclose(P[2 * nI + i], ctr, atol=1e-15)
+        # apex on the normal line through the centroid of the back-traced loop
+        d = P[3 * nI] - xb.mean(0)
+        assert np.linalg.norm(np.cross(d, g["face_nrm"][f])) < 1e-14
+        if fl & 2:
+            continue
+        o = X.mean(0)
+        vol = orc.poly_volume(P - o, _emfpa_faces(nI))
+        A = g["face_area"][f]
+        assert abs(vol - vd) <= 1e-14 * max(abs(vd), A ** 1.5), (f, vol, vd)
+        n_checked += 1
+    assert n_checked > 20
+
+
+def test_emfpa_backtrace_uses_midtime_velocity(orc):
+    """The time-modulated deformation field (Sec. 4.2), written out: the
+    back-traced vertex uses the velocity at t^{n+1/2} = t + dt/2."""
+    m = I.hex_mesh(4, jitter=0.2, seed=7)
+    om = orc.Mesh(m)
+    T, t, dt = 3.0, 0.4, 0.05
+    vel = I.deformation(T)
+
+    def u(x, tt):
+        s, s2 = np.sin(np.pi * x), np.sin(2 * np.pi * x)
+        gt = np.cos(np.pi * tt / T)
+        return gt * np.stack([2 * s[:, 0] ** 2 * s2[:, 1] * s2[:, 2],
+                              -s2[:, 0] * s[:, 1] ** 2 * s2[:, 2],
+                              -s2[:, 0] * s2[:, 1] * s[:, 2] ** 2], 1)
+
+    for f in range(0, len(m["owner"]), 4):
+        P, _, _ = om.emfpa(f, vel, t + 0.5 * dt, dt)
+        X = _face_nodes(m, f)
+        nI = len(X)
+        assert np.allclose(P[nI:2 * nI], X - dt * u(X, t + 0.5 * dt), atol=1e-15)
+    # and the whole step hands faceflux t, not the mid-time
+    st = om.reconstruct(I.init_fraction(m, I.sphere((0.45, 0.5, 0.5), 0.3), levels=2))
+    Vd, _, _ = om.faceflux(vel, t, dt, st, orc.EMFPA)
+    g = om.geometry()
+    uc = u(g["face_cen"], t + 0.5 * dt)
+    assert np.allclose(Vd, (uc * g["face_nrm"]).sum(1) * g["face_area"] * dt, atol=1e-17)
+
+
+@pytest.mark.parametrize("gen", ["hex", "tet", "trihex"])
+def test_emfpa_volume_equals_vd(orc, gen):
+    m = {"hex": lambda: I.hex_mesh(6, jitter=0.25, seed=1),
+         "tet": lambda: I.kuhn_tet_mesh(4, seed=3),
+         "trihex": lambda: I.trihex_mesh(3, seed=2)}[gen]()
+    om = orc.Mesh(m)
+    vel = I.deformation(3.0)
+    dt = 0.5 / 6 / 2
+    A = om.geometry()["face_area"]
+    n_checked = 0
+    for f in range(0, len(m["owner"]), 3):
+        P, vd, fl = om.emfpa(f, vel, 0.2, dt)
+        nI = (P.shape[0] - 1) // 3
+        if fl & 2:
+            continue
+        vol = orc.poly_volume(P - P[:nI].mean(0), _emfpa_faces(nI))
+        assert abs(vol - vd) <= 1e-14 * max(abs(vd), A[f] ** 1.5), (f, vol, vd)
+        n_checked += 1
+    assert n_checked > 20
+
+
+def test_emfpa_edge_matching(orc):
+    """Polyhedra of two faces sharing an edge have the same four side
+    triangles on it, and polyhedra of faces sharing a vertex the same
+    back-traced point: no over/underlap along shared edges and streak lines
+    (the edge-matched property, Sec. 2.2.1)."""
+    m = I.kuhn_tet_mesh(3, seed=9)
+    om = orc.Mesh(m)
+    vel = I.deformation(3.0)
+    fv, fp = m["face_vert"], m["face_ptr"]
+    polys = {}
+
+    def poly(f):
+        if f not in polys:
+            polys[f] = om.emfpa(f, vel, 0.3, 0.02)[0]
+        return polys[f]
+
+    edges, verts = {}, {}
+    for f in range(len(m["owner"])):
+        loop = list(fv[fp[f]:fp[f + 1]])
+        for i in range(len(loop)):
+            e = tuple(sorted((loop[i], loop[(i + 1) % len(loop)])))
+            edges.setdefault(e, []).append((f, i))
+            verts.setdefault(loop[i], []).append((f, i))
+    checked = 0
+    for e, lst in edges.items():
+        if len(lst) < 2:
+            continue
+        sides = []
+        for f, i in lst[:3]:
+            P = poly(f)
+            nI = (P.shape[0] - 1) // 3
+            ip = (i + 1) % nI
+            ends = {fv[fp[f] + i]: (P[i], P[nI + i]), fv[fp[f] + ip]: (P[ip], P[nI + ip])}
+            sides.append((ends, P[2 * nI + i]))
+        (e0, s0) = sides[0]
+        for ends, sc in sides[1:]:
+            assert np.allclose(sc, s0, atol=1e-15)
+            for v in e:
+                assert np.allclose(ends[v][0], e0[v][0], atol=1e-15)
+                assert np.allclose(ends[v][1], e0[v][1], atol=1e-15)
+        checked += 1
+        if checked > 60:
+            break
+    assert checked > 20
+    for v, lst in list(verts.items())[:40]:
+        pts = []
+        for f, i in lst:
+            P = poly(f)
+            nI = (P.shape[0] - 1) // 3
+            pts.append(P[nI + i])
+        assert np.ptp(np.array(pts), axis=0).max() < 1e-15
+
+
+def test_emfpa_and_fmfpa_agree_for_uniform_flow(orc):
+    """A uniform field gives both constructions the same exact prism on
+    every face (planar sides, no apex correction), so their fluid volumes
+    agree up to rounding although the surfaces are triangulated
+    differently."""
+    m = I.kuhn_tet_mesh(5, seed=8)
+    om = orc.Mesh(m)
+    st = om.reconstruct(I.init_fraction(m, I.sphere((0.5, 0.5, 0.5), 0.22), levels=3))
+    vel = I.translation((0.4, -0.3, 0.2))
+    dt = om.suggest_dt(vel, 0.0, 0.6, 10.0)
+    Vd0, VF0, s0 = om.faceflux(vel, 0.0, dt, st, orc.FMFPA)
+    Vd1, VF1, s1 = om.faceflux(vel, 0.0, dt, st, orc.EMFPA)
+    assert np.array_equal(Vd0, Vd1)
+    assert s0[0] == s1[0] > 50  # the same geometric faces
+    assert np.abs(VF1 - VF0).max() < 1e-15 * np.abs(Vd0).max() * 100
+
+
+def test_emfpa_cfl1_translation_shifts_exactly(orc):
+    """u = (1,0,0), dt = h on a uniform grid: each x-face EMFPA polyhedron is
+    the upstream cell and the others are flat, so F moves one cell per step
+    for ANY F."""
+    n = 6
+    m = I.hex_mesh(n)
+    om = orc.Mesh(m)
+    F0 = I.init_fraction(m, I.sphere((0.45, 0.52, 0.48), 0.27), levels=3)
+    st = om.reconstruct(F0)
+    vel = I.translation((1.0, 0.0, 0.0))
+    new = om.step(vel, 0.0, 1.0 / n, st, method=orc.EMFPA)
+    F = st["F"].reshape(n, n, n)
+    G = new["F_unclipped_cut"].reshape(n, n, n)
+    assert np.abs(G[:, :, 1:] - F[:, :, :-1]).max() < 2e-15
+    assert np.abs(G[:, :, 0]).max() == 0.0
+
+
+def test_emfpa_deformation_conserves_volume(orc):
+    m = I.hex_mesh(16)
+    om = orc.Mesh(m)
+    V = om.geometry()["cell_vol"]
+    st = om.reconstruct(I.init_fraction(m, I.sphere((0.35, 0.35, 0.35), 0.15)))
+    vel = I.deformation(3.0)
+    t = 0.0
+    for _ in range(4):
+        dt = om.suggest_dt(vel, t, 0.5, 3.0)
+        v0 = (V * st["F"]).sum()
+        new = om.step(vel, t, dt, st, method=orc.EMFPA)
+        assert abs((V * new["F_unclipped_cut"]).sum() - v0) < 1e-13 * v0
+        st, t = new, t + dt
+
+
 # ---------------------------------------------------------------- LSGIR
 def test_lsgir_exact_for_linear_field(orc):
     m = I.kuhn_tet_mesh(4, seed=4)
