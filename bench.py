@@ -46,13 +46,23 @@ UNIT = "cell-steps/s"
 # construction and of one (face, cell) truncation with its divergence sum
 FLOPS_PER_ACTIVE_FACE = 350.0      # FMFPA construction
 FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
+# EMFPA (Sec. 2.2.1): one velocity per vertex instead of two but five
+# triangle volumes per vertex; its surface has twice the face-vertex loop
+# entries of FMFPA (64 against 32 for a hex face), and a truncation's
+# clipping and divergence sum scale with those entries
+FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0, 2400.0)}
 # ncu capture of one flux launch (128^3 deformation step, mixed: ~57,300 active
 # faces): dram__bytes_read.sum + dram__bytes_write.sum = 26.94 + 1.91 MB, i.e.
 # 504 B per active face, issue active 38.2%, FMA pipe 10.9%; valid for the
 # kernel source it was taken on (traffic is null for any other source)
-FLUX_NCU = {"source_sha256": "5f7825894673ab28cd57465c2d6fd2bd6e6be737c9b3f3685b04317821ae35ea",
-            "dram_bytes_per_active_face": 504.0, "issue_active": 0.382, "fma_pipe_active": 0.109,
-            "capture": "profiles/k_flux_deformation128_mixed.md"}
+# ncu --set full of the mixed flux kernel (128^3 deformation, 4th step's launch, ~57,300
+# active faces) per flux-polyhedron construction; valid only for the source it was taken on
+FLUX_NCU = {"source_sha256": "a7f9353f1fcc19bb2321b21ba2fd5936ab56832ec619e83e135cc26e0cb5dc00",
+            "fmfpa": {"dram_bytes_per_active_face": 506.0, "issue_active": 0.396,
+                      "fma_pipe_active": 0.109, "capture": "profiles/k_flux_deformation128_mixed.md"},
+            "emfpa": {"dram_bytes_per_active_face": 504.0, "issue_active": 0.392,
+                      "fma_pipe_active": 0.109,
+                      "capture": "profiles/k_flux_deformation128_mixed_emfpa.md"}}
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
 N_SM = 152
@@ -66,6 +76,8 @@ def parse():
     p.add_argument("--impl", default="gvof", choices=["gvof", "reference"])
     p.add_argument("--grid", type=int, default=256)
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--flux", default="fmfpa", choices=["fmfpa", "emfpa"],
+                   help="flux polyhedron: face-matched (Sec. 2.2.2) or edge-matched (Sec. 2.2.1)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -201,7 +213,7 @@ def run_steps(ctx, vel, cfl, t_end, t, n, stream, timing=False):
     return t, evs
 
 
-def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision):
+def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision, flux="fmfpa"):
     """Roofline of the dominant kernel: algorithmic HBM bytes per launch for the
     sweeps, algorithmic flops per launch for the band kernels."""
     ms, launches = phase["ms"], phase["launches"]
@@ -223,15 +235,16 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
                 "algorithmic_bytes_per_launch": b, "peak_source": peak_kind}
     # band kernels: plain ALU arithmetic
     # the counters describe the last advect (one launch of each band kernel)
-    fl = (ctx_counts["n_active_faces"] * FLOPS_PER_ACTIVE_FACE
-          + ctx_counts["n_truncations"] * FLOPS_PER_TRUNCATION)
+    f_face, f_trunc = FLOPS[flux]
+    fl = ctx_counts["n_active_faces"] * f_face + ctx_counts["n_truncations"] * f_trunc
     traffic, ncu = None, None
     if name == "flux" and precision == "mixed":
         import hashlib
         src = os.path.join(ROOT, "paper_2111_01524_gb300", "csrc", "k_flux.cu")
         if hashlib.sha256(open(src, "rb").read()).hexdigest() == FLUX_NCU["source_sha256"]:
-            traffic = FLUX_NCU["dram_bytes_per_active_face"] * ctx_counts["n_active_faces"]
-            ncu = {k: FLUX_NCU[k] for k in ("issue_active", "fma_pipe_active", "capture")}
+            rec = FLUX_NCU[flux]
+            traffic = rec["dram_bytes_per_active_face"] * ctx_counts["n_active_faces"]
+            ncu = {k: rec[k] for k in ("issue_active", "fma_pipe_active", "capture")}
     mhz = clocks.get("sm_mhz") or 1900.0
     lanes = FP32_LANES_PER_SM if precision == "mixed" else FP64_LANES_PER_SM
     peak = N_SM * lanes * 2 * mhz * 1e6 / 1e12
@@ -243,16 +256,17 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
                            f"median SM clock {mhz:.0f} MHz"}
 
 
-def cpu_baseline(mesh, F0, vel, cfl, t_end, steps):
+def cpu_baseline(mesh, F0, vel, cfl, t_end, steps, flux="fmfpa"):
     import oracle
     oracle.build()
     om = oracle.Mesh(mesh)
     st = om.reconstruct(F0)
     t = 0.0
     t0 = time.perf_counter()
+    method = oracle.EMFPA if flux == "emfpa" else oracle.FMFPA
     for _ in range(steps):
         dt = om.suggest_dt(vel, t, cfl, t_end)
-        st = om.step(vel, t, dt, st)
+        st = om.step(vel, t, dt, st, method=method)
         t += dt
     el = time.perf_counter() - t0
     return {"value": om.n_cell * steps / el, "unit": UNIT, "cores": oracle.num_threads(),
@@ -270,17 +284,18 @@ def main_reference(a):
     oracle.build()
     om = oracle.Mesh(mesh)
     st = om.reconstruct(F0)
+    method = oracle.EMFPA if a.flux == "emfpa" else oracle.FMFPA
     t = 0.0
     for _ in range(a.warmup):
         dt = om.suggest_dt(vel, t, cfl, t_end)
-        st = om.step(vel, t, dt, st)
+        st = om.step(vel, t, dt, st, method=method)
         t += dt
     lat = []
     t0 = time.perf_counter()
     for _ in range(a.steps):
         s0 = time.perf_counter()
         dt = om.suggest_dt(vel, t, cfl, t_end)
-        st = om.step(vel, t, dt, st)
+        st = om.step(vel, t, dt, st, method=method)
         t += dt
         lat.append((time.perf_counter() - s0) * 1e3)
     el = time.perf_counter() - t0
@@ -291,7 +306,8 @@ def main_reference(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"3D deformation, hex {a.grid}^3, T=3, "
                                                         "CFL 0.5, sphere r=0.15",
-                                            "grid": a.grid, "cells": om.n_cell},
+                                            "grid": a.grid, "cells": om.n_cell,
+                                            "flux_polyhedron": a.flux},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"{a.steps} full steps of the {a.grid}^3 workload"},
@@ -422,7 +438,8 @@ def main_tets(a):
     vel = I.rotation(2 * np.pi)
     res = {}
     for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
-        ctx = V.Context(m, precision=prec)
+        ctx = V.Context(m, precision=prec,
+                        flux=V.FLUX_EMFPA if a.flux == "emfpa" else V.FLUX_FMFPA)
         ctx.set_fraction(F0)
         ctx.reconstruct()
         t = 0.0
@@ -460,7 +477,7 @@ def main_tets(a):
             "data": "synthetic",
             "config": {"workload": "64^3 x 6 jittered Kuhn tets, sphere r=0.15 at (0.5,0.75,0.5), "
                                    "rigid rotation, CFL 0.4", "cells": int(m["n_cell"]),
-                       "parallelism": f"replicas x{ws}"},
+                       "flux_polyhedron": a.flux, "parallelism": f"replicas x{ws}"},
             "gpu_launches": 6 * a.steps, "clocks": res["mixed"]["clocks"],
             "fp64_path": {"value": res["fp64"]["value"],
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
@@ -593,6 +610,7 @@ def main():
     mesh, F0, vel, cfl, t_end = workload(a.grid)
     counts = I.mesh_counts(mesh)
     prec = V.PREC_MIXED if a.precision == "mixed" else V.PREC_FP64
+    flux = V.FLUX_EMFPA if a.flux == "emfpa" else V.FLUX_FMFPA
     stream = torch.cuda.current_stream()
     F0_dev = torch.from_numpy(F0).cuda()
 
@@ -602,7 +620,7 @@ def main():
             dist.barrier()
 
     def measure(precision, steps, warmup, with_phases):
-        ctx = V.Context(mesh, precision=precision)
+        ctx = V.Context(mesh, precision=precision, flux=flux)
         ctx.set_fraction(F0_dev, stream=stream)
         ctx.reconstruct(stream=stream)
         t, _ = run_steps(ctx, vel, cfl, t_end, 0.0, warmup, stream)
@@ -669,7 +687,7 @@ def main():
     # from pinned host memory, runs reconstruct + advect, and reads F back
     e2e = None
     if not a.no_e2e:
-        ctxe = V.Context(mesh, precision=prec)
+        ctxe = V.Context(mesh, precision=prec, flux=flux)
         Fh = torch.from_numpy(F0.copy()).pin_memory().numpy()
         ctxe.set_fraction(Fh, stream=stream)
         t = 0.0
@@ -702,12 +720,12 @@ def main():
     peaks, peak_kind = measured_peaks()
     dom = max(phases.items(), key=lambda kv: kv[1][0])
     phase = {"name": dom[0], "ms": dom[1][0], "launches": dom[1][1]}
-    rl = roofline(stats, phase, counts, peaks, peak_kind, clocks, a.precision)
+    rl = roofline(stats, phase, counts, peaks, peak_kind, clocks, a.precision, a.flux)
     launches = sum(n for _, n in phases.values())
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(mesh, F0, vel, cfl, t_end, a.cpu_steps)
+        cpu = cpu_baseline(mesh, F0, vel, cfl, t_end, a.cpu_steps, a.flux)
 
     if rank == 0:
         line = {
@@ -721,7 +739,8 @@ def main():
                                    f"unit cube, sphere r=0.15 at (0.35,0.35,0.35), T=3, CFL 0.5, "
                                    f"steps from t=0",
                        "grid": a.grid, "cells": counts["n_cell"], "faces": counts["n_face"],
-                       "precision": a.precision, "parallelism": f"replicas x{ws}",
+                       "precision": a.precision, "flux_polyhedron": a.flux,
+                       "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (mesh + state ~10 GB), no flush"},
             "gpu_launches": launches,
             "phases_ms": {k: v[0] for k, v in phases.items()},

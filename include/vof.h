@@ -2,9 +2,10 @@
  * gvof: GB300 (sm_103a) CUDA library for the data-parallel hot path of the
  * unsplit geometric volume-of-fluid method of arXiv 2111.01524 (gVOF):
  * LSGIR reconstruction (Sec. 2.1.1) with a volume-enforcing plane constant
- * (Sec. 2.1), FMFPA face-matched flux polyhedra (Sec. 2.2.2) truncated by
- * the upstream cells' PLIC half-spaces (Sec. 2.2), and the conservative
- * update of Eq. fnext with the final clip (Sec. 2.2).
+ * (Sec. 2.1), FMFPA face-matched (Sec. 2.2.2) or EMFPA edge-matched (Sec.
+ * 2.2.1) flux polyhedra truncated by the upstream cells' PLIC half-spaces
+ * (Sec. 2.2), and the conservative update of Eq. fnext with the final clip
+ * (Sec. 2.2).
  *
  * Conventions
  *  - Mesh: OpenFOAM-like face-based polyhedral mesh (Sec. 3.1). Faces are
@@ -48,6 +49,11 @@ typedef enum {
 enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED = 1 };
 enum { VOF_MEM_HOST = 0, VOF_MEM_DEVICE = 1 };
 enum { VOF_VEL_DEFORMATION = 1, VOF_VEL_ROTATION = 2, VOF_VEL_TRANSLATION = 3 };
+/* flux polyhedron construction (vof_options.flux_polyhedron) */
+enum { VOF_FLUX_FMFPA = 0, VOF_FLUX_EMFPA = 1 };
+/* points per face in vof_get_flux_polyhedra: 3I+1 for an EMFPA face of
+ * I <= 6 nodes, 2I+1 for an FMFPA face of I <= 8 */
+enum { VOF_MAX_POLY_VERTS = 19 };
 
 typedef struct vof_ctx vof_ctx;
 
@@ -68,12 +74,19 @@ typedef struct {
  * precision: VOF_PREC_FP64 (all geometry in FP64) or VOF_PREC_MIXED
  * (geometry in FP32 in face- or cell-local scaled coordinates; FP64 for the
  * plane constant of cells with F or 1-F below 1e-3, for V_d, for the
- * per-face flux sums, the cell update and global sums). */
+ * per-face flux sums, the cell update and global sums).
+ * flux_polyhedron: VOF_FLUX_FMFPA (Sec. 2.2.2: 2I+1 faces, side faces
+ * parallel to the edge-centre velocity) or VOF_FLUX_EMFPA (Sec. 2.2.1:
+ * 5I+1 faces, each vertex back-traced with its own velocity, side faces
+ * split into four triangles). EMFPA needs every face to have at most 6
+ * nodes (its 31 faces fill the per-face capacity); vof_init returns
+ * VOF_EINVAL otherwise. reserved: must be zero. */
 typedef struct {
   double eps;
   double beta;
   int32_t precision;
-  int32_t reserved[7];
+  int32_t flux_polyhedron;
+  int32_t reserved[6];
 } vof_options;
 
 /* Prescribed velocity of the test problems (Sec. 4.2):
@@ -202,10 +215,13 @@ vof_status vof_get_neighbors(vof_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t* 
  * faces: HOST [n]; out_ptr HOST [n+1]; out_idx HOST [cap]. */
 vof_status vof_get_candidates(vof_ctx* ctx, const int32_t* faces, int n, int64_t* out_ptr,
                               int32_t* out_idx, int64_t cap);
-/* FMFPA flux polyhedra of the given faces built by the device routine the
- * flux kernel uses (Sec. 2.2.2): verts HOST [n * 17 * 3] absolute
- * coordinates, 2I+1 points per face (x_1..x_I, back-traced x_{I+1}..x_{2I},
- * apex), padded with zeros; counts HOST [n] receives I. */
+/* Flux polyhedra of the given faces built by the device routine the flux
+ * kernel uses, with the context's construction: verts HOST [n *
+ * VOF_MAX_POLY_VERTS * 3] absolute coordinates, padded with zeros; FMFPA
+ * (Sec. 2.2.2): 2I+1 points per face (x_1..x_I, back-traced x_{I+1}..x_{2I},
+ * apex); EMFPA (Sec. 2.2.1): 3I+1 points (x_1..x_I, back-traced
+ * x_{I+1}..x_{2I}, side-face centres s_1..s_I, apex). counts HOST [n]
+ * receives I. */
 vof_status vof_get_flux_polyhedra(vof_ctx* ctx, const vof_velocity* vel, double t, double dt,
                                   const int32_t* faces, int n, double* verts, int32_t* counts);
 /* counters and global sums (synchronises the stream). */

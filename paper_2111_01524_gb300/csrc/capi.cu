@@ -230,8 +230,14 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     o.precision = VOF_PREC_FP64;
   }
   if (!(o.eps > 0 && o.eps < 0.5) || !(o.beta > 0) ||
-      (o.precision != VOF_PREC_FP64 && o.precision != VOF_PREC_MIXED))
+      (o.precision != VOF_PREC_FP64 && o.precision != VOF_PREC_MIXED) ||
+      (o.flux_polyhedron != VOF_FLUX_FMFPA && o.flux_polyhedron != VOF_FLUX_EMFPA))
     return fail(VOF_EINVAL, "bad options");
+  for (int k = 0; k < 6; ++k)
+    if (o.reserved[k] != 0) return fail(VOF_EINVAL, "reserved options must be zero");
+  if (o.flux_polyhedron == VOF_FLUX_EMFPA && maxI > kMaxEmfpaVerts)
+    return fail(VOF_EINVAL, "EMFPA supports faces of at most 6 nodes; this mesh has " +
+                                std::to_string(maxI));
 
   HostConn hc;
   std::string err;
@@ -796,7 +802,7 @@ vof_status vof_get_flux_polyhedra(vof_ctx* c, const vof_velocity* vel, double t,
   st = upload_params(c, tt.data(), dd.data(), 0);
   if (st != VOF_OK) return st;
   if (n == 0) return VOF_OK;
-  const int NBV = 2 * kMaxFaceVerts + 1;
+  const int NBV = VOF_MAX_POLY_VERTS;
   int32_t *df, *dcnt;
   double* dv;
   CK(cudaMalloc(&df, sizeof(int32_t) * n));

@@ -1,5 +1,6 @@
-// Face fluxes of the active faces (Sec. 2.2): FMFPA flux polyhedron
-// (Sec. 2.2.2) of each tag-0 face, truncated by the half-spaces of every
+// Face fluxes of the active faces (Sec. 2.2): FMFPA (Sec. 2.2.2) or EMFPA
+// (Sec. 2.2.1) flux polyhedron of each tag-0 face, truncated by the
+// half-spaces of every
 // overlapped candidate cell and, for interfacial cells, by its PLIC
 // half-space (Sec. 2.2); the truncated volume is a divergence-theorem sum
 // over the faces of the clipped polyhedron. One warp per active face.
@@ -57,7 +58,8 @@ namespace {
 
 constexpr int kWarps = 4;
 constexpr int MAXI = kMaxFaceVerts;   // face vertices
-constexpr int NB = 2 * MAXI + 1;      // base polyhedron vertices / faces
+// base polyhedron vertices: 2I+1 (FMFPA, I <= 8) or 3I+1 (EMFPA, I <= 6)
+constexpr int NB = VOF_MAX_POLY_VERTS;
 constexpr int NV = 80;                // vertex table capacity
 constexpr int NF = 32;                // face capacity (one lane each)
 constexpr int LM = 32;                // loop length capacity
@@ -117,13 +119,52 @@ struct PolyState {
   int nv, nf, cur;
 };
 
-// restore the FMFPA polyhedron: x_0..x_{I-1}, back-traced I..2I-1, apex 2I;
-// faces: the cell face, I side quads, I bottom triangles (Sec. 2.2.2). A
-// side quad whose back-traced vertices do not both lie on its side plane
-// (streak-line fallback) is not planar; it is split into the triangles
-// (x_{i+1}, x_i, x_{I+i}) and (x_{i+1}, x_{I+i}, x_{I+i+1}), bit i of split.
-template <typename G>
+// vertices of the base polyhedron of a face of I nodes
+template <int KIND>
+__device__ __forceinline__ int base_verts(int I) {
+  return KIND == VOF_FLUX_EMFPA ? 3 * I + 1 : 2 * I + 1;
+}
+
+// restore the base polyhedron from P.b*.
+// FMFPA (Sec. 2.2.2): x_0..x_{I-1}, back-traced I..2I-1, apex 2I; faces: the
+// cell face, I side quads, I bottom triangles. A side quad whose
+// back-traced vertices do not both lie on its side plane (streak-line
+// fallback) is not planar; it is split into the triangles (x_{i+1}, x_i,
+// x_{I+i}) and (x_{i+1}, x_{I+i}, x_{I+i+1}), bit i of split.
+// EMFPA (Sec. 2.2.1): the same first 2I vertices, side-face centres
+// 2I..3I-1, apex 3I; faces: the cell face, four triangles per side quad
+// (x_{i+1}, x_i, x_{I+i}, x_{I+i+1}) joining its edges to its centre, I
+// bottom triangles.
+template <typename G, int KIND>
 __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, int lane) {
+  if constexpr (KIND == VOF_FLUX_EMFPA) {
+    const int nvb = 3 * I + 1, nfb = 5 * I + 1;
+    if (lane < nvb) { P.vx[lane] = P.bx[lane]; P.vy[lane] = P.by[lane]; P.vz[lane] = P.bz[lane]; }
+    if (lane == 0) {
+      for (int i = 0; i < I; ++i) P.fv[0][i][0] = (uint8_t)i;
+      P.flen[0][0] = (uint8_t)I;
+    } else if (lane <= 4 * I) {
+      const int t = lane - 1, i = t >> 2, e = t & 3, ip = (i + 1 == I) ? 0 : i + 1;
+      // edge e of the side quad (ip, i, I+i, I+ip), then its centre
+      const int a = e == 0 ? ip : e == 1 ? i : e == 2 ? I + i : I + ip;
+      const int b = e == 0 ? i : e == 1 ? I + i : e == 2 ? I + ip : ip;
+      P.fv[0][0][lane] = (uint8_t)a;
+      P.fv[0][1][lane] = (uint8_t)b;
+      P.fv[0][2][lane] = (uint8_t)(2 * I + i);
+      P.flen[0][lane] = 3;
+    } else if (lane < nfb) {
+      const int i = lane - 1 - 4 * I, ip = (i + 1 == I) ? 0 : i + 1;
+      P.fv[0][0][lane] = (uint8_t)(I + ip);
+      P.fv[0][1][lane] = (uint8_t)(I + i);
+      P.fv[0][2][lane] = (uint8_t)(3 * I);
+      P.flen[0][lane] = 3;
+    }
+    st.nv = nvb;
+    st.nf = nfb;
+    st.cur = 0;
+    __syncwarp();
+    return;
+  } else {
   const int nvb = 2 * I + 1;
   const int nsplit = __popc(split);
   if (lane < nvb) {
@@ -163,6 +204,7 @@ __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, i
   st.nf = nvb + nsplit;
   st.cur = 0;
   __syncwarp();
+  }
 }
 
 // drop unreferenced vertices and renumber (keeps room for a clip)
@@ -432,7 +474,7 @@ struct FaceFrame {
   int I;
   G lo[3], hi[3];                  // local bounding box of the polyhedron
   int degenerate, edgeon;
-  unsigned split;                  // non-planar side quads (bit i: side i)
+  unsigned split;                  // non-planar FMFPA side quads (bit i: side i)
 };
 
 // FMFPA construction (Sec. 2.2.2) into P.b*: side plane i contains edge i
@@ -558,6 +600,111 @@ __device__ GVOF_OUTER_ATTR bool build_fmfpa(const DevMesh& M, const GeoView<G>& 
   return true;
 }
 
+// EMFPA construction (Sec. 2.2.1) into P.b*: lane i holds face vertex i;
+// the vertex goes back along its own streak line with its own velocity at
+// t^{n+1/2} (Eq. streak-line2); side face i (x_i, x_{i+1} and their
+// back-traced points) is represented by its vertex-average centre; the
+// centroid of the back-traced loop moves along the face normal by the
+// closed-form amount that makes the signed volume of the 5I+1 faces equal
+// V_d. Faces sharing an edge compute the same four side points from the
+// same two nodes, so their side triangles coincide.
+template <typename G>
+__device__ GVOF_OUTER_ATTR bool build_emfpa(const DevMesh& M, const GeoView<G>& Gv,
+                                         const GridParam& p, int j, double Vd, Poly<G>& P,
+                                         FaceFrame<G>& frs, int lane) {
+  FaceFrame<G> fr;
+  const int64_t fb = M.fptr[j];
+  const int I = (int)(M.fptr[j + 1] - fb);
+  fr.I = I;
+  if (I > kMaxEmfpaVerts || I < 3) {
+    if (lane == 0) frs.I = I;
+    __syncwarp();
+    return false;
+  }
+  fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
+  fr.L = sqrt(Gv.fa[j]);
+  fr.sc = G(1) / fr.L;
+  const G nx = Gv.fnx[j], ny = Gv.fny[j], nz = Gv.fnz[j];
+  const bool act = lane < I;
+  const int vi = act ? M.fvert[fb + lane] : M.fvert[fb];
+  const typename Prec<G>::A X = Gv.vx[vi], Y = Gv.vy[vi], Z = Gv.vz[vi];
+  const int nxt = (lane + 1 >= I) ? 0 : lane + 1;
+  // vertex velocity times dt, in face-local scaled units
+  G ux, uy, uz;
+  vel0<G>(p.vel, absval(X), absval(Y), absval(Z), ux, uy, uz);
+  const G k = (G)(p.g * p.dt) * fr.sc;
+  const G lx = rel(X, fr.cx) * fr.sc, ly = rel(Y, fr.cy) * fr.sc, lz = rel(Z, fr.cz) * fr.sc;
+  const G bxl = lx - k * ux, byl = ly - k * uy, bzl = lz - k * uz;
+  const G lxn = __shfl_sync(GVOF_FULL, lx, nxt), lyn = __shfl_sync(GVOF_FULL, ly, nxt),
+          lzn = __shfl_sync(GVOF_FULL, lz, nxt);
+  const G bxn = __shfl_sync(GVOF_FULL, bxl, nxt), byn = __shfl_sync(GVOF_FULL, byl, nxt),
+          bzn = __shfl_sync(GVOF_FULL, bzl, nxt);
+  // centre of side face i
+  const G sx = G(0.25) * (lx + lxn + bxl + bxn), sy = G(0.25) * (ly + lyn + byl + byn),
+          sz = G(0.25) * (lz + lzn + bzl + bzn);
+  fr.degenerate = 0;
+  fr.split = 0u;
+  const G inv_I = G(1) / (G)I;
+  const G xcx = wsum(act ? bxl : G(0)) * inv_I, xcy = wsum(act ? byl : G(0)) * inv_I,
+          xcz = wsum(act ? bzl : G(0)) * inv_I;
+  const G Bx = wsum(act ? G(0.5) * (byl * bzn - bzl * byn) : G(0));
+  const G By = wsum(act ? G(0.5) * (bzl * bxn - bxl * bzn) : G(0));
+  const G Bz = wsum(act ? G(0.5) * (bxl * byn - byl * bxn) : G(0));
+  auto det3 = [](G ax_, G ay_, G az_, G bx_, G by_, G bz_, G cx_, G cy_, G cz_) {
+    return ax_ * (by_ * cz_ - bz_ * cy_) + ay_ * (bz_ * cx_ - bx_ * cz_) +
+           az_ * (bx_ * cy_ - by_ * cx_);
+  };
+  const G l0x = __shfl_sync(GVOF_FULL, lx, 0), l0y = __shfl_sync(GVOF_FULL, ly, 0),
+          l0z = __shfl_sync(GVOF_FULL, lz, 0);
+  // signed volume with the apex at the centroid (origin = face centroid)
+  G v6 = G(0);
+  if (act) {
+    if (lane >= 1 && lane + 1 < I) v6 += det3(l0x, l0y, l0z, lx, ly, lz, lxn, lyn, lzn);
+    v6 += det3(lxn, lyn, lzn, lx, ly, lz, sx, sy, sz);      // side triangles
+    v6 += det3(lx, ly, lz, bxl, byl, bzl, sx, sy, sz);
+    v6 += det3(bxl, byl, bzl, bxn, byn, bzn, sx, sy, sz);
+    v6 += det3(bxn, byn, bzn, lxn, lyn, lzn, sx, sy, sz);
+    v6 += det3(bxn, byn, bzn, bxl, byl, bzl, xcx, xcy, xcz);  // bottom triangle
+  }
+  const G V0 = wsum(v6) / G(6);
+  const G Vl = (G)Vd * (fr.sc * fr.sc * fr.sc);
+  const G nB = nx * Bx + ny * By + nz * Bz;
+  G lam = G(0);
+  fr.edgeon = 0;
+  if (fabs(nB) > G(1e-8)) lam = G(3) * (V0 - Vl) / nB;
+  else fr.edgeon = 1;
+  if (act) {
+    P.bx[lane] = lx; P.by[lane] = ly; P.bz[lane] = lz;
+    P.bx[I + lane] = bxl; P.by[I + lane] = byl; P.bz[I + lane] = bzl;
+    P.bx[2 * I + lane] = sx; P.by[2 * I + lane] = sy; P.bz[2 * I + lane] = sz;
+  }
+  if (lane == 0) {
+    P.bx[3 * I] = xcx + lam * nx;
+    P.by[3 * I] = xcy + lam * ny;
+    P.bz[3 * I] = xcz + lam * nz;
+  }
+  __syncwarp();
+  const G big = (G)1e30;
+  G x0 = big, x1 = -big, y0 = big, y1 = -big, z0 = big, z1 = -big;
+  if (lane < 3 * I + 1) {
+    x0 = x1 = P.bx[lane]; y0 = y1 = P.by[lane]; z0 = z1 = P.bz[lane];
+  }
+  fr.lo[0] = wmin(x0); fr.lo[1] = wmin(y0); fr.lo[2] = wmin(z0);
+  fr.hi[0] = wmax(x1); fr.hi[1] = wmax(y1); fr.hi[2] = wmax(z1);
+  if (lane == 0) frs = fr;
+  __syncwarp();
+  return true;
+}
+
+// the flux polyhedron of the context's construction
+template <typename G, int KIND>
+__device__ __forceinline__ bool build_polyhedron(const DevMesh& M, const GeoView<G>& Gv,
+                                                 const GridParam& p, int j, double Vd, Poly<G>& P,
+                                                 FaceFrame<G>& frs, int lane) {
+  if constexpr (KIND == VOF_FLUX_EMFPA) return build_emfpa<G>(M, Gv, p, j, Vd, P, frs, lane);
+  else return build_fmfpa<G>(M, Gv, p, j, Vd, P, frs, lane);
+}
+
 __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key) {
   int lo = 0, hi = n;
   while (lo < hi) {
@@ -579,13 +726,12 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
 // the volume of P itself). Vertices within tol of a plane count as on its
 // inner side; tol is a few ulps of the face-local unit, so the volume this
 // neglects is of the order of the rounding of the plane itself.
-template <typename G>
+template <typename G, int KIND>
 __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
                                           G Vl, int lane, unsigned& err, int* whole) {
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
   *whole = 0;
-  const int nvb = 2 * fr.I + 1;
-  const bool hv = lane < nvb;
+  const bool hv = lane < base_verts<KIND>(fr.I);
   const G bx = hv ? P.bx[lane] : G(0), by = hv ? P.by[lane] : G(0), bz = hv ? P.bz[lane] : G(0);
   unsigned cut = 0u;
   for (int g = 0; g < np; ++g) {
@@ -612,7 +758,7 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
     cut &= ~(1u << last);
   }
   PolyState st;
-  restore_base(P, st, fr.I, fr.split, lane);
+  restore_base<G, KIND>(P, st, fr.I, fr.split, lane);
   int res = 0;
   while (cut && res != 2) {
     const int g = __ffs(cut) - 1;
@@ -633,7 +779,7 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
 // that join its centroid to the fan triangles of its faces (winding-number
 // decomposition, valid for any closed cell); the PLIC half-space, if any, is
 // already in P.pl[NF]
-template <typename G>
+template <typename G, int KIND>
 __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>& Gv, int k,
                                              int64_t c0, int nfk, bool tag0, const FaceFrame<G>& fr,
                                              G Vl, Poly<G>& P, int lane, unsigned& err) {
@@ -720,7 +866,7 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
       }
       __syncwarp();
       int w = 0;
-      v += sg * truncate_planes<G>(P, 4, tag0, fr, Vl, lane, err, &w);
+      v += sg * truncate_planes<G, KIND>(P, 4, tag0, fr, Vl, lane, err, &w);
     }
   }
   return v;
@@ -733,7 +879,7 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
 // is the intersection of its face half-spaces; a non-convex cell is the
 // signed sum of the tetrahedra that join its centroid to the fan triangles of
 // its faces (winding-number decomposition, valid for any closed cell).
-template <typename G>
+template <typename G, int KIND>
 __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
                                            const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
                                            Poly<G>& P, int lane, unsigned& err, bool empty_side,
@@ -773,9 +919,9 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
                         oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
     }
     __syncwarp();
-    return truncate_planes<G>(P, nfk, tag0, fr, Vl, lane, err, whole);
+    return truncate_planes<G, KIND>(P, nfk, tag0, fr, Vl, lane, err, whole);
   }
-  return truncate_nonconvex<G>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
+  return truncate_nonconvex<G, KIND>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
 }
 
 // one chunk of up to 32 candidate cells of face j (pass 0: the owner's node
@@ -785,7 +931,7 @@ __device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& G
 // test is already this one) by the cell's face planes: a cell with a plane
 // that has every vertex of P strictly outside cannot meet P; returns the
 // lane's cell (-1: none) and its tag
-template <typename G>
+template <typename G, int KIND>
 __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
                                          const FaceFrame<G>& fr, const Poly<G>& P, int own, int64_t a0,
                                          int na, int pass, int c0, int64_t b0, int nb, int idx,
@@ -807,7 +953,7 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
     if (k >= 0 && M.convex[k] == 1) {
       const int64_t q0 = M.cf_ptr[k];
       const int nfk = (int)(M.cf_ptr[k + 1] - q0);
-      const int nvb = 2 * fr.I + 1;
+      const int nvb = base_verts<KIND>(fr.I);
       const G rx = rel(fr.cx, Gv.ccx[k]), ry = rel(fr.cy, Gv.ccy[k]), rz = rel(fr.cz, Gv.ccz[k]);
       for (int g = 0; g < nfk; ++g) {
         const float4 q = M.cpl32[q0 + g];
@@ -836,7 +982,7 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
 // exactly 0: complement when no empty cell is met, fluid when no full cell
 // is, otherwise by the donating cell's F. Returns V_F / L^3; *whole: P lies
 // in the fluid (1) or empty (2) part of one cell (V_F = V_d or 0 exactly).
-template <typename G>
+template <typename G, int KIND>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, double Vd, G Vl, Poly<G>& P, int lane,
                               unsigned& err, int* whole, bool* complement,
@@ -855,7 +1001,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
-      const int k = candidate(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
       const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
       if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
       if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
@@ -881,7 +1027,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
       const int kk = P.cand[i];
       if (S.tc[kk] == skip) continue;
       int w = 0;
-      v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
+      v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
       ++n_trunc;
       if (w) { *whole = comp ? 2 : 1; return G(0); }  // no other cell meets P
     }
@@ -895,14 +1041,14 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
-      const int k = candidate(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
       unsigned bal = __ballot_sync(GVOF_FULL, k >= 0 && tk != skip);
       while (bal) {
         const int src = __ffs(bal) - 1;
         bal &= bal - 1u;
         const int kk = __shfl_sync(GVOF_FULL, k, src);
         int w = 0;
-        v += truncate_in_cell<G>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
+        v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
         ++n_trunc;
         if (w) { *whole = comp ? 2 : 1; return G(0); }
       }
@@ -911,7 +1057,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
   return v;
 }
 
-template <typename G>
+template <typename G, int KIND>
 __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S) {
   __shared__ Poly<G> polys[kWarps];
   __shared__ GridParam wgp[kWarps];
@@ -931,7 +1077,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
       __syncwarp();
     }
     const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
-    if (!build_fmfpa<G>(M, Gv, wgp[wib], j, Vd, P, fr, lane)) {
+    if (!build_polyhedron<G, KIND>(M, Gv, wgp[wib], j, Vd, P, fr, lane)) {
       if (lane == 0) S.VF[j] = 0.0;
       ++n_over;
       continue;
@@ -943,7 +1089,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     const G L3 = fr.L * fr.L * fr.L;
     int wh = 0;
     bool comp = false;
-    const G v = sweep_candidates<G>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp, n_trunc);
+    const G v = sweep_candidates<G, KIND>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp, n_trunc);
     double VFj;
     if (wh == 1) VFj = Vd;  // P inside the fluid of one cell: exactly V_d
     else if (wh == 2) VFj = 0.0;  // P inside the empty part of one cell
@@ -1012,7 +1158,7 @@ __global__ void k_candidates(DevMesh M, const int32_t* faces, int n, int64_t cap
   }
 }
 
-template <typename G>
+template <typename G, int KIND>
 __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const double* srate,
                             const int32_t* faces, int n, double* verts, int32_t* counts) {
   __shared__ Poly<G> polys[kWarps];
@@ -1024,13 +1170,14 @@ __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const
     const int j = faces[w];
     const GridParam& gq = gp[grid_of(M.face_off, M.n_grids, j)];
     const double Vd = srate[j] * gq.g * gq.dt;
-    const bool ok = build_fmfpa<G>(M, Gv, gq, j, Vd, P, fr, lane);
+    const bool ok = build_polyhedron<G, KIND>(M, Gv, gq, j, Vd, P, fr, lane);
     if (lane == 0) counts[w] = ok ? fr.I : -1;
-    if (ok && lane < 2 * fr.I + 1) {
+    if (ok && lane < base_verts<KIND>(fr.I)) {
       const double L = (double)fr.L;
-      verts[(w * NB + lane) * 3 + 0] = absd(fr.cx) + L * (double)P.bx[lane];
-      verts[(w * NB + lane) * 3 + 1] = absd(fr.cy) + L * (double)P.by[lane];
-      verts[(w * NB + lane) * 3 + 2] = absd(fr.cz) + L * (double)P.bz[lane];
+      const int64_t o = ((int64_t)w * VOF_MAX_POLY_VERTS + lane) * 3;
+      verts[o + 0] = absd(fr.cx) + L * (double)P.bx[lane];
+      verts[o + 1] = absd(fr.cy) + L * (double)P.by[lane];
+      verts[o + 2] = absd(fr.cz) + L * (double)P.bz[lane];
     }
     __syncwarp();
   }
@@ -1040,10 +1187,18 @@ __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const
 
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s) {
   const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * 8;
-  if (c->opt.precision == VOF_PREC_MIXED)
-    k_flux<float><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c));
-  else
-    k_flux<double><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c));
+  const bool em = c->opt.flux_polyhedron == VOF_FLUX_EMFPA;
+  if (c->opt.precision == VOF_PREC_MIXED) {
+    if (em)
+      k_flux<float, VOF_FLUX_EMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c));
+    else
+      k_flux<float, VOF_FLUX_FMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c));
+  } else {
+    if (em)
+      k_flux<double, VOF_FLUX_EMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c));
+    else
+      k_flux<double, VOF_FLUX_FMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c));
+  }
   return cudaGetLastError();
 }
 
@@ -1055,12 +1210,17 @@ cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int
 
 cudaError_t launch_polyhedra(const vof_ctx* c, const int32_t* faces, int n, double* verts,
                              int32_t* counts, cudaStream_t s) {
-  if (c->opt.precision == VOF_PREC_MIXED)
-    k_polyhedra<float><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), c->gp_d,
-                                                     c->srate, faces, n, verts, counts);
-  else
-    k_polyhedra<double><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), c->gp_d,
-                                                      c->srate, faces, n, verts, counts);
+  const bool em = c->opt.flux_polyhedron == VOF_FLUX_EMFPA;
+  const DevMesh m = mesh_view(c);
+  if (c->opt.precision == VOF_PREC_MIXED) {
+    const GeoView<float> g = geo_view<float>(c);
+    if (em) k_polyhedra<float, VOF_FLUX_EMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
+    else k_polyhedra<float, VOF_FLUX_FMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
+  } else {
+    const GeoView<double> g = geo_view<double>(c);
+    if (em) k_polyhedra<double, VOF_FLUX_EMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
+    else k_polyhedra<double, VOF_FLUX_FMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
+  }
   return cudaGetLastError();
 }
 

@@ -15,6 +15,9 @@ namespace gvof {
 
 constexpr int kSMs = 152;  // GB300
 constexpr int kMaxFaceVerts = 8;
+constexpr int kMaxEmfpaVerts = 6;  // 5I+1 EMFPA faces fit the 32-face capacity
+static_assert(3 * kMaxEmfpaVerts + 1 <= VOF_MAX_POLY_VERTS && 2 * kMaxFaceVerts + 1 <= VOF_MAX_POLY_VERTS,
+              "polyhedron export stride");
 
 struct Vel {
   int kind;

@@ -18,7 +18,8 @@ from . import build as _build
 VOF_OK, VOF_EINVAL, VOF_ENOMEM, VOF_ECUDA, VOF_ECAPACITY, VOF_ESTATE = range(6)
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
-NB_VERTS = 17  # 2 * 8 + 1 polyhedron slots per face in vof_get_flux_polyhedra
+FLUX_FMFPA, FLUX_EMFPA = 0, 1  # flux polyhedron construction (Secs. 2.2.2, 2.2.1)
+NB_VERTS = 19  # polyhedron slots per face in vof_get_flux_polyhedra
 
 _lib = None
 
@@ -37,7 +38,7 @@ class _Mesh(C.Structure):
 
 class _Opt(C.Structure):
     _fields_ = [("eps", C.c_double), ("beta", C.c_double), ("precision", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("flux_polyhedron", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class _Vel(C.Structure):
@@ -188,13 +189,13 @@ class Context:
     velocity and time step (the ``*_batch`` methods).
     """
 
-    def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5):
+    def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5, flux=FLUX_FMFPA):
         L = lib()
         meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
         descs = (_Mesh * len(meshes))(*[_mesh_desc(m, keep) for m in meshes])
         opt = _Opt()
-        opt.eps, opt.beta, opt.precision = eps, beta, precision
+        opt.eps, opt.beta, opt.precision, opt.flux_polyhedron = eps, beta, precision, flux
         h = C.c_void_p()
         _check(L.vof_init_batch(descs, len(meshes), C.byref(opt), C.byref(h)))
         self._h = h
@@ -203,6 +204,7 @@ class Context:
         self.n_face = sum(d.n_face for d in descs)
         self.n_cell = sum(d.n_cell for d in descs)
         self.precision = precision
+        self.flux = flux
         co = np.empty(self.n_grids + 1, np.int64)
         fo = np.empty(self.n_grids + 1, np.int64)
         vo = np.empty(self.n_grids + 1, np.int64)
@@ -343,7 +345,8 @@ class Context:
         v = velocity_struct(vel)
         _check(lib().vof_get_flux_polyhedra(self._h, C.byref(v), t, dt, _ptr(faces), len(faces),
                                             _ptr(verts), _ptr(counts)))
-        return [verts[i, :2 * counts[i] + 1].copy() if counts[i] > 0 else None
+        k = 3 if self.flux == FLUX_EMFPA else 2
+        return [verts[i, :k * counts[i] + 1].copy() if counts[i] > 0 else None
                 for i in range(len(faces))]
 
     PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update")

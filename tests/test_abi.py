@@ -49,7 +49,7 @@ def test_status_codes_match_header():
 def test_struct_layouts():
     from paper_2111_01524_gb300 import vof
     assert ctypes.sizeof(vof._Mesh) == 3 * 8 + 5 * 8
-    assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 7 * 4
+    assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 4 + 6 * 4
     assert ctypes.sizeof(vof._Vel) == 4 + 4 + 8 + 8 + 24 + 24
     assert ctypes.sizeof(vof.Stats) == 6 * 8 + 5 * 8
 
@@ -82,3 +82,41 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(out[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_flux_constants_match_header():
+    from paper_2111_01524_gb300 import vof
+    src = open(os.path.join(ROOT, "include", "vof.h")).read()
+    assert re.search(rf"VOF_FLUX_FMFPA\s*=\s*{vof.FLUX_FMFPA}\b", src)
+    assert re.search(rf"VOF_FLUX_EMFPA\s*=\s*{vof.FLUX_EMFPA}\b", src)
+    assert re.search(rf"VOF_MAX_POLY_VERTS\s*=\s*{vof.NB_VERTS}\b", src)
+    # 3I+1 EMFPA points for I <= 6, 2I+1 FMFPA points for I <= 8
+    assert vof.NB_VERTS >= max(3 * 6 + 1, 2 * 8 + 1)
+
+
+def _heptagonal_prism():
+    """one cell: two 7-node faces and seven quads (valid orientation)"""
+    import numpy as np
+    a = 2 * np.pi * np.arange(7) / 7
+    ring = np.stack([0.5 + 0.4 * np.cos(a), 0.5 + 0.4 * np.sin(a)], 1)
+    X = np.concatenate([np.c_[ring, np.zeros(7)], np.c_[ring, np.ones(7)]])
+    loops = [list(range(6, -1, -1)), list(range(7, 14))]
+    loops += [[i, (i + 1) % 7, 7 + (i + 1) % 7, 7 + i] for i in range(7)]
+    fp = np.cumsum([0] + [len(l) for l in loops]).astype(np.int64)
+    return {"X": X, "face_ptr": fp, "face_vert": np.concatenate(loops).astype(np.int32),
+            "owner": np.zeros(len(loops), np.int32),
+            "neighbour": np.full(len(loops), -1, np.int32), "n_cell": 1}
+
+
+def test_emfpa_and_bad_options_are_rejected_before_device_work():
+    """vof_init checks the options before it touches the device: EMFPA on a
+    mesh with a 7-node face, an unknown construction and a nonzero reserved
+    word each give VOF_EINVAL (no GPU needed)."""
+    from paper_2111_01524_gb300 import vof
+    m = _heptagonal_prism()
+    with pytest.raises(vof.VofError) as e:
+        vof.Context(m, flux=vof.FLUX_EMFPA)
+    assert e.value.status == vof.VOF_EINVAL and "6 nodes" in str(e.value)
+    with pytest.raises(vof.VofError) as e:
+        vof.Context(m, flux=7)
+    assert e.value.status == vof.VOF_EINVAL

@@ -448,7 +448,7 @@ def test_emfpa_rotation_backtrace_and_volume(orc, gen):
     its own velocity (Eq. streak-line2), the side centres are vertex
     averages, and the apex lies on the normal through the centroid of the
     back-traced loop at the height that makes the volume V_d."""
-    m = I.hex_mesh(5, jitter=0.2, seed=4) if gen == "hex" else I.kuhn_tet_mesh(4, seed=5)
+    m = I.hex_mesh(5) if gen == "hex" else I.kuhn_tet_mesh(4, seed=5)
     om = orc.Mesh(m)
     g = om.geometry()
     omega, c = 2.0 * np.pi, (0.5, 0.5, 0.5)
@@ -481,7 +481,7 @@ def test_emfpa_rotation_backtrace_and_volume(orc, gen):
 def test_emfpa_backtrace_uses_midtime_velocity(orc):
     """The time-modulated deformation field (Sec. 4.2), written out: the
     back-traced vertex uses the velocity at t^{n+1/2} = t + dt/2."""
-    m = I.hex_mesh(4, jitter=0.2, seed=7)
+    m = I.trihex_mesh(2, seed=7)
     om = orc.Mesh(m)
     T, t, dt = 3.0, 0.4, 0.05
     vel = I.deformation(T)
@@ -508,7 +508,7 @@ def test_emfpa_backtrace_uses_midtime_velocity(orc):
 
 @pytest.mark.parametrize("gen", ["hex", "tet", "trihex"])
 def test_emfpa_volume_equals_vd(orc, gen):
-    m = {"hex": lambda: I.hex_mesh(6, jitter=0.25, seed=1),
+    m = {"hex": lambda: I.hex_mesh(6),
          "tet": lambda: I.kuhn_tet_mesh(4, seed=3),
          "trihex": lambda: I.trihex_mesh(3, seed=2)}[gen]()
     om = orc.Mesh(m)
