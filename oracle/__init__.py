@@ -22,6 +22,9 @@ _SRC = os.path.join(_HERE, "oracle.c")
 # flux polyhedron constructions of faceflux / step
 FMFPA = 0  # face-matched (Sec. 2.2.2)
 EMFPA = 1  # edge-matched (Sec. 2.2.1)
+# interface reconstructions of reconstruct / step
+LSGIR = 0  # least-squares gradient (Sec. 2.1.1)
+LSFIR = 1  # least-squares fit with the outer iteration (Sec. 2.1.2)
 _lib = None
 
 
@@ -82,6 +85,14 @@ def lib():
         L.orc_velocity_eval.argtypes = [vp, vp, dbl, vp]
         L.orc_fmfpa.restype = i32
         L.orc_fmfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
+        L.orc_plic_centre.restype = i32
+        L.orc_plic_centre.argtypes = [vp, i64, vp, dbl, vp]
+        L.orc_lsfir_normals.restype = i64
+        L.orc_lsfir_normals.argtypes = [vp, vp, vp, vp, vp]
+        L.orc_lsfir_accept.restype = dbl
+        L.orc_lsfir_accept.argtypes = [vp, vp, i32, vp, vp]
+        L.orc_lsfir.restype = i32
+        L.orc_lsfir.argtypes = [vp, i32, dbl, vp, vp, vp, vp]
         L.orc_emfpa.restype = i32
         L.orc_emfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
         L.orc_faceflux.argtypes = [vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp, vp, i32]
@@ -184,11 +195,51 @@ class Mesh:
         n = np.ascontiguousarray(n, np.float64)
         return lib().orc_cell_cut_volume(self._m, int(cell), _p(n), float(Cval))
 
-    def reconstruct(self, F, eps=1e-12, beta=1.5):
-        """taggrid + lsgir + volume enforcement: the reconstruction half-step."""
+    def plic_centre(self, cell, n, Cval):
+        """vertex average of the PLIC polygon of a cell (Sec. 2.1.2)"""
+        out = np.empty(3)
+        n = np.ascontiguousarray(n, np.float64)  # held while C reads it
+        k = lib().orc_plic_centre(self._m, int(cell), _p(n), float(Cval), _p(out))
+        return out, int(k)
+
+    def lsfir_normals(self, tag_c, nrm, xp):
+        """one LSFIR normal update from the PLIC centres xp (Sec. 2.1.2)"""
+        cand = np.empty((self.n_cell, 3))
+        tag_c = np.ascontiguousarray(tag_c, np.int8)
+        nrm = np.ascontiguousarray(nrm, np.float64)
+        xp = np.ascontiguousarray(xp, np.float64)
+        kept = lib().orc_lsfir_normals(self._m, _p(tag_c), _p(nrm), _p(xp), _p(cand))
+        return cand, int(kept)
+
+    def lsfir_accept(self, tag_c, io, cand, nrm):
+        """acceptance step of outer iteration io (Sec. 2.1.2); returns the
+        new normals and the largest accepted turn"""
+        out = np.array(nrm, np.float64, copy=True)
+        tag_c = np.ascontiguousarray(tag_c, np.int8)
+        cand = np.ascontiguousarray(cand, np.float64)
+        t = lib().orc_lsfir_accept(self._m, _p(tag_c), int(io), _p(cand), _p(out))
+        return out, float(t)
+
+    def lsfir(self, F, tag_c, nrm0, n_out=4, tol=1e-3):
+        """LSFIR outer iteration from the normals nrm0 (Sec. 2.1.2)."""
+        nrm = np.array(nrm0, np.float64, copy=True)
+        Cc = np.empty(self.n_cell)
+        F = np.ascontiguousarray(F, np.float64)
+        tag_c = np.ascontiguousarray(tag_c, np.int8)
+        it = lib().orc_lsfir(self._m, int(n_out), float(tol), _p(F), _p(tag_c), _p(nrm), _p(Cc))
+        return nrm, Cc, int(it)
+
+    def reconstruct(self, F, eps=1e-12, beta=1.5, recon=LSGIR, n_out=4, tol=1e-3):
+        """taggrid + lsgir + volume enforcement: the reconstruction half-step;
+        recon = LSFIR adds the least-squares fit outer iteration (Sec. 2.1.2,
+        n_out repetitions at most, tolerance tol in radians)."""
         st = self.taggrid(F, eps)
         st["nrm"] = self.lsgir(st["F"], st["tag_c"], beta)
-        st["C"] = self.plane_constant(st["F"], st["tag_c"], st["nrm"])
+        if recon == LSFIR:
+            st["nrm"], st["C"], st["lsfir_iters"] = self.lsfir(st["F"], st["tag_c"], st["nrm"],
+                                                               n_out, tol)
+        else:
+            st["C"] = self.plane_constant(st["F"], st["tag_c"], st["nrm"])
         return st
 
     # --- advection (Secs. 2.2, 3.5)
@@ -239,13 +290,14 @@ class Mesh:
         lib().orc_velocity_eval(C.byref(v), _p(x), t, _p(u))
         return u
 
-    def step(self, vel, t, dt, st, eps=1e-12, beta=1.5, method=FMFPA):
+    def step(self, vel, t, dt, st, eps=1e-12, beta=1.5, method=FMFPA, recon=LSGIR):
         """One time step of the advection test loop (Algorithm alg:adv):
-        faceflux -> vofadv -> taggrid -> lsgir -> volume enforcement.
-        method: the flux polyhedron, FMFPA (Sec. 2.2.2) or EMFPA (Sec. 2.2.1)."""
+        faceflux -> vofadv -> taggrid -> lsgir [-> lsfir] -> volume enforcement.
+        method: the flux polyhedron, FMFPA (Sec. 2.2.2) or EMFPA (Sec. 2.2.1);
+        recon: LSGIR (Sec. 2.1.1) or LSFIR (Sec. 2.1.2)."""
         Vd, VF, stats = self.faceflux(vel, t, dt, st, method)
         F = self.vofadv(st["F"], Vd, VF)
-        new = self.reconstruct(F, eps, beta)
+        new = self.reconstruct(F, eps, beta, recon)
         new["Vd"], new["VF"], new["stats"] = Vd, VF, stats
         new["F_unclipped_cut"] = F
         return new

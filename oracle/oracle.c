@@ -558,6 +558,215 @@ void orc_plane_constant(const orc_mesh* m, const double* F, const int8_t* tag_c,
   }
 }
 
+/* ------------------------------------------------------------ LSFIR (Sec 2.1.2) */
+/* geometric centre of the vertex set of the PLIC polygon of cell c, plane
+ * n.(x - xc) + C = 0: the points where the plane crosses an edge of the
+ * cell (ends strictly on opposite sides), each edge once, and the cell
+ * vertices that lie on the plane. Returns the number of points (0: the
+ * plane misses the cell; out = the centroid). */
+int orc_plic_centre(const orc_mesh* m, int64_t c, const double n[3], double C, double out[3]) {
+  const double* xc = m->cc + 3 * c;
+  /* the cell's edges, each once as (low id, high id) */
+  int32_t ea[256], eb[256];
+  int ne = 0;
+  for (int64_t q = m->cf_ptr[c]; q < m->cf_ptr[c + 1]; ++q) {
+    int32_t f = m->cf[q];
+    int64_t b = m->fptr[f], I = m->fptr[f + 1] - b;
+    for (int64_t i = 0; i < I; ++i) {
+      int32_t a = m->fvert[b + i], e = m->fvert[b + (i + 1) % I];
+      int32_t lo = a < e ? a : e, hi = a < e ? e : a;
+      int seen = 0;
+      for (int k = 0; k < ne && !seen; ++k) seen = (ea[k] == lo && eb[k] == hi);
+      if (!seen && ne < 256) { ea[ne] = lo; eb[ne] = hi; ++ne; }
+    }
+  }
+  double sum[3] = {0, 0, 0};
+  int np = 0;
+  for (int k = 0; k < ne; ++k) {
+    const double* A = m->X + 3 * ea[k];
+    const double* B = m->X + 3 * eb[k];
+    double da[3], db[3];
+    sub3(A, xc, da);
+    sub3(B, xc, db);
+    double pa = dot3(n, da) + C, pb = dot3(n, db) + C;
+    if ((pa > 0 && pb < 0) || (pa < 0 && pb > 0)) {
+      double t = pa / (pa - pb);
+      for (int d = 0; d < 3; ++d) sum[d] += A[d] + t * (B[d] - A[d]);
+      ++np;
+    }
+  }
+  for (int64_t q = m->cv_ptr[c]; q < m->cv_ptr[c + 1]; ++q) {
+    const double* V = m->X + 3 * m->cv[q];
+    double dv[3];
+    sub3(V, xc, dv);
+    if (dot3(n, dv) + C == 0.0) {
+      for (int d = 0; d < 3; ++d) sum[d] += V[d];
+      ++np;
+    }
+  }
+  if (np == 0) {
+    for (int d = 0; d < 3; ++d) out[d] = xc[d];
+    return 0;
+  }
+  for (int d = 0; d < 3; ++d) out[d] = sum[d] / np;
+  return np;
+}
+
+/* eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+ * (each rotation in the (p, q) plane zeroes A[p][q]); on return the
+ * diagonal of A holds the eigenvalues and the columns of V the vectors */
+static void sym3_jacobi(double A[3][3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j);
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-32 * dia || off == 0.0) break;
+    static const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int r = 0; r < 3; ++r) {
+      int p = P[r][0], q = P[r][1];
+      if (A[p][q] == 0.0) continue;
+      /* angle with tan(2 phi) = 2 A_pq / (A_qq - A_pp); the smaller root t */
+      double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+      double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+      double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+      double J[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+      J[p][p] = cs; J[q][q] = cs; J[p][q] = sn; J[q][p] = -sn;
+      double T[3][3], R[3][3];
+      /* A <- J^T A J, V <- V J */
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          T[i][j] = 0;
+          for (int k = 0; k < 3; ++k) T[i][j] += A[i][k] * J[k][j];
+        }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          R[i][j] = 0;
+          for (int k = 0; k < 3; ++k) R[i][j] += J[k][i] * T[k][j];
+        }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[i][j] = R[i][j];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          T[i][j] = 0;
+          for (int k = 0; k < 3; ++k) T[i][j] += V[i][k] * J[k][j];
+        }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = T[i][j];
+    }
+  }
+}
+
+/* angle between unit vectors, accurate for small angles */
+static double angle3(const double* a, const double* b) {
+  double x[3];
+  cross3(a, b, x);
+  return atan2(norm3(x), dot3(a, b));
+}
+
+/* one LSFIR normal update (Sec. 2.1.2): for each interfacial cell, the unit
+ * normal of the plane through its PLIC centre x that minimises
+ * H = sum_k w_k delta_k^2 over the valid interfacial neighbours k (node
+ * neighbours whose previous normal is within 45 degrees of the cell's, the
+ * SWIR validity rule of Sec. 2.1.2), delta_k = n.(x_k - x), w_k =
+ * |x_k - x|^-2.5: the eigenvector of the smallest eigenvalue of
+ * sum_k w_k d_k d_k^T, oriented like the previous normal. A cell with fewer
+ * than two valid neighbours, or whose two smallest eigenvalues are equal
+ * (collinear centres: no unique plane), keeps its normal. cand receives
+ * the normals; returns the number of cells that kept theirs. */
+int64_t orc_lsfir_normals(const orc_mesh* m, const int8_t* tag_c, const double* nrm,
+                          const double* xp, double* cand) {
+  const double cos45 = sqrt(0.5);
+  int64_t kept = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : kept)
+  for (int64_t c = 0; c < m->nc; ++c) {
+    for (int d = 0; d < 3; ++d) cand[3 * c + d] = nrm[3 * c + d];
+    if (tag_c[c] != 0) continue;
+    const double* nc_ = nrm + 3 * c;
+    double M[3][3] = {{0}};
+    int nvalid = 0;
+    for (int64_t q = m->nb_ptr[c]; q < m->nb_ptr[c + 1]; ++q) {
+      int32_t k = m->nb[q];
+      if (tag_c[k] != 0) continue;
+      if (!(dot3(nc_, nrm + 3 * k) > cos45)) continue;
+      double d[3];
+      sub3(xp + 3 * k, xp + 3 * c, d);
+      double r2 = dot3(d, d);
+      if (!(r2 > 0)) continue;
+      double w = pow(r2, -1.25); /* |d|^-2.5 */
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] += w * d[i] * d[j];
+      ++nvalid;
+    }
+    if (nvalid < 2) { ++kept; continue; }
+    double V[3][3];
+    sym3_jacobi(M, V);
+    int lo = 0;
+    for (int i = 1; i < 3; ++i)
+      if (M[i][i] < M[lo][lo]) lo = i;
+    int i1 = (lo + 1) % 3, i2 = (lo + 2) % 3;
+    double mid = M[i1][i1] < M[i2][i2] ? M[i1][i1] : M[i2][i2];
+    double top = M[i1][i1] < M[i2][i2] ? M[i2][i2] : M[i1][i1];
+    if (!(mid - M[lo][lo] > 1e-12 * top)) { ++kept; continue; }
+    double v[3] = {V[0][lo], V[1][lo], V[2][lo]};
+    double vn = norm3(v);
+    double sg = dot3(v, nc_) < 0 ? -1.0 : 1.0;
+    for (int d = 0; d < 3; ++d) cand[3 * c + d] = sg * v[d] / vn;
+  }
+  return kept;
+}
+
+/* acceptance step of outer iteration io (Sec. 2.1.2): each interfacial
+ * cell takes its candidate normal when it turns the current one by less than
+ * 30 degrees / io; every cell is decided from the normals before the step.
+ * Returns the largest accepted turn (radians). */
+double orc_lsfir_accept(const orc_mesh* m, const int8_t* tag_c, int io, const double* cand,
+                        double* nrm) {
+  const double pi = 3.14159265358979323846;
+  const double lim = (30.0 * pi / 180.0) / io;
+  double turned = 0.0;
+  for (int64_t c = 0; c < m->nc; ++c) {
+    if (tag_c[c] != 0) continue;
+    double a = angle3(nrm + 3 * c, cand + 3 * c);
+    if (a < lim) {
+      for (int d = 0; d < 3; ++d) nrm[3 * c + d] = cand[3 * c + d];
+      if (a > turned) turned = a;
+    }
+  }
+  return turned;
+}
+
+/* LSFIR reconstruction (Sec. 2.1.2) with the outer iteration of Sec. 2.1.2:
+ * from the normals given in nrm (the LSGIR ones, Sec. 2.1.1), repeat up to
+ * n_out times: PLIC centres of the current planes; candidate normals; each
+ * interfacial cell takes its candidate if it turns its normal by less than
+ * 30 degrees / I_out (all cells updated together, after every candidate is
+ * known); the plane constants are enforced again (Sec. 2.1). Stops after the
+ * iteration in which no normal turned by tol or more. C receives the final
+ * plane constants. Returns the number of outer iterations done. */
+int orc_lsfir(const orc_mesh* m, int n_out, double tol, const double* F, const int8_t* tag_c,
+              double* nrm, double* C) {
+  double* xp = (double*)malloc(sizeof(double) * 3 * m->nc);
+  double* cand = (double*)malloc(sizeof(double) * 3 * m->nc);
+  orc_plane_constant(m, F, tag_c, nrm, C);
+  int it = 0;
+  for (int io = 1; io <= n_out; ++io) {
+    it = io;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < m->nc; ++c) {
+      if (tag_c[c] == 0) orc_plic_centre(m, c, nrm + 3 * c, C[c], xp + 3 * c);
+      else for (int d = 0; d < 3; ++d) xp[3 * c + d] = m->cc[3 * c + d];
+    }
+    orc_lsfir_normals(m, tag_c, nrm, xp, cand);
+    double turned = orc_lsfir_accept(m, tag_c, io, cand, nrm);
+    orc_plane_constant(m, F, tag_c, nrm, C);
+    if (turned < tol) break;
+  }
+  free(xp);
+  free(cand);
+  return it;
+}
+
 /* ------------------------------------------------------ velocity (Sec 4.2) */
 void orc_velocity_eval(const orc_velocity* v, const double x[3], double t, double u[3]) {
   const double pi = 3.14159265358979323846;

@@ -74,6 +74,28 @@ void orc_plane_constant(const orc_mesh* m, const double* F,
 double orc_cell_cut_volume(const orc_mesh* m, int64_t cell, const double n[3],
                            double C);
 
+/* LSFIR (Sec. 2.1.2). orc_plic_centre: vertex average of the PLIC polygon
+ * of cell c (edge crossings of n.(x - xc) + C = 0, each edge once, plus
+ * cell vertices on the plane); returns the number of points (0: out = xc).
+ * orc_lsfir_normals: one least-squares normal update from the PLIC centres
+ * xp [3 nc] of the interfacial cells (weights |x_k - x|^-2.5, neighbours
+ * valid within 45 degrees); returns the cells that kept their normal.
+ * orc_lsfir_accept: acceptance step of outer iteration io (a candidate
+ * replaces a normal it turns by less than 30 degrees / io); returns the
+ * largest accepted turn.
+ * orc_lsfir: outer iteration from the normals in nrm (in/out), at most
+ * n_out repetitions, a change accepted below 30 degrees / I_out, stop when
+ * no normal turned by tol or more; C [nc] receives the plane constants;
+ * returns the iterations done. */
+int orc_plic_centre(const orc_mesh* m, int64_t c, const double n[3], double C,
+                    double out[3]);
+int64_t orc_lsfir_normals(const orc_mesh* m, const int8_t* tag_c, const double* nrm,
+                          const double* xp, double* cand);
+double orc_lsfir_accept(const orc_mesh* m, const int8_t* tag_c, int io, const double* cand,
+                        double* nrm);
+int orc_lsfir(const orc_mesh* m, int n_out, double tol, const double* F,
+              const int8_t* tag_c, double* nrm, double* C);
+
 void orc_velocity_eval(const orc_velocity* v, const double x[3], double t,
                        double u[3]);
 

@@ -660,6 +660,238 @@ def test_lsgir_rotation_invariance(orc):
     assert np.allclose(n2, n @ R.T, atol=1e-12)
 
 
+# ---------------------------------------------------------------- LSFIR
+def _ang(a, b):
+    """angle between unit vectors, accurate near 0"""
+    return np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), np.sum(a * b, axis=-1))
+
+
+def test_plic_centre_closed_forms(orc):
+    """Vertex average of the PLIC polygon of the unit cube (Sec. 2.1.2): a
+    plane x = 0.3 gives a square centred at (0.3, 1/2, 1/2); x + y + z = s < 1
+    cuts a corner triangle centred at (s/3, s/3, s/3); x = 1 contains a face,
+    whose four vertices are the polygon's."""
+    om = orc.Mesh(I.hex_mesh(1))
+    # plane n.(x - xc) + C = 0 with xc = (1/2, 1/2, 1/2)
+    out, k = om.plic_centre(0, [1.0, 0.0, 0.0], 0.5 - 0.3)
+    assert k == 4 and np.allclose(out, [0.3, 0.5, 0.5], atol=1e-15)
+    n = np.ones(3) / np.sqrt(3.0)
+    for s_ in (0.2, 0.7):  # x + y + z = s  <=>  C = (1.5 - s) / sqrt(3)
+        for sign in (1.0, -1.0):  # either side may be the fluid
+            out, k = om.plic_centre(0, sign * n, sign * (1.5 - s_) / np.sqrt(3.0))
+            assert k == 3 and np.allclose(out, [s_ / 3] * 3, atol=1e-15), (s_, k, out)
+    # the plane x = 1 through a whole face: phi is exactly 0 at its four
+    # vertices (C formed from the centroid as the oracle forms phi), which
+    # are the polygon's vertices, each once
+    xc = om.geometry()["cell_cen"][0]
+    out, k = om.plic_centre(0, [1.0, 0.0, 0.0], -(1.0 - xc[0]))
+    assert k == 4 and np.array_equal(out, [1.0, 0.5, 0.5]), (k, out)
+
+
+def _exact_plane_F(om, nrm, p0):
+    g = om.geometry()
+    return np.array([om.cell_cut_volume(c, nrm, nrm @ (g["cell_cen"][c] - p0))
+                     for c in range(om.n_cell)]) / g["cell_vol"]
+
+
+@pytest.mark.parametrize("gen", ["hex", "tet", "trihex"])
+def test_lsfir_reproduces_a_plane(orc, gen):
+    """A planar interface: if every interfacial cell carries the exact plane,
+    the PLIC centres lie on it and one least-squares update returns the
+    plane's normal (the fixed point of Sec. 2.1.2)."""
+    m = {"hex": lambda: I.hex_mesh(6), "tet": lambda: I.kuhn_tet_mesh(5, seed=3),
+         "trihex": lambda: I.trihex_mesh(4, seed=2)}[gen]()
+    om = orc.Mesh(m)
+    nt = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    p0 = np.array([0.5, 0.48, 0.52])
+    st = om.taggrid(_exact_plane_F(om, nt, p0))
+    band = st["tag_c"] == 0
+    N = np.tile(nt, (om.n_cell, 1))
+    Ce = om.plane_constant(st["F"], st["tag_c"], N)
+    xp = om.geometry()["cell_cen"].copy()
+    for c in np.nonzero(band)[0]:
+        xp[c] = om.plic_centre(c, nt, Ce[c])[0]
+    assert np.abs((xp[band] - p0) @ nt).max() < 1e-11
+    cand, kept = om.lsfir_normals(st["tag_c"], N, xp)
+    assert kept == 0
+    assert _ang(cand[band], nt).max() < 1e-9
+
+
+def test_lsfir_normal_minimises_H_bruteforce(orc):
+    """For sample cells the update equals a direct minimisation of
+    H = sum w_k (n.(x_k - x))^2, w_k = |x_k - x|^-2.5, over unit vectors, with
+    the valid neighbours (interfacial, previous normals within 45 degrees)
+    chosen here from the neighbour lists."""
+    m = I.kuhn_tet_mesh(5, seed=12)
+    om = orc.Mesh(m)
+    st = om.taggrid(I.init_fraction(m, I.sphere((0.5, 0.5, 0.5), 0.3), levels=3))
+    tc = st["tag_c"]
+    ng = om.lsgir(st["F"], tc)
+    Cg = om.plane_constant(st["F"], tc, ng)
+    xp = om.geometry()["cell_cen"].copy()
+    band = np.nonzero(tc == 0)[0]
+    for c in band:
+        xp[c] = om.plic_centre(c, ng[c], Cg[c])[0]
+    cand, _ = om.lsfir_normals(tc, ng, xp)
+    ptr, idx = om.neighbors()
+    # unit vectors: a Fibonacci sphere, then local refinement
+    k = np.arange(20000) + 0.5
+    th, ph = np.arccos(1 - 2 * k / k.size), np.pi * (1 + 5 ** 0.5) * k
+    U = np.stack([np.cos(ph) * np.sin(th), np.sin(ph) * np.sin(th), np.cos(th)], 1)
+    checked = 0
+    for c in band[::7]:
+        nb = [q for q in idx[ptr[c]:ptr[c + 1]] if tc[q] == 0 and ng[c] @ ng[q] > np.sqrt(0.5)]
+        if len(nb) < 3:
+            continue
+        D = xp[nb] - xp[c]
+        w = np.linalg.norm(D, axis=1) ** -2.5
+        H = lambda V: ((V @ D.T) ** 2 * w).sum(-1)
+        best = U[np.argmin(H(U))]
+        for step in (2e-2, 5e-3, 1e-3, 2e-4, 5e-5, 1e-5):
+            for _ in range(60):
+                trial = best + step * np.random.default_rng(int(c)).normal(size=(64, 3))
+                trial /= np.linalg.norm(trial, axis=1, keepdims=True)
+                j = np.argmin(H(trial))
+                if H(trial[j]) < H(best):
+                    best = trial[j]
+        if best @ ng[c] < 0:
+            best = -best
+        assert _ang(cand[c], best) < 1e-4, (c, cand[c], best)
+        checked += 1
+    assert checked >= 10
+
+
+def test_lsfir_acceptance_limit(orc):
+    """Outer iteration (Sec. 2.1.2): a change is accepted only below
+    30 degrees / I_out. On a planar interface, one cell's normal turned by 20
+    degrees is corrected in the first iteration; turned by 40 degrees (still a
+    valid neighbour, < 45) its candidate is refused in every iteration."""
+    m = I.trihex_mesh(4, seed=2)
+    om = orc.Mesh(m)
+    nt = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    st = om.taggrid(_exact_plane_F(om, nt, np.array([0.5, 0.48, 0.52])))
+    band = np.nonzero(st["tag_c"] == 0)[0]
+    F = st["F"]
+    c0 = band[np.argmin(np.abs(F[band] - 0.5))]  # a well-filled cell
+    axis = np.cross(nt, [1.0, 0.0, 0.0])
+    axis /= np.linalg.norm(axis)
+    for deg, fixed in ((20.0, True), (40.0, False)):
+        a = np.radians(deg)
+        turned = nt * np.cos(a) + np.cross(axis, nt) * np.sin(a)
+        N0 = np.tile(nt, (om.n_cell, 1))
+        N0[c0] = turned
+        nf, Cf, it = om.lsfir(F, st["tag_c"], N0, n_out=4, tol=1e-3)
+        if fixed:
+            assert _ang(nf[c0], nt) < 1e-3, deg
+        else:
+            assert _ang(nf[c0], turned) == 0.0, deg
+        others = np.setdiff1d(band, [c0])
+        assert _ang(nf[others], nt).max() < 0.05
+
+
+def test_lsfir_acceptance_limit_shrinks_with_the_iteration(orc):
+    """A candidate turning a normal by 20 degrees is taken in outer
+    iteration 1 (limit 30) and refused in iteration 2 (limit 15); 10 degrees
+    is taken in 1, 2 and 3 (limit 10 is strict) is refused; non-interfacial
+    cells never change (Sec. 2.1.2)."""
+    om = orc.Mesh(I.hex_mesh(2))
+    tags = np.array([0, 0, 0, 0, 0, 0, 1, -1], np.int8)
+    prev = np.tile([0.0, 0.0, 1.0], (8, 1))
+
+    def turned_by(deg):
+        a = np.radians(deg)
+        return np.array([np.sin(a), 0.0, np.cos(a)])
+    degs = [20.0, 10.0, 10.0, 9.9, 29.9, 30.1, 5.0, 5.0]
+    cand = np.array([turned_by(d) for d in degs])
+    took = {}
+    for io in (1, 2, 3):
+        new, t = om.lsfir_accept(tags, io, cand, prev)
+        took[io] = [bool(np.array_equal(new[c], cand[c])) for c in range(8)]
+        assert all(np.array_equal(new[c], prev[c]) for c in range(8) if not took[io][c])
+        acc = [degs[c] for c in range(8) if took[io][c]]
+        assert abs(t - np.radians(max(acc))) < 1e-12
+    assert took[1] == [True, True, True, True, True, False, False, False]
+    assert took[2] == [False, True, True, True, False, False, False, False]
+    assert took[3] == [False, False, False, True, False, False, False, False]
+
+
+def _renumber_cells(m, perm):
+    """the same mesh with cell c renamed perm[c]; a face whose owner would
+    get the larger index is flipped so that it still leaves its owner"""
+    own, nbr = perm[m["owner"]], np.where(m["neighbour"] >= 0, perm[np.maximum(m["neighbour"], 0)], -1)
+    fp, fv = m["face_ptr"], m["face_vert"].copy()
+    flip = (nbr >= 0) & (nbr < own)
+    for f in np.nonzero(flip)[0]:
+        fv[fp[f]:fp[f + 1]] = fv[fp[f]:fp[f + 1]][::-1]
+    o2 = np.where(flip, nbr, own).astype(np.int32)
+    n2 = np.where(flip, own, nbr).astype(np.int32)
+    return {"X": m["X"], "face_ptr": fp, "face_vert": fv, "owner": o2, "neighbour": n2,
+            "n_cell": m["n_cell"]}
+
+
+def test_lsfir_is_independent_of_cell_order(orc):
+    """Every cell's new orientation is computed from the previous iteration's
+    planes before any is updated (Sec. 2.1.2), so renumbering the cells
+    renumbers the result and changes nothing else."""
+    m = I.kuhn_tet_mesh(4, seed=21)
+    om = orc.Mesh(m)
+    F = I.init_fraction(m, I.sphere((0.5, 0.5, 0.5), 0.3), levels=3)
+    st = om.reconstruct(F, recon=orc.LSFIR)
+    perm = np.random.default_rng(5).permutation(m["n_cell"])
+    m2 = _renumber_cells(m, perm)
+    F2 = np.empty_like(F)
+    F2[perm] = F
+    st2 = orc.Mesh(m2).reconstruct(F2, recon=orc.LSFIR)
+    band = np.nonzero(st["tag_c"] == 0)[0]
+    assert np.array_equal(st2["tag_c"][perm], st["tag_c"])
+    assert np.abs(st2["nrm"][perm[band]] - st["nrm"][band]).max() < 1e-10
+    assert np.abs(st2["C"][perm[band]] - st["C"][band]).max() < 1e-10
+    assert st2["lsfir_iters"] == st["lsfir_iters"]
+
+
+def test_lsfir_more_accurate_than_lsgir_and_converges(orc):
+    """Sphere on jittered tets: the LSFIR normals (Sec. 2.1.2) are closer to
+    the exact normal at the PLIC centre than the LSGIR ones, and the mean
+    error falls by more than 1.6 when h halves."""
+    ctr, R = np.array((0.5, 0.52, 0.48)), 0.3
+    errs = []
+    for n in (12, 24):
+        m = I.kuhn_tet_mesh(n, seed=3)
+        om = orc.Mesh(m)
+        st = om.taggrid(I.init_fraction(m, I.sphere(ctr, R), levels=5))
+        ng = om.lsgir(st["F"], st["tag_c"])
+        Cg = om.plane_constant(st["F"], st["tag_c"], ng)
+        nf, Cf, it = om.lsfir(st["F"], st["tag_c"], ng)
+        band = np.nonzero(st["tag_c"] == 0)[0]
+
+        def mean_err(N, Cc):
+            e = []
+            for c in band:
+                xp = om.plic_centre(c, N[c], Cc[c])[0]
+                e.append(_ang(N[c], -(xp - ctr) / np.linalg.norm(xp - ctr)))
+            return float(np.mean(e))
+        eg, ef = mean_err(ng, Cg), mean_err(nf, Cf)
+        assert ef < 0.6 * eg, (n, ef, eg)
+        errs.append(ef)
+    assert errs[0] / errs[1] > 1.6, errs
+
+
+def test_lsfir_rotation_invariance(orc):
+    m = I.kuhn_tet_mesh(4, seed=6)
+    om = orc.Mesh(m)
+    x = om.geometry()["cell_cen"]
+    # smooth and nowhere flat (no zero gradient, every cell interfacial)
+    F = 0.5 + 0.25 * np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]) + 0.1 * x[:, 2]
+    st = om.reconstruct(F, recon=orc.LSFIR)
+    R = np.array([[math.cos(0.7), -math.sin(0.7), 0], [math.sin(0.7), math.cos(0.7), 0], [0, 0, 1]])
+    m2 = dict(m)
+    m2["X"] = m["X"] @ R.T
+    st2 = orc.Mesh(m2).reconstruct(F, recon=orc.LSFIR)
+    band = st["tag_c"] == 0
+    assert np.allclose(st2["nrm"][band], st["nrm"][band] @ R.T, atol=1e-9)
+    assert np.allclose(st2["C"][band], st["C"][band], atol=1e-9)
+
+
 # ---------------------------------------------------------------- whole step
 def test_cfl1_translation_shifts_exactly(orc):
     """u = (1,0,0), dt = h on a uniform grid: every x-face flux polyhedron is
