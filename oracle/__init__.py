@@ -22,6 +22,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 # flux polyhedron constructions of faceflux / step
 FMFPA = 0  # face-matched (Sec. 2.2.2)
 EMFPA = 1  # edge-matched (Sec. 2.2.1)
+NMFPA = 2  # non-matched (Sec. 2.2.3)
 # interface reconstructions of reconstruct / step
 LSGIR = 0  # least-squares gradient (Sec. 2.1.1)
 LSFIR = 1  # least-squares fit with the outer iteration (Sec. 2.1.2)
@@ -93,6 +94,8 @@ def lib():
         L.orc_lsfir_accept.argtypes = [vp, vp, i32, vp, vp]
         L.orc_lsfir.restype = i32
         L.orc_lsfir.argtypes = [vp, i32, dbl, vp, vp, vp, vp]
+        L.orc_nmfpa.restype = i32
+        L.orc_nmfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
         L.orc_emfpa.restype = i32
         L.orc_emfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
         L.orc_faceflux.argtypes = [vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp, vp, i32]
@@ -264,6 +267,17 @@ class Mesh:
             raise ValueError("face too large")
         return out[:3 * I + 1].copy(), float(vd[0]), int(fl[0])
 
+    def nmfpa(self, face, vel, t_half, dt):
+        """NMFPA flux polyhedron (Sec. 2.2.3): 2I points."""
+        out = np.empty((64, 3))
+        vd = np.zeros(1)
+        fl = np.zeros(1, np.int32)
+        v = _vel(vel)
+        I = lib().orc_nmfpa(self._m, int(face), C.byref(v), t_half, dt, _p(out), 32, _p(vd), _p(fl))
+        if I < 0:
+            raise ValueError("face too large")
+        return out[:2 * I].copy(), float(vd[0]), int(fl[0])
+
     def faceflux(self, vel, t, dt, st, method=FMFPA):
         Vd = np.empty(self.n_face)
         VF = np.empty(self.n_face)
@@ -293,7 +307,8 @@ class Mesh:
     def step(self, vel, t, dt, st, eps=1e-12, beta=1.5, method=FMFPA, recon=LSGIR):
         """One time step of the advection test loop (Algorithm alg:adv):
         faceflux -> vofadv -> taggrid -> lsgir [-> lsfir] -> volume enforcement.
-        method: the flux polyhedron, FMFPA (Sec. 2.2.2) or EMFPA (Sec. 2.2.1);
+        method: the flux polyhedron, FMFPA (Sec. 2.2.2), EMFPA (Sec. 2.2.1) or
+        NMFPA (Sec. 2.2.3);
         recon: LSGIR (Sec. 2.1.1) or LSFIR (Sec. 2.1.2)."""
         Vd, VF, stats = self.faceflux(vel, t, dt, st, method)
         F = self.vofadv(st["F"], Vd, VF)

@@ -1,10 +1,10 @@
 /*
- * Oracle for the unsplit geometric VOF step (LSGIR + FMFPA / EMFPA) -- TEST
+ * Oracle for the unsplit geometric VOF step (LSGIR / LSFIR + FMFPA / EMFPA / NMFPA) -- TEST
  * INFRASTRUCTURE ONLY: called by tests/, the smoke check and the CPU-baseline
  * timing; never by the product path. Plain FP64 C, written from the paper
  * (arXiv 2111.01524): Sec. 2.1 (cut-off, PLIC, volume enforcement), Sec.
- * 2.1.1 (LSGIR), Sec. 2.2 (flux volumes, Eq. fnext, clip), Sec. 2.2.1
- * (EMFPA), Sec. 2.2.2 (FMFPA), Sec. 3 (grid, taggrid), Sec. 4.2 (Eq. eq:cfl, velocity fields).
+ * 2.1.1 (LSGIR), Sec. 2.1.2 (LSFIR), Sec. 2.2 (flux volumes, Eq. fnext,
+ * clip), Sec. 2.2.1 (EMFPA), Sec. 2.2.2 (FMFPA), Sec. 2.2.3 (NMFPA), Sec. 3 (grid, taggrid), Sec. 4.2 (Eq. eq:cfl, velocity fields).
  *
  * Numerics are deliberately simple and independent of the CUDA library:
  *   - every volume is a sum of signed tetrahedra;
@@ -797,7 +797,9 @@ static double poly_volume_loops(int nv, const double* V, int nf, const int* fp, 
  * method 1, EMFPA (Sec. 2.2.1): vertices as above, then the side-face
  *   centres s_0..s_{I-1} at 2I..3I-1 and the apex at 3I; each side face
  *   (x_{i+1}, x_i, x_{I+i}, x_{I+i+1}) is replaced by the four triangles
- *   that join its edges to s_i (5I+1 faces). */
+ *   that join its edges to s_i (5I+1 faces).
+ * method 2, NMFPA (Sec. 2.2.3): vertices x_0..x_{2I-1} only; loops: the
+ *   cell face, I planar side quads, the back-traced face (I+2 faces). */
 static int flux_loops(int method, int I, int* fp, int* fi) {
   int nfp = 0, k = 0;
   fp[0] = 0;
@@ -815,6 +817,12 @@ static int flux_loops(int method, int I, int* fp, int* fi) {
       for (int e = 0; e < 4; ++e) fi[k++] = q[e];
       fp[++nfp] = k;
     }
+  }
+  if (method == 2) {
+    /* the back-traced face, reversed (its outward normal is -n) */
+    for (int i = I - 1; i >= 0; --i) fi[k++] = I + i;
+    fp[++nfp] = k;
+    return nfp;
   }
   int apex = method == 1 ? 3 * I : 2 * I;
   for (int i = 0; i < I; ++i) {
@@ -889,6 +897,34 @@ int orc_emfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
   *flags = place_apex(nvp, P, nfp, fp, fi, xb, I, n, m->fa[f], *Vd, 3 * I);
   for (int i = 0; i < nvp; ++i)
     for (int q = 0; q < 3; ++q) out[3 * i + q] = P[i][q] + c[q];
+  return I;
+}
+
+/* --------------------------------------------------------- NMFPA (Sec 2.2.3) */
+/* every vertex of the face goes back with the one velocity of the face
+ * centre at t^{n+1/2} (Eq. streak-line2 with u_c): the polyhedron is the
+ * prism between the face and its translate, whose volume is V_d itself
+ * (no apex, no adjustment) */
+int orc_nmfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
+              double dt, double* out, int capI, double* Vd, int* flags) {
+  int64_t b = m->fptr[f];
+  int I = (int)(m->fptr[f + 1] - b);
+  if (I > capI || I > 32) return -1;
+  const double* c = m->fc + 3 * f;
+  const double* n = m->fn + 3 * f;
+  double uc[3];
+  orc_velocity_eval(vel, c, th, uc);
+  *Vd = dot3(uc, n) * m->fa[f] * dt; /* Eq. a-donacion */
+  *flags = 0;
+  for (int i = 0; i < I; ++i) {
+    const double* xa = m->X + 3 * m->fvert[b + i];
+    double x[3];
+    sub3(xa, c, x);
+    for (int q = 0; q < 3; ++q) {
+      out[3 * i + q] = x[q] + c[q];
+      out[3 * (I + i) + q] = (x[q] - dt * uc[q]) + c[q];
+    }
+  }
   return I;
 }
 
@@ -1171,11 +1207,12 @@ void orc_faceflux(const orc_mesh* m, const orc_velocity* vel, double t, double d
     double P[97 * 3];
     double vdd;
     int flags;
-    int I = method == 1 ? orc_emfpa(m, f, vel, th, dt, P, 32, &vdd, &flags)
-                        : orc_fmfpa(m, f, vel, th, dt, P, 32, &vdd, &flags);
+    int I = method == 1   ? orc_emfpa(m, f, vel, th, dt, P, 32, &vdd, &flags)
+            : method == 2 ? orc_nmfpa(m, f, vel, th, dt, P, 32, &vdd, &flags)
+                          : orc_fmfpa(m, f, vel, th, dt, P, 32, &vdd, &flags);
     if (flags & 1) ++n_deg;
     if (flags & 2) ++n_edge;
-    int nvp = method == 1 ? 3 * I + 1 : 2 * I + 1;
+    int nvp = method == 1 ? 3 * I + 1 : method == 2 ? 2 * I : 2 * I + 1;
     /* local frame at the face centroid */
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < nvp; ++i)

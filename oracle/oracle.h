@@ -1,5 +1,5 @@
 /*
- * Oracle for the unsplit geometric VOF step (LSGIR + FMFPA / EMFPA) -- TEST
+ * Oracle for the unsplit geometric VOF step (LSGIR / LSFIR + FMFPA / EMFPA / NMFPA) -- TEST
  * INFRASTRUCTURE ONLY.
  *
  * A plain, slow FP64 CPU implementation of what one time step computes, used
@@ -118,8 +118,15 @@ int orc_emfpa(const orc_mesh* m, int64_t face, const orc_velocity* v,
               double t_half, double dt, double* verts, int cap_I, double* Vd,
               int* flags);
 
+/* NMFPA flux polyhedron of one face (Sec. 2.2.3): verts receives 2I
+ * points, x_1..x_I and x_i - dt u_c (u_c the face-centre velocity at
+ * t_half). Returns I, or -1 if I > cap_I. *Vd = (u_c.n) A dt; flags = 0. */
+int orc_nmfpa(const orc_mesh* m, int64_t face, const orc_velocity* v,
+              double t_half, double dt, double* verts, int cap_I, double* Vd,
+              int* flags);
+
 /* faceflux (Sec. 3.5 with Sec. 2.2): V_d and V_F for every face, with the
- * flux polyhedra of `method` (0: FMFPA, 1: EMFPA). stats[0] = geometric
+ * flux polyhedra of `method` (0: FMFPA, 1: EMFPA, 2: NMFPA). stats[0] = geometric
  * faces, [1] = degenerate-line fallbacks, [2] = edge-on faces, [3] =
  * (face, cell) truncations evaluated. Threads: OpenMP over faces. */
 void orc_faceflux(const orc_mesh* m, const orc_velocity* v, double t,

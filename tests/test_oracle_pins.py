@@ -660,6 +660,153 @@ def test_lsgir_rotation_invariance(orc):
     assert np.allclose(n2, n @ R.T, atol=1e-12)
 
 
+# ---------------------------------------------------------------- NMFPA
+def _nmfpa_faces(nI):
+    """Faces of the non-matched polyhedron as Sec. 2.2.3 states them: the
+    cell face, I side faces, the back-traced face (I+2 faces)."""
+    faces = [list(range(nI))]
+    faces += [[(i + 1) % nI, i, nI + i, nI + (i + 1) % nI] for i in range(nI)]
+    faces.append([nI + i for i in range(nI - 1, -1, -1)])
+    return faces
+
+
+@pytest.mark.parametrize("gen", ["hex", "tet", "trihex"])
+def test_nmfpa_is_the_prism_of_the_face_velocity(orc, gen):
+    """Every vertex moves back by dt u(x_c, t^{n+1/2}) (the written-out
+    rotation field at the face centre): the side faces are parallelograms,
+    the back-traced face is the face's translate, and the volume of the
+    I+2 faces equals V_d without any adjustment."""
+    m = {"hex": lambda: I.hex_mesh(5), "tet": lambda: I.kuhn_tet_mesh(4, seed=5),
+         "trihex": lambda: I.trihex_mesh(3, seed=2)}[gen]()
+    om = orc.Mesh(m)
+    g = om.geometry()
+    omega, c = 2.0 * np.pi, (0.5, 0.5, 0.5)
+    vel = I.rotation(omega, c)
+    dt = 0.02
+    for f in range(0, len(m["owner"]), 3):
+        P, vd, fl = om.nmfpa(f, vel, 0.1, dt)
+        X = _face_nodes(m, f)
+        nI = len(X)
+        assert P.shape[0] == 2 * nI and fl == 0
+        uc = _rot_u(g["face_cen"][f][None, :], omega, c)[0]
+        assert np.allclose(P[:nI], X, atol=1e-15)
+        assert np.allclose(P[nI:], X - dt * uc, atol=1e-15)
+        assert abs(vd - uc @ g["face_nrm"][f] * g["face_area"][f] * dt) < 1e-18
+        vol = orc.poly_volume(P - X.mean(0), _nmfpa_faces(nI))
+        A = g["face_area"][f]
+        assert abs(vol - vd) <= 1e-14 * max(abs(vd), A ** 1.5), (f, vol, vd)
+
+
+def test_nmfpa_and_fmfpa_agree_for_uniform_flow(orc):
+    """A uniform field gives the same exact prism to every construction."""
+    m = I.kuhn_tet_mesh(5, seed=8)
+    om = orc.Mesh(m)
+    st = om.reconstruct(I.init_fraction(m, I.sphere((0.5, 0.5, 0.5), 0.22), levels=3))
+    vel = I.translation((0.4, -0.3, 0.2))
+    dt = om.suggest_dt(vel, 0.0, 0.6, 10.0)
+    Vd0, VF0, _ = om.faceflux(vel, 0.0, dt, st, orc.FMFPA)
+    Vd2, VF2, s2 = om.faceflux(vel, 0.0, dt, st, orc.NMFPA)
+    assert np.array_equal(Vd0, Vd2) and s2[1] == 0 and s2[2] == 0
+    assert np.abs(VF2 - VF0).max() < 1e-15 * np.abs(Vd0).max() * 100
+
+
+def test_nmfpa_cfl1_translation_shifts_exactly(orc):
+    n = 6
+    m = I.hex_mesh(n)
+    om = orc.Mesh(m)
+    st = om.reconstruct(I.init_fraction(m, I.sphere((0.45, 0.52, 0.48), 0.27), levels=3))
+    new = om.step(I.translation((1.0, 0.0, 0.0)), 0.0, 1.0 / n, st, method=orc.NMFPA)
+    F = st["F"].reshape(n, n, n)
+    G = new["F_unclipped_cut"].reshape(n, n, n)
+    assert np.abs(G[:, :, 1:] - F[:, :, :-1]).max() < 2e-15
+    assert np.abs(G[:, :, 0]).max() == 0.0
+
+
+def test_nmfpa_is_not_strictly_conservative(orc):
+    """Sec. 4: NMFPA is not strictly conservative because the polyhedra of
+    neighbouring faces overlap or leave gaps, so F leaves [0, 1] and the
+    final clip removes volume; with the face-matched polyhedra the same
+    rotation keeps the volume to rounding (the field is linear, so the
+    discrete divergence vanishes and only the clip could change it)."""
+    m = I.hex_mesh(16)
+    om = orc.Mesh(m)
+    V = om.geometry()["cell_vol"]
+    F0 = I.init_fraction(m, I.sphere((0.5, 0.75, 0.5), 0.15), levels=3)
+    vel = I.rotation(1.0, (0.5, 0.5, 0.5))
+    loss = {}
+    for meth in (orc.FMFPA, orc.NMFPA):
+        st = om.reconstruct(F0)
+        v0 = (V * st["F"]).sum()
+        t, worst = 0.0, 0.0
+        for _ in range(6):
+            dt = om.suggest_dt(vel, t, 0.9, 100.0)
+            vb = (V * st["F"]).sum()
+            new = om.step(vel, t, dt, st, method=meth)
+            worst = max(worst, abs((V * new["F_unclipped_cut"]).sum() - vb) / v0)
+            st, t = new, t + dt
+        loss[meth] = worst
+    assert loss[orc.FMFPA] < 1e-13, loss
+    assert loss[orc.NMFPA] > 1e-8, loss
+
+
+def test_nmfpa_uses_the_midtime_face_velocity(orc):
+    """Time-modulated deformation field (Sec. 4.2), written out: the shift
+    of every vertex is dt u(x_c, t + dt/2)."""
+    m = I.hex_mesh(4)
+    om = orc.Mesh(m)
+    T, t, dt = 3.0, 0.4, 0.05
+    g = om.geometry()
+
+    def u(x, tt):
+        s_, s2 = np.sin(np.pi * x), np.sin(2 * np.pi * x)
+        return np.cos(np.pi * tt / T) * np.array([2 * s_[0] ** 2 * s2[1] * s2[2],
+                                                  -s2[0] * s_[1] ** 2 * s2[2],
+                                                  -s2[0] * s2[1] * s_[2] ** 2])
+    for f in range(0, len(m["owner"]), 5):
+        P, _, _ = om.nmfpa(f, I.deformation(T), t + 0.5 * dt, dt)
+        nI = P.shape[0] // 2
+        assert np.allclose(P[nI:] - P[:nI], -dt * u(g["face_cen"][f], t + 0.5 * dt), atol=1e-16)
+
+
+@pytest.mark.parametrize("method", ["FMFPA", "EMFPA", "NMFPA"])
+def test_faceflux_monte_carlo(orc, method):
+    """V_F of sample active faces (Sec. 2.2) against a Monte-Carlo integral of
+    the fluid indicator (full cells 1, interfacial cells their PLIC half-
+    space, empty cells 0; cells located on the uniform grid by index) times
+    the winding number of the face's flux polyhedron (points and faces from
+    the construction, written out here)."""
+    n = 8
+    m = I.hex_mesh(n)
+    om = orc.Mesh(m)
+    st = om.reconstruct(I.init_fraction(m, I.sphere((0.5, 0.55, 0.5), 0.27), levels=3))
+    vel, t, dt = I.rotation(2 * np.pi), 0.0, 0.02
+    meth = getattr(orc, method)
+    Vd, VF, _ = om.faceflux(vel, t, dt, st, meth)
+    g = om.geometry()
+    build = {"FMFPA": (om.fmfpa, _fmfpa_faces), "EMFPA": (om.emfpa, _emfpa_faces),
+             "NMFPA": (om.nmfpa, _nmfpa_faces)}[method]
+    active = np.nonzero(st["tag_f"] == 0)[0]
+    rng = np.random.default_rng(17)
+    for f in rng.choice(active, 6, replace=False):
+        P, vd, _ = build[0](int(f), vel, t + 0.5 * dt, dt)
+        nI = {"FMFPA": (P.shape[0] - 1) // 2, "EMFPA": (P.shape[0] - 1) // 3,
+              "NMFPA": P.shape[0] // 2}[method]
+        tris = fan_tris(P, build[1](nI))
+        lo, hi = P.min(0), P.max(0)
+        N = 200000
+        X = lo + (hi - lo) * rng.random((N, 3))
+        w = winding_number(X, tris)
+        ijk = np.clip(np.floor(X * n).astype(int), 0, n - 1)
+        cell = ijk[:, 0] + n * (ijk[:, 1] + n * ijk[:, 2])
+        tc = st["tag_c"][cell]
+        side = np.einsum("ij,ij->i", st["nrm"][cell], X - g["cell_cen"][cell]) + st["C"][cell]
+        fluid = (tc == 1) | ((tc == 0) & (side >= 0))
+        box = np.prod(hi - lo)
+        vals = w * fluid
+        mc, sig = vals.mean() * box, vals.std() * box / np.sqrt(N)
+        assert abs(VF[f] - mc) < 5 * sig + 1e-12, (method, f, VF[f], mc, sig)
+
+
 # ---------------------------------------------------------------- LSFIR
 def _ang(a, b):
     """angle between unit vectors, accurate near 0"""
