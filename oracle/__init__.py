@@ -60,6 +60,21 @@ def _vel(v):
     return s
 
 
+class _Body(C.Structure):
+    _fields_ = [("kind", C.c_int), ("pad", C.c_int), ("c", C.c_double * 3),
+                ("a", C.c_double * 3), ("r", C.c_double)]
+
+
+def _body(b):
+    s = _Body()
+    s.kind = b.kind
+    for i in range(3):
+        s.c[i] = b.c[i]
+        s.a[i] = b.a[i]
+    s.r = b.r
+    return s
+
+
 def _p(a):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -86,6 +101,7 @@ def lib():
         L.orc_velocity_eval.argtypes = [vp, vp, dbl, vp]
         L.orc_fmfpa.restype = i32
         L.orc_fmfpa.argtypes = [vp, i64, vp, dbl, dbl, vp, i32, vp, vp]
+        L.orc_initfgrid.argtypes = [vp, vp, i32, vp]
         L.orc_plic_centre.restype = i32
         L.orc_plic_centre.argtypes = [vp, i64, vp, dbl, vp]
         L.orc_lsfir_normals.restype = i64
@@ -197,6 +213,14 @@ class Mesh:
     def cell_cut_volume(self, cell, n, Cval):
         n = np.ascontiguousarray(n, np.float64)
         return lib().orc_cell_cut_volume(self._m, int(cell), _p(n), float(Cval))
+
+    def initfgrid(self, shape, ndiv=10):
+        """initial F by refinement (Sec. 3.2): ndiv^3 pieces per tetrahedron of
+        each cell near the surface of ``shape`` (inputs.Shape)."""
+        F = np.empty(self.n_cell)
+        b = _body(shape)
+        lib().orc_initfgrid(self._m, C.byref(b), int(ndiv), _p(F))
+        return F
 
     def plic_centre(self, cell, n, Cval):
         """vertex average of the PLIC polygon of a cell (Sec. 2.1.2)"""

@@ -558,6 +558,105 @@ void orc_plane_constant(const orc_mesh* m, const double* F, const int8_t* tag_c,
   }
 }
 
+/* ------------------------------------------------------- initfgrid (Sec 3.2) */
+/* implicit function of the initial fluid body: negative inside; a signed
+ * distance (1-Lipschitz) for every kind, so that a cell whose bounding ball
+ * lies on one side is entirely fluid or empty.
+ * kind 1: sphere (centre c, radius r); 2: infinite cylinder (axis through c
+ * along the unit vector a, radius r); 3: half-space a.(x - c) < 0 (a unit). */
+static double body_phi(const orc_body* b, const double x[3]) {
+  double d[3];
+  sub3(x, b->c, d);
+  if (b->kind == 1) return norm3(d) - b->r;
+  if (b->kind == 2) {
+    double t = dot3(d, b->a);
+    double p[3] = {d[0] - t * b->a[0], d[1] - t * b->a[1], d[2] - t * b->a[2]};
+    return norm3(p) - b->r;
+  }
+  return dot3(b->a, d);
+}
+
+/* volume fraction of the fluid (the part of every cell where the piecewise
+ * linear interpolant of phi is negative) by refinement: each cell is the
+ * signed sum of the tetrahedra joining its vertex average to the fan
+ * triangles of its faces; each tetrahedron (v0, v1, v2, v3) is divided into
+ * ndiv^3 equal tetrahedra (Freudenthal: in the coordinates x with point
+ * v0 + (x1 (v1 - v0) + x2 (v2 - v1) + x3 (v3 - v2)) / ndiv, the simplex is
+ * ndiv >= x1 >= x2 >= x3 >= 0, and its pieces are the Kuhn tetrahedra of the
+ * unit lattice cubes that lie in it); phi is evaluated at their vertices
+ * and the negative part of each piece is exact for the linear interpolant.
+ * Cells whose bounding ball about the centroid lies on one side of the body
+ * are 0 or 1 without refinement. */
+void orc_initfgrid(const orc_mesh* m, const orc_body* body, int ndiv, double* F) {
+  static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t c = 0; c < m->nc; ++c) {
+    const double* xc = m->cc + 3 * c;
+    double R = 0.0;
+    for (int64_t q = m->cv_ptr[c]; q < m->cv_ptr[c + 1]; ++q) {
+      double d[3];
+      sub3(m->X + 3 * m->cv[q], xc, d);
+      double l = norm3(d);
+      if (l > R) R = l;
+    }
+    double pc = body_phi(body, xc);
+    if (pc > R) { F[c] = 0.0; continue; }
+    if (pc < -R) { F[c] = 1.0; continue; }
+    double r[3] = {0, 0, 0};
+    int64_t ncv = m->cv_ptr[c + 1] - m->cv_ptr[c];
+    for (int64_t q = m->cv_ptr[c]; q < m->cv_ptr[c + 1]; ++q)
+      for (int d = 0; d < 3; ++d) r[d] += m->X[3 * m->cv[q] + d];
+    for (int d = 0; d < 3; ++d) r[d] /= (double)ncv;
+    double vol = 0.0;
+    for (int64_t q = m->cf_ptr[c]; q < m->cf_ptr[c + 1]; ++q) {
+      int32_t f = m->cf[q];
+      int out = (m->own[f] == c);
+      int64_t b = m->fptr[f], I = m->fptr[f + 1] - b;
+      const double* p0 = m->fp0 + 3 * f;
+      for (int64_t i = 0; i < I; ++i) {
+        const double* a = m->X + 3 * m->fvert[b + i];
+        const double* e = m->X + 3 * m->fvert[b + (i + 1) % I];
+        double T[4][3];
+        for (int d = 0; d < 3; ++d) {
+          T[0][d] = r[d]; T[1][d] = p0[d];
+          T[2][d] = out ? a[d] : e[d];
+          T[3][d] = out ? e[d] : a[d];
+        }
+        double v = det6(T[0], T[1], T[2], T[3]) / 6.0;
+        if (v == 0.0) continue;
+        double w[3][3]; /* v1 - v0, v2 - v1, v3 - v2 */
+        for (int k = 0; k < 3; ++k)
+          for (int d = 0; d < 3; ++d) w[k][d] = T[k + 1][d] - T[k][d];
+        double frac = 0.0;
+        for (int a1 = 0; a1 < ndiv; ++a1)
+          for (int a2 = 0; a2 <= a1; ++a2)
+            for (int a3 = 0; a3 <= a2; ++a3) {
+              int base[3] = {a1, a2, a3};
+              for (int pi = 0; pi < 6; ++pi) {
+                const int* pr = perm[pi];
+                /* where two base coordinates tie, the lower index steps first */
+                int pos[3];
+                for (int k = 0; k < 3; ++k) pos[pr[k]] = k;
+                if ((a1 == a2 && pos[0] > pos[1]) || (a2 == a3 && pos[1] > pos[2])) continue;
+                double S[4][3], sv[4];
+                int x[3] = {base[0], base[1], base[2]};
+                for (int k = 0; k < 4; ++k) {
+                  if (k > 0) x[pr[k - 1]] += 1;
+                  for (int d = 0; d < 3; ++d)
+                    S[k][d] = T[0][d] + (x[0] * w[0][d] + x[1] * w[1][d] + x[2] * w[2][d]) / ndiv;
+                  sv[k] = -body_phi(body, S[k]);
+                }
+                frac += tet_inside_fraction(S, sv);
+              }
+            }
+        vol += v * frac / ((double)ndiv * ndiv * ndiv);
+      }
+    }
+    double Fc = vol / m->cvol[c];
+    F[c] = Fc < 0.0 ? 0.0 : (Fc > 1.0 ? 1.0 : Fc);
+  }
+}
+
 /* ------------------------------------------------------------ LSFIR (Sec 2.1.2) */
 /* geometric centre of the vertex set of the PLIC polygon of cell c, plane
  * n.(x - xc) + C = 0: the points where the plane crosses an edge of the

@@ -74,6 +74,22 @@ void orc_plane_constant(const orc_mesh* m, const double* F,
 double orc_cell_cut_volume(const orc_mesh* m, int64_t cell, const double n[3],
                            double C);
 
+/* initial fluid body (Sec. 3.2, initfgrid): kind 1 sphere (centre c,
+ * radius r), 2 infinite cylinder (axis through c along unit a, radius r),
+ * 3 half-space a.(x - c) < 0 (a unit). */
+typedef struct {
+  int kind;
+  int pad;
+  double c[3];
+  double a[3];
+  double r;
+} orc_body;
+
+/* initfgrid (Sec. 3.2): F of every cell by refinement, each cell's
+ * tetrahedra divided into ndiv^3 pieces on which the fluid is where the
+ * linear interpolant of the body's signed distance is negative. */
+void orc_initfgrid(const orc_mesh* m, const orc_body* body, int ndiv, double* F);
+
 /* LSFIR (Sec. 2.1.2). orc_plic_centre: vertex average of the PLIC polygon
  * of cell c (edge crossings of n.(x - xc) + C = 0, each edge once, plus
  * cell vertices on the plane); returns the number of points (0: out = xc).

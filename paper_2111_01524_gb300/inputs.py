@@ -398,6 +398,34 @@ def sphere(center, radius):
     return Body(center, [radius, radius, radius])
 
 
+class Shape:
+    """Parameters of an initial fluid body for the refinement initialisation
+    (``initfgrid``, Sec. 3.2): a description only, evaluated by the oracle
+    and by the device routine on their own. kind 1: sphere (centre c, radius
+    r); 2: infinite cylinder (axis through c along the unit vector a, radius
+    r); 3: half-space a.(x - c) < 0 (a unit)."""
+    SPHERE, CYLINDER, HALFSPACE = 1, 2, 3
+
+    def __init__(self, kind, c, a=(0.0, 0.0, 1.0), r=0.0):
+        self.kind = int(kind)
+        self.c = tuple(float(v) for v in c)
+        a = np.asarray(a, np.float64)
+        self.a = tuple(float(v) for v in a / np.linalg.norm(a))
+        self.r = float(r)
+
+
+def shape_sphere(center, radius):
+    return Shape(Shape.SPHERE, center, r=radius)
+
+
+def shape_cylinder(point, axis, radius):
+    return Shape(Shape.CYLINDER, point, axis, radius)
+
+
+def shape_halfspace(point, normal):
+    return Shape(Shape.HALFSPACE, point, normal)
+
+
 def ellipsoid(center, axes):
     return Body(center, axes)
 

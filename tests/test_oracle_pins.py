@@ -1039,6 +1039,52 @@ def test_lsfir_rotation_invariance(orc):
     assert np.allclose(st2["C"][band], st["C"][band], atol=1e-9)
 
 
+# ---------------------------------------------------------------- initfgrid
+@pytest.mark.parametrize("gen", ["hex", "tet", "trihex"])
+def test_initfgrid_halfspace_is_exact(orc, gen):
+    """A planar surface is its own linear interpolant: the refinement gives
+    every cell's exact cut volume (Sec. 2.1 closed forms pin the cut
+    volume), for convex and non-convex cells alike."""
+    m = {"hex": lambda: I.hex_mesh(5), "tet": lambda: I.kuhn_tet_mesh(4, seed=2),
+         "trihex": lambda: I.trihex_mesh(3, seed=4)}[gen]()
+    om = orc.Mesh(m)
+    g = om.geometry()
+    nt = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    p0 = np.array([0.5, 0.48, 0.52])
+    F = om.initfgrid(I.shape_halfspace(p0, nt), 3)
+    # fluid a.(x - p0) < 0: the cut volume of the plane with normal -a
+    ex = np.array([om.cell_cut_volume(c, -nt, -nt @ (g["cell_cen"][c] - p0))
+                   for c in range(om.n_cell)]) / g["cell_vol"]
+    assert np.abs(F - ex).max() < 1e-13
+    assert ((F > 0) & (F < 1)).sum() > 10
+
+
+@pytest.mark.parametrize("shape", ["sphere", "cylinder"])
+def test_initfgrid_converges_at_second_order(orc, shape):
+    """Total fluid volume against the body's closed-form volume: the piecewise
+    linear interpolant errs by O((h/ndiv)^2), so doubling ndiv divides the
+    error by about four; cells away from the surface are exactly 0 or 1."""
+    m = I.hex_mesh(12)
+    om = orc.Mesh(m)
+    V = om.geometry()["cell_vol"]
+    if shape == "sphere":
+        sh, exact = I.shape_sphere((0.5, 0.52, 0.48), 0.3), 4.0 / 3.0 * np.pi * 0.3 ** 3
+    else:  # axis along y through the whole domain (the 2D test's cylinder, Sec. 4)
+        sh, exact = I.shape_cylinder((0.5, 0.0, 0.55), (0.0, 1.0, 0.0), 0.25), np.pi * 0.25 ** 2
+    err = []
+    for n in (4, 8, 16):
+        F = om.initfgrid(sh, n)
+        assert F.min() >= 0 and F.max() <= 1
+        err.append((V * F).sum() - exact)
+    assert 3.3 < err[0] / err[1] < 4.7 and 3.3 < err[1] / err[2] < 4.7, err
+    assert abs(err[2]) < 1e-4 * exact
+    x = om.geometry()["cell_cen"]
+    far = np.abs(np.linalg.norm((x - sh.c) * ([1, 0, 1] if shape == "cylinder" else 1), axis=1)
+                 - sh.r) > 0.1
+    F = om.initfgrid(sh, 4)
+    assert set(np.unique(F[far])) <= {0.0, 1.0}
+
+
 # ---------------------------------------------------------------- whole step
 def test_cfl1_translation_shifts_exactly(orc):
     """u = (1,0,0), dt = h on a uniform grid: every x-face flux polyhedron is
