@@ -50,19 +50,25 @@ FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
 # triangle volumes per vertex; its surface has twice the face-vertex loop
 # entries of FMFPA (64 against 32 for a hex face), and a truncation's
 # clipping and divergence sum scale with those entries
-FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0, 2400.0)}
+# NMFPA (Sec. 2.2.3): one velocity per face and a translation; its prism has
+# 6I loop entries (24 for a hex face, against 32)
+FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0, 2400.0),
+         "nmfpa": (100.0, 900.0)}
 # ncu capture of one flux launch (128^3 deformation step, mixed: ~57,300 active
 # faces): dram__bytes_read.sum + dram__bytes_write.sum = 26.94 + 1.91 MB, i.e.
 # 504 B per active face, issue active 38.2%, FMA pipe 10.9%; valid for the
 # kernel source it was taken on (traffic is null for any other source)
 # ncu --set full of the mixed flux kernel (128^3 deformation, 4th step's launch, ~57,300
 # active faces) per flux-polyhedron construction; valid only for the source it was taken on
-FLUX_NCU = {"source_sha256": "a7f9353f1fcc19bb2321b21ba2fd5936ab56832ec619e83e135cc26e0cb5dc00",
-            "fmfpa": {"dram_bytes_per_active_face": 506.0, "issue_active": 0.396,
-                      "fma_pipe_active": 0.109, "capture": "profiles/k_flux_deformation128_mixed.md"},
-            "emfpa": {"dram_bytes_per_active_face": 504.0, "issue_active": 0.392,
-                      "fma_pipe_active": 0.109,
-                      "capture": "profiles/k_flux_deformation128_mixed_emfpa.md"}}
+FLUX_NCU = {"source_sha256": "7a54b07b36045e719d40c159eae763db9087befd9d978edae4e98ceaf4bb58bc",
+            "fmfpa": {"dram_bytes_per_active_face": 505.0, "issue_active": 0.398,
+                      "fma_pipe_active": 0.110, "capture": "profiles/k_flux_deformation128_mixed.md"},
+            "emfpa": {"dram_bytes_per_active_face": 505.0, "issue_active": 0.394,
+                      "fma_pipe_active": 0.108,
+                      "capture": "profiles/k_flux_deformation128_mixed_emfpa.md"},
+            "nmfpa": {"dram_bytes_per_active_face": 436.0, "issue_active": 0.398,
+                      "fma_pipe_active": 0.110,
+                      "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
 N_SM = 152
@@ -76,8 +82,11 @@ def parse():
     p.add_argument("--impl", default="gvof", choices=["gvof", "reference"])
     p.add_argument("--grid", type=int, default=256)
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    p.add_argument("--flux", default="fmfpa", choices=["fmfpa", "emfpa"],
-                   help="flux polyhedron: face-matched (Sec. 2.2.2) or edge-matched (Sec. 2.2.1)")
+    p.add_argument("--flux", default="fmfpa", choices=["fmfpa", "emfpa", "nmfpa"],
+                   help="flux polyhedron: face-matched (Sec. 2.2.2), edge-matched (Sec. 2.2.1) "
+                        "or non-matched (Sec. 2.2.3)")
+    p.add_argument("--recon", default="lsgir", choices=["lsgir", "lsfir"],
+                   help="interface reconstruction: LSGIR (Sec. 2.1.1) or LSFIR (Sec. 2.1.2)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -241,8 +250,10 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
     if name == "flux" and precision == "mixed":
         import hashlib
         src = os.path.join(ROOT, "paper_2111_01524_gb300", "csrc", "k_flux.cu")
+        rec = None  # the capture's figures, if it was taken on this source
         if hashlib.sha256(open(src, "rb").read()).hexdigest() == FLUX_NCU["source_sha256"]:
-            rec = FLUX_NCU[flux]
+            rec = FLUX_NCU.get(flux)
+        if rec is not None:
             traffic = rec["dram_bytes_per_active_face"] * ctx_counts["n_active_faces"]
             ncu = {k: rec[k] for k in ("issue_active", "fma_pipe_active", "capture")}
     mhz = clocks.get("sm_mhz") or 1900.0
@@ -256,17 +267,20 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
                            f"median SM clock {mhz:.0f} MHz"}
 
 
-def cpu_baseline(mesh, F0, vel, cfl, t_end, steps, flux="fmfpa"):
+def cpu_baseline(mesh, F0, vel, cfl, t_end, steps, flux="fmfpa", recon="lsgir"):
     import oracle
     oracle.build()
     om = oracle.Mesh(mesh)
     st = om.reconstruct(F0)
     t = 0.0
     t0 = time.perf_counter()
-    method = oracle.EMFPA if flux == "emfpa" else oracle.FMFPA
+    method = {"emfpa": oracle.EMFPA, "nmfpa": oracle.NMFPA}.get(flux, oracle.FMFPA)
+    rc = oracle.LSFIR if recon == "lsfir" else oracle.LSGIR
+    if rc == oracle.LSFIR:
+        st = om.reconstruct(F0, recon=rc)
     for _ in range(steps):
         dt = om.suggest_dt(vel, t, cfl, t_end)
-        st = om.step(vel, t, dt, st, method=method)
+        st = om.step(vel, t, dt, st, method=method, recon=rc)
         t += dt
     el = time.perf_counter() - t0
     return {"value": om.n_cell * steps / el, "unit": UNIT, "cores": oracle.num_threads(),
@@ -284,18 +298,21 @@ def main_reference(a):
     oracle.build()
     om = oracle.Mesh(mesh)
     st = om.reconstruct(F0)
-    method = oracle.EMFPA if a.flux == "emfpa" else oracle.FMFPA
+    method = {"emfpa": oracle.EMFPA, "nmfpa": oracle.NMFPA}.get(a.flux, oracle.FMFPA)
+    rc = oracle.LSFIR if a.recon == "lsfir" else oracle.LSGIR
+    if rc == oracle.LSFIR:
+        st = om.reconstruct(F0, recon=rc)
     t = 0.0
     for _ in range(a.warmup):
         dt = om.suggest_dt(vel, t, cfl, t_end)
-        st = om.step(vel, t, dt, st, method=method)
+        st = om.step(vel, t, dt, st, method=method, recon=rc)
         t += dt
     lat = []
     t0 = time.perf_counter()
     for _ in range(a.steps):
         s0 = time.perf_counter()
         dt = om.suggest_dt(vel, t, cfl, t_end)
-        st = om.step(vel, t, dt, st, method=method)
+        st = om.step(vel, t, dt, st, method=method, recon=rc)
         t += dt
         lat.append((time.perf_counter() - s0) * 1e3)
     el = time.perf_counter() - t0
@@ -307,7 +324,8 @@ def main_reference(a):
             "data": "synthetic", "config": {"workload": f"3D deformation, hex {a.grid}^3, T=3, "
                                                         "CFL 0.5, sphere r=0.15",
                                             "grid": a.grid, "cells": om.n_cell,
-                                            "flux_polyhedron": a.flux},
+                                            "flux_polyhedron": a.flux,
+                                            "reconstruction": a.recon},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"{a.steps} full steps of the {a.grid}^3 workload"},
@@ -439,7 +457,8 @@ def main_tets(a):
     res = {}
     for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
         ctx = V.Context(m, precision=prec,
-                        flux=V.FLUX_EMFPA if a.flux == "emfpa" else V.FLUX_FMFPA)
+                        flux={"emfpa": V.FLUX_EMFPA, "nmfpa": V.FLUX_NMFPA}.get(a.flux, V.FLUX_FMFPA),
+                        recon=V.RECON_LSFIR if a.recon == "lsfir" else V.RECON_LSGIR)
         ctx.set_fraction(F0)
         ctx.reconstruct()
         t = 0.0
@@ -477,7 +496,8 @@ def main_tets(a):
             "data": "synthetic",
             "config": {"workload": "64^3 x 6 jittered Kuhn tets, sphere r=0.15 at (0.5,0.75,0.5), "
                                    "rigid rotation, CFL 0.4", "cells": int(m["n_cell"]),
-                       "flux_polyhedron": a.flux, "parallelism": f"replicas x{ws}"},
+                       "flux_polyhedron": a.flux, "reconstruction": a.recon,
+                       "parallelism": f"replicas x{ws}"},
             "gpu_launches": 6 * a.steps, "clocks": res["mixed"]["clocks"],
             "fp64_path": {"value": res["fp64"]["value"],
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
@@ -610,7 +630,8 @@ def main():
     mesh, F0, vel, cfl, t_end = workload(a.grid)
     counts = I.mesh_counts(mesh)
     prec = V.PREC_MIXED if a.precision == "mixed" else V.PREC_FP64
-    flux = V.FLUX_EMFPA if a.flux == "emfpa" else V.FLUX_FMFPA
+    flux = {"emfpa": V.FLUX_EMFPA, "nmfpa": V.FLUX_NMFPA}.get(a.flux, V.FLUX_FMFPA)
+    recon = V.RECON_LSFIR if a.recon == "lsfir" else V.RECON_LSGIR
     stream = torch.cuda.current_stream()
     F0_dev = torch.from_numpy(F0).cuda()
 
@@ -620,7 +641,7 @@ def main():
             dist.barrier()
 
     def measure(precision, steps, warmup, with_phases):
-        ctx = V.Context(mesh, precision=precision, flux=flux)
+        ctx = V.Context(mesh, precision=precision, flux=flux, recon=recon)
         ctx.set_fraction(F0_dev, stream=stream)
         ctx.reconstruct(stream=stream)
         t, _ = run_steps(ctx, vel, cfl, t_end, 0.0, warmup, stream)
@@ -680,6 +701,10 @@ def main():
                          "active_faces": st64["n_active_faces"]},
                 "mixed_over_fp64": value / v64,
                 "max_abs_F_diff_mixed_vs_fp64": float(np.abs(Fm - F64).max()),
+                # the integral measure (as E_shape, Sec. 4.2): robust where a
+                # discontinuous decision (LSFIR's acceptance) flips in a few cells
+                "l1_rel_F_diff_mixed_vs_fp64": float((g["cell_vol"] * np.abs(Fm - F64)).sum()
+                                                     / (g["cell_vol"] * F64).sum()),
                 "after_steps": fsteps + a.warmup}
         del ctx64, ctxm
 
@@ -687,7 +712,7 @@ def main():
     # from pinned host memory, runs reconstruct + advect, and reads F back
     e2e = None
     if not a.no_e2e:
-        ctxe = V.Context(mesh, precision=prec, flux=flux)
+        ctxe = V.Context(mesh, precision=prec, flux=flux, recon=recon)
         Fh = torch.from_numpy(F0.copy()).pin_memory().numpy()
         ctxe.set_fraction(Fh, stream=stream)
         t = 0.0
@@ -725,7 +750,7 @@ def main():
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(mesh, F0, vel, cfl, t_end, a.cpu_steps, a.flux)
+        cpu = cpu_baseline(mesh, F0, vel, cfl, t_end, a.cpu_steps, a.flux, a.recon)
 
     if rank == 0:
         line = {
@@ -740,6 +765,7 @@ def main():
                                    f"steps from t=0",
                        "grid": a.grid, "cells": counts["n_cell"], "faces": counts["n_face"],
                        "precision": a.precision, "flux_polyhedron": a.flux,
+                       "reconstruction": a.recon,
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (mesh + state ~10 GB), no flush"},
             "gpu_launches": launches,

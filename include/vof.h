@@ -1,11 +1,12 @@
 /*
  * gvof: GB300 (sm_103a) CUDA library for the data-parallel hot path of the
  * unsplit geometric volume-of-fluid method of arXiv 2111.01524 (gVOF):
- * LSGIR reconstruction (Sec. 2.1.1) with a volume-enforcing plane constant
- * (Sec. 2.1), FMFPA face-matched (Sec. 2.2.2) or EMFPA edge-matched (Sec.
- * 2.2.1) flux polyhedra truncated by the upstream cells' PLIC half-spaces
- * (Sec. 2.2), and the conservative update of Eq. fnext with the final clip
- * (Sec. 2.2).
+ * LSGIR reconstruction (Sec. 2.1.1), optionally refined by LSFIR (Sec.
+ * 2.1.2), with a volume-enforcing plane constant (Sec. 2.1); FMFPA
+ * face-matched (Sec. 2.2.2), EMFPA edge-matched (Sec. 2.2.1) or NMFPA
+ * non-matched (Sec. 2.2.3) flux polyhedra truncated by the upstream cells'
+ * PLIC half-spaces (Sec. 2.2); and the conservative update of Eq. fnext with
+ * the final clip (Sec. 2.2).
  *
  * Conventions
  *  - Mesh: OpenFOAM-like face-based polyhedral mesh (Sec. 3.1). Faces are
@@ -50,7 +51,9 @@ enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED = 1 };
 enum { VOF_MEM_HOST = 0, VOF_MEM_DEVICE = 1 };
 enum { VOF_VEL_DEFORMATION = 1, VOF_VEL_ROTATION = 2, VOF_VEL_TRANSLATION = 3 };
 /* flux polyhedron construction (vof_options.flux_polyhedron) */
-enum { VOF_FLUX_FMFPA = 0, VOF_FLUX_EMFPA = 1 };
+enum { VOF_FLUX_FMFPA = 0, VOF_FLUX_EMFPA = 1, VOF_FLUX_NMFPA = 2 };
+/* interface reconstruction (vof_options.reconstruction) */
+enum { VOF_RECON_LSGIR = 0, VOF_RECON_LSFIR = 1 };
 /* points per face in vof_get_flux_polyhedra: 3I+1 for an EMFPA face of
  * I <= 6 nodes, 2I+1 for an FMFPA face of I <= 8 */
 enum { VOF_MAX_POLY_VERTS = 19 };
@@ -78,15 +81,29 @@ typedef struct {
  * flux_polyhedron: VOF_FLUX_FMFPA (Sec. 2.2.2: 2I+1 faces, side faces
  * parallel to the edge-centre velocity) or VOF_FLUX_EMFPA (Sec. 2.2.1:
  * 5I+1 faces, each vertex back-traced with its own velocity, side faces
- * split into four triangles). EMFPA needs every face to have at most 6
- * nodes (its 31 faces fill the per-face capacity); vof_init returns
- * VOF_EINVAL otherwise. reserved: must be zero. */
+ * split into four triangles) or VOF_FLUX_NMFPA (Sec. 2.2.3: I+2 planar
+ * faces, every vertex moved back with the face-centre velocity; not
+ * strictly conservative, as the paper notes). EMFPA needs every face to
+ * have at most 6 nodes (its 31 faces fill the per-face capacity); vof_init
+ * returns VOF_EINVAL otherwise.
+ * reconstruction: VOF_RECON_LSGIR (Sec. 2.1.1) or VOF_RECON_LSFIR (Sec.
+ * 2.1.2: from the LSGIR planes, up to lsfir_max_iter outer iterations, each
+ * fitting every interfacial cell's normal to the PLIC vertex-average
+ * centres of its valid neighbours (weights |dx|^-2.5, previous normals
+ * within 45 degrees), taking it where it turns the normal by less than
+ * 30 degrees / iteration, and enforcing the plane constants again; stops
+ * after an iteration in which no accepted turn reached lsfir_tol radians).
+ * lsfir_max_iter: 0 means 4 (the paper's n_out), at most 16. lsfir_tol: 0
+ * means 1e-3 rad. reserved: must be zero. */
 typedef struct {
   double eps;
   double beta;
   int32_t precision;
   int32_t flux_polyhedron;
-  int32_t reserved[6];
+  int32_t reconstruction;
+  int32_t lsfir_max_iter;
+  double lsfir_tol;
+  int32_t reserved[2];
 } vof_options;
 
 /* Prescribed velocity of the test problems (Sec. 4.2):
@@ -149,7 +166,9 @@ vof_status vof_get_fraction(vof_ctx* ctx, double* F, int mem, void* stream);
 
 /* taggrid (cut-off of F, node F* by inverse-distance weighting, node/face/
  * cell tags; Sec. 2.1, Sec. 3.3) then LSGIR normals and plane constants of
- * the interfacial cells (Secs. 2.1, 2.1.1). */
+ * the interfacial cells (Secs. 2.1, 2.1.1), refined by the LSFIR outer
+ * iteration (Sec. 2.1.2) when the context was made with
+ * VOF_RECON_LSFIR. */
 vof_status vof_reconstruct(vof_ctx* ctx, void* stream);
 
 /* faceflux + vofadv (Sec. 3.5): V_d of every face (Eq. a-donacion), FMFPA
@@ -220,8 +239,8 @@ vof_status vof_get_candidates(vof_ctx* ctx, const int32_t* faces, int n, int64_t
  * VOF_MAX_POLY_VERTS * 3] absolute coordinates, padded with zeros; FMFPA
  * (Sec. 2.2.2): 2I+1 points per face (x_1..x_I, back-traced x_{I+1}..x_{2I},
  * apex); EMFPA (Sec. 2.2.1): 3I+1 points (x_1..x_I, back-traced
- * x_{I+1}..x_{2I}, side-face centres s_1..s_I, apex). counts HOST [n]
- * receives I. */
+ * x_{I+1}..x_{2I}, side-face centres s_1..s_I, apex); NMFPA (Sec. 2.2.3):
+ * 2I points (x_1..x_I, x_i - dt u_c). counts HOST [n] receives I. */
 vof_status vof_get_flux_polyhedra(vof_ctx* ctx, const vof_velocity* vel, double t, double dt,
                                   const int32_t* faces, int n, double* verts, int32_t* counts);
 /* counters and global sums (synchronises the stream). */

@@ -48,7 +48,9 @@ void free_all(vof_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* ptrs2[] = {c->cpl32, c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces, c->vf_ptr, c->vf,
-                   c->stamp_c, c->stamp_v, c->stamp_f, c->bcells, c->bnodes};
+                   c->stamp_c, c->stamp_v, c->stamp_f, c->bcells, c->bnodes, c->lxp, c->lyp,
+                   c->lzp, c->lxr, c->lyr, c->lzr, c->lnx, c->lny, c->lnz, c->lnx32, c->lny32,
+                   c->lnz32, c->lturn};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -151,11 +153,13 @@ struct PhaseTimer {
   vof_ctx* c;
   cudaStream_t s;
   int slot;
-  PhaseTimer(vof_ctx* c_, int phase, cudaStream_t s_) : c(c_), s(s_), slot(-1) {
+  // launches: kernels the phase launches between the two events
+  PhaseTimer(vof_ctx* c_, int phase, cudaStream_t s_, int launches = 1) : c(c_), s(s_), slot(-1) {
     if (!c->timing) return;
     if (c->n_ev_pairs >= 256) flush_timing(c);
     slot = c->n_ev_pairs++;
     c->ev_phase[slot] = phase;
+    c->ev_n[slot] = launches;
     cudaEventRecord(c->ev[2 * slot], s);
   }
   ~PhaseTimer() {
@@ -167,7 +171,7 @@ struct PhaseTimer {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]);
       c->phase_ms[c->ev_phase[i]] += ms;
-      c->phase_n[c->ev_phase[i]] += 1;
+      c->phase_n[c->ev_phase[i]] += c->ev_n[i];
     }
     c->n_ev_pairs = 0;
   }
@@ -231,9 +235,15 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
   }
   if (!(o.eps > 0 && o.eps < 0.5) || !(o.beta > 0) ||
       (o.precision != VOF_PREC_FP64 && o.precision != VOF_PREC_MIXED) ||
-      (o.flux_polyhedron != VOF_FLUX_FMFPA && o.flux_polyhedron != VOF_FLUX_EMFPA))
+      (o.flux_polyhedron != VOF_FLUX_FMFPA && o.flux_polyhedron != VOF_FLUX_EMFPA &&
+       o.flux_polyhedron != VOF_FLUX_NMFPA) ||
+      (o.reconstruction != VOF_RECON_LSGIR && o.reconstruction != VOF_RECON_LSFIR))
     return fail(VOF_EINVAL, "bad options");
-  for (int k = 0; k < 6; ++k)
+  if (o.lsfir_max_iter < 0 || o.lsfir_max_iter > kMaxLsfirIter || !(o.lsfir_tol >= 0.0))
+    return fail(VOF_EINVAL, "lsfir_max_iter must be in 0..16 and lsfir_tol >= 0");
+  if (o.lsfir_max_iter == 0) o.lsfir_max_iter = 4;  // n_out of Sec. 3.6
+  if (o.lsfir_tol == 0.0) o.lsfir_tol = 1e-3;
+  for (int k = 0; k < 2; ++k)
     if (o.reserved[k] != 0) return fail(VOF_EINVAL, "reserved options must be zero");
   if (o.flux_polyhedron == VOF_FLUX_EMFPA && maxI > kMaxEmfpaVerts)
     return fail(VOF_EINVAL, "EMFPA supports faces of at most 6 nodes; this mesh has " +
@@ -336,6 +346,17 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     CKI(dalloc(c, &c->nx32, nc)); CKI(dalloc(c, &c->ny32, nc)); CKI(dalloc(c, &c->nz32, nc));
     CKI(dalloc(c, &c->C32, nc));
     CKI(dalloc(c, &c->cpl32, c->ncf));
+  }
+  if (o.reconstruction == VOF_RECON_LSFIR) {
+    // PLIC centres by cell, accepted normals by band position, max turn per iteration
+    if (o.precision == VOF_PREC_MIXED) {
+      CKI(dalloc(c, &c->lxr, nc)); CKI(dalloc(c, &c->lyr, nc)); CKI(dalloc(c, &c->lzr, nc));
+      CKI(dalloc(c, &c->lnx32, nc)); CKI(dalloc(c, &c->lny32, nc)); CKI(dalloc(c, &c->lnz32, nc));
+    } else {
+      CKI(dalloc(c, &c->lxp, nc)); CKI(dalloc(c, &c->lyp, nc)); CKI(dalloc(c, &c->lzp, nc));
+      CKI(dalloc(c, &c->lnx, nc)); CKI(dalloc(c, &c->lny, nc)); CKI(dalloc(c, &c->lnz, nc));
+    }
+    CKI(dalloc(c, &c->lturn, kMaxLsfirIter + 1));
   }
   CKI(cudaMallocHost(&c->pinned, 4096));
   CKI(dalloc(c, &c->face_off_d, ng + 1));
@@ -530,7 +551,7 @@ static vof_status advect_launches(vof_ctx* c, cudaStream_t s) {
 static vof_status reconstruct_launches(vof_ctx* c, cudaStream_t s) {
   { PhaseTimer t(c, VOF_PHASE_CELL_TAGS, s); CK(launch_cell_tags(c, s)); }
   { PhaseTimer t(c, VOF_PHASE_NODE_TAGS, s); CK(launch_node_tags(c, s)); }
-  { PhaseTimer t(c, VOF_PHASE_RECONSTRUCT, s); CK(launch_reconstruct(c, s)); }
+  { PhaseTimer t(c, VOF_PHASE_RECONSTRUCT, s, reconstruct_launch_count(c)); CK(launch_reconstruct(c, s)); }
   return VOF_OK;
 }
 

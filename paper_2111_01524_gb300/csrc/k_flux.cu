@@ -1,6 +1,6 @@
-// Face fluxes of the active faces (Sec. 2.2): FMFPA (Sec. 2.2.2) or EMFPA
-// (Sec. 2.2.1) flux polyhedron of each tag-0 face, truncated by the
-// half-spaces of every
+// Face fluxes of the active faces (Sec. 2.2): FMFPA (Sec. 2.2.2), EMFPA
+// (Sec. 2.2.1) or NMFPA (Sec. 2.2.3) flux polyhedron of each tag-0 face,
+// truncated by the half-spaces of every
 // overlapped candidate cell and, for interfacial cells, by its PLIC
 // half-space (Sec. 2.2); the truncated volume is a divergence-theorem sum
 // over the faces of the clipped polyhedron. One warp per active face.
@@ -122,7 +122,7 @@ struct PolyState {
 // vertices of the base polyhedron of a face of I nodes
 template <int KIND>
 __device__ __forceinline__ int base_verts(int I) {
-  return KIND == VOF_FLUX_EMFPA ? 3 * I + 1 : 2 * I + 1;
+  return KIND == VOF_FLUX_EMFPA ? 3 * I + 1 : KIND == VOF_FLUX_NMFPA ? 2 * I : 2 * I + 1;
 }
 
 // restore the base polyhedron from P.b*.
@@ -135,9 +135,33 @@ __device__ __forceinline__ int base_verts(int I) {
 // 2I..3I-1, apex 3I; faces: the cell face, four triangles per side quad
 // (x_{i+1}, x_i, x_{I+i}, x_{I+i+1}) joining its edges to its centre, I
 // bottom triangles.
+// NMFPA (Sec. 2.2.3): the first 2I vertices only; faces: the cell face, I
+// planar side quads, the back-traced face (reversed: its normal is -n).
 template <typename G, int KIND>
 __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, int lane) {
-  if constexpr (KIND == VOF_FLUX_EMFPA) {
+  if constexpr (KIND == VOF_FLUX_NMFPA) {
+    const int nvb = 2 * I;
+    if (lane < nvb) { P.vx[lane] = P.bx[lane]; P.vy[lane] = P.by[lane]; P.vz[lane] = P.bz[lane]; }
+    if (lane == 0) {
+      for (int i = 0; i < I; ++i) P.fv[0][i][0] = (uint8_t)i;
+      P.flen[0][0] = (uint8_t)I;
+    } else if (lane <= I) {
+      const int i = lane - 1, ip = (i + 1 == I) ? 0 : i + 1;
+      P.fv[0][0][lane] = (uint8_t)ip;
+      P.fv[0][1][lane] = (uint8_t)i;
+      P.fv[0][2][lane] = (uint8_t)(I + i);
+      P.fv[0][3][lane] = (uint8_t)(I + ip);
+      P.flen[0][lane] = 4;
+    } else if (lane == I + 1) {
+      for (int i = 0; i < I; ++i) P.fv[0][i][lane] = (uint8_t)(2 * I - 1 - i);
+      P.flen[0][lane] = (uint8_t)I;
+    }
+    st.nv = nvb;
+    st.nf = I + 2;
+    st.cur = 0;
+    __syncwarp();
+    return;
+  } else if constexpr (KIND == VOF_FLUX_EMFPA) {
     const int nvb = 3 * I + 1, nfb = 5 * I + 1;
     if (lane < nvb) { P.vx[lane] = P.bx[lane]; P.vy[lane] = P.by[lane]; P.vz[lane] = P.bz[lane]; }
     if (lane == 0) {
@@ -696,12 +720,62 @@ __device__ GVOF_OUTER_ATTR bool build_emfpa(const DevMesh& M, const GeoView<G>& 
   return true;
 }
 
+// NMFPA construction (Sec. 2.2.3) into P.b*: every vertex moves back by
+// dt times the velocity at the face centre at t^{n+1/2}, so the polyhedron
+// is the prism between the face and its translate, of volume V_d by itself
+template <typename G>
+__device__ GVOF_OUTER_ATTR bool build_nmfpa(const DevMesh& M, const GeoView<G>& Gv,
+                                         const GridParam& p, int j, Poly<G>& P, FaceFrame<G>& frs,
+                                         int lane) {
+  FaceFrame<G> fr;
+  const int64_t fb = M.fptr[j];
+  const int I = (int)(M.fptr[j + 1] - fb);
+  fr.I = I;
+  if (I > MAXI || I < 3) {
+    if (lane == 0) frs.I = I;
+    __syncwarp();
+    return false;
+  }
+  fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
+  fr.L = sqrt(Gv.fa[j]);
+  fr.sc = G(1) / fr.L;
+  fr.degenerate = 0;
+  fr.edgeon = 0;
+  fr.split = 0u;
+  const bool act = lane < I;
+  const int vi = act ? M.fvert[fb + lane] : M.fvert[fb];
+  G ux, uy, uz;
+  vel0<G>(p.vel, absval(fr.cx), absval(fr.cy), absval(fr.cz), ux, uy, uz);
+  const G k = (G)(p.g * p.dt) * fr.sc;
+  const G lx = rel(Gv.vx[vi], fr.cx) * fr.sc, ly = rel(Gv.vy[vi], fr.cy) * fr.sc,
+          lz = rel(Gv.vz[vi], fr.cz) * fr.sc;
+  const G bxl = lx - k * ux, byl = ly - k * uy, bzl = lz - k * uz;
+  if (act) {
+    P.bx[lane] = lx; P.by[lane] = ly; P.bz[lane] = lz;
+    P.bx[I + lane] = bxl; P.by[I + lane] = byl; P.bz[I + lane] = bzl;
+  }
+  const G big = (G)1e30;
+  G x0 = big, x1 = -big, y0 = big, y1 = -big, z0 = big, z1 = -big;
+  if (act) {
+    x0 = fmin(lx, bxl); x1 = fmax(lx, bxl);
+    y0 = fmin(ly, byl); y1 = fmax(ly, byl);
+    z0 = fmin(lz, bzl); z1 = fmax(lz, bzl);
+  }
+  fr.lo[0] = wmin(x0); fr.lo[1] = wmin(y0); fr.lo[2] = wmin(z0);
+  fr.hi[0] = wmax(x1); fr.hi[1] = wmax(y1); fr.hi[2] = wmax(z1);
+  __syncwarp();
+  if (lane == 0) frs = fr;
+  __syncwarp();
+  return true;
+}
+
 // the flux polyhedron of the context's construction
 template <typename G, int KIND>
 __device__ __forceinline__ bool build_polyhedron(const DevMesh& M, const GeoView<G>& Gv,
                                                  const GridParam& p, int j, double Vd, Poly<G>& P,
                                                  FaceFrame<G>& frs, int lane) {
   if constexpr (KIND == VOF_FLUX_EMFPA) return build_emfpa<G>(M, Gv, p, j, Vd, P, frs, lane);
+  else if constexpr (KIND == VOF_FLUX_NMFPA) return build_nmfpa<G>(M, Gv, p, j, P, frs, lane);
   else return build_fmfpa<G>(M, Gv, p, j, Vd, P, frs, lane);
 }
 
@@ -1185,20 +1259,40 @@ __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const
 
 }  // namespace
 
+namespace {
+template <typename G, int KIND>
+void flux_launch(const vof_ctx* c, int grid, cudaStream_t s) {
+  k_flux<G, KIND><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
+}
+template <typename G>
+void flux_launch_kind(const vof_ctx* c, int grid, cudaStream_t s) {
+  switch (c->opt.flux_polyhedron) {
+    case VOF_FLUX_EMFPA: flux_launch<G, VOF_FLUX_EMFPA>(c, grid, s); break;
+    case VOF_FLUX_NMFPA: flux_launch<G, VOF_FLUX_NMFPA>(c, grid, s); break;
+    default: flux_launch<G, VOF_FLUX_FMFPA>(c, grid, s); break;
+  }
+}
+template <typename G, int KIND>
+void polyhedra_launch(const vof_ctx* c, const int32_t* faces, int n, double* verts, int32_t* counts,
+                      cudaStream_t s) {
+  k_polyhedra<G, KIND><<<kSMs, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<G>(c), c->gp_d, c->srate,
+                                                    faces, n, verts, counts);
+}
+template <typename G>
+void polyhedra_launch_kind(const vof_ctx* c, const int32_t* faces, int n, double* verts,
+                           int32_t* counts, cudaStream_t s) {
+  switch (c->opt.flux_polyhedron) {
+    case VOF_FLUX_EMFPA: polyhedra_launch<G, VOF_FLUX_EMFPA>(c, faces, n, verts, counts, s); break;
+    case VOF_FLUX_NMFPA: polyhedra_launch<G, VOF_FLUX_NMFPA>(c, faces, n, verts, counts, s); break;
+    default: polyhedra_launch<G, VOF_FLUX_FMFPA>(c, faces, n, verts, counts, s); break;
+  }
+}
+}  // namespace
+
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s) {
   const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * 8;
-  const bool em = c->opt.flux_polyhedron == VOF_FLUX_EMFPA;
-  if (c->opt.precision == VOF_PREC_MIXED) {
-    if (em)
-      k_flux<float, VOF_FLUX_EMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c));
-    else
-      k_flux<float, VOF_FLUX_FMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c), state_view(c));
-  } else {
-    if (em)
-      k_flux<double, VOF_FLUX_EMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c));
-    else
-      k_flux<double, VOF_FLUX_FMFPA><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c), state_view(c));
-  }
+  if (c->opt.precision == VOF_PREC_MIXED) flux_launch_kind<float>(c, grid, s);
+  else flux_launch_kind<double>(c, grid, s);
   return cudaGetLastError();
 }
 
@@ -1210,17 +1304,8 @@ cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int
 
 cudaError_t launch_polyhedra(const vof_ctx* c, const int32_t* faces, int n, double* verts,
                              int32_t* counts, cudaStream_t s) {
-  const bool em = c->opt.flux_polyhedron == VOF_FLUX_EMFPA;
-  const DevMesh m = mesh_view(c);
-  if (c->opt.precision == VOF_PREC_MIXED) {
-    const GeoView<float> g = geo_view<float>(c);
-    if (em) k_polyhedra<float, VOF_FLUX_EMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
-    else k_polyhedra<float, VOF_FLUX_FMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
-  } else {
-    const GeoView<double> g = geo_view<double>(c);
-    if (em) k_polyhedra<double, VOF_FLUX_EMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
-    else k_polyhedra<double, VOF_FLUX_FMFPA><<<kSMs, kWarps * 32, 0, s>>>(m, g, c->gp_d, c->srate, faces, n, verts, counts);
-  }
+  if (c->opt.precision == VOF_PREC_MIXED) polyhedra_launch_kind<float>(c, faces, n, verts, counts, s);
+  else polyhedra_launch_kind<double>(c, faces, n, verts, counts, s);
   return cudaGetLastError();
 }
 

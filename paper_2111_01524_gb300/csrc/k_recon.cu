@@ -1,6 +1,7 @@
 // PLIC reconstruction of the interfacial cells: LSGIR normal (Sec. 2.1.1,
 // Eqs. eq:lsgir1, eq:lsgir2, lsgir-beta) and the volume-enforcing plane
-// constant (Sec. 2.1, Eq. plic-eq). One warp per interfacial cell.
+// constant (Sec. 2.1, Eq. plic-eq), optionally refined by the LSFIR outer
+// iteration (Sec. 2.1.2). One warp per interfacial cell.
 //
 // Plane constant, GPU design: V(C) = vol(cell ∩ {n.x + C >= 0}) is evaluated
 // by clipping each face of the cell (Sutherland-Hodgman) and summing the
@@ -344,9 +345,244 @@ __device__ void load_loops(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm
   __syncwarp();
 }
 
+// Vertex average of the PLIC polygon n.x + C = 0 (Sec. 2.1.2) in the
+// scaled cell-local frame of the loops last loaded in precision P: each loop
+// edge whose ends lie strictly on opposite sides gives its crossing, formed
+// from the end with the lower vertex id so that the two loops through an
+// edge give the same point; a cell vertex exactly on the plane (lane v < ncv
+// holds vertex v at (vx, vy, vz), formed as the loops form their vertices)
+// counts as often as an edge, twice. Returns (0, 0, 0), the centroid, when
+// the plane misses the cell.
+template <typename P>
+__device__ void plic_centre(const ReconSmem& S, int nfc, P nx, P ny, P nz, P C, bool vact, P vx,
+                            P vy, P vz, int lane, P& cx, P& cy, P& cz) {
+  const LoopSmem<P>& L = loops(S, P(0));
+  P sx = P(0), sy = P(0), sz = P(0);
+  int cnt = 0;
+  if (lane < nfc) {
+    const int b = S.fs[lane], e = S.fs[lane + 1];
+    for (int i = b; i < e; ++i) {
+      const int j = (i + 1 < e) ? i + 1 : b;
+      const bool sw = S.vid[j] < S.vid[i];
+      const int a = sw ? j : i, o = sw ? i : j;
+      const P pa = nx * L.x[a] + ny * L.y[a] + nz * L.z[a] + C;
+      const P po = nx * L.x[o] + ny * L.y[o] + nz * L.z[o] + C;
+      if ((pa > P(0) && po < P(0)) || (pa < P(0) && po > P(0))) {
+        const P t = pa / (pa - po);
+        sx += L.x[a] + t * (L.x[o] - L.x[a]);
+        sy += L.y[a] + t * (L.y[o] - L.y[a]);
+        sz += L.z[a] + t * (L.z[o] - L.z[a]);
+        ++cnt;
+      }
+    }
+  }
+  if (vact && nx * vx + ny * vy + nz * vz + C == P(0)) {
+    sx += P(2) * vx; sy += P(2) * vy; sz += P(2) * vz;
+    cnt += 2;
+  }
+  sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+  cnt = warp_sum(cnt);
+  if (cnt == 0) {
+    cx = cy = cz = P(0);
+  } else {
+    cx = sx / (P)cnt; cy = sy / (P)cnt; cz = sz / (P)cnt;
+  }
+}
+
+// PLIC centre of cell c from the loops in precision P (scaled frame, C the
+// scaled constant, h the cell size that unscales it), stored for LSFIR: FP64
+// path absolute, mixed path as FP32 offsets from the centroid
+template <typename P, typename G, bool kMixed>
+__device__ void store_centre(const DevMesh& M, const DevState& S, const ReconSmem& Sm, int c, int nfc,
+                             P nx, P ny, P nz, P C, bool vact, P vx, P vy, P vz, double h, int lane) {
+  P cx, cy, cz;
+  plic_centre<P>(Sm, nfc, nx, ny, nz, C, vact, vx, vy, vz, lane, cx, cy, cz);
+  if (lane == 0) {
+    if constexpr (kMixed) {
+      S.lxr[c] = (float)((double)cx * h); S.lyr[c] = (float)((double)cy * h); S.lzr[c] = (float)((double)cz * h);
+    } else {
+      S.lxp[c] = M.ccx[c] + (double)cx * h;
+      S.lyp[c] = M.ccy[c] + (double)cy * h;
+      S.lzp[c] = M.ccz[c] + (double)cz * h;
+    }
+  }
+}
+
+// eigen-decomposition of the symmetric 3x3 matrix A by cyclic Jacobi
+// rotations (each zeroes A[p][q]): on return the diagonal holds the
+// eigenvalues and the columns of V the eigenvectors
+template <typename T>
+__device__ void sym3_jacobi(T A[3][3], T V[3][3]) {
+  const T tol = sizeof(T) == 8 ? T(1e-32) : T(1e-14);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = T(i == j);
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    const T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const T dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= tol * dia || off == T(0)) break;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;
+      if (A[p][q] == T(0)) continue;
+      const T th = (A[q][q] - A[p][p]) / (T(2) * A[p][q]);
+      const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+      const T cs = T(1) / sqrt(t * t + T(1)), sn = t * cs;
+      // A <- J^T A J, V <- V J with J = I except J_pp = J_qq = cs, J_pq = sn, J_qp = -sn
+      T Ap[3], Aq[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Ap[k] = A[k][p] * cs - A[k][q] * sn;  // column p of A J
+        Aq[k] = A[k][p] * sn + A[k][q] * cs;  // column q of A J
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { A[k][p] = Ap[k]; A[k][q] = Aq[k]; }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Ap[k] = cs * A[p][k] - sn * A[q][k];  // row p of J^T (A J)
+        Aq[k] = sn * A[p][k] + cs * A[q][k];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { A[p][k] = Ap[k]; A[q][k] = Aq[k]; }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T vp = V[k][p] * cs - V[k][q] * sn, vq = V[k][p] * sn + V[k][q] * cs;
+        V[k][p] = vp; V[k][q] = vq;
+      }
+    }
+  }
+}
+
+// LSFIR normal update of outer iteration io (Sec. 2.1.2): the plane through
+// the cell's PLIC centre x that minimises sum_k w_k (n.(x_k - x))^2 over the
+// valid neighbours (interfacial node neighbours whose normal is within 45
+// degrees of the cell's, both of the previous iteration), w_k =
+// |x_k - x|^-2.5: the eigenvector of the smallest eigenvalue of
+// sum_k w_k d_k d_k^T (distances scaled by the cell size, which leaves it
+// unchanged), oriented like the previous normal. The cell takes it if it
+// turns its normal by less than lim = 30 degrees / io (kept otherwise, and
+// with fewer than two valid neighbours or collinear centres); the result
+// goes to the band-position buffer, so that every cell is decided from the
+// previous iteration, and the largest accepted turn to S.lturn[io]. Nothing
+// is done once an earlier iteration turned no normal by tol or more.
+// Work split: a warp gathers and reduces the sums of 32 cells one after the
+// other (lanes over neighbours), then lane i solves cell i's eigenproblem,
+// so the FP64 solve runs once per cell (the FP64 pipe processes a warp
+// instruction at the same cost whatever its active lanes). The fit is FP64
+// in both paths: in FP32 the eigenvector of a nearly degenerate matrix
+// drifts from the FP64 result; the mixed path forms the distances in FP32
+// from (hi, lo) centroids and FP32 centre offsets.
 template <typename G, bool kMixed>
+__global__ void __launch_bounds__(kWarps * 32) k_lsfir_normals(DevMesh M, GeoView<G> Gv, DevState S,
+                                                            int io, double lim, double tol) {
+  if (io > 1 && __longlong_as_double((long long)S.lturn[io - 1]) < tol) return;
+  __shared__ double sums[kWarps][6][32];
+  __shared__ int nval[kWarps][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned n_ic = (unsigned)S.cnt[kNIcells];
+  const double cos45 = sqrt(0.5);
+  for (unsigned base = (blockIdx.x * kWarps + wib) * 32u; base < n_ic;
+       base += gridDim.x * kWarps * 32u) {
+    const int nb = (int)min(32u, n_ic - base);
+    for (int i = 0; i < nb; ++i) {
+      const int c = S.icells[base + i];
+      const double ncx = Gv.pnx[c], ncy = Gv.pny[c], ncz = Gv.pnz[c];
+      const G sc = G(1) / cbrt(Gv.cvol[c]);
+      double m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0;
+      int nv = 0;
+      const int64_t q0 = M.nb_ptr[c], q1 = M.nb_ptr[c + 1];
+      for (int64_t q = q0 + lane; q < q1; q += 32) {
+        const int k = M.nb[q];
+        if (S.tc[k] != 0) continue;
+        if (!(ncx * (double)Gv.pnx[k] + ncy * (double)Gv.pny[k] + ncz * (double)Gv.pnz[k] > cos45))
+          continue;
+        G dx, dy, dz;
+        if constexpr (kMixed) {
+          dx = (rel(Gv.ccx[k], Gv.ccx[c]) + (S.lxr[k] - S.lxr[c])) * sc;
+          dy = (rel(Gv.ccy[k], Gv.ccy[c]) + (S.lyr[k] - S.lyr[c])) * sc;
+          dz = (rel(Gv.ccz[k], Gv.ccz[c]) + (S.lzr[k] - S.lzr[c])) * sc;
+        } else {
+          dx = (S.lxp[k] - S.lxp[c]) * sc;
+          dy = (S.lyp[k] - S.lyp[c]) * sc;
+          dz = (S.lzp[k] - S.lzp[c]) * sc;
+        }
+        const double ex = dx, ey = dy, ez = dz;
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (!(r2 > 0.0)) continue;
+        const double wk = 1.0 / (r2 * sqrt(sqrt(r2)));  // |d|^-2.5
+        m00 += wk * ex * ex; m01 += wk * ex * ey; m02 += wk * ex * ez;
+        m11 += wk * ey * ey; m12 += wk * ey * ez; m22 += wk * ez * ez;
+        ++nv;
+      }
+      m00 = warp_sum(m00); m01 = warp_sum(m01); m02 = warp_sum(m02);
+      m11 = warp_sum(m11); m12 = warp_sum(m12); m22 = warp_sum(m22);
+      nv = warp_sum(nv);
+      if (lane == i) {
+        sums[wib][0][i] = m00; sums[wib][1][i] = m01; sums[wib][2][i] = m02;
+        sums[wib][3][i] = m11; sums[wib][4][i] = m12; sums[wib][5][i] = m22;
+        nval[wib][i] = nv;
+      }
+    }
+    __syncwarp();
+    double turned = 0.0;
+    if (lane < nb) {
+      const unsigned w = base + lane;
+      const int c = S.icells[w];
+      const double ncx = Gv.pnx[c], ncy = Gv.pny[c], ncz = Gv.pnz[c];
+      double vx = ncx, vy = ncy, vz = ncz;
+      if (nval[wib][lane] >= 2) {
+        const double m00 = sums[wib][0][lane], m01 = sums[wib][1][lane], m02 = sums[wib][2][lane];
+        const double m11 = sums[wib][3][lane], m12 = sums[wib][4][lane], m22 = sums[wib][5][lane];
+        double A[3][3] = {{m00, m01, m02}, {m01, m11, m12}, {m02, m12, m22}}, V[3][3];
+        sym3_jacobi(A, V);
+        int lo = 0;
+        if (A[1][1] < A[lo][lo]) lo = 1;
+        if (A[2][2] < A[lo][lo]) lo = 2;
+        const int i1 = lo == 0 ? 1 : 0, i2 = lo == 2 ? 1 : 2;
+        const double e1 = A[i1][i1], e2 = A[i2][i2];
+        const double mid = e1 < e2 ? e1 : e2, top = e1 < e2 ? e2 : e1;
+        if (mid - A[lo][lo] > 1e-12 * top) {
+          double ex = V[0][lo], ey = V[1][lo], ez = V[2][lo];
+          const double en = sqrt(ex * ex + ey * ey + ez * ez);
+          const double sg = (ex * ncx + ey * ncy + ez * ncz < 0.0) ? -1.0 : 1.0;
+          ex = sg * ex / en; ey = sg * ey / en; ez = sg * ez / en;
+          const double cx = ncy * ez - ncz * ey, cy = ncz * ex - ncx * ez, cz = ncx * ey - ncy * ex;
+          const double ang = atan2(sqrt(cx * cx + cy * cy + cz * cz), ncx * ex + ncy * ey + ncz * ez);
+          if (ang < lim) {
+            vx = ex; vy = ey; vz = ez;
+            turned = ang;
+          }
+        }
+      }
+      if constexpr (kMixed) {
+        S.lnx32[w] = (float)vx; S.lny32[w] = (float)vy; S.lnz32[w] = (float)vz;
+      } else {
+        S.lnx[w] = vx; S.lny[w] = vy; S.lnz[w] = vz;
+      }
+    }
+    // the batch's largest accepted turn, one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) turned = fmax(turned, __shfl_xor_sync(GVOF_FULL, turned, o));
+    if (lane == 0 && turned > 0.0)
+      atomicMax(S.lturn + io, (unsigned long long)__double_as_longlong(turned));
+    __syncwarp();
+  }
+}
+
+// MODE 0: LSGIR normal and plane constant. MODE 1: the same, then the
+// PLIC centre for LSFIR, and the per-iteration turn slots cleared. MODE 2
+// (LSFIR outer iteration io): the normal accepted by k_lsfir_normals, its
+// plane constant and PLIC centre; nothing once an earlier iteration turned
+// no normal by tol or more.
+template <typename G, bool kMixed, int MODE>
 __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(DevMesh M, GeoView<G> Gv, DevState S,
-                                                             double beta) {
+                                                             double beta, int io, double tol) {
+  if constexpr (MODE == 2) {
+    if (io > 1 && __longlong_as_double((long long)S.lturn[io - 1]) < tol) return;
+  }
+  if constexpr (MODE == 1) {
+    if (blockIdx.x == 0 && threadIdx.x <= kMaxLsfirIter) S.lturn[threadIdx.x] = 0ull;
+  }
   __shared__ ReconSmem smem[kWarps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   ReconSmem& Sm = smem[wib];
@@ -359,10 +595,18 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
     const G V = Gv.cvol[c];
     const G hc = cbrt(V), sc = G(1) / hc;
     const double Fc = S.F[c];
+    const G Fcg = (G)Fc;
+    G nx, ny, nz;
+    if constexpr (MODE == 2) {
+      if constexpr (kMixed) {
+        nx = S.lnx32[w]; ny = S.lny32[w]; nz = S.lnz32[w];
+      } else {
+        nx = S.lnx[w]; ny = S.lny[w]; nz = S.lnz[w];
+      }
+    } else {
     // ---- LSGIR: weighted least squares for grad F (Sec. 2.1.1)
     G m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0, r0 = 0, r1 = 0, r2 = 0;
     const int64_t q0 = M.nb_ptr[c], q1 = M.nb_ptr[c + 1];
-    const G Fcg = (G)Fc;
     for (int64_t q = q0 + lane; q < q1; q += 32) {
       const int k = M.nb[q];
       const G dx = rel(Gv.ccx[k], xc) * sc, dy = rel(Gv.ccy[k], yc) * sc, dz = rel(Gv.ccz[k], zc) * sc;
@@ -393,7 +637,8 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
     }
     G gn = sqrt(gx * gx + gy * gy + gz * gz);
     if (!(gn > G(0))) { gx = 1; gy = 0; gz = 0; gn = 1; }
-    const G nx = gx / gn, ny = gy / gn, nz = gz / gn;
+    nx = gx / gn; ny = gy / gn; nz = gz / gn;
+    }
 
     // ---- plane constant
     const int nfc = (int)(M.cf_ptr[c + 1] - M.cf_ptr[c]);
@@ -415,6 +660,11 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
           S.nx[c] = (double)nx; S.ny[c] = (double)ny; S.nz[c] = (double)nz; S.C[c] = Cout;
           S.nx32[c] = (float)nx; S.ny32[c] = (float)ny; S.nz32[c] = (float)nz; S.C32[c] = (float)Cout;
         }
+        if constexpr (MODE >= 1) {
+          const G vx = rel(Gv.vx[vl], xc) * sc, vy = rel(Gv.vy[vl], yc) * sc, vz = rel(Gv.vz[vl], zc) * sc;
+          store_centre<G, G, kMixed>(M, S, Sm, c, nfc, nx, ny, nz, (G)C32c, lane < ncv, vx, vy, vz,
+                                     (double)hc, lane);
+        }
         __syncwarp();
         continue;
       }
@@ -433,6 +683,12 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
             S.nx32[c] = (float)nx; S.ny32[c] = (float)ny; S.nz32[c] = (float)nz; S.C32[c] = (float)Cout;
           }
         }
+        if constexpr (MODE >= 1) {
+          const double vx = (M.x[vl] - M.ccx[c]) * scd, vy = (M.y[vl] - M.ccy[c]) * scd,
+                       vz = (M.z[vl] - M.ccz[c]) * scd;
+          store_centre<double, G, kMixed>(M, S, Sm, c, nfc, nxd, nyd, nzd, Cout * scd, lane < ncv, vx,
+                                          vy, vz, hcd, lane);
+        }
         __syncwarp();
         continue;
       }
@@ -444,13 +700,26 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
       const double s = nxd * (M.x[vl] - M.ccx[c]) * scd + nyd * (M.y[vl] - M.ccy[c]) * scd +
                        nzd * (M.z[vl] - M.ccz[c]) * scd;
       const double T = Fc * M.cvol[c] * scd * scd * scd;
-      Cout = plane_constant<double>(Sm, nfc, ncv, s, nxd, nyd, nzd, T, lane) * hcd;
+      const double Cs = plane_constant<double>(Sm, nfc, ncv, s, nxd, nyd, nzd, T, lane);
+      Cout = Cs * hcd;
+      if constexpr (MODE >= 1) {
+        const double vx = (M.x[vl] - M.ccx[c]) * scd, vy = (M.y[vl] - M.ccy[c]) * scd,
+                     vz = (M.z[vl] - M.ccz[c]) * scd;
+        store_centre<double, G, kMixed>(M, S, Sm, c, nfc, nxd, nyd, nzd, Cs, lane < ncv, vx, vy, vz,
+                                        hcd, lane);
+      }
     } else {
       load_loops<G, G>(M, Gv, Sm, c, xc, yc, zc, (double)sc, nfc, lane);
       const G s = nx * rel(Gv.vx[vl], xc) * sc + ny * rel(Gv.vy[vl], yc) * sc +
                   nz * rel(Gv.vz[vl], zc) * sc;
       const G T = Fcg * V * sc * sc * sc;
-      Cout = (double)(plane_constant<G>(Sm, nfc, ncv, s, nx, ny, nz, T, lane) * hc);
+      const G Cs = plane_constant<G>(Sm, nfc, ncv, s, nx, ny, nz, T, lane);
+      Cout = (double)(Cs * hc);
+      if constexpr (MODE >= 1) {
+        const G vx = rel(Gv.vx[vl], xc) * sc, vy = rel(Gv.vy[vl], yc) * sc, vz = rel(Gv.vz[vl], zc) * sc;
+        store_centre<G, G, kMixed>(M, S, Sm, c, nfc, nx, ny, nz, Cs, lane < ncv, vx, vy, vz, (double)hc,
+                                   lane);
+      }
     }
     if (lane == 0) {
       S.nx[c] = (double)nx; S.ny[c] = (double)ny; S.nz[c] = (double)nz; S.C[c] = Cout;
@@ -464,15 +733,38 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
 
 }  // namespace
 
-cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s) {
+int reconstruct_launch_count(const vof_ctx* c) {
+  return c->opt.reconstruction == VOF_RECON_LSFIR ? 1 + 2 * c->opt.lsfir_max_iter : 1;
+}
+
+namespace {
+template <typename G, bool kMixed>
+cudaError_t reconstruct_launches(const vof_ctx* c, cudaStream_t s) {
   const int grid = c->recon_blocks > 0 ? c->recon_blocks : kSMs * 8;
-  if (c->opt.precision == VOF_PREC_MIXED)
-    k_reconstruct<float, true><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<float>(c),
-                                                            state_view(c), c->opt.beta);
-  else
-    k_reconstruct<double, false><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<double>(c),
-                                                              state_view(c), c->opt.beta);
+  const DevMesh m = mesh_view(c);
+  const GeoView<G> g = geo_view<G>(c);
+  const DevState st = state_view(c);
+  const double beta = c->opt.beta;
+  if (c->opt.reconstruction != VOF_RECON_LSFIR) {
+    k_reconstruct<G, kMixed, 0><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, 0, 0.0);
+    return cudaGetLastError();
+  }
+  // LSFIR (Sec. 2.1.2): LSGIR start, then the outer iterations; each
+  // launch skips its work once the iteration has converged, so the launch
+  // sequence is fixed (and can be captured in a graph)
+  const double lim30 = 30.0 * 3.14159265358979323846 / 180.0, tol = c->opt.lsfir_tol;
+  k_reconstruct<G, kMixed, 1><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, 0, tol);
+  for (int io = 1; io <= c->opt.lsfir_max_iter; ++io) {
+    k_lsfir_normals<G, kMixed><<<kSMs * 8, kWarps * 32, 0, s>>>(m, g, st, io, lim30 / io, tol);
+    k_reconstruct<G, kMixed, 2><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, io, tol);
+  }
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s) {
+  if (c->opt.precision == VOF_PREC_MIXED) return reconstruct_launches<float, true>(c, s);
+  return reconstruct_launches<double, false>(c, s);
 }
 
 }  // namespace gvof

@@ -16,6 +16,7 @@ namespace gvof {
 constexpr int kSMs = 152;  // GB300
 constexpr int kMaxFaceVerts = 8;
 constexpr int kMaxEmfpaVerts = 6;  // 5I+1 EMFPA faces fit the 32-face capacity
+constexpr int kMaxLsfirIter = 16;  // LSFIR outer iterations at most
 static_assert(3 * kMaxEmfpaVerts + 1 <= VOF_MAX_POLY_VERTS && 2 * kMaxFaceVerts + 1 <= VOF_MAX_POLY_VERTS,
               "polyhedron export stride");
 
@@ -98,6 +99,15 @@ struct DevState {
   double* red;               // reduction scratch [kRedSlots]
   float *nx32, *ny32, *nz32, *C32;  // FP32 copies of the planes (mixed only)
   const GridParam* gp;              // [n_grids] parameters of the current step
+  // LSFIR (allocated with VOF_RECON_LSFIR only): PLIC vertex-average
+  // centres by cell (FP64: absolute; mixed: FP32 offsets from the cell
+  // centroid), accepted normals by band position, and per outer iteration
+  // the largest accepted turn (bit pattern of a non-negative double)
+  double *lxp, *lyp, *lzp;
+  float *lxr, *lyr, *lzr;
+  double *lnx, *lny, *lnz;
+  float *lnx32, *lny32, *lnz32;
+  unsigned long long* lturn;
 };
 
 enum Cnt {
@@ -230,6 +240,12 @@ struct vof_ctx {
   float *fnx32, *fny32, *fnz32, *fa32, *cvol32;
   float4* cpl32;
   float *nx32, *ny32, *nz32, *C32;
+  // LSFIR scratch (see DevState)
+  double *lxp, *lyp, *lzp;
+  float *lxr, *lyr, *lzr;
+  double *lnx, *lny, *lnz;
+  float *lnx32, *lny32, *lnz32;
+  unsigned long long* lturn;
   // state (device)
   double* F;
   double *nx, *ny, *nz, *C;
@@ -277,6 +293,7 @@ struct vof_ctx {
   int n_ev_pairs;
   cudaEvent_t ev[2 * 256];
   int ev_phase[256];
+  int ev_n[256];
   double phase_ms[8];
   int64_t phase_n[8];
 };
@@ -311,6 +328,11 @@ inline DevState state_view(const vof_ctx* c) {
   s.icells = c->icells; s.afaces = c->afaces; s.cnt = c->cnt; s.red = c->red;
   s.nx32 = c->nx32; s.ny32 = c->ny32; s.nz32 = c->nz32; s.C32 = c->C32;
   s.gp = c->gp_d;
+  s.lxp = c->lxp; s.lyp = c->lyp; s.lzp = c->lzp;
+  s.lxr = c->lxr; s.lyr = c->lyr; s.lzr = c->lzr;
+  s.lnx = c->lnx; s.lny = c->lny; s.lnz = c->lnz;
+  s.lnx32 = c->lnx32; s.lny32 = c->lny32; s.lnz32 = c->lnz32;
+  s.lturn = c->lturn;
   return s;
 }
 
@@ -370,7 +392,9 @@ cudaError_t launch_update(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s);  // writes red[0], red[1]
 // reconstruction (k_recon.cu)
+// LSGIR (+ the LSFIR outer iteration when the context asks for it)
 cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);
+int reconstruct_launch_count(const vof_ctx* c);
 // flux (k_flux.cu)
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int64_t cap_per_face,

@@ -18,7 +18,8 @@ from . import build as _build
 VOF_OK, VOF_EINVAL, VOF_ENOMEM, VOF_ECUDA, VOF_ECAPACITY, VOF_ESTATE = range(6)
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
-FLUX_FMFPA, FLUX_EMFPA = 0, 1  # flux polyhedron construction (Secs. 2.2.2, 2.2.1)
+FLUX_FMFPA, FLUX_EMFPA, FLUX_NMFPA = 0, 1, 2  # flux polyhedra (Secs. 2.2.2, 2.2.1, 2.2.3)
+RECON_LSGIR, RECON_LSFIR = 0, 1  # interface reconstruction (Secs. 2.1.1, 2.1.2)
 NB_VERTS = 19  # polyhedron slots per face in vof_get_flux_polyhedra
 
 _lib = None
@@ -38,7 +39,9 @@ class _Mesh(C.Structure):
 
 class _Opt(C.Structure):
     _fields_ = [("eps", C.c_double), ("beta", C.c_double), ("precision", C.c_int32),
-                ("flux_polyhedron", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("flux_polyhedron", C.c_int32), ("reconstruction", C.c_int32),
+                ("lsfir_max_iter", C.c_int32), ("lsfir_tol", C.c_double),
+                ("reserved", C.c_int32 * 2)]
 
 
 class _Vel(C.Structure):
@@ -189,13 +192,15 @@ class Context:
     velocity and time step (the ``*_batch`` methods).
     """
 
-    def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5, flux=FLUX_FMFPA):
+    def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5, flux=FLUX_FMFPA,
+                 recon=RECON_LSGIR, lsfir_max_iter=0, lsfir_tol=0.0):
         L = lib()
         meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
         descs = (_Mesh * len(meshes))(*[_mesh_desc(m, keep) for m in meshes])
         opt = _Opt()
         opt.eps, opt.beta, opt.precision, opt.flux_polyhedron = eps, beta, precision, flux
+        opt.reconstruction, opt.lsfir_max_iter, opt.lsfir_tol = recon, lsfir_max_iter, lsfir_tol
         h = C.c_void_p()
         _check(L.vof_init_batch(descs, len(meshes), C.byref(opt), C.byref(h)))
         self._h = h
@@ -205,6 +210,7 @@ class Context:
         self.n_cell = sum(d.n_cell for d in descs)
         self.precision = precision
         self.flux = flux
+        self.recon = recon
         co = np.empty(self.n_grids + 1, np.int64)
         fo = np.empty(self.n_grids + 1, np.int64)
         vo = np.empty(self.n_grids + 1, np.int64)
@@ -345,8 +351,9 @@ class Context:
         v = velocity_struct(vel)
         _check(lib().vof_get_flux_polyhedra(self._h, C.byref(v), t, dt, _ptr(faces), len(faces),
                                             _ptr(verts), _ptr(counts)))
-        k = 3 if self.flux == FLUX_EMFPA else 2
-        return [verts[i, :k * counts[i] + 1].copy() if counts[i] > 0 else None
+        def npts(nI):  # 3I+1 (EMFPA), 2I (NMFPA), 2I+1 (FMFPA)
+            return 3 * nI + 1 if self.flux == FLUX_EMFPA else 2 * nI + (self.flux != FLUX_NMFPA)
+        return [verts[i, :npts(counts[i])].copy() if counts[i] > 0 else None
                 for i in range(len(faces))]
 
     PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update")

@@ -49,7 +49,7 @@ def test_status_codes_match_header():
 def test_struct_layouts():
     from paper_2111_01524_gb300 import vof
     assert ctypes.sizeof(vof._Mesh) == 3 * 8 + 5 * 8
-    assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 4 + 6 * 4
+    assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 4 + 4 + 4 + 8 + 2 * 4
     assert ctypes.sizeof(vof._Vel) == 4 + 4 + 8 + 8 + 24 + 24
     assert ctypes.sizeof(vof.Stats) == 6 * 8 + 5 * 8
 
@@ -89,7 +89,10 @@ def test_flux_constants_match_header():
     src = open(os.path.join(ROOT, "include", "vof.h")).read()
     assert re.search(rf"VOF_FLUX_FMFPA\s*=\s*{vof.FLUX_FMFPA}\b", src)
     assert re.search(rf"VOF_FLUX_EMFPA\s*=\s*{vof.FLUX_EMFPA}\b", src)
+    assert re.search(rf"VOF_FLUX_NMFPA\s*=\s*{vof.FLUX_NMFPA}\b", src)
     assert re.search(rf"VOF_MAX_POLY_VERTS\s*=\s*{vof.NB_VERTS}\b", src)
+    assert re.search(rf"VOF_RECON_LSGIR\s*=\s*{vof.RECON_LSGIR}\b", src)
+    assert re.search(rf"VOF_RECON_LSFIR\s*=\s*{vof.RECON_LSFIR}\b", src)
     # 3I+1 EMFPA points for I <= 6, 2I+1 FMFPA points for I <= 8
     assert vof.NB_VERTS >= max(3 * 6 + 1, 2 * 8 + 1)
 
@@ -110,8 +113,8 @@ def _heptagonal_prism():
 
 def test_emfpa_and_bad_options_are_rejected_before_device_work():
     """vof_init checks the options before it touches the device: EMFPA on a
-    mesh with a 7-node face, an unknown construction and a nonzero reserved
-    word each give VOF_EINVAL (no GPU needed)."""
+    mesh with a 7-node face, an unknown construction or reconstruction and
+    LSFIR limits out of range each give VOF_EINVAL (no GPU needed)."""
     from paper_2111_01524_gb300 import vof
     m = _heptagonal_prism()
     with pytest.raises(vof.VofError) as e:
@@ -120,3 +123,9 @@ def test_emfpa_and_bad_options_are_rejected_before_device_work():
     with pytest.raises(vof.VofError) as e:
         vof.Context(m, flux=7)
     assert e.value.status == vof.VOF_EINVAL
+    for bad in ({"recon": 2}, {"recon": vof.RECON_LSFIR, "lsfir_max_iter": 17},
+                {"recon": vof.RECON_LSFIR, "lsfir_max_iter": -1},
+                {"recon": vof.RECON_LSFIR, "lsfir_tol": -1e-3}):
+        with pytest.raises(vof.VofError) as e:
+            vof.Context(m, **bad)
+        assert e.value.status == vof.VOF_EINVAL, bad
