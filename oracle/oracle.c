@@ -395,6 +395,7 @@ void orc_taggrid(const orc_mesh* m, double eps, double* F, double* Fnode,
 }
 
 /* ----------------------------------------------------------- LSGIR (Sec 2.1.1) */
+static void sym3_jacobi(double A[3][3], double V[3][3]);
 static int solve3(double M[3][3], double r[3], double g[3]) {
   /* Gaussian elimination with partial pivoting */
   int piv[3] = {0, 1, 2};
@@ -445,7 +446,24 @@ void orc_lsgir(const orc_mesh* m, double beta, const double* F,
       }
     }
     double g[3];
-    if (solve3(M, r, g) != 0) { g[0] = 1; g[1] = 0; g[2] = 0; }
+    if (solve3(M, r, g) != 0) {
+      /* singular stencil (e.g. a quasi-2D grid, one cell thick: every
+       * neighbour offset lies in the plane): least-squares solution of
+       * minimum norm, by the pseudo-inverse over the eigenvalues above
+       * 1e-12 of the largest */
+      double A[3][3], V[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[i][j] = M[i][j];
+      sym3_jacobi(A, V);
+      double top = fmax(A[0][0], fmax(A[1][1], A[2][2]));
+      g[0] = g[1] = g[2] = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        if (!(A[k][k] > 1e-12 * top)) continue;
+        double vr = V[0][k] * r[0] + V[1][k] * r[1] + V[2][k] * r[2];
+        for (int i = 0; i < 3; ++i) g[i] += vr / A[k][k] * V[i][k];
+      }
+      if (!(norm3(g) > 0)) { g[0] = 1; g[1] = 0; g[2] = 0; }
+    }
     double gn = norm3(g);
     if (!(gn > 0)) { g[0] = 1; g[1] = 0; g[2] = 0; gn = 1; }
     for (int i = 0; i < 3; ++i) nrm[3 * c + i] = g[i] / gn;
@@ -876,6 +894,12 @@ void orc_velocity_eval(const orc_velocity* v, const double x[3], double t, doubl
     u[0] = 2.0 * sx * sx * s2y * s2z * g;
     u[1] = -s2x * sy * sy * s2z * g;
     u[2] = -s2x * s2y * sz * sz * g;
+  } else if (v->kind == 4) { /* 2D deformation in the x-z plane (Sec. 4.3) */
+    double g = cos(pi * t / v->period);
+    double sx = sin(pi * x[0]), sz = sin(pi * x[2]);
+    u[0] = -2.0 * sx * sx * sz * cos(pi * x[2]) * g;
+    u[1] = 0.0;
+    u[2] = 2.0 * sz * sz * sx * cos(pi * x[0]) * g;
   } else if (v->kind == 2) { /* rigid rotation about a z-parallel axis */
     u[0] = -v->omega * (x[1] - v->center[1]);
     u[1] = v->omega * (x[0] - v->center[0]);

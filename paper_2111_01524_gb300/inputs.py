@@ -48,10 +48,11 @@ class Velocity:
     kind 1: 3D deformation with period ``period`` (Sec. 4.2.3);
     kind 2: rigid rotation about the z-parallel axis through ``center`` with
             angular rate ``omega`` (Sec. 4.2.2);
-    kind 3: uniform translation ``u0`` (Sec. 4.2.1).
+    kind 3: uniform translation ``u0`` (Sec. 4.2.1);
+    kind 4: 2D deformation in the x-z plane with period ``period`` (Sec. 4.3).
     """
 
-    DEFORMATION, ROTATION, TRANSLATION = 1, 2, 3
+    DEFORMATION, ROTATION, TRANSLATION, DEFORMATION2D = 1, 2, 3, 4
 
     def __init__(self, kind, period=3.0, omega=0.0, center=(0.5, 0.5, 0.5),
                  u0=(0.0, 0.0, 0.0)):
@@ -76,6 +77,10 @@ def rotation(omega=2.0 * np.pi, center=(0.5, 0.5, 0.5)):
 
 def translation(u0):
     return Velocity(Velocity.TRANSLATION, u0=u0)
+
+
+def deformation2d(period=8.0):
+    return Velocity(Velocity.DEFORMATION2D, period=period)
 
 
 # ----------------------------------------------------------------------------
@@ -234,6 +239,59 @@ def hex_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.0, seed=0):
     return dict(X=X, face_ptr=ptr, face_vert=fv, owner=owner, neighbour=nbr,
                 n_cell=n ** 3, cell_corners=corners, cell_tets=tets, cell_box=box,
                 kind="hex", n=n, h=h)
+
+
+def slab_mesh(n):
+    """Quasi-2D grid of the 2D tests (Sec. 4.3): n x 1 x n cells on the unit
+    cube, one cell across y (the paper's 3D grids with a single cell along
+    one coordinate direction, Sec. 3.2). Faces as in ``hex_mesh``: internal
+    faces leave the lower-index cell, boundary faces leave the domain."""
+    n1 = n + 1
+
+    def vid(i, j, k):
+        return i + n1 * (j + 2 * k)
+
+    def cid(i, k):
+        return i + n * k
+    r, rp = np.arange(n), np.arange(n1)
+    loops, lower, upper = [], [], []
+    # x-faces (plane i), loop normal +x
+    k, i = np.meshgrid(r, rp, indexing="ij")
+    i, k = i.ravel(), k.ravel()
+    loops.append(np.stack([vid(i, 0, k), vid(i, 1, k), vid(i, 1, k + 1), vid(i, 0, k + 1)], 1))
+    lower.append(np.where(i > 0, cid(np.maximum(i - 1, 0), k), -1))
+    upper.append(np.where(i < n, cid(np.minimum(i, n - 1), k), -1))
+    # y-faces (j = 0, 1), loop normal +y
+    for j in (0, 1):
+        k, i = np.meshgrid(r, r, indexing="ij")
+        i, k = i.ravel(), k.ravel()
+        loops.append(np.stack([vid(i, j, k), vid(i, j, k + 1), vid(i + 1, j, k + 1), vid(i + 1, j, k)], 1))
+        lower.append(cid(i, k) if j == 1 else np.full(i.shape, -1))
+        upper.append(cid(i, k) if j == 0 else np.full(i.shape, -1))
+    # z-faces (plane k), loop normal +z
+    k, i = np.meshgrid(rp, r, indexing="ij")
+    i, k = i.ravel(), k.ravel()
+    loops.append(np.stack([vid(i, 0, k), vid(i + 1, 0, k), vid(i + 1, 1, k), vid(i, 1, k)], 1))
+    lower.append(np.where(k > 0, cid(i, np.maximum(k - 1, 0)), -1))
+    upper.append(np.where(k < n, cid(i, np.minimum(k, n - 1)), -1))
+    L = np.concatenate(loops)
+    lo_, up_ = np.concatenate(lower), np.concatenate(upper)
+    owner = np.where(lo_ >= 0, lo_, up_)
+    neighbour = np.where(lo_ >= 0, up_, -1)
+    flip = lo_ < 0
+    L[flip] = L[flip][:, ::-1]
+    kk, jj, ii = np.meshgrid(rp, np.arange(2), rp, indexing="ij")
+    X = np.stack([ii.ravel() / n, jj.ravel().astype(np.float64), kk.ravel() / n], 1)
+    ptr, fv = _csr(L.astype(np.int32))
+
+    def corners(cells):
+        cells = np.asarray(cells, np.int64)
+        i, k = cells % n, cells // n
+        return np.stack([vid(i + (b & 1), (b >> 1) & 1, k + ((b >> 2) & 1)) for b in range(8)], 1)
+
+    return dict(X=X, face_ptr=ptr, face_vert=fv, owner=owner.astype(np.int32),
+                neighbour=neighbour.astype(np.int32), n_cell=n * n, cell_corners=corners,
+                kind="slab", n=n)
 
 
 def kuhn_tet_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter=0.2, seed=0):

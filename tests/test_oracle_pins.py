@@ -1085,6 +1085,90 @@ def test_initfgrid_converges_at_second_order(orc, shape):
     assert set(np.unique(F[far])) <= {0.0, 1.0}
 
 
+# ---------------------------------------------------------------- quasi-2D
+def test_slab_geometry_closed_form(orc):
+    """n x 1 x n cells on the unit cube (the 2D tests' grids, Sec. 4.3)."""
+    n = 6
+    m = I.slab_mesh(n)
+    om = orc.Mesh(m)
+    g = om.geometry()
+    assert om.n_cell == n * n
+    assert np.allclose(g["cell_vol"], 1.0 / n ** 2, rtol=1e-14)
+    i, k = np.arange(n * n) % n, np.arange(n * n) // n
+    assert np.allclose(g["cell_cen"], np.stack([(i + 0.5) / n, 0.5 + 0 * i, (k + 0.5) / n], 1),
+                       atol=1e-15)
+    # every cell is closed: the outward face vectors sum to zero
+    A = g["face_nrm"] * g["face_area"][:, None]
+    S = np.zeros((om.n_cell, 3))
+    np.add.at(S, m["owner"], A)
+    inner = m["neighbour"] >= 0
+    np.add.at(S, m["neighbour"][inner], -A[inner])
+    assert np.abs(S).max() < 1e-15
+    # node neighbours: 8 inside, 3 at a corner
+    ptr, idx = om.neighbors()
+    cnt = np.diff(ptr)
+    assert cnt.max() == 8 and cnt.min() == 3
+
+
+def test_lsgir_quasi2d_pseudo_inverse(orc):
+    """On a slab every neighbour offset has dy = 0, so the LSGIR system of
+    Sec. 2.1.1 is singular; the minimum-norm least-squares solution recovers
+    a linear field's in-plane gradient exactly, and drops a y-gradient the
+    stencil cannot see."""
+    m = I.slab_mesh(8)
+    om = orc.Mesh(m)
+    x = om.geometry()["cell_cen"]
+    for a in ([0.3, 0.0, -0.4], [0.3, 0.25, -0.4], [-0.05, 0.0, 0.6]):
+        a = np.array(a)
+        st = om.taggrid(0.5 + (x - 0.5) @ a)
+        n = om.lsgir(st["F"], st["tag_c"])
+        band = st["tag_c"] == 0
+        e = a * [1, 0, 1]
+        assert band.sum() > 10
+        assert np.abs(n[band] - e / np.linalg.norm(e)).max() < 1e-13, a
+
+
+def test_deformation2d_field(orc):
+    """The 2D deformation field of Sec. 4.3 at hand-evaluated points, its zero
+    divergence and its zero y-component."""
+    om = orc.Mesh(I.slab_mesh(2))
+    vel = I.deformation2d(8.0)
+    # x = z = 1/4: sin^2 = 1/2, sin cos = 1/2 -> u = -1/2, w = 1/2 (times cos(pi t/8))
+    assert np.allclose(om.velocity(vel, [0.25, 0.3, 0.25], 0.0), [-0.5, 0.0, 0.5], atol=1e-15)
+    assert np.allclose(om.velocity(vel, [0.25, 0.7, 0.25], 8.0 / 3.0), [-0.25, 0.0, 0.25], atol=1e-15)
+    # x = 1/2, z = 1/4: u = -2 * 1 * 1/2 = -1, w = 2 * 1/2 * 0 = 0
+    assert np.allclose(om.velocity(vel, [0.5, 0.1, 0.25], 0.0), [-1.0, 0.0, 0.0], atol=1e-15)
+    rng = np.random.default_rng(4)
+    h = 1e-5
+    for X in rng.random((20, 3)):
+        div = 0.0
+        for d in range(3):
+            e = np.zeros(3); e[d] = h
+            div += (om.velocity(vel, X + e, 1.0)[d] - om.velocity(vel, X - e, 1.0)[d]) / (2 * h)
+        assert abs(div) < 1e-8
+        assert om.velocity(vel, X, 1.0)[1] == 0.0
+
+
+def test_deformation2d_on_slab_conserves_and_stays_2d(orc):
+    """A few steps of the 2D deformation test on a slab: the y-faces carry
+    nothing, the volume is conserved (zero divergence, the body away from the
+    walls), and F stays between 0 and 1."""
+    m = I.slab_mesh(24)
+    om = orc.Mesh(m)
+    V = om.geometry()["cell_vol"]
+    st = om.reconstruct(om.initfgrid(I.shape_cylinder((0.5, 0.0, 0.75), (0, 1, 0), 0.15), 10))
+    vel = I.deformation2d(8.0)
+    ny = np.abs(om.geometry()["face_nrm"][:, 1]) > 0.5
+    t = 0.0
+    for _ in range(4):
+        dt = om.suggest_dt(vel, t, 0.5, 8.0)
+        v0 = (V * st["F"]).sum()
+        new = om.step(vel, t, dt, st)
+        assert np.all(new["Vd"][ny] == 0.0) and np.all(new["VF"][ny] == 0.0)
+        assert abs((V * new["F_unclipped_cut"]).sum() - v0) < 1e-13 * v0
+        st, t = new, t + dt
+
+
 # ---------------------------------------------------------------- whole step
 def test_cfl1_translation_shifts_exactly(orc):
     """u = (1,0,0), dt = h on a uniform grid: every x-face flux polyhedron is
