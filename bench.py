@@ -81,6 +81,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gvof", choices=["gvof", "reference"])
     p.add_argument("--grid", type=int, default=256)
+    p.add_argument("--grid2d", type=int, default=1024, help="n of the n x 1 x n 2D grid")
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--flux", default="fmfpa", choices=["fmfpa", "emfpa", "nmfpa"],
                    help="flux polyhedron: face-matched (Sec. 2.2.2), edge-matched (Sec. 2.2.1) "
@@ -90,12 +91,13 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-init", action="store_true", help="skip timing the device initialisation")
     p.add_argument("--cpu-steps", type=int, default=1)
     p.add_argument("--workload", default="deformation",
-                   choices=["deformation", "tets", "batch", "serve"],
+                   choices=["deformation", "tets", "batch", "serve", "deform2d"],
                    help="deformation: hex grid, Enright field (default line); tets: jittered Kuhn "
                         "tets in rotation; batch: 64 distorted grids advanced together; serve: "
-                        "Poisson request stream")
+                        "Poisson request stream; deform2d: 2D deformation on a quasi-2D grid")
     p.add_argument("--requests", type=int, default=48)
     return p.parse_args()
 
@@ -509,6 +511,77 @@ def main_tets(a):
     return 0
 
 
+def main_deform2d(a):
+    """2D deformation test (Sec. 4.3) on a quasi-2D grid n x 1 x n (n =
+    --grid2d): the cylinder r = 0.15 at (0.5, 0.75) initialised on the device
+    (initfgrid, ndiv = 10), the x-z field with period 8, CFL 0.5, steps from
+    t = 0; replicas on N GPUs."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import vof as V
+    B.build()
+    n = a.grid2d
+    m = I.slab_mesh(n)
+    vel = I.deformation2d(8.0)
+    cyl = I.shape_cylinder((0.5, 0.0, 0.75), (0.0, 1.0, 0.0), 0.15)
+    res = {}
+    for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
+        ctx = V.Context(m, precision=prec)
+        ctx.init_fraction(cyl, 10)
+        ctx.reconstruct()
+        t = 0.0
+        for _ in range(a.warmup):
+            dt = ctx.suggest_dt(vel, t, 0.5, 8.0)
+            ctx.step(vel, t, dt)
+            t += dt
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clk = ClockSampler(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            dt = ctx.suggest_dt(vel, t, 0.5, 8.0)
+            ctx.step(vel, t, dt)
+            t += dt
+        e1.record()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = clk.stop()
+        ms = over_ranks(dist, e0.elapsed_time(e1), "max")
+        res[name] = {"value": ws * m["n_cell"] * a.steps / (ms * 1e-3), "ms_per_step": ms / a.steps,
+                     "F": ctx.get_fraction(), "stats": ctx.stats(), "clocks": clocks}
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["mixed"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"2D deformation (Sec. 4.3), quasi-2D grid {n} x 1 x {n}, "
+                                   "cylinder r=0.15 at (0.5, 0.75), period 8, CFL 0.5, steps from t=0",
+                       "cells": int(m["n_cell"]), "parallelism": f"replicas x{ws}"},
+            "gpu_launches": 6 * a.steps, "clocks": res["mixed"]["clocks"],
+            "fp64_path": {"value": res["fp64"]["value"],
+                          "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+                          "max_abs_F_diff_mixed_vs_fp64":
+                              float(np.abs(res["mixed"]["F"] - res["fp64"]["F"]).max())},
+            "band": {k: res["mixed"]["stats"][k] for k in ("n_interfacial", "n_active_faces",
+                                                           "n_truncations", "n_overflow")}}
+    print(json.dumps(line))
+    return 0
+
+
 def _make_request_inputs(args):
     kind, side, seed, body, axes = args
     if kind == "hex":
@@ -617,6 +690,8 @@ def main():
         return main_tets(a)
     if a.workload == "serve":
         return main_serve(a)
+    if a.workload == "deform2d":
+        return main_deform2d(a)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -742,6 +817,26 @@ def main():
                "d2h_bytes_per_step": 8 * counts["n_cell"]}
         del ctxe
 
+    # the initial F computed on the device (initfgrid, Sec. 3.2: ndiv = 10, the
+    # paper's refinement) for the same sphere: time and volume error
+    init = None
+    if not a.no_init:
+        ctxi = V.Context(mesh, precision=prec, flux=flux, recon=recon)
+        sph = I.shape_sphere((0.35, 0.35, 0.35), 0.15)
+        ctxi.init_fraction(sph, 10, stream=stream)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctxi.init_fraction(sph, 10, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        Fi = ctxi.get_fraction()
+        exact = 4.0 / 3.0 * np.pi * 0.15 ** 3
+        init = {"ms": e0.elapsed_time(e1), "ndiv": 10,
+                "volume_rel_error": float(abs((g["cell_vol"] * Fi).sum() - exact) / exact),
+                "interfacial_cells": int(((Fi > 0) & (Fi < 1)).sum())}
+        del ctxi
+
     peaks, peak_kind = measured_peaks()
     dom = max(phases.items(), key=lambda kv: kv[1][0])
     phase = {"name": dom[0], "ms": dom[1][0], "launches": dom[1][1]}
@@ -777,7 +872,7 @@ def main():
             "volume_rel_change": vol_rel,
             "volume_bookkeeping_rel_residual": book_rel,
             "clip_loss_rel": stats["clip_loss"] / vol0,
-            "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
+            "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "device_init": init,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

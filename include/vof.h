@@ -49,7 +49,8 @@ typedef enum {
 
 enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED = 1 };
 enum { VOF_MEM_HOST = 0, VOF_MEM_DEVICE = 1 };
-enum { VOF_VEL_DEFORMATION = 1, VOF_VEL_ROTATION = 2, VOF_VEL_TRANSLATION = 3 };
+enum { VOF_VEL_DEFORMATION = 1, VOF_VEL_ROTATION = 2, VOF_VEL_TRANSLATION = 3,
+       VOF_VEL_DEFORMATION2D = 4 };
 /* flux polyhedron construction (vof_options.flux_polyhedron) */
 enum { VOF_FLUX_FMFPA = 0, VOF_FLUX_EMFPA = 1, VOF_FLUX_NMFPA = 2 };
 /* interface reconstruction (vof_options.reconstruction) */
@@ -106,8 +107,11 @@ typedef struct {
   int32_t reserved[2];
 } vof_options;
 
-/* Prescribed velocity of the test problems (Sec. 4.2):
+/* Prescribed velocity of the test problems (Sec. 4.2, Sec. 4.3):
  * DEFORMATION: Enright field of Sec. 4.2.3 with period `period`;
+ * DEFORMATION2D: the x-z field of the 2D deformation test (Sec. 4.3),
+ *   u = -2 sin^2(pi x) sin(pi z) cos(pi z) g, v = 0,
+ *   w = 2 sin^2(pi z) sin(pi x) cos(pi x) g, g = cos(pi t / period);
  * ROTATION: u = -omega (y - center[1]), v = omega (x - center[0]), w = 0;
  * TRANSLATION: u = u0. Velocities are evaluated exactly at face centres,
  * edge centres and vertices at the mid-time t + dt/2 (Sec. 4.2). */
@@ -158,6 +162,33 @@ vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_op
 /* offsets [n_grids+1] of each grid's cells, faces, nodes (any may be NULL) */
 vof_status vof_batch_offsets(vof_ctx* ctx, int* n_grids, int64_t* cell_off, int64_t* face_off,
                              int64_t* vert_off);
+
+/* Initial fluid body for vof_init_fraction (initfgrid, Sec. 3.2): the fluid
+ * is where the body's signed distance is negative.
+ * VOF_SHAPE_SPHERE: centre c, radius r. VOF_SHAPE_CYLINDER: infinite, axis
+ * through c along the unit vector a, radius r. VOF_SHAPE_HALFSPACE:
+ * a.(x - c) < 0 with a a unit vector (r unused). */
+enum { VOF_SHAPE_SPHERE = 1, VOF_SHAPE_CYLINDER = 2, VOF_SHAPE_HALFSPACE = 3 };
+typedef struct {
+  int32_t kind;
+  int32_t pad;
+  double c[3];
+  double a[3];
+  double r;
+} vof_shape;
+
+/* initfgrid (Sec. 3.2) on the device: F of every cell by refinement. Each
+ * cell is the signed sum of the tetrahedra joining its vertex average to
+ * the fan triangles (face vertex average, edge) of its faces; each
+ * tetrahedron is divided into ndiv^3 equal tetrahedra (Freudenthal) on
+ * which the fluid is where the linear interpolant of the signed distance
+ * is negative. Cells whose bounding ball about the centroid lies on one
+ * side of the surface get 0 or 1. ndiv in 1..16 (the paper uses 10). Every
+ * grid of a batch gets the same body. Replaces F like vof_set_fraction
+ * (the reconstruction must follow); asynchronous on `stream`.
+ * VOF_EINVAL for an unknown kind, a non-unit axis or normal (|1 - |a|| >
+ * 1e-12), r <= 0 for a sphere or cylinder, or ndiv out of range. */
+vof_status vof_init_fraction(vof_ctx* ctx, const vof_shape* shape, int ndiv, void* stream);
 
 /* Volume fraction F [n_cell] (host or device pointer, see `mem`). Setting F
  * invalidates the reconstruction: call vof_reconstruct next. */

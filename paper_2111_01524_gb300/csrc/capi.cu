@@ -88,9 +88,9 @@ bool same_vel(const Vel& a, const Vel& b) {
 }
 
 vof_status check_velocity(const vof_velocity& v) {
-  if (v.kind < VOF_VEL_DEFORMATION || v.kind > VOF_VEL_TRANSLATION)
+  if (v.kind < VOF_VEL_DEFORMATION || v.kind > VOF_VEL_DEFORMATION2D)
     return fail(VOF_EINVAL, "unknown velocity kind");
-  if (v.kind == VOF_VEL_DEFORMATION && !(v.period > 0))
+  if ((v.kind == VOF_VEL_DEFORMATION || v.kind == VOF_VEL_DEFORMATION2D) && !(v.period > 0))
     return fail(VOF_EINVAL, "deformation period must be > 0");
   return VOF_OK;
 }
@@ -520,6 +520,31 @@ vof_status vof_set_fraction(vof_ctx* c, const double* F, int mem, void* stream) 
   CK(cudaMemsetAsync(c->acc, 0, sizeof(double) * kNAcc * kAccSlots, s));
   CK(cudaMemsetAsync(c->cnt + kBandCellsOk, 0, 2 * sizeof(unsigned long long), s));
   if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
+  c->recon_valid = false;
+  return VOF_OK;
+}
+
+vof_status vof_init_fraction(vof_ctx* c, const vof_shape* shape, int ndiv, void* stream) {
+  if (!c || !shape) return fail(VOF_EINVAL, "NULL argument");
+  if (shape->kind != VOF_SHAPE_SPHERE && shape->kind != VOF_SHAPE_CYLINDER &&
+      shape->kind != VOF_SHAPE_HALFSPACE)
+    return fail(VOF_EINVAL, "unknown shape kind");
+  if (ndiv < 1 || ndiv > 16) return fail(VOF_EINVAL, "ndiv must be in 1..16");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(shape->c[d]) || !std::isfinite(shape->a[d]))
+      return fail(VOF_EINVAL, "shape coordinates must be finite");
+  if (shape->kind != VOF_SHAPE_SPHERE) {
+    const double n = std::sqrt(shape->a[0] * shape->a[0] + shape->a[1] * shape->a[1] +
+                               shape->a[2] * shape->a[2]);
+    if (!(std::fabs(n - 1.0) <= 1e-12)) return fail(VOF_EINVAL, "shape axis must be a unit vector");
+  }
+  if (shape->kind != VOF_SHAPE_HALFSPACE && !(shape->r > 0.0 && std::isfinite(shape->r)))
+    return fail(VOF_EINVAL, "shape radius must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_init_fraction(c, shape, ndiv, s));
+  // as vof_set_fraction: bookkeeping from this F, full sweeps next
+  CK(cudaMemsetAsync(c->acc, 0, sizeof(double) * kNAcc * kAccSlots, s));
+  CK(cudaMemsetAsync(c->cnt + kBandCellsOk, 0, 2 * sizeof(unsigned long long), s));
   c->recon_valid = false;
   return VOF_OK;
 }

@@ -454,6 +454,27 @@ __device__ void sym3_jacobi(T A[3][3], T V[3][3]) {
   }
 }
 
+// Minimum-norm least-squares gradient of a singular LSGIR system (Sec.
+// 2.1.1), e.g. on a quasi-2D grid one cell thick, where every neighbour
+// offset lies in the plane: the pseudo-inverse of A^T A over its eigenvalues
+// above a relative threshold (FP64 1e-12, FP32 1e-6) applied to A^T b;
+// (1, 0, 0) if that leaves nothing. Out of line: it is the rare branch.
+template <typename G>
+__device__ __noinline__ void lsgir_pinv(G m00, G m01, G m02, G m11, G m12, G m22, G r0, G r1, G r2,
+                                        G& gx, G& gy, G& gz) {
+  G A[3][3] = {{m00, m01, m02}, {m01, m11, m12}, {m02, m12, m22}}, V[3][3];
+  sym3_jacobi(A, V);
+  const G top = fmax(A[0][0], fmax(A[1][1], A[2][2]));
+  const G thr = (sizeof(G) == 8 ? G(1e-12) : G(1e-6)) * top;
+  gx = gy = gz = G(0);
+  for (int k = 0; k < 3; ++k) {
+    if (!(A[k][k] > thr)) continue;
+    const G c = (V[0][k] * r0 + V[1][k] * r1 + V[2][k] * r2) / A[k][k];
+    gx += c * V[0][k]; gy += c * V[1][k]; gz += c * V[2][k];
+  }
+  if (!(gx * gx + gy * gy + gz * gz > G(0))) { gx = 1; gy = 0; gz = 0; }
+}
+
 // LSFIR normal update of outer iteration io (Sec. 2.1.2): the plane through
 // the cell's PLIC centre x that minimises sum_k w_k (n.(x_k - x))^2 over the
 // valid neighbours (interfacial node neighbours whose normal is within 45
@@ -633,7 +654,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
       gz = a02 * r0 + a12 * r1 + a22 * r2;
       if (det < G(0)) { gx = -gx; gy = -gy; gz = -gz; }
     } else {
-      gx = 1; gy = 0; gz = 0;
+      lsgir_pinv<G>(m00, m01, m02, m11, m12, m22, r0, r1, r2, gx, gy, gz);
     }
     G gn = sqrt(gx * gx + gy * gy + gz * gz);
     if (!(gn > G(0))) { gx = 1; gy = 0; gz = 0; gn = 1; }

@@ -124,6 +124,7 @@ enum Cnt {
   kEpoch = 11,       // step counter for the de-duplication stamps
   kBandCellsOk = 12, // the band cell list of the last advect is valid
   kBandNodesOk = 13, // the band node list of the last reconstruction is valid
+  kNInitList = 14,   // cells the initial surface may cross (vof_init_fraction)
   kNCnt = 16
 };
 constexpr int kRedSlots = 2 * 1024;
@@ -148,6 +149,13 @@ __device__ __forceinline__ void vel0<double>(const Vel& v, double x, double y, d
     u = 2.0 * sx * sx * s2y * s2z;
     w = -s2x * sy * sy * s2z;
     s = -s2x * s2y * sz * sz;
+  } else if (v.kind == VOF_VEL_DEFORMATION2D) {
+    double sx, cx, sz, cz;
+    sincospi(x, &sx, &cx);
+    sincospi(z, &sz, &cz);
+    u = -2.0 * sx * sx * sz * cz;
+    w = 0.0;
+    s = 2.0 * sz * sz * sx * cx;
   } else if (v.kind == VOF_VEL_ROTATION) {
     u = -v.omega * (y - v.cy);
     w = v.omega * (x - v.cx);
@@ -171,6 +179,13 @@ __device__ __forceinline__ void vel0<float>(const Vel& v, float x, float y, floa
     u = 2.0f * sx * sx * s2y * s2z;
     w = -s2x * sy * sy * s2z;
     s = -s2x * s2y * sz * sz;
+  } else if (v.kind == VOF_VEL_DEFORMATION2D) {
+    float sx, cx, sz, cz;
+    sincospif(x, &sx, &cx);
+    sincospif(z, &sz, &cz);
+    u = -2.0f * sx * sx * sz * cz;
+    w = 0.0f;
+    s = 2.0f * sz * sz * sx * cx;
   } else if (v.kind == VOF_VEL_ROTATION) {
     u = (float)(-v.omega) * (y - (float)v.cy);
     w = (float)v.omega * (x - (float)v.cx);
@@ -371,7 +386,8 @@ inline Vel to_vel(const vof_velocity& v) {
 
 // time factor g(t) of the separable fields u(x, t) = g(t) u0(x)
 inline double time_factor(const Vel& v, double t) {
-  if (v.kind == VOF_VEL_DEFORMATION) return std::cos(3.14159265358979323846 * t / v.period);
+  if (v.kind == VOF_VEL_DEFORMATION || v.kind == VOF_VEL_DEFORMATION2D)
+    return std::cos(3.14159265358979323846 * t / v.period);
   return 1.0;
 }
 
@@ -391,6 +407,8 @@ cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s);  // writes red[0], red[1]
+// initial volume fraction (k_init.cu)
+cudaError_t launch_init_fraction(const vof_ctx* c, const vof_shape* shape, int ndiv, cudaStream_t s);
 // reconstruction (k_recon.cu)
 // LSGIR (+ the LSFIR outer iteration when the context asks for it)
 cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);

@@ -44,6 +44,22 @@ class _Opt(C.Structure):
                 ("reserved", C.c_int32 * 2)]
 
 
+class _Shape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("c", C.c_double * 3),
+                ("a", C.c_double * 3), ("r", C.c_double)]
+
+
+def shape_struct(shape):
+    """vof_shape from an inputs.Shape record (kind, c, a, r)."""
+    s = _Shape()
+    s.kind = int(shape.kind)
+    for i in range(3):
+        s.c[i] = shape.c[i]
+        s.a[i] = shape.a[i]
+    s.r = shape.r
+    return s
+
+
 class _Vel(C.Structure):
     _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("period", C.c_double),
                 ("omega", C.c_double), ("center", C.c_double * 3), ("u0", C.c_double * 3)]
@@ -79,6 +95,7 @@ def lib():
         L.vof_destroy.argtypes = [vp]
         L.vof_destroy.restype = None
         L.vof_set_fraction.argtypes = [vp, vp, i32, vp]
+        L.vof_init_fraction.argtypes = [vp, vp, i32, vp]
         L.vof_get_fraction.argtypes = [vp, vp, i32, vp]
         L.vof_reconstruct.argtypes = [vp, vp]
         L.vof_advect.argtypes = [vp, vp, dbl, dbl, vp]
@@ -110,7 +127,8 @@ def lib():
         L.vof_volume_sum_noalloc.restype = C.c_int
         L.vof_device_bytes.restype = i64
         L.vof_device_bytes.argtypes = [vp]
-        for name in ("vof_init", "vof_set_fraction", "vof_get_fraction", "vof_reconstruct",
+        for name in ("vof_init", "vof_set_fraction", "vof_init_fraction", "vof_get_fraction",
+                     "vof_reconstruct",
                      "vof_advect", "vof_step", "vof_suggest_dt", "vof_get_planes",
                      "vof_get_tags", "vof_get_face_flux", "vof_get_geometry",
                      "vof_get_neighbors", "vof_get_candidates", "vof_get_flux_polyhedra",
@@ -238,6 +256,11 @@ class Context:
         if not hasattr(F, "data_ptr"):
             F = np.ascontiguousarray(F, np.float64)
         _check(lib().vof_set_fraction(self._h, _ptr(F), _mem(F), _stream(stream)))
+
+    def init_fraction(self, shape, ndiv=10, stream=None):
+        """initfgrid (Sec. 3.2) on the device: F from a body (inputs.Shape)."""
+        s = shape_struct(shape)
+        _check(lib().vof_init_fraction(self._h, C.byref(s), int(ndiv), _stream(stream)))
 
     def get_fraction(self, out=None, stream=None):
         if out is None:

@@ -52,6 +52,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 4 + 4 + 4 + 8 + 2 * 4
     assert ctypes.sizeof(vof._Vel) == 4 + 4 + 8 + 8 + 24 + 24
     assert ctypes.sizeof(vof.Stats) == 6 * 8 + 5 * 8
+    assert ctypes.sizeof(vof._Shape) == 4 + 4 + 24 + 24 + 8
 
 
 def test_struct_layouts_match_the_header(tmp_path):
@@ -65,7 +66,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no host C compiler")
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     structs = {"vof_mesh_desc": vof._Mesh, "vof_options": vof._Opt, "vof_velocity": vof._Vel,
-               "vof_stats": vof.Stats}
+               "vof_stats": vof.Stats, "vof_shape": vof._Shape}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vof.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
@@ -93,6 +94,10 @@ def test_flux_constants_match_header():
     assert re.search(rf"VOF_MAX_POLY_VERTS\s*=\s*{vof.NB_VERTS}\b", src)
     assert re.search(rf"VOF_RECON_LSGIR\s*=\s*{vof.RECON_LSGIR}\b", src)
     assert re.search(rf"VOF_RECON_LSFIR\s*=\s*{vof.RECON_LSFIR}\b", src)
+    from paper_2111_01524_gb300 import inputs as I
+    for name, val in (("SPHERE", I.Shape.SPHERE), ("CYLINDER", I.Shape.CYLINDER),
+                      ("HALFSPACE", I.Shape.HALFSPACE)):
+        assert re.search(rf"VOF_SHAPE_{name}\s*=\s*{val}\b", src), name
     # 3I+1 EMFPA points for I <= 6, 2I+1 FMFPA points for I <= 8
     assert vof.NB_VERTS >= max(3 * 6 + 1, 2 * 8 + 1)
 
