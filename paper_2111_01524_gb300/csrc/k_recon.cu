@@ -172,6 +172,99 @@ __device__ P plane_constant(const ReconSmem& S, int nfc, int ncv, P s_lane, P nx
 // plane distance D from the vertex, so D = cbrt(6 T |n.e1 n.e2 n.e3| / |det|).
 // FP64; returns false when the corner does not apply (the bracketing method
 // is used then). Needs the loops' vertex ids in smem and s_lane = n.(x_v-xc).
+// the vertices that follow v in the cell's outward loops (its edge
+// neighbours), up to 4 into Sm.corner; returns how many there are
+__device__ int vertex_neighbours(const DevMesh& M, ReconSmem& Sm, int c, int v, int lane) {
+  const int nent = Sm.fs[M.cf_ptr[c + 1] - M.cf_ptr[c]];
+  int found = 0;
+  for (int base = 0; base < nent; base += 32) {
+    const int e = base + lane;
+    int nb = -1;
+    if (e < nent && Sm.vid[e] == v) {
+      int f = 0;
+      while (Sm.fs[f + 1] <= e) ++f;
+      const int nxt = (e + 1 == Sm.fs[f + 1]) ? Sm.fs[f] : e + 1;
+      nb = Sm.vid[nxt];
+    }
+    const unsigned bal = __ballot_sync(GVOF_FULL, nb >= 0);
+    if (nb >= 0) {
+      const int pos = found + __popc(bal & ((1u << lane) - 1u));
+      if (pos < 4) Sm.corner[pos] = nb;
+    }
+    found += __popc(bal);
+  }
+  __syncwarp();
+  return found;
+}
+
+// Prism form of the corner solution, for an extreme projection shared by
+// exactly two vertices v1, v1b joined by an edge e3 that lies in the plane
+// (a cell extruded along e3, e.g. a quasi-2D grid's): when both ends have
+// their other two edges e1, e2 equal, the region within distance D of the
+// top is the corner triangle (v1, v1 + D/a1 e1, v1 + D/a2 e2) swept along
+// e3, of volume D^2 |det(e1, e2, e3)| / (2 a1 a2), a_i = n.e_i towards the
+// region, valid up to the next breakpoint k3. E holds the edges' coordinate
+// differences (v1's edges to its neighbours; the same for v1b), in the
+// units of a (absolute for FP64, scaled for FP32). Returns D or -1.
+template <typename T>
+__device__ T prism_distance(const T e1[3], const T e2[3], const T e3[3], T a1, T a2, T vol, T dmax,
+                            T tiny) {
+  const T det = fabs(e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                     e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]));
+  if (!(a1 > tiny && a2 > tiny) || !(det > T(0))) return T(-1);
+  if (!(vol <= dmax * dmax * det / (T(2) * a1 * a2))) return T(-1);
+  return sqrt(T(2) * vol * a1 * a2 / det);
+}
+
+// the prism form (prism_distance) of corner_constant, out of line: it runs
+// for cells whose extreme projection is shared by two vertices
+__device__ __noinline__ bool corner_prism(const DevMesh& M, ReconSmem& Sm, int c, int ncv, int vl,
+                                          double key, double k1, int v1, double sgn, bool low,
+                                          double nx, double ny, double nz, double F, double Vc,
+                                          int lane, double* Cout) {
+  const unsigned tie = __ballot_sync(GVOF_FULL, lane < ncv && key == k1);
+  if (__popc(tie) != 2) return false;
+  const int la = __ffs(tie) - 1, lb = 31 - __clz(tie);
+  const int va = __shfl_sync(GVOF_FULL, vl, la), vb = __shfl_sync(GVOF_FULL, vl, lb);
+  const int v1b = va == v1 ? vb : va;
+  double k3 = (lane < ncv && key < k1) ? key : -1e300;
+  for (int o = 16; o > 0; o >>= 1) k3 = fmax(k3, __shfl_xor_sync(GVOF_FULL, k3, o));
+  if (vertex_neighbours(M, Sm, c, v1, lane) != 3) return false;
+  int na[3] = {Sm.corner[0], Sm.corner[1], Sm.corner[2]};
+  __syncwarp();
+  if (vertex_neighbours(M, Sm, c, v1b, lane) != 3) return false;
+  const int nbv[3] = {Sm.corner[0], Sm.corner[1], Sm.corner[2]};
+  __syncwarp();
+  // v1's edges: e3 to v1b, e1 and e2 to the others
+  int j = 0;
+  double E[2][3], e3[3] = {M.x[v1b] - M.x[v1], M.y[v1b] - M.y[v1], M.z[v1b] - M.z[v1]};
+  for (int i = 0; i < 3; ++i) {
+    if (na[i] == v1b) continue;
+    if (j == 2) return false;
+    E[j][0] = M.x[na[i]] - M.x[v1]; E[j][1] = M.y[na[i]] - M.y[v1]; E[j][2] = M.z[na[i]] - M.z[v1];
+    ++j;
+  }
+  if (j != 2) return false;
+  // v1b's other two edges must be the same vectors
+  int matched = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (nbv[i] == v1) continue;
+    const double d0 = M.x[nbv[i]] - M.x[v1b], d1 = M.y[nbv[i]] - M.y[v1b], d2 = M.z[nbv[i]] - M.z[v1b];
+    for (int q = 0; q < 2; ++q)
+      if (d0 == E[q][0] && d1 == E[q][1] && d2 == E[q][2]) matched |= 1 << q;
+  }
+  if (matched != 3) return false;
+  const double a1 = -sgn * (nx * E[0][0] + ny * E[0][1] + nz * E[0][2]);
+  const double a2 = -sgn * (nx * E[1][0] + ny * E[1][1] + nz * E[1][2]);
+  const double hs = cbrt(Vc), hsc = 1.0 / hs;
+  const double T = (low ? F : 1.0 - F) * Vc;
+  const double D = prism_distance<double>(E[0], E[1], e3, a1, a2, T, (k1 - k3) / hsc, 1e-9 * hs);
+  if (!(D >= 0.0)) return false;
+  const double s_top = k1 / hsc;
+  *Cout = low ? (D - s_top) : (s_top - D);
+  return true;
+}
+
 __device__ bool corner_constant(const DevMesh& M, ReconSmem& Sm, int c, int ncv, int vl,
                                 double s_lane, double nx, double ny, double nz, double F,
                                 double Vc, int lane, double* Cout) {
@@ -191,29 +284,11 @@ __device__ bool corner_constant(const DevMesh& M, ReconSmem& Sm, int c, int ncv,
       k2 = fmax(k2, ok1);
     }
   }
-  // neighbours of v1: the entry after v1 in every outward loop
-  const int nent = Sm.fs[M.cf_ptr[c + 1] - M.cf_ptr[c]];
-  int found = 0;
-  for (int base = 0; base < nent; base += 32) {
-    const int e = base + lane;
-    int nb = -1;
-    if (e < nent && Sm.vid[e] == v1) {
-      // loop that holds entry e
-      int f = 0;
-      while (Sm.fs[f + 1] <= e) ++f;
-      const int nxt = (e + 1 == Sm.fs[f + 1]) ? Sm.fs[f] : e + 1;
-      nb = Sm.vid[nxt];
-    }
-    const unsigned bal = __ballot_sync(GVOF_FULL, nb >= 0);
-    if (nb >= 0) {
-      const int pos = found + __popc(bal & ((1u << lane) - 1u));
-      if (pos < 4) Sm.corner[pos] = nb;
-    }
-    found += __popc(bal);
-  }
-  __syncwarp();
-  if (found != 3) return false;
   const double sgn = low ? 1.0 : -1.0;
+  if (k2 == k1) return corner_prism(M, Sm, c, ncv, vl, key, k1, v1, sgn, low, nx, ny, nz, F, Vc, lane, Cout);
+  // neighbours of v1: the entry after v1 in every outward loop
+  const int found = vertex_neighbours(M, Sm, c, v1, lane);
+  if (found != 3) return false;
   double e[3][3], a[3];
   for (int i = 0; i < 3; ++i) {
     const int w = Sm.corner[i];
@@ -242,6 +317,57 @@ __device__ bool corner_constant(const DevMesh& M, ReconSmem& Sm, int c, int ncv,
 // the scaled cell-local frame, edges from the (hi, lo) positions. The mixed
 // path stores its plane constants in FP32, whose rounding (a few 1e-8 of the
 // cell size) bounds what an FP64 root would add. Returns the scaled C.
+// the prism form (prism_distance) of corner_constant32, out of line
+template <typename G>
+__device__ __noinline__ bool corner_prism32(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm, int c,
+                                            int ncv, int vl, float key, float k1, int v1, float sgn,
+                                            bool low, float nx, float ny, float nz, double F, float Vs,
+                                            float sc, int lane, float* Cout) {
+  const unsigned tie = __ballot_sync(GVOF_FULL, lane < ncv && key == k1);
+  if (__popc(tie) != 2) return false;
+  const int la = __ffs(tie) - 1, lb = 31 - __clz(tie);
+  const int va = __shfl_sync(GVOF_FULL, vl, la), vb = __shfl_sync(GVOF_FULL, vl, lb);
+  const int v1b = va == v1 ? vb : va;
+  float k3 = (lane < ncv && key < k1) ? key : -1e30f;
+  for (int o = 16; o > 0; o >>= 1) k3 = fmaxf(k3, __shfl_xor_sync(GVOF_FULL, k3, o));
+  if (vertex_neighbours(M, Sm, c, v1, lane) != 3) return false;
+  int na[3] = {Sm.corner[0], Sm.corner[1], Sm.corner[2]};
+  __syncwarp();
+  if (vertex_neighbours(M, Sm, c, v1b, lane) != 3) return false;
+  const int nbv[3] = {Sm.corner[0], Sm.corner[1], Sm.corner[2]};
+  __syncwarp();
+  int j = 0;
+  float E[2][3];
+  const float e3[3] = {(float)(rel(Gv.vx[v1b], Gv.vx[v1]) * sc), (float)(rel(Gv.vy[v1b], Gv.vy[v1]) * sc),
+                       (float)(rel(Gv.vz[v1b], Gv.vz[v1]) * sc)};
+  for (int i = 0; i < 3; ++i) {
+    if (na[i] == v1b) continue;
+    if (j == 2) return false;
+    E[j][0] = (float)(rel(Gv.vx[na[i]], Gv.vx[v1]) * sc);
+    E[j][1] = (float)(rel(Gv.vy[na[i]], Gv.vy[v1]) * sc);
+    E[j][2] = (float)(rel(Gv.vz[na[i]], Gv.vz[v1]) * sc);
+    ++j;
+  }
+  if (j != 2) return false;
+  int matched = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (nbv[i] == v1) continue;
+    const float d0 = (float)(rel(Gv.vx[nbv[i]], Gv.vx[v1b]) * sc),
+                d1 = (float)(rel(Gv.vy[nbv[i]], Gv.vy[v1b]) * sc),
+                d2 = (float)(rel(Gv.vz[nbv[i]], Gv.vz[v1b]) * sc);
+    for (int q = 0; q < 2; ++q)
+      if (d0 == E[q][0] && d1 == E[q][1] && d2 == E[q][2]) matched |= 1 << q;
+  }
+  if (matched != 3) return false;
+  const float a1 = -sgn * (nx * E[0][0] + ny * E[0][1] + nz * E[0][2]);
+  const float a2 = -sgn * (nx * E[1][0] + ny * E[1][1] + nz * E[1][2]);
+  const float T = (float)((low ? F : 1.0 - F) * (double)Vs);
+  const float D = prism_distance<float>(E[0], E[1], e3, a1, a2, T, k1 - k3, 1e-6f);
+  if (!(D >= 0.f)) return false;
+  *Cout = low ? (D - k1) : (k1 - D);
+  return true;
+}
+
 template <typename G>
 __device__ bool corner_constant32(const DevMesh& M, const GeoView<G>& Gv, ReconSmem& Sm, int c, int ncv,
                                   int vl, float s_lane, float nx, float ny, float nz, double F, float Vs,
@@ -261,27 +387,10 @@ __device__ bool corner_constant32(const DevMesh& M, const GeoView<G>& Gv, ReconS
       k2 = fmaxf(k2, ok1);
     }
   }
-  const int nent = Sm.fs[M.cf_ptr[c + 1] - M.cf_ptr[c]];
-  int found = 0;
-  for (int base = 0; base < nent; base += 32) {
-    const int e = base + lane;
-    int nb = -1;
-    if (e < nent && Sm.vid[e] == v1) {
-      int f = 0;
-      while (Sm.fs[f + 1] <= e) ++f;
-      const int nxt = (e + 1 == Sm.fs[f + 1]) ? Sm.fs[f] : e + 1;
-      nb = Sm.vid[nxt];
-    }
-    const unsigned bal = __ballot_sync(GVOF_FULL, nb >= 0);
-    if (nb >= 0) {
-      const int pos = found + __popc(bal & ((1u << lane) - 1u));
-      if (pos < 4) Sm.corner[pos] = nb;
-    }
-    found += __popc(bal);
-  }
-  __syncwarp();
-  if (found != 3) return false;
   const float sgn = low ? 1.f : -1.f;
+  if (k2 == k1) return corner_prism32<G>(M, Gv, Sm, c, ncv, vl, key, k1, v1, sgn, low, nx, ny, nz, F, Vs, sc, lane, Cout);
+  const int found = vertex_neighbours(M, Sm, c, v1, lane);
+  if (found != 3) return false;
   float e[3][3], a[3];
   for (int i = 0; i < 3; ++i) {
     const int w = Sm.corner[i];
@@ -490,10 +599,11 @@ __device__ __noinline__ void lsgir_pinv(G m00, G m01, G m02, G m11, G m12, G m22
 // Work split: a warp gathers and reduces the sums of 32 cells one after the
 // other (lanes over neighbours), then lane i solves cell i's eigenproblem,
 // so the FP64 solve runs once per cell (the FP64 pipe processes a warp
-// instruction at the same cost whatever its active lanes). The fit is FP64
-// in both paths: in FP32 the eigenvector of a nearly degenerate matrix
-// drifts from the FP64 result; the mixed path forms the distances in FP32
-// from (hi, lo) centroids and FP32 centre offsets.
+// instruction at the same cost whatever its active lanes). The sums and the
+// solve are FP64 in both paths: in FP32 the eigenvector of a nearly
+// degenerate matrix drifts from the FP64 result; the mixed path forms the
+// distances and weights in FP32 (from (hi, lo) centroids and FP32 centre
+// offsets), the FP64 path in FP64.
 template <typename G, bool kMixed>
 __global__ void __launch_bounds__(kWarps * 32) k_lsfir_normals(DevMesh M, GeoView<G> Gv, DevState S,
                                                             int io, double lim, double tol) {
@@ -529,9 +639,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_lsfir_normals(DevMesh M, GeoVie
           dz = (S.lzp[k] - S.lzp[c]) * sc;
         }
         const double ex = dx, ey = dy, ez = dz;
-        const double r2 = ex * ex + ey * ey + ez * ez;
-        if (!(r2 > 0.0)) continue;
-        const double wk = 1.0 / (r2 * sqrt(sqrt(r2)));  // |d|^-2.5
+        double wk;  // |d|^-2.5: FP32 on the mixed path (its distances are FP32)
+        if constexpr (kMixed) {
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (!(r2 > 0.f)) continue;
+          wk = 1.f / (r2 * sqrtf(sqrtf(r2)));
+        } else {
+          const double r2 = ex * ex + ey * ey + ez * ez;
+          if (!(r2 > 0.0)) continue;
+          wk = 1.0 / (r2 * sqrt(sqrt(r2)));
+        }
         m00 += wk * ex * ex; m01 += wk * ex * ey; m02 += wk * ex * ez;
         m11 += wk * ey * ey; m12 += wk * ey * ez; m22 += wk * ez * ez;
         ++nv;
