@@ -533,7 +533,14 @@ def main_deform2d(a):
     res = {}
     for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
         ctx = V.Context(m, precision=prec)
+        ctx.init_fraction(cyl, 10)  # warm-up of the initialisation
+        i0 = torch.cuda.Event(enable_timing=True)
+        i1 = torch.cuda.Event(enable_timing=True)
+        i0.record()
         ctx.init_fraction(cyl, 10)
+        i1.record()
+        torch.cuda.synchronize()
+        init_ms = i0.elapsed_time(i1)
         ctx.reconstruct()
         t = 0.0
         for _ in range(a.warmup):
@@ -559,7 +566,8 @@ def main_deform2d(a):
         clocks = clk.stop()
         ms = over_ranks(dist, e0.elapsed_time(e1), "max")
         res[name] = {"value": ws * m["n_cell"] * a.steps / (ms * 1e-3), "ms_per_step": ms / a.steps,
-                     "F": ctx.get_fraction(), "stats": ctx.stats(), "clocks": clocks}
+                     "F": ctx.get_fraction(), "stats": ctx.stats(), "clocks": clocks,
+                     "init_ms": init_ms}
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
@@ -576,6 +584,7 @@ def main_deform2d(a):
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
                           "max_abs_F_diff_mixed_vs_fp64":
                               float(np.abs(res["mixed"]["F"] - res["fp64"]["F"]).max())},
+            "device_init": {"ms": res["mixed"]["init_ms"], "ndiv": 10},
             "band": {k: res["mixed"]["stats"][k] for k in ("n_interfacial", "n_active_faces",
                                                            "n_truncations", "n_overflow")}}
     print(json.dumps(line))

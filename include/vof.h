@@ -274,6 +274,21 @@ vof_status vof_get_candidates(vof_ctx* ctx, const int32_t* faces, int n, int64_t
  * 2I points (x_1..x_I, x_i - dt u_c). counts HOST [n] receives I. */
 vof_status vof_get_flux_polyhedra(vof_ctx* ctx, const vof_velocity* vel, double t, double dt,
                                   const int32_t* faces, int n, double* verts, int32_t* counts);
+/* Checkpoint / resume (no counterpart in the paper): the state a step
+ * continues from, taken after a reconstruction (vof_reconstruct or
+ * vof_step): F, the PLIC planes (n, C) and the node and cell tags of the last
+ * reconstruction, and the volume bookkeeping. buf is an opaque HOST buffer
+ * of *need bytes (vof_get_state with buf = NULL only reports *need). A
+ * context of the same mesh (cell and node counts are checked) restored with
+ * vof_set_state continues like the one that saved it: F and the planes bit
+ * for bit (its next sweeps are full, which give the band-limited sweeps'
+ * results), the bookkeeping sums to rounding (their per-block partial sums
+ * follow the sweep's assignment of cells to blocks). Both
+ * synchronise `stream`. VOF_ESTATE if the reconstruction is not current;
+ * VOF_EINVAL for a short or foreign buffer. */
+vof_status vof_get_state(vof_ctx* ctx, void* buf, int64_t bytes, int64_t* need, void* stream);
+vof_status vof_set_state(vof_ctx* ctx, const void* buf, int64_t bytes, void* stream);
+
 /* counters and global sums (synchronises the stream). */
 vof_status vof_get_stats(vof_ctx* ctx, vof_stats* out, void* stream);
 /* Per-phase device timing with CUDA events recorded on the launching

@@ -738,6 +738,85 @@ vof_status vof_autotune(vof_ctx* c, const vof_velocity* vels, const double* t, c
   return VOF_OK;
 }
 
+namespace {
+constexpr uint64_t kStateMagic = 0x45544154534f5647ull;  // "GVOSTATE"
+struct StateHeader {
+  uint64_t magic;
+  int64_t version, nc, nv, nacc;
+};
+int64_t state_bytes(const vof_ctx* c) {
+  return (int64_t)sizeof(StateHeader) + 5 * 8 * c->nc + c->nc + c->nv + 8 * (int64_t)kNAcc * kAccSlots;
+}
+__global__ void k_planes32(int64_t nc, const double* nx, const double* ny, const double* nz,
+                           const double* C, float* nx32, float* ny32, float* nz32, float* C32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    nx32[i] = (float)nx[i]; ny32[i] = (float)ny[i]; nz32[i] = (float)nz[i]; C32[i] = (float)C[i];
+  }
+}
+}  // namespace
+
+vof_status vof_get_state(vof_ctx* c, void* buf, int64_t bytes, int64_t* need, void* stream) {
+  if (!c) return fail(VOF_EINVAL, "NULL context");
+  const int64_t n = state_bytes(c);
+  if (need) *need = n;
+  if (!buf) return VOF_OK;
+  if (bytes < n) return fail(VOF_EINVAL, "state buffer too small");
+  if (!c->recon_valid) return fail(VOF_ESTATE, "the state is taken after a reconstruction");
+  cudaStream_t s = (cudaStream_t)stream;
+  StateHeader h{kStateMagic, 1, c->nc, c->nv, (int64_t)kNAcc * kAccSlots};
+  char* p = (char*)buf;
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  const size_t d = sizeof(double) * c->nc;
+  for (const double* a : {c->F, c->nx, c->ny, c->nz, c->C}) {
+    CK(cudaMemcpyAsync(p, a, d, cudaMemcpyDeviceToHost, s));
+    p += d;
+  }
+  CK(cudaMemcpyAsync(p, c->tc, c->nc, cudaMemcpyDeviceToHost, s));
+  p += c->nc;
+  CK(cudaMemcpyAsync(p, c->tv, c->nv, cudaMemcpyDeviceToHost, s));
+  p += c->nv;
+  CK(cudaMemcpyAsync(p, c->acc, sizeof(double) * kNAcc * kAccSlots, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return VOF_OK;
+}
+
+vof_status vof_set_state(vof_ctx* c, const void* buf, int64_t bytes, void* stream) {
+  if (!c || !buf) return fail(VOF_EINVAL, "NULL argument");
+  const int64_t n = state_bytes(c);
+  StateHeader h;
+  if (bytes < (int64_t)sizeof h) return fail(VOF_EINVAL, "state buffer too small");
+  std::memcpy(&h, buf, sizeof h);
+  if (h.magic != kStateMagic || h.version != 1) return fail(VOF_EINVAL, "not a saved state");
+  if (h.nc != c->nc || h.nv != c->nv || h.nacc != (int64_t)kNAcc * kAccSlots)
+    return fail(VOF_EINVAL, "the state was saved from another mesh");
+  if (bytes < n) return fail(VOF_EINVAL, "state buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* p = (const char*)buf + sizeof h;
+  const size_t d = sizeof(double) * c->nc;
+  for (double* a : {c->F, c->nx, c->ny, c->nz, c->C}) {
+    CK(cudaMemcpyAsync(a, p, d, cudaMemcpyHostToDevice, s));
+    p += d;
+  }
+  CK(cudaMemcpyAsync(c->tc, p, c->nc, cudaMemcpyHostToDevice, s));
+  p += c->nc;
+  CK(cudaMemcpyAsync(c->tv, p, c->nv, cudaMemcpyHostToDevice, s));
+  p += c->nv;
+  CK(cudaMemcpyAsync(c->acc, p, sizeof(double) * kNAcc * kAccSlots, cudaMemcpyHostToDevice, s));
+  // the FP32 planes are the FP64 ones rounded (so stored); band lists are
+  // rebuilt by full sweeps
+  if (c->opt.precision == VOF_PREC_MIXED) {
+    k_planes32<<<kSMs * 4, 256, 0, s>>>(c->nc, c->nx, c->ny, c->nz, c->C, c->nx32, c->ny32, c->nz32,
+                                        c->C32);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemsetAsync(c->cnt + kBandCellsOk, 0, 2 * sizeof(unsigned long long), s));
+  CK(cudaStreamSynchronize(s));
+  c->recon_valid = true;
+  return VOF_OK;
+}
+
 vof_status vof_get_planes(vof_ctx* c, double* planes, int mem, void* stream) {
   if (!c || !planes) return fail(VOF_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;

@@ -10,11 +10,15 @@
 // tetrahedra of the unit lattice cubes inside that simplex). Cells whose
 // bounding ball about the centroid lies on one side of the body are 0 or 1.
 //
-// GPU design: one thread per cell classifies by the ball test and lists the
-// cells the surface may cross; one warp per listed cell then walks its
-// tetrahedra. A tetrahedron whose own bounding ball lies on one side is
-// whole or empty (the distance is 1-Lipschitz, so every lattice value has
-// that sign and every piece the same fraction). Otherwise the lanes evaluate
+// GPU design: one thread per cell classifies it and lists the cells the
+// surface may cross; one warp per listed cell then walks its tetrahedra. The
+// classification bounds the range of the distance over a cell (or a
+// tetrahedron) about its value at the centre by the body's own geometry,
+// tighter than the bounding ball: the largest offset from the centre for a
+// sphere, its part across the axis for a cylinder (a slab cell of a quasi-2D
+// grid is long along the axis), its part along the normal for a half-space.
+// A cell or tetrahedron on one side has the same sign at every lattice
+// point, so its fraction is exactly 0 or 1 as the refinement would give. Otherwise the lanes evaluate
 // the distance once per lattice point into shared memory (286 points for
 // ndiv = 10, against 4000 piece vertices), then share the pieces; a piece
 // whose four values agree in sign is 0 or 1, and only the cut ones form
@@ -45,6 +49,19 @@ __device__ __forceinline__ double shape_phi(const Shape& b, double x, double y, 
     return sqrt(px * px + py * py + pz * pz) - b.r;
   }
   return b.ax * dx + b.ay * dy + b.az * dz;
+}
+
+// how far the distance can move from its value at a point when the point
+// moves by d: |d| for a sphere, d across the axis for a cylinder, d along the
+// normal for a half-space (each exact for its body)
+__device__ __forceinline__ double shape_spread(const Shape& b, double dx, double dy, double dz) {
+  if (b.kind == VOF_SHAPE_SPHERE) return sqrt(dx * dx + dy * dy + dz * dz);
+  const double t = dx * b.ax + dy * b.ay + dz * b.az;
+  if (b.kind == VOF_SHAPE_CYLINDER) {
+    const double px = dx - t * b.ax, py = dy - t * b.ay, pz = dz - t * b.az;
+    return sqrt(px * px + py * py + pz * pz);
+  }
+  return fabs(t);
 }
 
 __device__ __forceinline__ int lattice_index(int x1, int x2, int x3) {
@@ -105,13 +122,12 @@ __global__ void k_init_classify(DevMesh M, DevState S, Shape b, int32_t* list,
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M.nc;
        c += (int64_t)gridDim.x * blockDim.x) {
     const double xc = M.ccx[c], yc = M.ccy[c], zc = M.ccz[c];
-    double R2 = 0.0;
+    double R = 0.0;
     for (int64_t q = M.cv_ptr[c]; q < M.cv_ptr[c + 1]; ++q) {
       const int v = M.cv[q];
-      const double dx = M.x[v] - xc, dy = M.y[v] - yc, dz = M.z[v] - zc;
-      R2 = fmax(R2, dx * dx + dy * dy + dz * dz);
+      R = fmax(R, shape_spread(b, M.x[v] - xc, M.y[v] - yc, M.z[v] - zc));
     }
-    const double R = sqrt(R2), pc = shape_phi(b, xc, yc, zc);
+    const double pc = shape_phi(b, xc, yc, zc);
     if (pc > R) {
       S.F[c] = 0.0;
     } else if (pc < -R) {
@@ -127,8 +143,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_init_refine(DevMesh M, DevState
                                                           const int32_t* list,
                                                           const unsigned long long* nlist) {
   __shared__ double lat[kWarps][kLattice];
+  // the ndiv^3 pieces of a tetrahedron: base (a1, a2, a3) and step order,
+  // packed 4 + 4 + 4 + 3 bits, enumerated once per block
+  __shared__ uint16_t pieces[kMaxDiv * kMaxDiv * kMaxDiv];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* phi = lat[wib];
+  if (threadIdx.x == 0) {
+    int np = 0;
+    for (int a1 = 0; a1 < ndiv; ++a1)
+      for (int a2 = 0; a2 <= a1; ++a2)
+        for (int a3 = 0; a3 <= a2; ++a3)
+          for (int pi = 0; pi < 6; ++pi) {
+            const int s0 = pi >> 1, r0 = pi & 1;
+            const int s1 = s0 == 0 ? (r0 ? 2 : 1) : (s0 == 1 ? (r0 ? 2 : 0) : (r0 ? 1 : 0));
+            const int s2 = 3 - s0 - s1;
+            int pos[3];
+            pos[s0] = 0; pos[s1] = 1; pos[s2] = 2;
+            // where two base coordinates tie, the lower index steps first
+            if ((a1 == a2 && pos[0] > pos[1]) || (a2 == a3 && pos[1] > pos[2])) continue;
+            pieces[np++] = (uint16_t)(a1 | (a2 << 4) | (a3 << 8) | (pi << 12));
+          }
+  }
+  __syncthreads();
+  const int npieces = ndiv * ndiv * ndiv;
   const unsigned n = (unsigned)*nlist;
   const double inv = 1.0 / ndiv;
   for (unsigned w = blockIdx.x * kWarps + wib; w < n; w += gridDim.x * kWarps) {
@@ -172,13 +209,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_init_refine(DevMesh M, DevState
         const double v = det3(T[0], T[1], T[2], T[3]) / 6.0;
         if (v == 0.0) continue;
         {
-          double tc[3], R2 = 0.0;
+          double tc[3], Rt = 0.0;
           for (int d = 0; d < 3; ++d) tc[d] = 0.25 * (T[0][d] + T[1][d] + T[2][d] + T[3][d]);
-          for (int k = 0; k < 4; ++k) {
-            const double dx = T[k][0] - tc[0], dy = T[k][1] - tc[1], dz = T[k][2] - tc[2];
-            R2 = fmax(R2, dx * dx + dy * dy + dz * dz);
-          }
-          const double pt = shape_phi(b, tc[0], tc[1], tc[2]), Rt = sqrt(R2);
+          for (int k = 0; k < 4; ++k)
+            Rt = fmax(Rt, shape_spread(b, T[k][0] - tc[0], T[k][1] - tc[1], T[k][2] - tc[2]));
+          const double pt = shape_phi(b, tc[0], tc[1], tc[2]);
           if (pt > Rt) continue;              // no fluid in this tetrahedron
           if (pt < -Rt) {                     // all fluid
             if (lane == 0) vol += v;
@@ -203,39 +238,31 @@ __global__ void __launch_bounds__(kWarps * 32) k_init_refine(DevMesh M, DevState
         // the pieces: Kuhn tetrahedra of the lattice cubes at base (a1, a2,
         // a3), a1 >= a2 >= a3, whose steps keep x1 >= x2 >= x3
         double frac = 0.0;
-        cnt = 0;
-        for (int a1 = 0; a1 < ndiv; ++a1)
-          for (int a2 = 0; a2 <= a1; ++a2)
-            for (int a3 = 0; a3 <= a2; ++a3, ++cnt) {
-              if ((cnt & 31) != lane) continue;
-              for (int pi = 0; pi < 6; ++pi) {
-                // step order of the three coordinates
-                const int s0 = pi >> 1, r0 = pi & 1;
-                const int s1 = s0 == 0 ? (r0 ? 2 : 1) : (s0 == 1 ? (r0 ? 2 : 0) : (r0 ? 1 : 0));
-                const int s2 = 3 - s0 - s1;
-                int pos[3];
-                pos[s0] = 0; pos[s1] = 1; pos[s2] = 2;
-                if ((a1 == a2 && pos[0] > pos[1]) || (a2 == a3 && pos[1] > pos[2])) continue;
-                int x[3] = {a1, a2, a3};
-                int xs[4][3];
-                double sv[4];
-                int npos = 0;
-                for (int k = 0; k < 4; ++k) {
-                  if (k == 1) ++x[s0];
-                  if (k == 2) ++x[s1];
-                  if (k == 3) ++x[s2];
-                  xs[k][0] = x[0]; xs[k][1] = x[1]; xs[k][2] = x[2];
-                  sv[k] = phi[lattice_index(x[0], x[1], x[2])];
-                  npos += sv[k] > 0.0;
-                }
-                if (npos == 0) continue;
-                if (npos == 4) { frac += 1.0; continue; }
-                double P[4][3];
-                for (int k = 0; k < 4; ++k)
-                  for (int d = 0; d < 3; ++d) P[k][d] = xs[k][d];
-                frac += piece_fraction(P, sv);
-              }
-            }
+        for (int p = lane; p < npieces; p += 32) {
+          const int code = pieces[p];
+          const int pi = code >> 12;
+          const int s0 = pi >> 1, r0 = pi & 1;
+          const int s1 = s0 == 0 ? (r0 ? 2 : 1) : (s0 == 1 ? (r0 ? 2 : 0) : (r0 ? 1 : 0));
+          const int s2 = 3 - s0 - s1;
+          int x[3] = {code & 15, (code >> 4) & 15, (code >> 8) & 15};
+          int xs[4][3];
+          double sv[4];
+          int npos = 0;
+          for (int k = 0; k < 4; ++k) {
+            if (k == 1) ++x[s0];
+            if (k == 2) ++x[s1];
+            if (k == 3) ++x[s2];
+            xs[k][0] = x[0]; xs[k][1] = x[1]; xs[k][2] = x[2];
+            sv[k] = phi[lattice_index(x[0], x[1], x[2])];
+            npos += sv[k] > 0.0;
+          }
+          if (npos == 0) continue;
+          if (npos == 4) { frac += 1.0; continue; }
+          double P[4][3];
+          for (int k = 0; k < 4; ++k)
+            for (int d = 0; d < 3; ++d) P[k][d] = xs[k][d];
+          frac += piece_fraction(P, sv);
+        }
         vol += v * frac * (inv * inv * inv);
         __syncwarp();
       }

@@ -96,6 +96,8 @@ def lib():
         L.vof_destroy.restype = None
         L.vof_set_fraction.argtypes = [vp, vp, i32, vp]
         L.vof_init_fraction.argtypes = [vp, vp, i32, vp]
+        L.vof_get_state.argtypes = [vp, vp, i64, C.POINTER(i64), vp]
+        L.vof_set_state.argtypes = [vp, vp, i64, vp]
         L.vof_get_fraction.argtypes = [vp, vp, i32, vp]
         L.vof_reconstruct.argtypes = [vp, vp]
         L.vof_advect.argtypes = [vp, vp, dbl, dbl, vp]
@@ -128,7 +130,7 @@ def lib():
         L.vof_device_bytes.restype = i64
         L.vof_device_bytes.argtypes = [vp]
         for name in ("vof_init", "vof_set_fraction", "vof_init_fraction", "vof_get_fraction",
-                     "vof_reconstruct",
+                     "vof_reconstruct", "vof_get_state", "vof_set_state",
                      "vof_advect", "vof_step", "vof_suggest_dt", "vof_get_planes",
                      "vof_get_tags", "vof_get_face_flux", "vof_get_geometry",
                      "vof_get_neighbors", "vof_get_candidates", "vof_get_flux_polyhedra",
@@ -261,6 +263,18 @@ class Context:
         """initfgrid (Sec. 3.2) on the device: F from a body (inputs.Shape)."""
         s = shape_struct(shape)
         _check(lib().vof_init_fraction(self._h, C.byref(s), int(ndiv), _stream(stream)))
+
+    def get_state(self, stream=None):
+        """checkpoint: the state a step continues from, as bytes (numpy uint8)"""
+        need = C.c_int64()
+        _check(lib().vof_get_state(self._h, None, 0, C.byref(need), _stream(stream)))
+        buf = np.empty(need.value, np.uint8)
+        _check(lib().vof_get_state(self._h, _ptr(buf), buf.size, None, _stream(stream)))
+        return buf
+
+    def set_state(self, buf, stream=None):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(lib().vof_set_state(self._h, _ptr(buf), buf.size, _stream(stream)))
 
     def get_fraction(self, out=None, stream=None):
         if out is None:
