@@ -50,7 +50,7 @@ void free_all(vof_ctx* c) {
   void* ptrs2[] = {c->cpl32, c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces, c->vf_ptr, c->vf,
                    c->stamp_c, c->stamp_v, c->stamp_f, c->bcells, c->bnodes, c->lxp, c->lyp,
                    c->lzp, c->lxr, c->lyr, c->lzr, c->lnx, c->lny, c->lnz, c->lnx32, c->lny32,
-                   c->lnz32, c->lturn};
+                   c->lnz32, c->lturn, c->fm_v, c->fm_f, c->fm_meta, c->fm_split};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -347,6 +347,16 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     CKI(dalloc(c, &c->C32, nc));
     CKI(dalloc(c, &c->cpl32, c->ncf));
   }
+  if (o.flux_polyhedron == VOF_FLUX_FMFPA) {
+    // room for the polyhedra the flux kernel reads prebuilt
+    c->fm_cap = std::min<int64_t>(nf, kFmCap);
+    const size_t gs = o.precision == VOF_PREC_MIXED ? sizeof(float) : sizeof(double);
+    CKI(cudaMalloc(&c->fm_v, gs * 3 * kFmSlots * c->fm_cap));
+    CKI(cudaMalloc(&c->fm_f, gs * 7 * c->fm_cap));
+    c->bytes += (int64_t)(gs * (3 * kFmSlots + 7) * c->fm_cap);
+    CKI(dalloc(c, &c->fm_meta, c->fm_cap));
+    CKI(dalloc(c, &c->fm_split, c->fm_cap));
+  }
   if (o.reconstruction == VOF_RECON_LSFIR) {
     // PLIC centres by cell, accepted normals by band position, max turn per iteration
     if (o.precision == VOF_PREC_MIXED) {
@@ -568,7 +578,7 @@ vof_status vof_reconstruct(vof_ctx* c, void* stream) {
 
 static vof_status advect_launches(vof_ctx* c, cudaStream_t s) {
   { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s); CK(launch_face_sweep(c, s)); }
-  { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_FLUX, s, flux_launch_count(c)); CK(launch_flux(c, s)); }
   { PhaseTimer tm(c, VOF_PHASE_UPDATE, s); CK(launch_update(c, s)); }
   return VOF_OK;
 }

@@ -501,127 +501,137 @@ struct FaceFrame {
   unsigned split;                  // non-planar FMFPA side quads (bit i: side i)
 };
 
-// FMFPA construction (Sec. 2.2.2) into P.b*: side plane i contains edge i
-// and is parallel to the velocity at the edge centre; back-traced vertex i
-// is the projection of the streak-line point x_i - dt u_i (Eq.
-// streak-line2) on the line where side planes i-1 and i meet; the centroid
-// of the back-traced loop moves along the face normal by the closed-form
-// amount that makes the signed volume equal V_d.
+// FMFPA construction (Sec. 2.2.2) by one thread: side plane i contains
+// edge i and is parallel to the velocity at the edge centre; back-traced
+// vertex i is the projection of the streak-line point x_i - dt u_i (Eq.
+// streak-line2) on the line where side planes i-1 and i meet (the
+// streak-line point itself where that line or a plane is ill-conditioned,
+// sin < 1e-3); the centroid of the back-traced loop moves along the face
+// normal by the closed-form amount that makes the signed volume equal V_d.
+// Writes the 2I+1 vertices (face-local, scaled by 1/sqrt(A)) to v* and the
+// frame to fr. One thread per face, so that a warp builds 32 polyhedra at
+// once (the construction has one vertex per lane otherwise, 4 of 32 busy for
+// a hex face); the flux kernel, its fallback and the polyhedron export all
+// use this same arithmetic.
 template <typename G>
-__device__ GVOF_OUTER_ATTR bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv,
-                                         const GridParam& p, int j, double Vd, Poly<G>& P,
-                                         FaceFrame<G>& frs, int lane) {
-  FaceFrame<G> fr;  // built in registers, published to shared memory at the end
+__device__ __noinline__ bool fmfpa_scalar(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p, int j,
+                             double Vd, G* vx, G* vy, G* vz, FaceFrame<G>& fr) {
   const int64_t fb = M.fptr[j];
   const int I = (int)(M.fptr[j + 1] - fb);
   fr.I = I;
-  if (I > MAXI || I < 3) {
-    if (lane == 0) frs.I = I;
-    __syncwarp();
-    return false;
-  }
+  fr.degenerate = 0;
+  fr.edgeon = 0;
+  fr.split = 0u;
+  if (I > MAXI || I < 3) return false;
   fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
   fr.L = sqrt(Gv.fa[j]);
   fr.sc = G(1) / fr.L;
   const G nx = Gv.fnx[j], ny = Gv.fny[j], nz = Gv.fnz[j];
-  const bool act = lane < I;
-  const int vi = act ? M.fvert[fb + lane] : M.fvert[fb];
-  const typename Prec<G>::A X = Gv.vx[vi], Y = Gv.vy[vi], Z = Gv.vz[vi];
-  const int nxt = (lane + 1 >= I) ? 0 : lane + 1;
-  const int prv = (lane == 0) ? I - 1 : lane - 1;
-  const G ax = absval(X), ay = absval(Y), az = absval(Z);
-  const G axn = __shfl_sync(GVOF_FULL, ax, nxt), ayn = __shfl_sync(GVOF_FULL, ay, nxt),
-          azn = __shfl_sync(GVOF_FULL, az, nxt);
-  // velocities at the vertex and at the centre of edge (i, i+1), times dt,
-  // in face-local scaled units
-  G ux, uy, uz, ex_u, ey_u, ez_u;
-  vel0<G>(p.vel, ax, ay, az, ux, uy, uz);
-  vel0<G>(p.vel, G(0.5) * (ax + axn), G(0.5) * (ay + ayn), G(0.5) * (az + azn), ex_u, ey_u, ez_u);
   const G k = (G)(p.g * p.dt) * fr.sc;
-  ux *= k; uy *= k; uz *= k; ex_u *= k; ey_u *= k; ez_u *= k;
-  const G lx = rel(X, fr.cx) * fr.sc, ly = rel(Y, fr.cy) * fr.sc, lz = rel(Z, fr.cz) * fr.sc;
-  const G lxn = __shfl_sync(GVOF_FULL, lx, nxt), lyn = __shfl_sync(GVOF_FULL, ly, nxt),
-          lzn = __shfl_sync(GVOF_FULL, lz, nxt);
-  const G ex = lxn - lx, ey = lyn - ly, ez = lzn - lz;
-  // side plane normal s_i = e_i x u_e,i
-  const G sx = ey * ez_u - ez * ey_u, sy = ez * ex_u - ex * ez_u, sz = ex * ey_u - ey * ex_u;
-  const G spx = __shfl_sync(GVOF_FULL, sx, prv), spy = __shfl_sync(GVOF_FULL, sy, prv),
-          spz = __shfl_sync(GVOF_FULL, sz, prv);
-  const G dx = spy * sz - spz * sy, dy = spz * sx - spx * sz, dz = spx * sy - spy * sx;
-  const G ns = sqrt(sx * sx + sy * sy + sz * sz), nsp = __shfl_sync(GVOF_FULL, ns, prv);
-  const G ne = sqrt(ex * ex + ey * ey + ez * ez);
-  const G nue = sqrt(ex_u * ex_u + ey_u * ey_u + ez_u * ez_u);
-  const G nep = __shfl_sync(GVOF_FULL, ne, prv), nuep = __shfl_sync(GVOF_FULL, nue, prv);
-  const G dd = dx * dx + dy * dy + dz * dz;
-  // below sin(angle) = 1e-3 the side plane or the line is ill-conditioned
-  // (relative error eps/sin) and the streak-line point is used instead
-  const G tol = (G)1e-3;
-  const bool ok = ns > tol * ne * nue && nsp > tol * nep * nuep && sqrt(dd) > tol * nsp * ns;
-  G bxl, byl, bzl;
-  if (ok) {
-    const G kk = (ux * dx + uy * dy + uz * dz) / dd;
-    bxl = lx - kk * dx; byl = ly - kk * dy; bzl = lz - kk * dz;
-  } else {
-    bxl = lx - ux; byl = ly - uy; bzl = lz - uz;
+  G lx[MAXI], ly[MAXI], lz[MAXI], ax[MAXI], ay[MAXI], az[MAXI], ux[MAXI], uy[MAXI], uz[MAXI];
+  for (int i = 0; i < I; ++i) {
+    const int vi = M.fvert[fb + i];
+    const typename Prec<G>::A X = Gv.vx[vi], Y = Gv.vy[vi], Z = Gv.vz[vi];
+    ax[i] = absval(X); ay[i] = absval(Y); az[i] = absval(Z);
+    vel0<G>(p.vel, ax[i], ay[i], az[i], ux[i], uy[i], uz[i]);
+    ux[i] *= k; uy[i] *= k; uz[i] *= k;
+    lx[i] = rel(X, fr.cx) * fr.sc; ly[i] = rel(Y, fr.cy) * fr.sc; lz[i] = rel(Z, fr.cz) * fr.sc;
   }
-  const unsigned bad = __ballot_sync(GVOF_FULL, act && !ok);
+  // side plane normal s_i = e_i x u_e,i, with the norms of s, e and u_e
+  G sx[MAXI], sy[MAXI], sz[MAXI], ns[MAXI], ne[MAXI], nue[MAXI];
+  for (int i = 0; i < I; ++i) {
+    const int n = (i + 1 >= I) ? 0 : i + 1;
+    G eux, euy, euz;
+    vel0<G>(p.vel, G(0.5) * (ax[i] + ax[n]), G(0.5) * (ay[i] + ay[n]), G(0.5) * (az[i] + az[n]), eux,
+            euy, euz);
+    eux *= k; euy *= k; euz *= k;
+    const G ex = lx[n] - lx[i], ey = ly[n] - ly[i], ez = lz[n] - lz[i];
+    sx[i] = ey * euz - ez * euy; sy[i] = ez * eux - ex * euz; sz[i] = ex * euy - ey * eux;
+    ns[i] = sqrt(sx[i] * sx[i] + sy[i] * sy[i] + sz[i] * sz[i]);
+    ne[i] = sqrt(ex * ex + ey * ey + ez * ez);
+    nue[i] = sqrt(eux * eux + euy * euy + euz * euz);
+  }
+  const G tol = (G)1e-3;
+  unsigned bad = 0u;
+  G bxl[MAXI], byl[MAXI], bzl[MAXI];
+  for (int i = 0; i < I; ++i) {
+    const int pv = (i == 0) ? I - 1 : i - 1;
+    const G dx = sy[pv] * sz[i] - sz[pv] * sy[i], dy = sz[pv] * sx[i] - sx[pv] * sz[i],
+            dz = sx[pv] * sy[i] - sy[pv] * sx[i];
+    const G dd = dx * dx + dy * dy + dz * dz;
+    const bool ok = ns[i] > tol * ne[i] * nue[i] && ns[pv] > tol * ne[pv] * nue[pv] &&
+                    sqrt(dd) > tol * ns[pv] * ns[i];
+    if (ok) {
+      const G kk = (ux[i] * dx + uy[i] * dy + uz[i] * dz) / dd;
+      bxl[i] = lx[i] - kk * dx; byl[i] = ly[i] - kk * dy; bzl[i] = lz[i] - kk * dz;
+    } else {
+      bxl[i] = lx[i] - ux[i]; byl[i] = ly[i] - uy[i]; bzl[i] = lz[i] - uz[i];
+      bad |= 1u << i;
+    }
+  }
   fr.degenerate = __popc(bad);
   // side i joins back-traced vertices i and i+1: planar only if both lie
   // on its side plane
   const unsigned full_mask = (I >= 32) ? 0xffffffffu : ((1u << I) - 1u);
   fr.split = (bad | (((bad >> 1) | (bad << (I - 1))) & full_mask)) & full_mask;
-  // centroid of the back-traced loop and its vector area B
-  const G bxn = __shfl_sync(GVOF_FULL, bxl, nxt), byn = __shfl_sync(GVOF_FULL, byl, nxt),
-          bzn = __shfl_sync(GVOF_FULL, bzl, nxt);
-  const G inv_I = G(1) / (G)I;
-  const G xcx = wsum(act ? bxl : G(0)) * inv_I, xcy = wsum(act ? byl : G(0)) * inv_I,
-          xcz = wsum(act ? bzl : G(0)) * inv_I;
-  const G Bx = wsum(act ? G(0.5) * (byl * bzn - bzl * byn) : G(0));
-  const G By = wsum(act ? G(0.5) * (bzl * bxn - bxl * bzn) : G(0));
-  const G Bz = wsum(act ? G(0.5) * (bxl * byn - byl * bxn) : G(0));
-  // signed volume with the apex at the centroid (origin = face centroid)
+  // centroid of the back-traced loop, its vector area B, and the signed
+  // volume with the apex at the centroid (origin = face centroid)
   auto det3 = [](G ax_, G ay_, G az_, G bx_, G by_, G bz_, G cx_, G cy_, G cz_) {
     return ax_ * (by_ * cz_ - bz_ * cy_) + ay_ * (bz_ * cx_ - bx_ * cz_) +
            az_ * (bx_ * cy_ - by_ * cx_);
   };
-  const G l0x = __shfl_sync(GVOF_FULL, lx, 0), l0y = __shfl_sync(GVOF_FULL, ly, 0),
-          l0z = __shfl_sync(GVOF_FULL, lz, 0);
-  G v6 = G(0);
-  if (act) {
-    if (lane >= 1 && lane + 1 < I) v6 += det3(l0x, l0y, l0z, lx, ly, lz, lxn, lyn, lzn);
-    v6 += det3(lxn, lyn, lzn, lx, ly, lz, bxl, byl, bzl);       // side quad, fan
-    v6 += det3(lxn, lyn, lzn, bxl, byl, bzl, bxn, byn, bzn);    // from x_{i+1}
-    v6 += det3(bxn, byn, bzn, bxl, byl, bzl, xcx, xcy, xcz);    // bottom triangle
+  const G inv_I = G(1) / (G)I;
+  G sxc = 0, syc = 0, szc = 0, Bx = 0, By = 0, Bz = 0;
+  for (int i = 0; i < I; ++i) {
+    const int n = (i + 1 >= I) ? 0 : i + 1;
+    sxc += bxl[i]; syc += byl[i]; szc += bzl[i];
+    Bx += G(0.5) * (byl[i] * bzl[n] - bzl[i] * byl[n]);
+    By += G(0.5) * (bzl[i] * bxl[n] - bxl[i] * bzl[n]);
+    Bz += G(0.5) * (bxl[i] * byl[n] - byl[i] * bxl[n]);
   }
-  const G V0 = wsum(v6) / G(6);
+  const G xcx = sxc * inv_I, xcy = syc * inv_I, xcz = szc * inv_I;
+  G v6 = G(0);
+  for (int i = 0; i < I; ++i) {
+    const int n = (i + 1 >= I) ? 0 : i + 1;
+    if (i >= 1 && i + 1 < I) v6 += det3(lx[0], ly[0], lz[0], lx[i], ly[i], lz[i], lx[n], ly[n], lz[n]);
+    v6 += det3(lx[n], ly[n], lz[n], lx[i], ly[i], lz[i], bxl[i], byl[i], bzl[i]);       // side quad,
+    v6 += det3(lx[n], ly[n], lz[n], bxl[i], byl[i], bzl[i], bxl[n], byl[n], bzl[n]);    // fan from x_{i+1}
+    v6 += det3(bxl[n], byl[n], bzl[n], bxl[i], byl[i], bzl[i], xcx, xcy, xcz);          // bottom triangle
+  }
+  const G V0 = v6 / G(6);
   const G Vl = (G)Vd * (fr.sc * fr.sc * fr.sc);
   const G nB = nx * Bx + ny * By + nz * Bz;
   G lam = G(0);
-  fr.edgeon = 0;
   if (fabs(nB) > G(1e-8)) lam = G(3) * (V0 - Vl) / nB;
   else fr.edgeon = 1;
-  if (act) {
-    P.bx[lane] = lx; P.by[lane] = ly; P.bz[lane] = lz;
-    P.bx[I + lane] = bxl; P.by[I + lane] = byl; P.bz[I + lane] = bzl;
+  for (int i = 0; i < I; ++i) {
+    vx[i] = lx[i]; vy[i] = ly[i]; vz[i] = lz[i];
+    vx[I + i] = bxl[i]; vy[I + i] = byl[i]; vz[I + i] = bzl[i];
   }
-  if (lane == 0) {
-    P.bx[2 * I] = xcx + lam * nx;
-    P.by[2 * I] = xcy + lam * ny;
-    P.bz[2 * I] = xcz + lam * nz;
-  }
-  __syncwarp();
+  vx[2 * I] = xcx + lam * nx;
+  vy[2 * I] = xcy + lam * ny;
+  vz[2 * I] = xcz + lam * nz;
   // local bounding box of the polyhedron
-  const int nvb = 2 * I + 1;
-  const G big = (G)1e30;
-  G x0 = big, x1 = -big, y0 = big, y1 = -big, z0 = big, z1 = -big;
-  if (lane < nvb) {
-    x0 = x1 = P.bx[lane]; y0 = y1 = P.by[lane]; z0 = z1 = P.bz[lane];
+  fr.lo[0] = fr.hi[0] = vx[0]; fr.lo[1] = fr.hi[1] = vy[0]; fr.lo[2] = fr.hi[2] = vz[0];
+  for (int v = 1; v <= 2 * I; ++v) {
+    fr.lo[0] = min(fr.lo[0], vx[v]); fr.hi[0] = max(fr.hi[0], vx[v]);
+    fr.lo[1] = min(fr.lo[1], vy[v]); fr.hi[1] = max(fr.hi[1], vy[v]);
+    fr.lo[2] = min(fr.lo[2], vz[v]); fr.hi[2] = max(fr.hi[2], vz[v]);
   }
-  fr.lo[0] = wmin(x0); fr.lo[1] = wmin(y0); fr.lo[2] = wmin(z0);
-  fr.hi[0] = wmax(x1); fr.hi[1] = wmax(y1); fr.hi[2] = wmax(z1);
-  if (lane == 0) frs = fr;
-  __syncwarp();
   return true;
+}
+
+// FMFPA polyhedron of face j into shared memory by lane 0 (the other lanes
+// wait): the flux kernel's fallback beyond the prebuilt capacity and the
+// polyhedron export
+template <typename G>
+__device__ __noinline__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p, int j,
+                            double Vd, Poly<G>& P, FaceFrame<G>& frs, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = fmfpa_scalar<G>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
+  ok = __shfl_sync(GVOF_FULL, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 
 // EMFPA construction (Sec. 2.2.1) into P.b*: lane i holds face vertex i;
@@ -1131,6 +1141,68 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
   return v;
 }
 
+// FMFPA polyhedra of the first fm_cap active faces, one thread per face
+// (fmfpa_scalar), into the prebuilt buffer the flux kernel reads
+template <typename G>
+__global__ void __launch_bounds__(128) k_prebuild_fmfpa(DevMesh M, GeoView<G> Gv, DevState S) {
+  const unsigned n_af = (unsigned)S.cnt[kNAfaces];
+  const unsigned nb = (unsigned)min((int64_t)n_af, S.fm_cap);
+  G* fv = (G*)S.fm_v;
+  G* ff = (G*)S.fm_f;
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < nb; w += gridDim.x * blockDim.x) {
+    const int j = S.afaces[w];
+    const GridParam& gp = S.gp[M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j)];
+    const double Vd = S.srate[j] * gp.gdt;
+    G vx[kFmSlots], vy[kFmSlots], vz[kFmSlots];
+    FaceFrame<G> fr;
+    const bool ok = fmfpa_scalar<G>(M, Gv, gp, j, Vd, vx, vy, vz, fr);
+    S.fm_meta[w] = (uint32_t)fr.I | ((uint32_t)fr.degenerate << 8) | ((uint32_t)fr.edgeon << 16) |
+                   ((uint32_t)(ok ? 1 : 0) << 24);
+    if (!ok) continue;
+    S.fm_split[w] = fr.split;
+    G* f = ff + (size_t)w * 7;
+    f[0] = fr.L;
+    f[1] = fr.lo[0]; f[2] = fr.lo[1]; f[3] = fr.lo[2];
+    f[4] = fr.hi[0]; f[5] = fr.hi[1]; f[6] = fr.hi[2];
+    G* v = fv + (size_t)w * kFmSlots * 3;
+    for (int q = 0; q <= 2 * fr.I; ++q) {
+      v[3 * q] = vx[q]; v[3 * q + 1] = vy[q]; v[3 * q + 2] = vz[q];
+    }
+  }
+}
+
+// the FMFPA polyhedron of active face w: prebuilt below fm_cap, else built
+// here by lane 0 with the same arithmetic
+template <typename G>
+__device__ bool fmfpa_for_face(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, unsigned w,
+                               int j, const GridParam& p, double Vd, Poly<G>& P, FaceFrame<G>& fr,
+                               int lane) {
+  if ((int64_t)w >= S.fm_cap) return build_fmfpa<G>(M, Gv, p, j, Vd, P, fr, lane);
+  const uint32_t meta = S.fm_meta[w];
+  const int I = (int)(meta & 255u);
+  const bool ok = (meta >> 24) & 1u;
+  if (lane == 0) {
+    fr.I = I;
+    fr.degenerate = (int)((meta >> 8) & 255u);
+    fr.edgeon = (int)((meta >> 16) & 255u);
+    if (ok) {
+      const G* f = (const G*)S.fm_f + (size_t)w * 7;
+      fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
+      fr.L = f[0];
+      fr.sc = G(1) / fr.L;
+      fr.lo[0] = f[1]; fr.lo[1] = f[2]; fr.lo[2] = f[3];
+      fr.hi[0] = f[4]; fr.hi[1] = f[5]; fr.hi[2] = f[6];
+      fr.split = S.fm_split[w];
+    }
+  }
+  if (ok && lane <= 2 * I) {
+    const G* v = (const G*)S.fm_v + ((size_t)w * kFmSlots + lane) * 3;
+    P.bx[lane] = v[0]; P.by[lane] = v[1]; P.bz[lane] = v[2];
+  }
+  __syncwarp();
+  return ok;
+}
+
 template <typename G, int KIND>
 __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S) {
   __shared__ Poly<G> polys[kWarps];
@@ -1151,7 +1223,10 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
       __syncwarp();
     }
     const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
-    if (!build_polyhedron<G, KIND>(M, Gv, wgp[wib], j, Vd, P, fr, lane)) {
+    bool built;
+    if constexpr (KIND == VOF_FLUX_FMFPA) built = fmfpa_for_face<G>(M, Gv, S, w, j, wgp[wib], Vd, P, fr, lane);
+    else built = build_polyhedron<G, KIND>(M, Gv, wgp[wib], j, Vd, P, fr, lane);
+    if (!built) {
       if (lane == 0) S.VF[j] = 0.0;
       ++n_over;
       continue;
@@ -1262,6 +1337,8 @@ __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const
 namespace {
 template <typename G, int KIND>
 void flux_launch(const vof_ctx* c, int grid, cudaStream_t s) {
+  if constexpr (KIND == VOF_FLUX_FMFPA)
+    k_prebuild_fmfpa<G><<<kSMs * 8, 128, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
   k_flux<G, KIND><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
 }
 template <typename G>
@@ -1288,6 +1365,10 @@ void polyhedra_launch_kind(const vof_ctx* c, const int32_t* faces, int n, double
   }
 }
 }  // namespace
+
+int flux_launch_count(const vof_ctx* c) {
+  return c->opt.flux_polyhedron == VOF_FLUX_FMFPA ? 2 : 1;
+}
 
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s) {
   const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * 8;

@@ -17,6 +17,11 @@ constexpr int kSMs = 152;  // GB300
 constexpr int kMaxFaceVerts = 8;
 constexpr int kMaxEmfpaVerts = 6;  // 5I+1 EMFPA faces fit the 32-face capacity
 constexpr int kMaxLsfirIter = 16;  // LSFIR outer iterations at most
+// FMFPA polyhedra built ahead of the flux kernel: vertex slots per face and
+// the faces a context keeps room for (later active faces are built in the
+// flux kernel itself, with the same arithmetic)
+constexpr int kFmSlots = 2 * kMaxFaceVerts + 1;
+constexpr int64_t kFmCap = int64_t(4) << 20;
 static_assert(3 * kMaxEmfpaVerts + 1 <= VOF_MAX_POLY_VERTS && 2 * kMaxFaceVerts + 1 <= VOF_MAX_POLY_VERTS,
               "polyhedron export stride");
 
@@ -108,6 +113,14 @@ struct DevState {
   double *lnx, *lny, *lnz;
   float *lnx32, *lny32, *lnz32;
   unsigned long long* lturn;
+  // prebuilt FMFPA polyhedra of the first fm_cap active faces (FMFPA
+  // contexts): vertices [(w kFmSlots + k) 3 + d], frame [w 7] (L, lo xyz, hi
+  // xyz), meta [w] (I | degenerate << 8 | edge-on << 16 | built << 24),
+  // split [w]; in the precision of the path (float or double)
+  void* fm_v;
+  void* fm_f;
+  uint32_t *fm_meta, *fm_split;
+  int64_t fm_cap;
 };
 
 enum Cnt {
@@ -261,6 +274,9 @@ struct vof_ctx {
   double *lnx, *lny, *lnz;
   float *lnx32, *lny32, *lnz32;
   unsigned long long* lturn;
+  void *fm_v, *fm_f;
+  uint32_t *fm_meta, *fm_split;
+  int64_t fm_cap;
   // state (device)
   double* F;
   double *nx, *ny, *nz, *C;
@@ -348,6 +364,8 @@ inline DevState state_view(const vof_ctx* c) {
   s.lnx = c->lnx; s.lny = c->lny; s.lnz = c->lnz;
   s.lnx32 = c->lnx32; s.lny32 = c->lny32; s.lnz32 = c->lnz32;
   s.lturn = c->lturn;
+  s.fm_v = c->fm_v; s.fm_f = c->fm_f; s.fm_meta = c->fm_meta; s.fm_split = c->fm_split;
+  s.fm_cap = c->fm_cap;
   return s;
 }
 
@@ -415,6 +433,7 @@ cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);
 int reconstruct_launch_count(const vof_ctx* c);
 // flux (k_flux.cu)
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s);
+int flux_launch_count(const vof_ctx* c);
 cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int64_t cap_per_face,
                               int32_t* out, int32_t* counts, cudaStream_t s);
 cudaError_t launch_polyhedra(const vof_ctx* c, const int32_t* faces, int n, double* verts,
