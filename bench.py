@@ -42,8 +42,9 @@ from paper_2111_01524_gb300 import inputs as I  # noqa: E402
 
 METRIC = "VOF cell-steps/s (recon+advect) mixed vs FP64 at stated F error; p50/p99 latency"
 UNIT = "cell-steps/s"
-# algorithmic work per unit of the band kernels: flops of one FMFPA
-# construction and of one (face, cell) truncation with its divergence sum
+# algorithmic work per unit of the band kernels: flops of one flux-polyhedron
+# construction (k_prebuild, per active face) and of one (face, cell)
+# truncation with its divergence sum (k_flux)
 FLOPS_PER_ACTIVE_FACE = 350.0      # FMFPA construction
 FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
 # EMFPA (Sec. 2.2.1): one velocity per vertex instead of two but five
@@ -54,21 +55,27 @@ FLOPS_PER_TRUNCATION = 1200.0      # one (face, cell) truncation incl. volume
 # 6I loop entries (24 for a hex face, against 32)
 FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0, 2400.0),
          "nmfpa": (100.0, 900.0)}
-# ncu capture of one flux launch (128^3 deformation step, mixed: ~57,300 active
-# faces): dram__bytes_read.sum + dram__bytes_write.sum = 26.94 + 1.91 MB, i.e.
-# 504 B per active face, issue active 38.2%, FMA pipe 10.9%; valid for the
-# kernel source it was taken on (traffic is null for any other source)
-# ncu --set full of the mixed flux kernel (128^3 deformation, 4th step's launch, ~57,300
-# active faces) per flux-polyhedron construction; valid only for the source it was taken on
-FLUX_NCU = {"source_sha256": "7a54b07b36045e719d40c159eae763db9087befd9d978edae4e98ceaf4bb58bc",
-            "fmfpa": {"dram_bytes_per_active_face": 505.0, "issue_active": 0.398,
-                      "fma_pipe_active": 0.110, "capture": "profiles/k_flux_deformation128_mixed.md"},
-            "emfpa": {"dram_bytes_per_active_face": 505.0, "issue_active": 0.394,
-                      "fma_pipe_active": 0.108,
+# ncu --set full of the mixed flux kernel (128^3 deformation, 4th step's launch, ~57,400
+# active faces) per flux-polyhedron construction: dram__bytes_read.sum +
+# dram__bytes_write.sum per active face (the face and node data, the prebuilt
+# polyhedron, the candidate cells' tags, boxes and planes), issue-slot and FMA-pipe
+# use; valid only for the source it was taken on (traffic is null for any other)
+FLUX_NCU = {"source_sha256": "c02e1d7a480fd1d630b262a347e9a5d217555784cb478368906eb6a40b7dc49a",
+            "fmfpa": {"dram_bytes_per_active_face": 623.0, "issue_active": 0.472,
+                      "fma_pipe_active": 0.117, "capture": "profiles/k_flux_deformation128_mixed.md"},
+            "emfpa": {"dram_bytes_per_active_face": 629.0, "issue_active": 0.473,
+                      "fma_pipe_active": 0.124,
                       "capture": "profiles/k_flux_deformation128_mixed_emfpa.md"},
-            "nmfpa": {"dram_bytes_per_active_face": 436.0, "issue_active": 0.398,
-                      "fma_pipe_active": 0.110,
+            "nmfpa": {"dram_bytes_per_active_face": 598.0, "issue_active": 0.424,
+                      "fma_pipe_active": 0.118,
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
+# kernels one step launches: reconstruction (cell tags 1, node tags 3,
+# LSGIR 1 or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,
+# flux 1, update 2); the phase timers count the same kernels
+def kernels_per_step(recon="lsgir", n_out=4):
+    return 4 + (1 + 2 * n_out if recon == "lsfir" else 1) + 6
+
+
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
 N_SM = 152
@@ -225,10 +232,11 @@ def run_steps(ctx, vel, cfl, t_end, t, n, stream, timing=False):
 
 
 def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision, flux="fmfpa"):
-    """Roofline of the dominant kernel: algorithmic HBM bytes per launch for the
-    sweeps, algorithmic flops per launch for the band kernels."""
-    ms, launches = phase["ms"], phase["launches"]
-    per_launch_ms = ms / max(launches, 1)
+    """Roofline of the dominant phase's main kernel: algorithmic HBM bytes per
+    launch for the sweeps, algorithmic flops per launch for the band kernels.
+    Each phase runs once per step; the flux phase is the one k_flux launch."""
+    ms, calls = phase["ms"], phase["calls"]
+    per_launch_ms = ms / max(calls, 1)
     nc, nf, nv = grid_counts["n_cell"], grid_counts["n_face"], grid_counts["n_vert"]
     name = phase["name"]
     hbm_bytes = {
@@ -245,9 +253,13 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_bytes_per_launch": b, "peak_source": peak_kind}
     # band kernels: plain ALU arithmetic
-    # the counters describe the last advect (one launch of each band kernel)
+    # the counters describe the last advect (one launch of each band kernel);
+    # the flux kernel truncates polyhedra built by the polyhedra phase
     f_face, f_trunc = FLOPS[flux]
-    fl = ctx_counts["n_active_faces"] * f_face + ctx_counts["n_truncations"] * f_trunc
+    if name == "polyhedra":
+        fl = ctx_counts["n_active_faces"] * f_face
+    else:
+        fl = ctx_counts["n_truncations"] * f_trunc
     traffic, ncu = None, None
     if name == "flux" and precision == "mixed":
         import hashlib
@@ -436,7 +448,7 @@ def main_batch(a):
                        "rank0": {"grids": n, "cells": cells, "faces": int(ctx.n_face),
                                  "sides": [int(x) for x in sides], "autotuned_blocks": list(tuned)},
                        "parallelism": f"grids sharded over {ws} rank(s) by cells"},
-            "gpu_launches": 6 * a.steps,
+            "gpu_launches": kernels_per_step() * a.steps,
             "band": {"interfacial_cells": st["n_interfacial"], "active_faces": st["n_active_faces"],
                      "truncations_last_step": st["n_truncations"], "overflow": st["n_overflow"]},
             "clocks": clocks}
@@ -500,7 +512,7 @@ def main_tets(a):
                                    "rigid rotation, CFL 0.4", "cells": int(m["n_cell"]),
                        "flux_polyhedron": a.flux, "reconstruction": a.recon,
                        "parallelism": f"replicas x{ws}"},
-            "gpu_launches": 6 * a.steps, "clocks": res["mixed"]["clocks"],
+            "gpu_launches": kernels_per_step(a.recon) * a.steps, "clocks": res["mixed"]["clocks"],
             "fp64_path": {"value": res["fp64"]["value"],
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
                           "max_abs_F_diff_mixed_vs_fp64":
@@ -579,7 +591,7 @@ def main_deform2d(a):
             "config": {"workload": f"2D deformation (Sec. 4.3), quasi-2D grid {n} x 1 x {n}, "
                                    "cylinder r=0.15 at (0.5, 0.75), period 8, CFL 0.5, steps from t=0",
                        "cells": int(m["n_cell"]), "parallelism": f"replicas x{ws}"},
-            "gpu_launches": 6 * a.steps, "clocks": res["mixed"]["clocks"],
+            "gpu_launches": kernels_per_step() * a.steps, "clocks": res["mixed"]["clocks"],
             "fp64_path": {"value": res["fp64"]["value"],
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
                           "max_abs_F_diff_mixed_vs_fp64":
@@ -682,8 +694,9 @@ def main_serve(a):
                                    "grids of side log-uniform 24..64, N ~ U{10..200} steps",
                        "requests": n, "budget_bytes": srv.budget,
                        "parallelism": f"requests sharded over {ws} rank(s) by cell-steps"},
-            # per request: the first reconstruction (3 kernels), then 6 per step
-            "gpu_launches": int(sum(3 + 6 * r.n_steps for r in reqs)), "clocks": clocks,
+            # per request: the first reconstruction, then whole steps
+            "gpu_launches": int(sum(kernels_per_step() - 6 + kernels_per_step() * r.n_steps
+                                    for r in reqs)), "clocks": clocks,
             "serve": sm}
     print(json.dumps(line))
     return 0
@@ -847,8 +860,11 @@ def main():
         del ctxi
 
     peaks, peak_kind = measured_peaks()
-    dom = max(phases.items(), key=lambda kv: kv[1][0])
-    phase = {"name": dom[0], "ms": dom[1][0], "launches": dom[1][1]}
+    # the dominant kernel: the phase with the longest average launch (the flux
+    # phase is its one k_flux launch per step; LSFIR's reconstruction phase
+    # takes longer in total but over 1 + 2 n_out shorter launches)
+    dom = max(phases.items(), key=lambda kv: kv[1][0] / max(kv[1][1], 1))
+    phase = {"name": dom[0], "ms": dom[1][0], "calls": a.steps}
     rl = roofline(stats, phase, counts, peaks, peak_kind, clocks, a.precision, a.flux)
     launches = sum(n for _, n in phases.values())
 

@@ -293,12 +293,15 @@ vof_status vof_set_state(vof_ctx* ctx, const void* buf, int64_t bytes, void* str
 vof_status vof_get_stats(vof_ctx* ctx, vof_stats* out, void* stream);
 /* Per-phase device timing with CUDA events recorded on the launching
  * stream around each kernel of the step (off by default). Phases:
- * 0 cell tags, 1 node tags, 2 reconstruct (LSGIR + plane constant),
- * 3 face sweep, 4 flux (FMFPA + truncation), 5 update. vof_get_timing
- * synchronises, returns the accumulated milliseconds and launch counts of
- * the first n phases and resets them. */
+ * 0 cell tags, 1 node tags, 2 reconstruct (LSGIR or LSFIR + plane
+ * constant), 3 face sweep, 4 flux (truncation of the flux polyhedra),
+ * 5 update, 6 polyhedra (their construction, Sec. 2.2). vof_get_timing
+ * synchronises, returns the accumulated milliseconds and kernel launch
+ * counts (band-list kernels included) of the first n phases and resets
+ * them. */
 enum { VOF_PHASE_CELL_TAGS = 0, VOF_PHASE_NODE_TAGS = 1, VOF_PHASE_RECONSTRUCT = 2,
-       VOF_PHASE_FACE_SWEEP = 3, VOF_PHASE_FLUX = 4, VOF_PHASE_UPDATE = 5, VOF_NUM_PHASES = 6 };
+       VOF_PHASE_FACE_SWEEP = 3, VOF_PHASE_FLUX = 4, VOF_PHASE_UPDATE = 5,
+       VOF_PHASE_POLYHEDRA = 6, VOF_NUM_PHASES = 7 };
 vof_status vof_set_timing(vof_ctx* ctx, int on);
 vof_status vof_get_timing(vof_ctx* ctx, double* ms, int64_t* launches, int n);
 /* Allocation-free weighted sum: *out = sum over i < n of w[i] * F[i] (the

@@ -347,7 +347,7 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     CKI(dalloc(c, &c->C32, nc));
     CKI(dalloc(c, &c->cpl32, c->ncf));
   }
-  if (o.flux_polyhedron == VOF_FLUX_FMFPA) {
+  {
     // room for the polyhedra the flux kernel reads prebuilt
     c->fm_cap = std::min<int64_t>(nf, kFmCap);
     const size_t gs = o.precision == VOF_PREC_MIXED ? sizeof(float) : sizeof(double);
@@ -577,15 +577,17 @@ vof_status vof_reconstruct(vof_ctx* c, void* stream) {
 }
 
 static vof_status advect_launches(vof_ctx* c, cudaStream_t s) {
-  { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s); CK(launch_face_sweep(c, s)); }
-  { PhaseTimer tm(c, VOF_PHASE_FLUX, s, flux_launch_count(c)); CK(launch_flux(c, s)); }
-  { PhaseTimer tm(c, VOF_PHASE_UPDATE, s); CK(launch_update(c, s)); }
+  // launch counts: the kernels each phase launches (band-list kernels included)
+  { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s, 2); CK(launch_face_sweep(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_POLYHEDRA, s); CK(launch_prebuild(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_UPDATE, s, 2); CK(launch_update(c, s)); }
   return VOF_OK;
 }
 
 static vof_status reconstruct_launches(vof_ctx* c, cudaStream_t s) {
   { PhaseTimer t(c, VOF_PHASE_CELL_TAGS, s); CK(launch_cell_tags(c, s)); }
-  { PhaseTimer t(c, VOF_PHASE_NODE_TAGS, s); CK(launch_node_tags(c, s)); }
+  { PhaseTimer t(c, VOF_PHASE_NODE_TAGS, s, 3); CK(launch_node_tags(c, s)); }
   { PhaseTimer t(c, VOF_PHASE_RECONSTRUCT, s, reconstruct_launch_count(c)); CK(launch_reconstruct(c, s)); }
   return VOF_OK;
 }
@@ -716,6 +718,7 @@ vof_status vof_autotune(vof_ctx* c, const vof_velocity* vels, const double* t, c
   const bool timing = c->timing;
   c->timing = false;
   CK(launch_face_sweep(c, s));  // active faces of the current state (F is not changed)
+  CK(launch_prebuild(c, s));     // their flux polyhedra, which the flux launches only read
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

@@ -621,172 +621,145 @@ __device__ __noinline__ bool fmfpa_scalar(const DevMesh& M, const GeoView<G>& Gv
   return true;
 }
 
-// FMFPA polyhedron of face j into shared memory by lane 0 (the other lanes
-// wait): the flux kernel's fallback beyond the prebuilt capacity and the
-// polyhedron export
+// EMFPA construction (Sec. 2.2.1) by one thread: every vertex goes back
+// along its own streak line with its own velocity at t^{n+1/2} (Eq.
+// streak-line2); side face i (x_i, x_{i+1} and their back-traced points) is
+// represented by its vertex-average centre; the centroid of the back-traced
+// loop moves along the face normal by the closed-form amount that makes the
+// signed volume of the 5I+1 faces equal V_d. Faces sharing an edge compute
+// the same four side points from the same two nodes, so their side
+// triangles coincide. Vertices: x_0..x_{I-1}, back-traced I..2I-1, side
+// centres 2I..3I-1, apex 3I.
 template <typename G>
-__device__ __noinline__ bool build_fmfpa(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p, int j,
-                            double Vd, Poly<G>& P, FaceFrame<G>& frs, int lane) {
-  int ok = 0;
-  if (lane == 0) ok = fmfpa_scalar<G>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
-  ok = __shfl_sync(GVOF_FULL, ok, 0);
-  __syncwarp();
-  return ok != 0;
-}
-
-// EMFPA construction (Sec. 2.2.1) into P.b*: lane i holds face vertex i;
-// the vertex goes back along its own streak line with its own velocity at
-// t^{n+1/2} (Eq. streak-line2); side face i (x_i, x_{i+1} and their
-// back-traced points) is represented by its vertex-average centre; the
-// centroid of the back-traced loop moves along the face normal by the
-// closed-form amount that makes the signed volume of the 5I+1 faces equal
-// V_d. Faces sharing an edge compute the same four side points from the
-// same two nodes, so their side triangles coincide.
-template <typename G>
-__device__ GVOF_OUTER_ATTR bool build_emfpa(const DevMesh& M, const GeoView<G>& Gv,
-                                         const GridParam& p, int j, double Vd, Poly<G>& P,
-                                         FaceFrame<G>& frs, int lane) {
-  FaceFrame<G> fr;
+__device__ __noinline__ bool emfpa_scalar(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p, int j,
+                                          double Vd, G* vx, G* vy, G* vz, FaceFrame<G>& fr) {
   const int64_t fb = M.fptr[j];
   const int I = (int)(M.fptr[j + 1] - fb);
   fr.I = I;
-  if (I > kMaxEmfpaVerts || I < 3) {
-    if (lane == 0) frs.I = I;
-    __syncwarp();
-    return false;
-  }
+  fr.degenerate = 0;
+  fr.edgeon = 0;
+  fr.split = 0u;
+  if (I > kMaxEmfpaVerts || I < 3) return false;
   fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
   fr.L = sqrt(Gv.fa[j]);
   fr.sc = G(1) / fr.L;
   const G nx = Gv.fnx[j], ny = Gv.fny[j], nz = Gv.fnz[j];
-  const bool act = lane < I;
-  const int vi = act ? M.fvert[fb + lane] : M.fvert[fb];
-  const typename Prec<G>::A X = Gv.vx[vi], Y = Gv.vy[vi], Z = Gv.vz[vi];
-  const int nxt = (lane + 1 >= I) ? 0 : lane + 1;
-  // vertex velocity times dt, in face-local scaled units
-  G ux, uy, uz;
-  vel0<G>(p.vel, absval(X), absval(Y), absval(Z), ux, uy, uz);
   const G k = (G)(p.g * p.dt) * fr.sc;
-  const G lx = rel(X, fr.cx) * fr.sc, ly = rel(Y, fr.cy) * fr.sc, lz = rel(Z, fr.cz) * fr.sc;
-  const G bxl = lx - k * ux, byl = ly - k * uy, bzl = lz - k * uz;
-  const G lxn = __shfl_sync(GVOF_FULL, lx, nxt), lyn = __shfl_sync(GVOF_FULL, ly, nxt),
-          lzn = __shfl_sync(GVOF_FULL, lz, nxt);
-  const G bxn = __shfl_sync(GVOF_FULL, bxl, nxt), byn = __shfl_sync(GVOF_FULL, byl, nxt),
-          bzn = __shfl_sync(GVOF_FULL, bzl, nxt);
-  // centre of side face i
-  const G sx = G(0.25) * (lx + lxn + bxl + bxn), sy = G(0.25) * (ly + lyn + byl + byn),
-          sz = G(0.25) * (lz + lzn + bzl + bzn);
-  fr.degenerate = 0;
-  fr.split = 0u;
-  const G inv_I = G(1) / (G)I;
-  const G xcx = wsum(act ? bxl : G(0)) * inv_I, xcy = wsum(act ? byl : G(0)) * inv_I,
-          xcz = wsum(act ? bzl : G(0)) * inv_I;
-  const G Bx = wsum(act ? G(0.5) * (byl * bzn - bzl * byn) : G(0));
-  const G By = wsum(act ? G(0.5) * (bzl * bxn - bxl * bzn) : G(0));
-  const G Bz = wsum(act ? G(0.5) * (bxl * byn - byl * bxn) : G(0));
+  for (int i = 0; i < I; ++i) {
+    const int vi = M.fvert[fb + i];
+    const typename Prec<G>::A X = Gv.vx[vi], Y = Gv.vy[vi], Z = Gv.vz[vi];
+    G ux, uy, uz;
+    vel0<G>(p.vel, absval(X), absval(Y), absval(Z), ux, uy, uz);
+    const G lx = rel(X, fr.cx) * fr.sc, ly = rel(Y, fr.cy) * fr.sc, lz = rel(Z, fr.cz) * fr.sc;
+    vx[i] = lx; vy[i] = ly; vz[i] = lz;
+    vx[I + i] = lx - k * ux; vy[I + i] = ly - k * uy; vz[I + i] = lz - k * uz;
+  }
   auto det3 = [](G ax_, G ay_, G az_, G bx_, G by_, G bz_, G cx_, G cy_, G cz_) {
     return ax_ * (by_ * cz_ - bz_ * cy_) + ay_ * (bz_ * cx_ - bx_ * cz_) +
            az_ * (bx_ * cy_ - by_ * cx_);
   };
-  const G l0x = __shfl_sync(GVOF_FULL, lx, 0), l0y = __shfl_sync(GVOF_FULL, ly, 0),
-          l0z = __shfl_sync(GVOF_FULL, lz, 0);
+  const G inv_I = G(1) / (G)I;
+  G sxc = 0, syc = 0, szc = 0, Bx = 0, By = 0, Bz = 0;
+  for (int i = 0; i < I; ++i) {
+    const int n = (i + 1 >= I) ? 0 : i + 1;
+    // centre of side face i
+    vx[2 * I + i] = G(0.25) * (vx[i] + vx[n] + vx[I + i] + vx[I + n]);
+    vy[2 * I + i] = G(0.25) * (vy[i] + vy[n] + vy[I + i] + vy[I + n]);
+    vz[2 * I + i] = G(0.25) * (vz[i] + vz[n] + vz[I + i] + vz[I + n]);
+    const G bx = vx[I + i], by = vy[I + i], bz = vz[I + i], bxn = vx[I + n], byn = vy[I + n], bzn = vz[I + n];
+    sxc += bx; syc += by; szc += bz;
+    Bx += G(0.5) * (by * bzn - bz * byn);
+    By += G(0.5) * (bz * bxn - bx * bzn);
+    Bz += G(0.5) * (bx * byn - by * bxn);
+  }
+  const G xcx = sxc * inv_I, xcy = syc * inv_I, xcz = szc * inv_I;
   // signed volume with the apex at the centroid (origin = face centroid)
   G v6 = G(0);
-  if (act) {
-    if (lane >= 1 && lane + 1 < I) v6 += det3(l0x, l0y, l0z, lx, ly, lz, lxn, lyn, lzn);
-    v6 += det3(lxn, lyn, lzn, lx, ly, lz, sx, sy, sz);      // side triangles
-    v6 += det3(lx, ly, lz, bxl, byl, bzl, sx, sy, sz);
-    v6 += det3(bxl, byl, bzl, bxn, byn, bzn, sx, sy, sz);
+  for (int i = 0; i < I; ++i) {
+    const int n = (i + 1 >= I) ? 0 : i + 1;
+    const G lx = vx[i], ly = vy[i], lz = vz[i], lxn = vx[n], lyn = vy[n], lzn = vz[n];
+    const G bx = vx[I + i], by = vy[I + i], bz = vz[I + i], bxn = vx[I + n], byn = vy[I + n], bzn = vz[I + n];
+    const G sx = vx[2 * I + i], sy = vy[2 * I + i], sz = vz[2 * I + i];
+    if (i >= 1 && i + 1 < I) v6 += det3(vx[0], vy[0], vz[0], lx, ly, lz, lxn, lyn, lzn);
+    v6 += det3(lxn, lyn, lzn, lx, ly, lz, sx, sy, sz);  // side triangles
+    v6 += det3(lx, ly, lz, bx, by, bz, sx, sy, sz);
+    v6 += det3(bx, by, bz, bxn, byn, bzn, sx, sy, sz);
     v6 += det3(bxn, byn, bzn, lxn, lyn, lzn, sx, sy, sz);
-    v6 += det3(bxn, byn, bzn, bxl, byl, bzl, xcx, xcy, xcz);  // bottom triangle
+    v6 += det3(bxn, byn, bzn, bx, by, bz, xcx, xcy, xcz);  // bottom triangle
   }
-  const G V0 = wsum(v6) / G(6);
+  const G V0 = v6 / G(6);
   const G Vl = (G)Vd * (fr.sc * fr.sc * fr.sc);
   const G nB = nx * Bx + ny * By + nz * Bz;
   G lam = G(0);
-  fr.edgeon = 0;
   if (fabs(nB) > G(1e-8)) lam = G(3) * (V0 - Vl) / nB;
   else fr.edgeon = 1;
-  if (act) {
-    P.bx[lane] = lx; P.by[lane] = ly; P.bz[lane] = lz;
-    P.bx[I + lane] = bxl; P.by[I + lane] = byl; P.bz[I + lane] = bzl;
-    P.bx[2 * I + lane] = sx; P.by[2 * I + lane] = sy; P.bz[2 * I + lane] = sz;
+  vx[3 * I] = xcx + lam * nx;
+  vy[3 * I] = xcy + lam * ny;
+  vz[3 * I] = xcz + lam * nz;
+  fr.lo[0] = fr.hi[0] = vx[0]; fr.lo[1] = fr.hi[1] = vy[0]; fr.lo[2] = fr.hi[2] = vz[0];
+  for (int v = 1; v <= 3 * I; ++v) {
+    fr.lo[0] = min(fr.lo[0], vx[v]); fr.hi[0] = max(fr.hi[0], vx[v]);
+    fr.lo[1] = min(fr.lo[1], vy[v]); fr.hi[1] = max(fr.hi[1], vy[v]);
+    fr.lo[2] = min(fr.lo[2], vz[v]); fr.hi[2] = max(fr.hi[2], vz[v]);
   }
-  if (lane == 0) {
-    P.bx[3 * I] = xcx + lam * nx;
-    P.by[3 * I] = xcy + lam * ny;
-    P.bz[3 * I] = xcz + lam * nz;
-  }
-  __syncwarp();
-  const G big = (G)1e30;
-  G x0 = big, x1 = -big, y0 = big, y1 = -big, z0 = big, z1 = -big;
-  if (lane < 3 * I + 1) {
-    x0 = x1 = P.bx[lane]; y0 = y1 = P.by[lane]; z0 = z1 = P.bz[lane];
-  }
-  fr.lo[0] = wmin(x0); fr.lo[1] = wmin(y0); fr.lo[2] = wmin(z0);
-  fr.hi[0] = wmax(x1); fr.hi[1] = wmax(y1); fr.hi[2] = wmax(z1);
-  if (lane == 0) frs = fr;
-  __syncwarp();
   return true;
 }
 
-// NMFPA construction (Sec. 2.2.3) into P.b*: every vertex moves back by
+// NMFPA construction (Sec. 2.2.3) by one thread: every vertex moves back by
 // dt times the velocity at the face centre at t^{n+1/2}, so the polyhedron
 // is the prism between the face and its translate, of volume V_d by itself
 template <typename G>
-__device__ GVOF_OUTER_ATTR bool build_nmfpa(const DevMesh& M, const GeoView<G>& Gv,
-                                         const GridParam& p, int j, Poly<G>& P, FaceFrame<G>& frs,
-                                         int lane) {
-  FaceFrame<G> fr;
+__device__ __noinline__ bool nmfpa_scalar(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p, int j,
+                                          G* vx, G* vy, G* vz, FaceFrame<G>& fr) {
   const int64_t fb = M.fptr[j];
   const int I = (int)(M.fptr[j + 1] - fb);
   fr.I = I;
-  if (I > MAXI || I < 3) {
-    if (lane == 0) frs.I = I;
-    __syncwarp();
-    return false;
-  }
-  fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
-  fr.L = sqrt(Gv.fa[j]);
-  fr.sc = G(1) / fr.L;
   fr.degenerate = 0;
   fr.edgeon = 0;
   fr.split = 0u;
-  const bool act = lane < I;
-  const int vi = act ? M.fvert[fb + lane] : M.fvert[fb];
+  if (I > MAXI || I < 3) return false;
+  fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
+  fr.L = sqrt(Gv.fa[j]);
+  fr.sc = G(1) / fr.L;
   G ux, uy, uz;
   vel0<G>(p.vel, absval(fr.cx), absval(fr.cy), absval(fr.cz), ux, uy, uz);
   const G k = (G)(p.g * p.dt) * fr.sc;
-  const G lx = rel(Gv.vx[vi], fr.cx) * fr.sc, ly = rel(Gv.vy[vi], fr.cy) * fr.sc,
-          lz = rel(Gv.vz[vi], fr.cz) * fr.sc;
-  const G bxl = lx - k * ux, byl = ly - k * uy, bzl = lz - k * uz;
-  if (act) {
-    P.bx[lane] = lx; P.by[lane] = ly; P.bz[lane] = lz;
-    P.bx[I + lane] = bxl; P.by[I + lane] = byl; P.bz[I + lane] = bzl;
+  for (int i = 0; i < I; ++i) {
+    const int vi = M.fvert[fb + i];
+    const G lx = rel(Gv.vx[vi], fr.cx) * fr.sc, ly = rel(Gv.vy[vi], fr.cy) * fr.sc,
+            lz = rel(Gv.vz[vi], fr.cz) * fr.sc;
+    vx[i] = lx; vy[i] = ly; vz[i] = lz;
+    vx[I + i] = lx - k * ux; vy[I + i] = ly - k * uy; vz[I + i] = lz - k * uz;
   }
-  const G big = (G)1e30;
-  G x0 = big, x1 = -big, y0 = big, y1 = -big, z0 = big, z1 = -big;
-  if (act) {
-    x0 = fmin(lx, bxl); x1 = fmax(lx, bxl);
-    y0 = fmin(ly, byl); y1 = fmax(ly, byl);
-    z0 = fmin(lz, bzl); z1 = fmax(lz, bzl);
+  fr.lo[0] = fr.hi[0] = vx[0]; fr.lo[1] = fr.hi[1] = vy[0]; fr.lo[2] = fr.hi[2] = vz[0];
+  for (int v = 1; v < 2 * I; ++v) {
+    fr.lo[0] = min(fr.lo[0], vx[v]); fr.hi[0] = max(fr.hi[0], vx[v]);
+    fr.lo[1] = min(fr.lo[1], vy[v]); fr.hi[1] = max(fr.hi[1], vy[v]);
+    fr.lo[2] = min(fr.lo[2], vz[v]); fr.hi[2] = max(fr.hi[2], vz[v]);
   }
-  fr.lo[0] = wmin(x0); fr.lo[1] = wmin(y0); fr.lo[2] = wmin(z0);
-  fr.hi[0] = wmax(x1); fr.hi[1] = wmax(y1); fr.hi[2] = wmax(z1);
-  __syncwarp();
-  if (lane == 0) frs = fr;
-  __syncwarp();
   return true;
 }
 
-// the flux polyhedron of the context's construction
+// the flux polyhedron of the context's construction, by one thread
 template <typename G, int KIND>
-__device__ __forceinline__ bool build_polyhedron(const DevMesh& M, const GeoView<G>& Gv,
-                                                 const GridParam& p, int j, double Vd, Poly<G>& P,
-                                                 FaceFrame<G>& frs, int lane) {
-  if constexpr (KIND == VOF_FLUX_EMFPA) return build_emfpa<G>(M, Gv, p, j, Vd, P, frs, lane);
-  else if constexpr (KIND == VOF_FLUX_NMFPA) return build_nmfpa<G>(M, Gv, p, j, P, frs, lane);
-  else return build_fmfpa<G>(M, Gv, p, j, Vd, P, frs, lane);
+__device__ __forceinline__ bool poly_scalar(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p,
+                                            int j, double Vd, G* vx, G* vy, G* vz, FaceFrame<G>& fr) {
+  if constexpr (KIND == VOF_FLUX_EMFPA) return emfpa_scalar<G>(M, Gv, p, j, Vd, vx, vy, vz, fr);
+  else if constexpr (KIND == VOF_FLUX_NMFPA) return nmfpa_scalar<G>(M, Gv, p, j, vx, vy, vz, fr);
+  else return fmfpa_scalar<G>(M, Gv, p, j, Vd, vx, vy, vz, fr);
+}
+
+// the polyhedron of face j into shared memory by lane 0 (the other lanes
+// wait): the flux kernel's fallback beyond the prebuilt capacity and the
+// polyhedron export
+template <typename G, int KIND>
+__device__ __noinline__ bool build_polyhedron(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p,
+                                              int j, double Vd, Poly<G>& P, FaceFrame<G>& frs, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = poly_scalar<G, KIND>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
+  ok = __shfl_sync(GVOF_FULL, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 
 __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key) {
@@ -1141,10 +1114,10 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
   return v;
 }
 
-// FMFPA polyhedra of the first fm_cap active faces, one thread per face
-// (fmfpa_scalar), into the prebuilt buffer the flux kernel reads
-template <typename G>
-__global__ void __launch_bounds__(128) k_prebuild_fmfpa(DevMesh M, GeoView<G> Gv, DevState S) {
+// flux polyhedra of the first fm_cap active faces, one thread per face
+// (poly_scalar), into the prebuilt buffer the flux kernel reads
+template <typename G, int KIND>
+__global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevState S) {
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
   const unsigned nb = (unsigned)min((int64_t)n_af, S.fm_cap);
   G* fv = (G*)S.fm_v;
@@ -1155,7 +1128,7 @@ __global__ void __launch_bounds__(128) k_prebuild_fmfpa(DevMesh M, GeoView<G> Gv
     const double Vd = S.srate[j] * gp.gdt;
     G vx[kFmSlots], vy[kFmSlots], vz[kFmSlots];
     FaceFrame<G> fr;
-    const bool ok = fmfpa_scalar<G>(M, Gv, gp, j, Vd, vx, vy, vz, fr);
+    const bool ok = poly_scalar<G, KIND>(M, Gv, gp, j, Vd, vx, vy, vz, fr);
     S.fm_meta[w] = (uint32_t)fr.I | ((uint32_t)fr.degenerate << 8) | ((uint32_t)fr.edgeon << 16) |
                    ((uint32_t)(ok ? 1 : 0) << 24);
     if (!ok) continue;
@@ -1165,19 +1138,19 @@ __global__ void __launch_bounds__(128) k_prebuild_fmfpa(DevMesh M, GeoView<G> Gv
     f[1] = fr.lo[0]; f[2] = fr.lo[1]; f[3] = fr.lo[2];
     f[4] = fr.hi[0]; f[5] = fr.hi[1]; f[6] = fr.hi[2];
     G* v = fv + (size_t)w * kFmSlots * 3;
-    for (int q = 0; q <= 2 * fr.I; ++q) {
+    for (int q = 0; q < base_verts<KIND>(fr.I); ++q) {
       v[3 * q] = vx[q]; v[3 * q + 1] = vy[q]; v[3 * q + 2] = vz[q];
     }
   }
 }
 
-// the FMFPA polyhedron of active face w: prebuilt below fm_cap, else built
+// the flux polyhedron of active face w: prebuilt below fm_cap, else built
 // here by lane 0 with the same arithmetic
-template <typename G>
-__device__ bool fmfpa_for_face(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, unsigned w,
-                               int j, const GridParam& p, double Vd, Poly<G>& P, FaceFrame<G>& fr,
-                               int lane) {
-  if ((int64_t)w >= S.fm_cap) return build_fmfpa<G>(M, Gv, p, j, Vd, P, fr, lane);
+template <typename G, int KIND>
+__device__ bool poly_for_face(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, unsigned w,
+                              int j, const GridParam& p, double Vd, Poly<G>& P, FaceFrame<G>& fr,
+                              int lane) {
+  if ((int64_t)w >= S.fm_cap) return build_polyhedron<G, KIND>(M, Gv, p, j, Vd, P, fr, lane);
   const uint32_t meta = S.fm_meta[w];
   const int I = (int)(meta & 255u);
   const bool ok = (meta >> 24) & 1u;
@@ -1195,12 +1168,21 @@ __device__ bool fmfpa_for_face(const DevMesh& M, const GeoView<G>& Gv, const Dev
       fr.split = S.fm_split[w];
     }
   }
-  if (ok && lane <= 2 * I) {
+  if (ok && lane < base_verts<KIND>(I)) {
     const G* v = (const G*)S.fm_v + ((size_t)w * kFmSlots + lane) * 3;
     P.bx[lane] = v[0]; P.by[lane] = v[1]; P.bz[lane] = v[2];
   }
   __syncwarp();
   return ok;
+}
+
+// the next active face for this warp: faces are dealt one at a time from a
+// counter, so a warp that drew cheap faces takes more and none idles while
+// another still holds a queue (the results do not depend on the order)
+__device__ __forceinline__ unsigned next_face(const DevState& S, int lane) {
+  unsigned w = 0u;
+  if (lane == 0) w = (unsigned)atomicAdd(S.cnt + kFluxNext, 1ull);
+  return __shfl_sync(GVOF_FULL, w, 0);
 }
 
 template <typename G, int KIND>
@@ -1213,7 +1195,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
   FaceFrame<G>& fr = wfr[wib];
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
   unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0;
-  for (unsigned w = blockIdx.x * kWarps + wib; w < n_af; w += gridDim.x * kWarps) {
+  for (unsigned w = next_face(S, lane); w < n_af; w = next_face(S, lane)) {
     const int j = S.afaces[w];
     // the face's grid parameters, staged in shared memory (read at use)
     {
@@ -1223,10 +1205,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
       __syncwarp();
     }
     const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
-    bool built;
-    if constexpr (KIND == VOF_FLUX_FMFPA) built = fmfpa_for_face<G>(M, Gv, S, w, j, wgp[wib], Vd, P, fr, lane);
-    else built = build_polyhedron<G, KIND>(M, Gv, wgp[wib], j, Vd, P, fr, lane);
-    if (!built) {
+    if (!poly_for_face<G, KIND>(M, Gv, S, w, j, wgp[wib], Vd, P, fr, lane)) {
       if (lane == 0) S.VF[j] = 0.0;
       ++n_over;
       continue;
@@ -1336,9 +1315,19 @@ __global__ void k_polyhedra(DevMesh M, GeoView<G> Gv, const GridParam* gp, const
 
 namespace {
 template <typename G, int KIND>
+void prebuild_launch(const vof_ctx* c, cudaStream_t s) {
+  k_prebuild<G, KIND><<<kSMs * 8, 128, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
+}
+template <typename G>
+void prebuild_launch_kind(const vof_ctx* c, cudaStream_t s) {
+  switch (c->opt.flux_polyhedron) {
+    case VOF_FLUX_EMFPA: prebuild_launch<G, VOF_FLUX_EMFPA>(c, s); break;
+    case VOF_FLUX_NMFPA: prebuild_launch<G, VOF_FLUX_NMFPA>(c, s); break;
+    default: prebuild_launch<G, VOF_FLUX_FMFPA>(c, s); break;
+  }
+}
+template <typename G, int KIND>
 void flux_launch(const vof_ctx* c, int grid, cudaStream_t s) {
-  if constexpr (KIND == VOF_FLUX_FMFPA)
-    k_prebuild_fmfpa<G><<<kSMs * 8, 128, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
   k_flux<G, KIND><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
 }
 template <typename G>
@@ -1366,12 +1355,16 @@ void polyhedra_launch_kind(const vof_ctx* c, const int32_t* faces, int n, double
 }
 }  // namespace
 
-int flux_launch_count(const vof_ctx* c) {
-  return c->opt.flux_polyhedron == VOF_FLUX_FMFPA ? 2 : 1;
+cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s) {
+  if (c->opt.precision == VOF_PREC_MIXED) prebuild_launch_kind<float>(c, s);
+  else prebuild_launch_kind<double>(c, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s) {
   const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * 8;
+  const cudaError_t e = cudaMemsetAsync(c->cnt + kFluxNext, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
   if (c->opt.precision == VOF_PREC_MIXED) flux_launch_kind<float>(c, grid, s);
   else flux_launch_kind<double>(c, grid, s);
   return cudaGetLastError();

@@ -17,10 +17,10 @@ constexpr int kSMs = 152;  // GB300
 constexpr int kMaxFaceVerts = 8;
 constexpr int kMaxEmfpaVerts = 6;  // 5I+1 EMFPA faces fit the 32-face capacity
 constexpr int kMaxLsfirIter = 16;  // LSFIR outer iterations at most
-// FMFPA polyhedra built ahead of the flux kernel: vertex slots per face and
+// flux polyhedra built ahead of the flux kernel: vertex slots per face and
 // the faces a context keeps room for (later active faces are built in the
 // flux kernel itself, with the same arithmetic)
-constexpr int kFmSlots = 2 * kMaxFaceVerts + 1;
+constexpr int kFmSlots = VOF_MAX_POLY_VERTS;
 constexpr int64_t kFmCap = int64_t(4) << 20;
 static_assert(3 * kMaxEmfpaVerts + 1 <= VOF_MAX_POLY_VERTS && 2 * kMaxFaceVerts + 1 <= VOF_MAX_POLY_VERTS,
               "polyhedron export stride");
@@ -113,8 +113,8 @@ struct DevState {
   double *lnx, *lny, *lnz;
   float *lnx32, *lny32, *lnz32;
   unsigned long long* lturn;
-  // prebuilt FMFPA polyhedra of the first fm_cap active faces (FMFPA
-  // contexts): vertices [(w kFmSlots + k) 3 + d], frame [w 7] (L, lo xyz, hi
+  // prebuilt flux polyhedra of the first fm_cap active faces: vertices
+  // [(w kFmSlots + k) 3 + d], frame [w 7] (L, lo xyz, hi
   // xyz), meta [w] (I | degenerate << 8 | edge-on << 16 | built << 24),
   // split [w]; in the precision of the path (float or double)
   void* fm_v;
@@ -138,6 +138,7 @@ enum Cnt {
   kBandCellsOk = 12, // the band cell list of the last advect is valid
   kBandNodesOk = 13, // the band node list of the last reconstruction is valid
   kNInitList = 14,   // cells the initial surface may cross (vof_init_fraction)
+  kFluxNext = 15,    // next active face a flux warp takes (reset before each launch)
   kNCnt = 16
 };
 constexpr int kRedSlots = 2 * 1024;
@@ -432,8 +433,9 @@ cudaError_t launch_init_fraction(const vof_ctx* c, const vof_shape* shape, int n
 cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);
 int reconstruct_launch_count(const vof_ctx* c);
 // flux (k_flux.cu)
+// the flux polyhedra of the active faces (up to fm_cap), then the truncations
+cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s);
-int flux_launch_count(const vof_ctx* c);
 cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int64_t cap_per_face,
                               int32_t* out, int32_t* counts, cudaStream_t s);
 cudaError_t launch_polyhedra(const vof_ctx* c, const int32_t* faces, int n, double* verts,

@@ -393,7 +393,7 @@ class Context:
         return [verts[i, :npts(counts[i])].copy() if counts[i] > 0 else None
                 for i in range(len(faces))]
 
-    PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update")
+    PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update", "polyhedra")
 
     def set_timing(self, on=True):
         _check(lib().vof_set_timing(self._h, 1 if on else 0))
