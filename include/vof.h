@@ -191,7 +191,16 @@ typedef struct {
 vof_status vof_init_fraction(vof_ctx* ctx, const vof_shape* shape, int ndiv, void* stream);
 
 /* Volume fraction F [n_cell] (host or device pointer, see `mem`). Setting F
- * invalidates the reconstruction: call vof_reconstruct next. */
+ * invalidates the reconstruction: call vof_reconstruct next. The volume
+ * bookkeeping of vof_stats restarts from this F. When F differs from the
+ * library's copy only in cells the last advect could change (its band:
+ * owner and neighbour of each active face, and the interfacial cells), the
+ * next sweeps stay band-limited, so a caller that reads F back and sets it
+ * again each step pays no full sweep; any other change makes them full. The
+ * results are those of full sweeps either way. A host F goes through a
+ * device copy and the call synchronises the stream before it returns.
+ * VOF_EINVAL for a NULL argument or (host F) a mesh with fewer faces than
+ * cells, which no closed mesh has. */
 vof_status vof_set_fraction(vof_ctx* ctx, const double* F, int mem, void* stream);
 vof_status vof_get_fraction(vof_ctx* ctx, double* F, int mem, void* stream);
 

@@ -525,10 +525,18 @@ void vof_destroy(vof_ctx* c) {
 vof_status vof_set_fraction(vof_ctx* c, const double* F, int mem, void* stream) {
   if (!c || !F) return fail(VOF_EINVAL, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(c->F, F, sizeof(double) * c->nc, kind_to_dev(mem), s));
-  // the volume bookkeeping starts from this F, and the next sweeps are full
+  // host values come in through the face-volume export buffer (n_face >= 2
+  // n_cell for any closed mesh; scratch between steps)
+  const double* src = F;
+  if (mem != VOF_MEM_DEVICE) {
+    if (c->nf < c->nc) return fail(VOF_EINVAL, "mesh has fewer faces than cells");
+    CK(cudaMemcpyAsync(c->Vd, F, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s));
+    src = c->Vd;
+  }
+  // the next sweeps stay band-limited if only band cells of the last advect
+  // change, else they are full; the volume bookkeeping starts from this F
+  CK(launch_set_fraction(c, src, s));
   CK(cudaMemsetAsync(c->acc, 0, sizeof(double) * kNAcc * kAccSlots, s));
-  CK(cudaMemsetAsync(c->cnt + kBandCellsOk, 0, 2 * sizeof(unsigned long long), s));
   if (mem != VOF_MEM_DEVICE) CK(cudaStreamSynchronize(s));
   c->recon_valid = false;
   return VOF_OK;

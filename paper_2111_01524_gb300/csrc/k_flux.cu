@@ -55,6 +55,16 @@ namespace {
 #else
 #define GVOF_OUTER_ATTR __noinline__
 #endif
+#ifdef GVOF_INLINE_CLIP
+#define GVOF_CLIP_ATTR __forceinline__
+#else
+#define GVOF_CLIP_ATTR __noinline__
+#endif
+#ifdef GVOF_INLINE_CELL
+#define GVOF_CELL_ATTR __forceinline__
+#else
+#define GVOF_CELL_ATTR __noinline__
+#endif
 
 constexpr int kWarps = 4;
 constexpr int MAXI = kMaxFaceVerts;   // face vertices
@@ -281,7 +291,7 @@ __device__ __noinline__ void compact(Poly<G>& P, PolyState& st, int lane) {
 // returns 0: unchanged, 1: clipped, 2: empty. err bit0: capacity overflow
 // or inconsistent topology (the face's V_F is then unreliable and counted).
 template <typename G>
-__device__ __noinline__ int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane,
+__device__ GVOF_CLIP_ATTR int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane,
                                  unsigned& err) {
   if (st.nv > NV - NR) compact(P, st, lane);
   bool vout = false;
@@ -430,7 +440,7 @@ __device__ __noinline__ G volume(const Poly<G>& P, const PolyState& st, int lane
 // (Sutherland-Hodgman) and fans it with the origin ON the plane, so the cap
 // the cut would close contributes nothing to the divergence sum
 template <typename G>
-__device__ __noinline__ G volume_cut(const Poly<G>& P, const PolyState& st, G a0, G a1, G a2, G b,
+__device__ GVOF_CLIP_ATTR G volume_cut(const Poly<G>& P, const PolyState& st, G a0, G a1, G a2, G b,
                                      int lane) {
   // origin: projection onto the plane of a vertex on the inner side, so that
   // the fan terms are of the size of the part that is kept (which may be a
@@ -937,7 +947,7 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
 // signed sum of the tetrahedra that join its centroid to the fan triangles of
 // its faces (winding-number decomposition, valid for any closed cell).
 template <typename G, int KIND>
-__device__ __noinline__ G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
+__device__ GVOF_CELL_ATTR G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
                                            const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
                                            Poly<G>& P, int lane, unsigned& err, bool empty_side,
                                            int* whole) {

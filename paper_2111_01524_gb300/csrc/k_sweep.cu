@@ -263,6 +263,31 @@ __global__ void k_band_nodes(DevMesh M, const int32_t* bcells, unsigned long lon
   }
 }
 
+// vof_set_fraction: F from Fin. The band-limited sweeps stay valid when every
+// cell whose value changes is a band cell of the last advect (the cells the
+// next sweeps revisit anyway: the argument above holds for any change of
+// their F); a change anywhere else, or with no band current, makes the next
+// sweeps full. Flags only go from valid to invalid, so blocks that read them
+// before or after another block clears them reach the same end state.
+__global__ void k_set_fraction(int64_t nc, const double* Fin, double* F, const int32_t* stamp_c,
+                               unsigned long long* cnt) {
+  const bool band = cnt[kBandCellsOk] != 0;
+  const int32_t epoch = (int32_t)cnt[kEpoch];
+  int outside = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double f = Fin[i];
+    if (dbits(f) != dbits(F[i])) {
+      F[i] = f;
+      outside |= (!band || stamp_c[i] != epoch) ? 1 : 0;
+    }
+  }
+  if (__syncthreads_or(outside) && threadIdx.x == 0) {
+    cnt[kBandCellsOk] = 0;
+    cnt[kBandNodesOk] = 0;
+  }
+}
+
 // end of a reconstruction: the band node list is valid for the next face
 // sweep only if this reconstruction was band-limited
 __global__ void k_band_end(unsigned long long* cnt) {
@@ -446,6 +471,10 @@ cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s) {
   k_band_begin<<<1, 32, 0, s>>>(c->cnt);
   k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->tf, c->afaces, c->cnt,
                                                     c->vf_ptr, c->vf, c->bnodes, c->stamp_f);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_fraction(const vof_ctx* c, const double* Fin, cudaStream_t s) {
+  k_set_fraction<<<kSMs * 8, 256, 0, s>>>(c->nc, Fin, c->F, c->stamp_c, c->cnt);
   return cudaGetLastError();
 }
 cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s) {

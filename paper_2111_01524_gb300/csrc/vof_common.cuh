@@ -424,6 +424,8 @@ cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s);
+// F from Fin (device); keeps the band-limited sweeps when only band cells change
+cudaError_t launch_set_fraction(const vof_ctx* c, const double* Fin, cudaStream_t s);
 cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_volume_sum(const vof_ctx* c, cudaStream_t s);  // writes red[0], red[1]
 // initial volume fraction (k_init.cu)
