@@ -60,14 +60,14 @@ FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0
 # dram__bytes_write.sum per active face (the face and node data, the prebuilt
 # polyhedron, the candidate cells' tags, boxes and planes), issue-slot and FMA-pipe
 # use; valid only for the source it was taken on (traffic is null for any other)
-FLUX_NCU = {"source_sha256": "c02e1d7a480fd1d630b262a347e9a5d217555784cb478368906eb6a40b7dc49a",
-            "fmfpa": {"dram_bytes_per_active_face": 623.0, "issue_active": 0.472,
-                      "fma_pipe_active": 0.117, "capture": "profiles/k_flux_deformation128_mixed.md"},
-            "emfpa": {"dram_bytes_per_active_face": 629.0, "issue_active": 0.473,
-                      "fma_pipe_active": 0.124,
+FLUX_NCU = {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66cc0f6bb326d8456",
+            "fmfpa": {"dram_bytes_per_active_face": 588.0, "issue_active": 0.549,
+                      "fma_pipe_active": 0.140, "capture": "profiles/k_flux_deformation128_mixed.md"},
+            "emfpa": {"dram_bytes_per_active_face": 590.0, "issue_active": 0.573,
+                      "fma_pipe_active": 0.149,
                       "capture": "profiles/k_flux_deformation128_mixed_emfpa.md"},
-            "nmfpa": {"dram_bytes_per_active_face": 598.0, "issue_active": 0.424,
-                      "fma_pipe_active": 0.118,
+            "nmfpa": {"dram_bytes_per_active_face": 566.0, "issue_active": 0.528,
+                      "fma_pipe_active": 0.136,
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 # kernels one step launches: reconstruction (cell tags 1, node tags 3,
 # LSGIR 1 or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,

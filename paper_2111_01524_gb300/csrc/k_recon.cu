@@ -712,6 +712,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_lsfir_normals(DevMesh M, GeoVie
 // (LSFIR outer iteration io): the normal accepted by k_lsfir_normals, its
 // plane constant and PLIC centre; nothing once an earlier iteration turned
 // no normal by tol or more.
+// the next interfacial cell for this warp, dealt from a counter like the flux
+// kernel's faces (cells near F = 0 or 1 take the corner form, the others the
+// bracketed solve: their costs differ)
+__device__ __forceinline__ unsigned next_cell(const DevState& S, int lane) {
+  unsigned w = 0u;
+  if (lane == 0) w = (unsigned)atomicAdd(S.cnt + kReconNext, 1ull);
+  return __shfl_sync(GVOF_FULL, w, 0);
+}
+
 template <typename G, bool kMixed, int MODE>
 __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(DevMesh M, GeoView<G> Gv, DevState S,
                                                              double beta, int io, double tol) {
@@ -727,7 +736,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
   const unsigned n_ic = (unsigned)S.cnt[kNIcells];
   const bool beta15 = (beta == 1.5);
   const G gbeta = (G)beta;
-  for (unsigned w = blockIdx.x * kWarps + wib; w < n_ic; w += gridDim.x * kWarps) {
+  for (unsigned w = next_cell(S, lane); w < n_ic; w = next_cell(S, lane)) {
     const int c = S.icells[w];
     const typename Prec<G>::A xc = Gv.ccx[c], yc = Gv.ccy[c], zc = Gv.ccz[c];
     const G V = Gv.cvol[c];
@@ -883,6 +892,12 @@ cudaError_t reconstruct_launches(const vof_ctx* c, cudaStream_t s) {
   const GeoView<G> g = geo_view<G>(c);
   const DevState st = state_view(c);
   const double beta = c->opt.beta;
+  // each k_reconstruct launch deals its cells from a fresh counter
+  auto reset = [&]() {
+    return cudaMemsetAsync(c->cnt + kReconNext, 0, sizeof(unsigned long long), s);
+  };
+  cudaError_t e = reset();
+  if (e != cudaSuccess) return e;
   if (c->opt.reconstruction != VOF_RECON_LSFIR) {
     k_reconstruct<G, kMixed, 0><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, 0, 0.0);
     return cudaGetLastError();
@@ -894,6 +909,7 @@ cudaError_t reconstruct_launches(const vof_ctx* c, cudaStream_t s) {
   k_reconstruct<G, kMixed, 1><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, 0, tol);
   for (int io = 1; io <= c->opt.lsfir_max_iter; ++io) {
     k_lsfir_normals<G, kMixed><<<kSMs * 8, kWarps * 32, 0, s>>>(m, g, st, io, lim30 / io, tol);
+    if ((e = reset()) != cudaSuccess) return e;
     k_reconstruct<G, kMixed, 2><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, io, tol);
   }
   return cudaGetLastError();

@@ -139,7 +139,8 @@ enum Cnt {
   kBandNodesOk = 13, // the band node list of the last reconstruction is valid
   kNInitList = 14,   // cells the initial surface may cross (vof_init_fraction)
   kFluxNext = 15,    // next active face a flux warp takes (reset before each launch)
-  kNCnt = 16
+  kReconNext = 16,   // next interfacial cell a reconstruction warp takes (likewise)
+  kNCnt = 17
 };
 constexpr int kRedSlots = 2 * 1024;
 // volume bookkeeping: per-block running sums, one region each (fixed block
