@@ -102,6 +102,19 @@ def test_flux_constants_match_header():
     assert vof.NB_VERTS >= max(3 * 6 + 1, 2 * 8 + 1)
 
 
+def test_timing_phases_match_header():
+    """vof.Context.timing() names the phases in the order of VOF_PHASE_*,
+    and asks for all VOF_NUM_PHASES of them."""
+    from paper_2111_01524_gb300 import vof
+    src = open(os.path.join(ROOT, "include", "vof.h")).read()
+    found = {m.group(1).lower(): int(m.group(2))
+             for m in re.finditer(r"VOF_PHASE_([A-Z_]+)\s*=\s*(\d+)", src)}
+    n = int(re.search(r"VOF_NUM_PHASES\s*=\s*(\d+)", src).group(1))
+    assert len(vof.Context.PHASES) == n == len(found)
+    for i, name in enumerate(vof.Context.PHASES):
+        assert found[name] == i, name
+
+
 def _heptagonal_prism():
     """one cell: two 7-node faces and seven quads (valid orientation)"""
     import numpy as np
