@@ -192,6 +192,53 @@ def test_cut_volume_matches_cuboid_closed_form(hex4):
         assert abs(got - exp) < 1e-13, (n, C, got, exp)
 
 
+def test_cut_volume_matches_tetrahedron_corner_closed_form(orc):
+    """A plane that leaves one vertex v0 of a tetrahedron on one side cuts
+    off the tetrahedron spanned by v0 and the three edge points, whose
+    volume is t1 t2 t3 V with t_i = phi(v0) / (phi(v0) - phi(v_i)) the edge
+    fractions (phi the plane's signed distance): the fluid part is that
+    corner when v0 is the one fluid vertex, and V minus it when v0 is the
+    one empty vertex. Jittered Kuhn tetrahedra, random planes through the
+    cell near each vertex."""
+    m = I.kuhn_tet_mesh(3, seed=5)
+    om = orc.Mesh(m)
+    g = om.geometry()
+    fv, fp = m["face_vert"], m["face_ptr"]
+    rng = np.random.default_rng(17)
+    checked = 0
+    for c in rng.choice(m["n_cell"], 12, replace=False):
+        faces = np.nonzero((m["owner"] == c) | (m["neighbour"] == c))[0]
+        verts = np.unique(np.concatenate([fv[fp[f]:fp[f + 1]] for f in faces]))
+        assert verts.size == 4
+        X = m["X"][verts]
+        V = abs(np.linalg.det(X[1:] - X[0])) / 6.0
+        assert abs(V - g["cell_vol"][c]) < 1e-15
+        xc = g["cell_cen"][c]
+        for i0 in range(4):
+            others = [i for i in range(4) if i != i0]
+            n = rng.normal(size=3)
+            n /= np.linalg.norm(n)
+            d = (X - xc) @ n
+            if any(abs(d[i0] - d[i]) < 0.2 * np.ptp(d) for i in others):
+                continue  # keep the edge fractions well conditioned
+            side = 1.0 if all(d[i0] > d[i] for i in others) else (
+                -1.0 if all(d[i0] < d[i] for i in others) else 0.0)
+            if side == 0.0:
+                continue
+            # a plane strictly between v0 and the other three
+            lim = max(d[i] for i in others) if side > 0 else min(d[i] for i in others)
+            s = rng.uniform(0.2, 0.8)
+            cut = lim + s * (d[i0] - lim)
+            C = -cut                                  # n.(x - xc) + C = 0 at the cut
+            t = [(d[i0] - cut) / (d[i0] - d[i]) for i in others]
+            corner = t[0] * t[1] * t[2] * V
+            exp = corner if side > 0 else V - corner  # fluid side: n.(x - xc) + C >= 0
+            got = om.cell_cut_volume(int(c), n, C)
+            assert abs(got - exp) < 1e-14 * V + 1e-18, (c, i0, got, exp)
+            checked += 1
+    assert checked >= 12
+
+
 def test_cut_volume_monte_carlo_nonconvex(orc):
     m = I.trihex_mesh(2, seed=11)
     om = orc.Mesh(m)
