@@ -63,9 +63,6 @@ void free_all(vof_ctx* c) {
   delete c->hmin_g; delete c->umax_g; delete c->vel_g;
 }
 
-cudaMemcpyKind kind_to_dev(int mem) {
-  return mem == VOF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-}
 cudaMemcpyKind kind_from_dev(int mem) {
   return mem == VOF_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
