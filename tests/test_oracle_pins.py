@@ -689,6 +689,35 @@ def test_lsgir_exact_for_linear_field(orc):
     assert np.allclose(n, a / np.linalg.norm(a), atol=1e-13)
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_lsgir_axis_normal_for_an_axis_aligned_interface(orc, axis):
+    """An interface plane x_axis = 0.43 on the uniform hex grid, with F the
+    exact cell fractions: every interior interfacial cell's stencil is
+    symmetric in the two other directions, where F is constant, so the LSGIR
+    normal is the axis itself, pointing into the fluid (towards larger F, Sec.
+    2.1.1), and the plane constant puts the plane at 0.43 exactly (Sec. 2.1).
+    A transposed moment, a wrong sign of the normal or of the plane constant
+    fails this."""
+    n = 8
+    m = I.hex_mesh(n)
+    om = orc.Mesh(m)
+    g = om.geometry()
+    h = 1.0 / n
+    x = g["cell_cen"][:, axis]
+    F = np.clip((0.43 - (x - 0.5 * h)) / h, 0.0, 1.0)   # fluid where x_axis < 0.43
+    st = om.reconstruct(F)
+    inter = st["tag_c"] == 0
+    lo = g["cell_cen"] - 0.5 * h
+    interior = np.all((lo > 1e-12) & (lo + h < 1 - 1e-12), axis=1)
+    sel = inter & interior
+    assert sel.sum() == (n - 2) ** 2
+    e = np.zeros(3)
+    e[axis] = -1.0
+    assert np.abs(st["nrm"][sel] - e).max() < 1e-14
+    # plane n.(x - xc) + C = 0 at x_axis = 0.43: C = 0.43 - xc_axis
+    assert np.abs(st["C"][sel] - (0.43 - x[sel])).max() < 1e-14
+
+
 def test_lsgir_rotation_invariance(orc):
     m = I.kuhn_tet_mesh(3, seed=6)
     om = orc.Mesh(m)
