@@ -147,3 +147,59 @@ def test_emfpa_and_bad_options_are_rejected_before_device_work():
         with pytest.raises(vof.VofError) as e:
             vof.Context(m, **bad)
         assert e.value.status == vof.VOF_EINVAL, bad
+
+
+def test_corrupted_meshes_are_rejected_before_device_work():
+    """vof_init validates the face-based mesh on the host before it touches
+    the device: a CSR that does not start at 0, faces of fewer than 3 or
+    more than 8 nodes (a non-monotone CSR shows up as one of these), an
+    owner out of range, a face whose neighbour is its owner, a node index
+    out of range and an empty mesh each give VOF_EINVAL with a message (no
+    GPU needed)."""
+    import numpy as np
+    from paper_2111_01524_gb300 import inputs as I
+    from paper_2111_01524_gb300 import vof
+    base = I.hex_mesh(2)
+
+    def bad(**kw):
+        m = {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in base.items()}
+        for k, f in kw.items():
+            f(m)
+        with pytest.raises(vof.VofError) as e:
+            vof.Context(m)
+        assert e.value.status == vof.VOF_EINVAL
+        assert str(e.value)
+        return str(e.value)
+
+    def shift_ptr(m):
+        m["face_ptr"] = m["face_ptr"] + 1
+    assert "face_ptr[0]" in bad(a=shift_ptr)
+
+    def two_nodes(m):
+        fp = m["face_ptr"].copy()
+        fp[1] = fp[0] + 2  # face 0 keeps 2 nodes, face 1 gets 6
+        m["face_ptr"] = fp
+    assert "nodes" in bad(a=two_nodes)
+
+    def non_monotone(m):
+        fp = m["face_ptr"].copy()
+        fp[2], fp[3] = fp[3], fp[2]
+        m["face_ptr"] = fp
+    assert "nodes" in bad(a=non_monotone)
+
+    def owner_out(m):
+        m["owner"][0] = m["n_cell"]
+    assert "owner" in bad(a=owner_out)
+
+    def self_neighbour(m):
+        f = int(np.nonzero(m["neighbour"] >= 0)[0][0])
+        m["neighbour"][f] = m["owner"][f]
+    assert "owner" in bad(a=self_neighbour)
+
+    def node_out(m):
+        m["face_vert"][5] = len(m["X"])
+    assert "out of range" in bad(a=node_out)
+
+    def empty(m):
+        m["n_cell"] = 0
+    bad(a=empty)
