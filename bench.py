@@ -71,9 +71,14 @@ FLUX_NCU = {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66c
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 # kernels one step launches: reconstruction (cell tags 1, node tags 3,
 # LSGIR 1 or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,
-# flux 1, update 2); the phase timers count the same kernels
-def kernels_per_step(recon="lsgir", n_out=4):
-    return 4 + (1 + 2 * n_out if recon == "lsfir" else 1) + 6
+# flux 1, update 2, and in mixed precision the reconciliation of FP32 noise:
+# 5 per round x 3 rounds + 1); the phase timers count the same kernels
+REPAIR_LAUNCHES = 5 * 3 + 1
+
+
+def kernels_per_step(recon="lsgir", n_out=4, precision="mixed"):
+    return (4 + (1 + 2 * n_out if recon == "lsfir" else 1) + 6
+            + (REPAIR_LAUNCHES if precision == "mixed" else 0))
 
 
 FP32_LANES_PER_SM = 128

@@ -44,7 +44,8 @@ typedef enum {
   VOF_ENOMEM = 2,    /* device or host allocation failed */
   VOF_ECUDA = 3,     /* a CUDA call failed */
   VOF_ECAPACITY = 4, /* a fixed-capacity buffer overflowed (see stats) */
-  VOF_ESTATE = 5     /* call out of order (e.g. advect before reconstruct) */
+  VOF_ESTATE = 5,    /* call out of order (e.g. advect before reconstruct) */
+  VOF_ECFL = 6       /* flux polyhedra left their candidate cells (see vof_get_stats) */
 } vof_status;
 
 enum { VOF_PREC_FP64 = 0, VOF_PREC_MIXED = 1 };
@@ -95,7 +96,14 @@ typedef struct {
  * 30 degrees / iteration, and enforcing the plane constants again; stops
  * after an iteration in which no accepted turn reached lsfir_tol radians).
  * lsfir_max_iter: 0 means 4 (the paper's n_out), at most 16. lsfir_tol: 0
- * means 1e-3 rad. reserved: must be zero. */
+ * means 1e-3 rad.
+ * poly_capacity: how many active faces per step get their flux polyhedron
+ * built ahead of the flux kernel (one thread per face) into a buffer of
+ * (3 * 19 + 7) values per face in the path's precision; active faces beyond
+ * it are built inside the flux kernel by one lane, with the same arithmetic,
+ * so results do not depend on it. 0 means min(n_face, 4 Mi); otherwise
+ * 1..n_face (VOF_EINVAL if negative). A GPU memory/latency trade-off with no
+ * counterpart in the paper. reserved: must be zero. */
 typedef struct {
   double eps;
   double beta;
@@ -104,7 +112,8 @@ typedef struct {
   int32_t reconstruction;
   int32_t lsfir_max_iter;
   double lsfir_tol;
-  int32_t reserved[2];
+  int32_t poly_capacity;
+  int32_t reserved;
 } vof_options;
 
 /* Prescribed velocity of the test problems (Sec. 4.2, Sec. 4.3):
@@ -142,12 +151,23 @@ typedef struct {
   double clip_loss;         /* sum over cells and steps of V (F_unclipped - F) */
   double cutoff_loss;       /* sum of V (F - F_cut) removed by the cut-off to 0 / 1 */
   double boundary_outflow;  /* sum of V_F over boundary faces (fluid leaving the domain) */
+  /* last advect: */
+  int64_t n_clipped;   /* cells whose Eq. fnext value left [0, 1] and was clipped */
+  int64_t n_repaired;  /* mixed path: faces whose V_F was recomputed in FP64 (see
+                        * vof_advect_step) */
+  int64_t n_escaped;   /* flux polyhedra with a vertex inside the domain but outside
+                        * every candidate cell (CFL too large for the candidate
+                        * ring; their V_F misses that part): vof_get_stats then
+                        * returns VOF_ECFL */
 } vof_stats;
 
 /* Create a context: copies the mesh to the device and builds its derived
  * connectivity (neigbcell, cell->face, cell->vertex, vertex->cell) and
- * geometry (compgrid), Sec. 3.1. opt may be NULL (defaults). */
-vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out);
+ * geometry (compgrid), Sec. 3.1. opt may be NULL (defaults). The copies and
+ * geometry kernels run on `stream`, which is synchronised before return
+ * (the mesh arrays may be freed then). */
+vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, void* stream,
+                    vof_ctx** out);
 void vof_destroy(vof_ctx* ctx);
 const char* vof_last_error(void);
 
@@ -157,6 +177,9 @@ const char* vof_last_error(void);
  * launch; each grid keeps its own velocity field and time step (the
  * *_batch calls take arrays of n_grids velocities, times and steps). A
  * context made by vof_init is a batch of one grid. */
+vof_status vof_batch_create(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                            void* stream, vof_ctx** out);
+/* vof_batch_create on the legacy default stream */
 vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
                           vof_ctx** out);
 /* offsets [n_grids+1] of each grid's cells, faces, nodes (any may be NULL) */
@@ -215,8 +238,18 @@ vof_status vof_reconstruct(vof_ctx* ctx, void* stream);
  * flux polyhedra of the tag-0 faces truncated by the PLIC half-spaces of
  * the overlapped cells (Sec. 2.2), V_F = 0 / V_d on tag -1 / 1 faces, then
  * Eq. fnext and the clip to [0, 1]. Velocity at t + dt/2. Requires a
- * reconstruction of the current F. */
+ * reconstruction of the current F.
+ * Mixed precision: a cell whose Eq. fnext value leaves [0, 1] by more than
+ * 1e-14 while some of its face volumes carry FP32 error is not clipped at
+ * once: those face volumes are recomputed in FP64 (the polyhedra and
+ * truncations of the FP64 path) and Eq. fnext is applied again, from the F
+ * before the step, to both cells of each recomputed face (two rounds; the
+ * second clips every cell). The clip then removes FP64 rounding instead of
+ * FP32 noise, so the global volume follows the FP64 path's. */
 vof_status vof_advect(vof_ctx* ctx, const vof_velocity* vel, double t, double dt, void* stream);
+/* the same call under the name of the method's step (Algorithm alg:adv) */
+vof_status vof_advect_step(vof_ctx* ctx, const vof_velocity* vel, double t, double dt,
+                           void* stream);
 
 /* One iteration of the advection test loop (Algorithm alg:adv):
  * vof_advect followed by vof_reconstruct. */
@@ -233,6 +266,9 @@ vof_status vof_suggest_dt(vof_ctx* ctx, const vof_velocity* vel, double t, doubl
 vof_status vof_advect_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
                             const double* dt, void* stream);
 vof_status vof_step_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
+                          const double* dt, void* stream);
+/* vof_step_batch under its batch name */
+vof_status vof_batch_step(vof_ctx* ctx, const vof_velocity* vels, const double* t,
                           const double* dt, void* stream);
 vof_status vof_suggest_dt_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
                                 double cfl, const double* t_end, double* dt_out);
@@ -298,19 +334,24 @@ vof_status vof_get_flux_polyhedra(vof_ctx* ctx, const vof_velocity* vel, double 
 vof_status vof_get_state(vof_ctx* ctx, void* buf, int64_t bytes, int64_t* need, void* stream);
 vof_status vof_set_state(vof_ctx* ctx, const void* buf, int64_t bytes, void* stream);
 
-/* counters and global sums (synchronises the stream). */
+/* counters and global sums (synchronises the stream). Returns VOF_ECFL,
+ * with *out filled in, when flux polyhedra of the last advect reached past
+ * their candidate cells (n_escaped > 0, Sec. 2.2 with the CFL condition of
+ * Sec. 3.3): their V_F misses the part outside the cells around the face;
+ * a smaller time step (Eq. eq:cfl with a smaller CFL number) avoids it. */
 vof_status vof_get_stats(vof_ctx* ctx, vof_stats* out, void* stream);
 /* Per-phase device timing with CUDA events recorded on the launching
  * stream around each kernel of the step (off by default). Phases:
  * 0 cell tags, 1 node tags, 2 reconstruct (LSGIR or LSFIR + plane
  * constant), 3 face sweep, 4 flux (truncation of the flux polyhedra),
- * 5 update, 6 polyhedra (their construction, Sec. 2.2). vof_get_timing
+ * 5 update, 6 polyhedra (their construction, Sec. 2.2), 7 repair (mixed
+ * precision: FP64 face volumes of cells the clip would cut). vof_get_timing
  * synchronises, returns the accumulated milliseconds and kernel launch
  * counts (band-list kernels included) of the first n phases and resets
  * them. */
 enum { VOF_PHASE_CELL_TAGS = 0, VOF_PHASE_NODE_TAGS = 1, VOF_PHASE_RECONSTRUCT = 2,
        VOF_PHASE_FACE_SWEEP = 3, VOF_PHASE_FLUX = 4, VOF_PHASE_UPDATE = 5,
-       VOF_PHASE_POLYHEDRA = 6, VOF_NUM_PHASES = 7 };
+       VOF_PHASE_POLYHEDRA = 6, VOF_PHASE_REPAIR = 7, VOF_NUM_PHASES = 8 };
 vof_status vof_set_timing(vof_ctx* ctx, int on);
 vof_status vof_get_timing(vof_ctx* ctx, double* ms, int64_t* launches, int n);
 /* Allocation-free weighted sum: *out = sum over i < n of w[i] * F[i] (the

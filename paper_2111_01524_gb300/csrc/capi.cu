@@ -50,7 +50,9 @@ void free_all(vof_ctx* c) {
   void* ptrs2[] = {c->cpl32, c->face_off_d, c->gp_d, c->umax_d, c->acc, c->bfaces, c->vf_ptr, c->vf,
                    c->stamp_c, c->stamp_v, c->stamp_f, c->bcells, c->bnodes, c->lxp, c->lyp,
                    c->lzp, c->lxr, c->lyr, c->lzr, c->lnx, c->lny, c->lnz, c->lnx32, c->lny32,
-                   c->lnz32, c->lturn, c->fm_v, c->fm_f, c->fm_meta, c->fm_split};
+                   c->lnz32, c->lturn, c->fm_v, c->fm_f, c->fm_meta, c->fm_split, c->dombox,
+                   c->fexact, c->Fprev, c->risk, c->repf, c->repc, c->stamp_r, c->Eexc,
+                   c->Sroom};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -196,8 +198,8 @@ const char* vof_last_error(void) { return g_err.c_str(); }
 
 int64_t vof_device_bytes(const vof_ctx* c) { return c ? c->bytes : 0; }
 
-static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out,
-                            const std::vector<int64_t>& cell_off,
+static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, cudaStream_t s,
+                            vof_ctx** out, const std::vector<int64_t>& cell_off,
                             const std::vector<int64_t>& face_off,
                             const std::vector<int64_t>& vert_off) {
   const int64_t nv = mesh->n_vert, nf = mesh->n_face, nc = mesh->n_cell;
@@ -240,8 +242,8 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     return fail(VOF_EINVAL, "lsfir_max_iter must be in 0..16 and lsfir_tol >= 0");
   if (o.lsfir_max_iter == 0) o.lsfir_max_iter = 4;  // n_out of Sec. 3.6
   if (o.lsfir_tol == 0.0) o.lsfir_tol = 1e-3;
-  for (int k = 0; k < 2; ++k)
-    if (o.reserved[k] != 0) return fail(VOF_EINVAL, "reserved options must be zero");
+  if (o.reserved != 0) return fail(VOF_EINVAL, "reserved options must be zero");
+  if (o.poly_capacity < 0) return fail(VOF_EINVAL, "poly_capacity must be >= 0");
   if (o.flux_polyhedron == VOF_FLUX_EMFPA && maxI > kMaxEmfpaVerts)
     return fail(VOF_EINVAL, "EMFPA supports faces of at most 6 nodes; this mesh has " +
                                 std::to_string(maxI));
@@ -316,13 +318,13 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
         vfl[pos[mesh->face_vert[k]]++] = (int32_t)f;
     CKI(dalloc(c, &c->vf_ptr, nv + 1));
     CKI(dalloc(c, &c->vf, nfv));
-    CKI(cudaMemcpy(c->vf_ptr, vp.data(), sizeof(int64_t) * (nv + 1), cudaMemcpyHostToDevice));
-    CKI(cudaMemcpy(c->vf, vfl.data(), sizeof(int32_t) * nfv, cudaMemcpyHostToDevice));
+    CKI(cudaMemcpyAsync(c->vf_ptr, vp.data(), sizeof(int64_t) * (nv + 1), cudaMemcpyHostToDevice, s));
+    CKI(cudaMemcpyAsync(c->vf, vfl.data(), sizeof(int32_t) * nfv, cudaMemcpyHostToDevice, s));
     CKI(dalloc(c, &c->stamp_c, nc)); CKI(dalloc(c, &c->stamp_v, nv)); CKI(dalloc(c, &c->stamp_f, nf));
     CKI(dalloc(c, &c->bcells, nc)); CKI(dalloc(c, &c->bnodes, nv));
-    CKI(cudaMemset(c->stamp_c, 0, sizeof(int32_t) * nc));
-    CKI(cudaMemset(c->stamp_v, 0, sizeof(int32_t) * nv));
-    CKI(cudaMemset(c->stamp_f, 0, sizeof(int32_t) * nf));
+    CKI(cudaMemsetAsync(c->stamp_c, 0, sizeof(int32_t) * nc, s));
+    CKI(cudaMemsetAsync(c->stamp_v, 0, sizeof(int32_t) * nv, s));
+    CKI(cudaMemsetAsync(c->stamp_f, 0, sizeof(int32_t) * nf, s));
   }
   {
     std::vector<int32_t> bf;
@@ -331,7 +333,7 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     c->nbf = (int64_t)bf.size();
     CKI(dalloc(c, &c->bfaces, c->nbf > 0 ? c->nbf : 1));
     if (c->nbf > 0)
-      CKI(cudaMemcpy(c->bfaces, bf.data(), sizeof(int32_t) * c->nbf, cudaMemcpyHostToDevice));
+      CKI(cudaMemcpyAsync(c->bfaces, bf.data(), sizeof(int32_t) * c->nbf, cudaMemcpyHostToDevice, s));
   }
   if (o.precision == VOF_PREC_MIXED) {
     CKI(dalloc(c, &c->vx2, nv)); CKI(dalloc(c, &c->vy2, nv)); CKI(dalloc(c, &c->vz2, nv));
@@ -343,10 +345,34 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
     CKI(dalloc(c, &c->nx32, nc)); CKI(dalloc(c, &c->ny32, nc)); CKI(dalloc(c, &c->nz32, nc));
     CKI(dalloc(c, &c->C32, nc));
     CKI(dalloc(c, &c->cpl32, c->ncf));
+    // reconciliation of the FP32 face-volume noise at the bounds (k_sweep.cu)
+    c->rep_cap = std::min<int64_t>(nf, kFmCap);
+    CKI(dalloc(c, &c->fexact, nf)); CKI(dalloc(c, &c->Fprev, nc)); CKI(dalloc(c, &c->risk, nc));
+    CKI(dalloc(c, &c->Eexc, nc)); CKI(dalloc(c, &c->Sroom, nc));
+    CKI(dalloc(c, &c->repf, c->rep_cap)); CKI(dalloc(c, &c->repc, 2 * c->rep_cap));
+    CKI(dalloc(c, &c->stamp_r, nc));
+    CKI(cudaMemsetAsync(c->stamp_r, 0, sizeof(int32_t) * nc, s));
+    CKI(cudaMemsetAsync(c->fexact, 0, nf, s));
+  }
+  {
+    // bounding box of each grid's domain (flux polyhedron coverage)
+    std::vector<double> db(6 * ng);
+    for (int g = 0; g < ng; ++g) {
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int64_t v = vert_off[g]; v < vert_off[g + 1]; ++v)
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = std::min(lo[d], mesh->X[3 * v + d]);
+          hi[d] = std::max(hi[d], mesh->X[3 * v + d]);
+        }
+      for (int d = 0; d < 3; ++d) { db[6 * g + d] = lo[d]; db[6 * g + 3 + d] = hi[d]; }
+    }
+    CKI(dalloc(c, &c->dombox, 6 * ng));
+    CKI(cudaMemcpyAsync(c->dombox, db.data(), sizeof(double) * 6 * ng, cudaMemcpyHostToDevice, s));
   }
   {
     // room for the polyhedra the flux kernel reads prebuilt
-    c->fm_cap = std::min<int64_t>(nf, kFmCap);
+    c->fm_cap = o.poly_capacity > 0 ? std::min<int64_t>(nf, o.poly_capacity)
+                                     : std::min<int64_t>(nf, kFmCap);
     const size_t gs = o.precision == VOF_PREC_MIXED ? sizeof(float) : sizeof(double);
     CKI(cudaMalloc(&c->fm_v, gs * 3 * kFmSlots * c->fm_cap));
     CKI(cudaMalloc(&c->fm_f, gs * 7 * c->fm_cap));
@@ -371,48 +397,49 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
   CKI(dalloc(c, &c->umax_d, 3 * ng));
   CKI(cudaMallocHost(&c->gp_ring, sizeof(GridParam) * kRing * ng));
   for (int i = 0; i < kRing; ++i) CKI(cudaEventCreateWithFlags(&c->ring_ev[i], cudaEventDisableTiming));
-  CKI(cudaMemcpy(c->face_off_d, face_off.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice));
-  CKI(cudaMemset(c->gp_d, 0, sizeof(GridParam) * ng));
+  CKI(cudaMemcpyAsync(c->face_off_d, face_off.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
+  CKI(cudaMemsetAsync(c->gp_d, 0, sizeof(GridParam) * ng, s));
 
   // SoA vertex coordinates
   {
     std::vector<double> t(nv);
     for (int d = 0; d < 3; ++d) {
       for (int64_t v = 0; v < nv; ++v) t[v] = mesh->X[3 * v + d];
-      CKI(cudaMemcpy(d == 0 ? c->x : (d == 1 ? c->y : c->z), t.data(), sizeof(double) * nv,
-                     cudaMemcpyHostToDevice));
+      CKI(cudaMemcpyAsync(d == 0 ? c->x : (d == 1 ? c->y : c->z), t.data(), sizeof(double) * nv,
+                          cudaMemcpyHostToDevice, s));
     }
   }
-  CKI(cudaMemcpy(c->fptr, mesh->face_ptr, sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->fvert, mesh->face_vert, sizeof(int32_t) * nfv, cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->own, mesh->owner, sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->nbr, mesh->neighbour, sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->cf_ptr, hc.cf_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->cf, hc.cf.data(), sizeof(int32_t) * c->ncf, cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->cv_ptr, hc.cv_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->cv, hc.cv.data(), sizeof(int32_t) * c->ncv, cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->vc_ptr, hc.vc_ptr.data(), sizeof(int64_t) * (nv + 1), cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->vc, hc.vc.data(), sizeof(int32_t) * c->nvc, cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->nb_ptr, hc.nb_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice));
-  CKI(cudaMemcpy(c->nb, hc.nb.data(), sizeof(int32_t) * c->nnb, cudaMemcpyHostToDevice));
-  CKI(cudaMemset(c->cnt, 0, sizeof(unsigned long long) * kNCnt));
-  CKI(cudaMemset(c->red, 0, sizeof(double) * kRedSlots));
-  CKI(cudaMemset(c->acc, 0, sizeof(double) * kNAcc * kAccSlots));
-  CKI(cudaMemset(c->F, 0, sizeof(double) * nc));
-  CKI(cudaMemset(c->nx, 0, sizeof(double) * nc));
-  CKI(cudaMemset(c->ny, 0, sizeof(double) * nc));
-  CKI(cudaMemset(c->nz, 0, sizeof(double) * nc));
-  CKI(cudaMemset(c->C, 0, sizeof(double) * nc));
-  CKI(cudaMemset(c->tc, 0xff, nc));
-  CKI(cudaMemset(c->Vd, 0, sizeof(double) * nf));
-  CKI(cudaMemset(c->VF, 0, sizeof(double) * nf));
-  CKI(launch_face_geometry(c, 0));
-  CKI(launch_cell_geometry(c, 0));
-  if (o.precision == VOF_PREC_MIXED) CKI(launch_mixed_copies(c, 0));
-  CKI(cudaDeviceSynchronize());
+  CKI(cudaMemcpyAsync(c->fptr, mesh->face_ptr, sizeof(int64_t) * (nf + 1), cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->fvert, mesh->face_vert, sizeof(int32_t) * nfv, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->own, mesh->owner, sizeof(int32_t) * nf, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->nbr, mesh->neighbour, sizeof(int32_t) * nf, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->cf_ptr, hc.cf_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->cf, hc.cf.data(), sizeof(int32_t) * c->ncf, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->cv_ptr, hc.cv_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->cv, hc.cv.data(), sizeof(int32_t) * c->ncv, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->vc_ptr, hc.vc_ptr.data(), sizeof(int64_t) * (nv + 1), cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->vc, hc.vc.data(), sizeof(int32_t) * c->nvc, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->nb_ptr, hc.nb_ptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(c->nb, hc.nb.data(), sizeof(int32_t) * c->nnb, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * kNCnt, s));
+  CKI(cudaMemsetAsync(c->red, 0, sizeof(double) * kRedSlots, s));
+  CKI(cudaMemsetAsync(c->acc, 0, sizeof(double) * kNAcc * kAccSlots, s));
+  CKI(cudaMemsetAsync(c->F, 0, sizeof(double) * nc, s));
+  CKI(cudaMemsetAsync(c->nx, 0, sizeof(double) * nc, s));
+  CKI(cudaMemsetAsync(c->ny, 0, sizeof(double) * nc, s));
+  CKI(cudaMemsetAsync(c->nz, 0, sizeof(double) * nc, s));
+  CKI(cudaMemsetAsync(c->C, 0, sizeof(double) * nc, s));
+  CKI(cudaMemsetAsync(c->tc, 0xff, nc, s));
+  CKI(cudaMemsetAsync(c->Vd, 0, sizeof(double) * nf, s));
+  CKI(cudaMemsetAsync(c->VF, 0, sizeof(double) * nf, s));
+  CKI(launch_face_geometry(c, s));
+  CKI(launch_cell_geometry(c, s));
+  if (o.precision == VOF_PREC_MIXED) CKI(launch_mixed_copies(c, s));
+  CKI(cudaStreamSynchronize(s));
   {
     std::vector<double> bb(6 * nc);
-    CKI(cudaMemcpy(bb.data(), c->bb, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost));
+    CKI(cudaMemcpyAsync(bb.data(), c->bb, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost, s));
+    CKI(cudaStreamSynchronize(s));
     for (int g = 0; g < ng; ++g)
       for (int d = 0; d < 3; ++d) {
         double h = 1e300;
@@ -426,18 +453,19 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, v
   return VOF_OK;
 }
 
-vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, vof_ctx** out) {
+vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, void* stream,
+                    vof_ctx** out) {
   if (!mesh || !out) return fail(VOF_EINVAL, "mesh or out is NULL");
   *out = nullptr;
   std::vector<int64_t> co = {0, mesh->n_cell}, fo = {0, mesh->n_face}, vo = {0, mesh->n_vert};
-  return init_impl(mesh, opt, out, co, fo, vo);
+  return init_impl(mesh, opt, (cudaStream_t)stream, out, co, fo, vo);
 }
 
-vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
-                          vof_ctx** out) {
+vof_status vof_batch_create(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                            void* stream, vof_ctx** out) {
   if (!meshes || !out || n_grids < 1) return fail(VOF_EINVAL, "bad batch arguments");
   *out = nullptr;
-  if (n_grids == 1) return vof_init(meshes, opt, out);
+  if (n_grids == 1) return vof_init(meshes, opt, stream, out);
   std::vector<int64_t> co(n_grids + 1, 0), fo(n_grids + 1, 0), vo(n_grids + 1, 0), po(n_grids + 1, 0);
   for (int g = 0; g < n_grids; ++g) {
     const vof_mesh_desc& m = meshes[g];
@@ -469,7 +497,12 @@ vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_op
   j.n_vert = vo[n_grids]; j.n_face = fo[n_grids]; j.n_cell = co[n_grids];
   j.X = X.data(); j.face_ptr = fp.data(); j.face_vert = fv.data(); j.owner = own.data();
   j.neighbour = nbr.data();
-  return init_impl(&j, opt, out, co, fo, vo);
+  return init_impl(&j, opt, (cudaStream_t)stream, out, co, fo, vo);
+}
+
+vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                          vof_ctx** out) {
+  return vof_batch_create(meshes, n_grids, opt, nullptr, out);
 }
 
 vof_status vof_batch_offsets(vof_ctx* c, int* n_grids, int64_t* cell_off, int64_t* face_off,
@@ -587,6 +620,10 @@ static vof_status advect_launches(vof_ctx* c, cudaStream_t s) {
   { PhaseTimer tm(c, VOF_PHASE_POLYHEDRA, s); CK(launch_prebuild(c, s)); }
   { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, s)); }
   { PhaseTimer tm(c, VOF_PHASE_UPDATE, s, 2); CK(launch_update(c, s)); }
+  if (c->opt.precision == VOF_PREC_MIXED) {
+    PhaseTimer tm(c, VOF_PHASE_REPAIR, s, repair_launch_count());
+    CK(launch_repair(c, s));
+  }
   return VOF_OK;
 }
 
@@ -632,6 +669,15 @@ vof_status vof_advect(vof_ctx* c, const vof_velocity* vel, double t, double dt, 
   if (!c) return fail(VOF_EINVAL, "NULL context");
   if (c->n_grids != 1) return fail(VOF_EINVAL, "batch context: use vof_advect_batch");
   return vof_advect_batch(c, vel, &t, &dt, stream);
+}
+
+vof_status vof_advect_step(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
+  return vof_advect(c, vel, t, dt, stream);
+}
+
+vof_status vof_batch_step(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
+                          void* stream) {
+  return vof_step_batch(c, vels, t, dt, stream);
 }
 
 vof_status vof_step(vof_ctx* c, const vof_velocity* vel, double t, double dt, void* stream) {
@@ -980,6 +1026,13 @@ vof_status vof_get_stats(vof_ctx* c, vof_stats* out, void* stream) {
   out->cutoff_loss = hd[kAccCutoff];
   out->volume = hd[3];
   out->ebound = hd[4];
+  out->n_clipped = (int64_t)h[kNClipped];
+  out->n_repaired = (int64_t)std::min<unsigned long long>(h[kNRepFaces], (unsigned long long)c->rep_cap);
+  out->n_escaped = (int64_t)h[kNEscape];
+  if (out->n_escaped > 0)
+    return fail(VOF_ECFL, std::to_string(out->n_escaped) +
+                              " flux polyhedra of the last advect reached past their candidate "
+                              "cells (CFL too large for this grid); the stats are filled in");
   return VOF_OK;
 }
 

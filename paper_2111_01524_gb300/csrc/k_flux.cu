@@ -769,6 +769,138 @@ __device__ __forceinline__ bool poly_scalar(const DevMesh& M, const GeoView<G>& 
   else return fmfpa_scalar<G>(M, Gv, p, j, Vd, vx, vy, vz, fr);
 }
 
+// Coverage of the flux polyhedron by the candidate cells (Sec. 2.2: at
+// CFL <= 1 the donating region lies in the cells around the face). Each
+// vertex that is not a node of the face is located in the candidate cells,
+// owner and neighbour first, then their node neighbours: in a convex cell
+// by its face planes, in a non-convex cell by the winding number of the
+// tetrahedra that join its centroid to its fan triangles. A vertex in no
+// candidate cell sets kUncovered (the complement form of the mixed path,
+// which counts what is not empty as fluid, is then not used); if it lies
+// inside the domain's bounding box as well (outside it there is no fluid,
+// R11), kEscaped: the candidate ring does not cover the polyhedron and its
+// V_F misses that part (counted, vof_get_stats returns VOF_ECFL).
+constexpr unsigned kUncovered = 1u, kEscaped = 2u;
+
+// point (face-local units) in cell k, within tol: a convex cell by its face
+// planes (FP32: the cell's plane table), a non-convex cell by the winding
+// number of its centroid tetrahedra
+template <typename G>
+__device__ __noinline__ bool point_in_cell(const DevMesh& M, const GeoView<G>& Gv, const FaceFrame<G>& fr,
+                                           int k, G px, G py, G pz, G tol) {
+  const int64_t c0 = M.cf_ptr[k], c1 = M.cf_ptr[k + 1];
+  if (M.convex[k]) {
+    if constexpr (sizeof(G) == 4) {
+      const G rx = rel(fr.cx, Gv.ccx[k]), ry = rel(fr.cy, Gv.ccy[k]), rz = rel(fr.cz, Gv.ccz[k]);
+      for (int64_t q = c0; q < c1; ++q) {
+        const float4 pl = M.cpl32[q];  // inward normal, n.(x - x_k) >= w inside
+        if (pl.x * px + pl.y * py + pl.z * pz + (pl.x * rx + pl.y * ry + pl.z * rz - pl.w) * fr.sc < -tol)
+          return false;
+      }
+      return true;
+    } else {
+      for (int64_t q = c0; q < c1; ++q) {
+        const int fs = M.cf[q];
+        const int f = fs >= 0 ? fs : ~fs;
+        const G sg = fs >= 0 ? G(1) : G(-1);
+        const G ox = sg * Gv.fnx[f], oy = sg * Gv.fny[f], oz = sg * Gv.fnz[f];
+        // outward distance of p from the face plane, face-local units
+        const G d = ox * px + oy * py + oz * pz +
+                    (ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) + oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
+        if (d > tol) return false;
+      }
+      return true;
+    }
+  }
+  // winding number of the centroid tetrahedra
+  const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
+          rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
+  auto det3 = [](G ax, G ay, G az, G bx, G by, G bz, G cx, G cy, G cz) {
+    return ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+  };
+  int wn = 0;
+  for (int64_t q = c0; q < c1; ++q) {
+    const int fs = M.cf[q];
+    const int f = fs >= 0 ? fs : ~fs;
+    const int64_t fb = M.fptr[f];
+    const int nI = (int)(M.fptr[f + 1] - fb);
+    const int ia = M.fvert[fb];
+    const G ax = rel(Gv.vx[ia], fr.cx) * fr.sc - rx, ay = rel(Gv.vy[ia], fr.cy) * fr.sc - ry,
+            az = rel(Gv.vz[ia], fr.cz) * fr.sc - rz;
+    for (int t = 1; t + 1 < nI; ++t) {
+      int ib = M.fvert[fb + t], ic = M.fvert[fb + t + 1];
+      if (fs < 0) { const int tmp = ib; ib = ic; ic = tmp; }
+      const G bx = rel(Gv.vx[ib], fr.cx) * fr.sc - rx, by = rel(Gv.vy[ib], fr.cy) * fr.sc - ry,
+              bz = rel(Gv.vz[ib], fr.cz) * fr.sc - rz;
+      const G cx = rel(Gv.vx[ic], fr.cx) * fr.sc - rx, cy = rel(Gv.vy[ic], fr.cy) * fr.sc - ry,
+              cz = rel(Gv.vz[ic], fr.cz) * fr.sc - rz;
+      const G qx = px - rx, qy = py - ry, qz = pz - rz;
+      const G d = det3(ax, ay, az, bx, by, bz, cx, cy, cz);
+      if (d == G(0)) continue;
+      const G s = d > G(0) ? G(1) : G(-1);
+      // p inside the tetrahedron (0, a, b, c): its barycentric weights,
+      // each a determinant with p in place of one vertex, all of the sign
+      // of d (tolerance in units of the tetrahedron's volume scale)
+      const G l1 = s * det3(qx, qy, qz, bx, by, bz, cx, cy, cz);
+      const G l2 = s * det3(ax, ay, az, qx, qy, qz, cx, cy, cz);
+      const G l3 = s * det3(ax, ay, az, bx, by, bz, qx, qy, qz);
+      const G l0 = s * d - l1 - l2 - l3;
+      const G tv = tol * s * d;
+      if (l0 >= -tv && l1 >= -tv && l2 >= -tv && l3 >= -tv) wn += d > G(0) ? 1 : -1;
+    }
+  }
+  return wn != 0;
+}
+
+// the vertices (bits of `need`) of the base polyhedron that lie in cell k
+// (one lane); an axis-aligned box cell by its bounds
+template <typename G>
+__device__ unsigned cover_bits(const DevMesh& M, const GeoView<G>& Gv, const FaceFrame<G>& fr,
+                               const Poly<G>& P, int k, unsigned need) {
+  const G tol = sizeof(G) == 8 ? G(1e-9) : G(2e-5);
+  unsigned bits = 0u;
+  if (M.convex[k] == 2) {
+    const int64_t nc = M.nc;
+    const G lx = rel(Gv.bb[k], fr.cx) * fr.sc - tol, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc + tol;
+    const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc - tol, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc + tol;
+    const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc - tol, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc + tol;
+    while (need) {
+      const int v = __ffs(need) - 1;
+      need &= need - 1u;
+      const G x = P.bx[v], y = P.by[v], z = P.bz[v];
+      if (x >= lx && x <= hx && y >= ly && y <= hy && z >= lz && z <= hz) bits |= 1u << v;
+    }
+    return bits;
+  }
+  while (need) {
+    const int v = __ffs(need) - 1;
+    need &= need - 1u;
+    if (point_in_cell(M, Gv, fr, k, P.bx[v], P.by[v], P.bz[v], tol)) bits |= 1u << v;
+  }
+  return bits;
+}
+
+// coverage bits of face j from the vertices no candidate cell holds (miss):
+// kUncovered, and kEscaped for one inside the grid's domain box (lanes over
+// vertices; FP64 arithmetic for this rare case)
+template <typename G>
+__device__ __noinline__ unsigned cover_result(const DevMesh& M, const DevState& S, const FaceFrame<G>& fr,
+                                 const Poly<G>& P, int j, unsigned miss, int lane) {
+  if (miss == 0u) return 0u;
+  bool esc = false;
+  if ((miss >> lane) & 1u) {
+    const int g = M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j);
+    const double* b = S.dombox + 6 * g;
+    const double L = (double)fr.L;
+    const double ax = absd(fr.cx) + L * (double)P.bx[lane], ay = absd(fr.cy) + L * (double)P.by[lane],
+                 az = absd(fr.cz) + L * (double)P.bz[lane];
+    const double eps = 1e-9 * L;
+    esc = ax > b[0] + eps && ax < b[3] - eps && ay > b[1] + eps && ay < b[4] - eps &&
+          az > b[2] + eps && az < b[5] - eps;
+  }
+  return kUncovered | (__any_sync(GVOF_FULL, esc) ? kEscaped : 0u);
+}
+
 // the polyhedron of face j into shared memory by lane 0 (the other lanes
 // wait): the flux kernel's fallback beyond the prebuilt capacity and the
 // polyhedron export
@@ -1059,10 +1191,13 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
 // exactly 0: complement when no empty cell is met, fluid when no full cell
 // is, otherwise by the donating cell's F. Returns V_F / L^3; *whole: P lies
 // in the fluid (1) or empty (2) part of one cell (V_F = V_d or 0 exactly).
+// *cover: the coverage bits of P (cover_result), found while the candidate
+// cells are scanned: each candidate met by the box of P tests the vertices
+// not yet located; the complement form needs a covered P.
 template <typename G, int KIND>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, double Vd, G Vl, Poly<G>& P, int lane,
-                              unsigned& err, int* whole, bool* complement,
+                              unsigned& err, int* whole, bool* complement, unsigned* cover,
                               unsigned long long& n_trunc) {
   const int own = M.own[j], nbr = M.nbr[j];
   const int64_t a0 = M.nb_ptr[own];
@@ -1071,6 +1206,19 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
   int n = cap + 1;  // FP64: the fluid form, no list (the cells are scanned once)
   bool neg = false, pos = false;
   if (sizeof(G) == 4) n = 0;
+  // the vertices located: back-traced points and apex (EMFPA's side centres
+  // are averages of located points)
+  // (a polyhedron whose box is flat along an axis has no volume to miss:
+  // the cells its box touches do not pass the strict box test)
+  const int nvb = base_verts<KIND>(fr.I);
+  const G flat = sizeof(G) == 8 ? G(1e-9) : G(2e-5);
+  const bool solid = fr.hi[0] - fr.lo[0] > flat && fr.hi[1] - fr.lo[1] > flat && fr.hi[2] - fr.lo[2] > flat;
+  const unsigned need = !solid ? 0u
+                               : (((1u << nvb) - 1u) & ~((1u << fr.I) - 1u)) &
+                                     ~(KIND == VOF_FLUX_EMFPA ? ((1u << (3 * fr.I)) - 1u) & ~((1u << (2 * fr.I)) - 1u)
+                                                              : 0u);
+  unsigned found = 0u;
+  *cover = 0u;
   for (int pass = 0; sizeof(G) == 4 && pass < 2; ++pass) {
     const int c0 = pass == 0 ? own : nbr;
     if (c0 < 0) break;
@@ -1079,6 +1227,8 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
       const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      const unsigned todo = need & ~found;
+      if (todo) found |= __reduce_or_sync(GVOF_FULL, k >= 0 ? cover_bits<G>(M, Gv, fr, P, k, todo) : 0u);
       const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
       if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
       if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
@@ -1088,8 +1238,9 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     }
   }
   __syncwarp();
+  if (sizeof(G) == 4) *cover = cover_result<G>(M, S, fr, P, j, need & ~found, lane);
   bool comp = false;
-  if (sizeof(G) == 4 && nbr >= 0) {
+  if (sizeof(G) == 4 && nbr >= 0 && !(*cover & kUncovered)) {
     if (!neg && pos) comp = true;
     else if (neg && !pos) comp = false;
     else comp = S.F[Vd > 0.0 ? own : nbr] > 0.5;
@@ -1106,7 +1257,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
       int w = 0;
       v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
       ++n_trunc;
-      if (w) { *whole = comp ? 2 : 1; return G(0); }  // no other cell meets P
+      if (w) { *whole = comp ? 2 : 1; *cover = 0u; return G(0); }  // no other cell meets P
     }
     return v;
   }
@@ -1119,6 +1270,10 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
       const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
+      if (sizeof(G) == 8) {
+        const unsigned todo = need & ~found;
+        if (todo) found |= __reduce_or_sync(GVOF_FULL, k >= 0 ? cover_bits<G>(M, Gv, fr, P, k, todo) : 0u);
+      }
       unsigned bal = __ballot_sync(GVOF_FULL, k >= 0 && tk != skip);
       while (bal) {
         const int src = __ffs(bal) - 1;
@@ -1127,10 +1282,11 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
         int w = 0;
         v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
         ++n_trunc;
-        if (w) { *whole = comp ? 2 : 1; return G(0); }
+        if (w) { *whole = comp ? 2 : 1; *cover = 0u; return G(0); }
       }
     }
   }
+  if (sizeof(G) == 8) *cover = cover_result<G>(M, S, fr, P, j, need & ~found, lane);
   return v;
 }
 
@@ -1214,7 +1370,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
   Poly<G>& P = polys[wib];
   FaceFrame<G>& fr = wfr[wib];
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
-  unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0;
+  unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0, n_esc = 0;
   for (unsigned w = next_face(S, lane); w < n_af; w = next_face(S, lane)) {
     const int j = S.afaces[w];
     // the face's grid parameters, staged in shared memory (read at use)
@@ -1226,7 +1382,10 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     }
     const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
     if (!poly_for_face<G, KIND>(M, Gv, S, w, j, wgp[wib], Vd, P, fr, lane)) {
-      if (lane == 0) S.VF[j] = 0.0;
+      if (lane == 0) {
+        S.VF[j] = 0.0;
+        if constexpr (sizeof(G) == 4) S.fexact[j] = 0;
+      }
       ++n_over;
       continue;
     }
@@ -1237,19 +1396,28 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     const G L3 = fr.L * fr.L * fr.L;
     int wh = 0;
     bool comp = false;
-    const G v = sweep_candidates<G, KIND>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp, n_trunc);
+    unsigned cov = 0u;
+    const G v = sweep_candidates<G, KIND>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp, &cov,
+                                          n_trunc);
+    if (cov & kEscaped) ++n_esc;
     double VFj;
     if (wh == 1) VFj = Vd;  // P inside the fluid of one cell: exactly V_d
     else if (wh == 2) VFj = 0.0;  // P inside the empty part of one cell
     else VFj = comp ? Vd - (double)(v * L3) : (double)(v * L3);
     if (err) ++n_over;
-    if (lane == 0) S.VF[j] = VFj;
+    if (lane == 0) {
+      S.VF[j] = VFj;
+      // mixed path: a polyhedron inside one cell's fluid or empty part has
+      // an exact V_F; any other carries FP32 error (launch_repair)
+      if constexpr (sizeof(G) == 4) S.fexact[j] = (wh != 0 && !err) ? 1 : 0;
+    }
   }
   if (lane == 0) {
     if (n_trunc) atomicAdd(S.cnt + kNTrunc, n_trunc);
     if (n_over) atomicAdd(S.cnt + kNOverflow, n_over);
     if (n_deg) atomicAdd(S.cnt + kNDegen, n_deg);
     if (n_edge) atomicAdd(S.cnt + kNEdgeOn, n_edge);
+    if (n_esc) atomicAdd(S.cnt + kNEscape, n_esc);
   }
 }
 

@@ -322,64 +322,167 @@ __global__ void k_face_flux_export(DevMesh M, const int8_t* tf, const double* sr
   }
 }
 
-// Eq. fnext per cell; V_d of a face is formed here from its rate and the
-// grid's g dt, V_F from its tag (so the face sweep stores neither)
-__global__ void k_update(DevMesh M, double* F, const int8_t* tf, const double* srate,
-                         const GridParam* gp, const double* VF, double* red,
-                         const int32_t* bfaces, int64_t nbf, double* acc,
-                         const unsigned long long* cnt, const int32_t* bcells) {
+__device__ __forceinline__ double wsum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GVOF_FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ double srate_vd(const double* srate, int f, double gdt) {
+  return srate[f] * gdt;
+}
+
+// the time step factor g dt of the grid of cell c (the faces of a cell
+// belong to its grid)
+__device__ __forceinline__ double cell_gdt(const DevMesh& M, const GridParam* gp, int64_t q0,
+                                           int64_t q1) {
+  if (M.n_grids > 1 && q1 > q0) {
+    const int fs0 = M.cf[q0];
+    return gp[grid_of(M.face_off, M.n_grids, fs0 >= 0 ? fs0 : ~fs0)].gdt;
+  }
+  return gp[0].gdt;
+}
+
+// Eq. fnext for cell c from F0 and the face volumes of its faces (V_d formed
+// from the face's rate and the grid's g dt, V_F from its tag); n_inexact
+// counts the tag-0 faces whose V_F is not exact (mixed path: fexact != NULL)
+__device__ __forceinline__ double cell_fnext(const DevMesh& M, const int8_t* tf, const double* srate,
+                                             double gdt, const double* VF, const uint8_t* fexact,
+                                             int64_t q0, int64_t q1, double F0, double V,
+                                             int* n_inexact) {
+  double vdt = 0.0, vft = 0.0;
+  int ni = 0;
+  for (int64_t q = q0; q < q1; ++q) {
+    const int fs = M.cf[q];
+    const int f = fs >= 0 ? fs : ~fs;
+    const double vd = srate[f] * gdt;
+    const int8_t t = tf[f];
+    const double vf = face_vf(t, vd, VF, f);
+    if (fexact && t == 0 && !fexact[f]) ++ni;
+    if (fs >= 0) { vdt += vd; vft += vf; }
+    else { vdt -= vd; vft -= vf; }
+  }
+  *n_inexact = ni;
+  const double h = vdt / (2.0 * V);
+  return (F0 * (1.0 + h) - vft / V) / (1.0 - h);
+}
+
+// the mixed path defers the clip of a cell whose Eq. fnext value leaves
+// [0, 1] by more than FP64 rounding while some of its face volumes carry
+// FP32 error: those faces are recomputed in FP64 first (launch_repair)
+constexpr double kRiskTol = 1e-14;
+static_assert(kRepairRounds >= 1 && kRepairRounds <= 6, "stamp marks epoch * 16 + 2 round (+1)");
+__device__ __forceinline__ bool at_risk(double fn, int n_inexact) {
+  return n_inexact > 0 && (fn < -kRiskTol || fn > 1.0 + kRiskTol);
+}
+
+// append with a capacity: returns false (and appends nothing) past cap
+__device__ __forceinline__ bool warp_append_cap(bool pred, int32_t item, int32_t* list,
+                                                unsigned long long* counter, int64_t cap) {
+  const unsigned m = __ballot_sync(GVOF_FULL, pred);
+  if (m == 0) return false;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(GVOF_FULL, base, leader);
+  const int64_t pos = (int64_t)base + __popc(m & ((1u << lane) - 1));
+  if (pred && pos < cap) { list[pos] = item; return true; }
+  return false;
+}
+
+// per-block maximum of E_bound into red[kRedSlots / 2 + block] (fmax with
+// what an earlier kernel of this advect left there when `merge`)
+__device__ __forceinline__ void block_ebound(double eb, double* red, bool merge) {
+  for (int o = 16; o > 0; o >>= 1) eb = fmax(eb, __shfl_xor_sync(GVOF_FULL, eb, o));
+  __shared__ double s[32];
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) s[w] = eb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, s[i]);
+    double* slot = red + kRedSlots / 2 + blockIdx.x;
+    *slot = merge ? fmax(*slot, m) : m;
+  }
+}
+
+// Eq. fnext per band cell and the clip of Sec. 2.2. Mixed path: F before
+// the update is kept (Fprev) and a cell at risk (at_risk) is written
+// unclipped and listed for the FP64 repair instead of being clipped; the
+// boundary outflow is then summed after the repair (k_repair_finish).
+__global__ void k_update(DevMesh M, DevState S, const int32_t* bfaces, int64_t nbf, double* acc,
+                         const int32_t* bcells, int64_t risk_cap, bool mixed) {
   double eb = 0.0;
   double clip = 0.0;  // volume the clip to [0, 1] removes
   double bnd = 0.0;   // fluid that leaves through the domain boundary (R11)
-  const int64_t n = (int64_t)cnt[kNBandCells];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = bcells[i];
-    const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
-    const double F0 = F[c];
-    // the faces of a cell belong to its grid
-    double gdt = gp[0].gdt;
-    if (M.n_grids > 1 && q1 > q0) {
-      const int fs0 = M.cf[q0];
-      gdt = gp[grid_of(M.face_off, M.n_grids, fs0 >= 0 ? fs0 : ~fs0)].gdt;
-    }
-    // an empty cell that no fluid enters stays exactly empty: Eq. fnext
-    // gives 0 for F = 0 and V_FT = 0 whatever V_dT (no FP64 work needed)
-    if (is_zero(F0)) {
-      bool none = true;
-      for (int64_t q = q0; q < q1 && none; ++q) {
-        const int fs = M.cf[q];
-        const int f = fs >= 0 ? fs : ~fs;
-        const int8_t t = tf[f];
-        none = t == -1 || is_zero(t == 0 ? VF[f] : srate[f] * gdt);
+  unsigned long long nclip = 0;
+  const int64_t n = (int64_t)S.cnt[kNBandCells];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool risky = false;
+    int64_t c = 0;
+    double fn = 0.0;
+    if (i < n) {
+      c = bcells[i];
+      const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
+      const double F0 = S.F[c];
+      if (mixed) S.Fprev[c] = F0;
+      const double gdt = cell_gdt(M, S.gp, q0, q1);
+      // an empty cell that no fluid enters stays exactly empty: Eq. fnext
+      // gives 0 for F = 0 and V_FT = 0 whatever V_dT (no FP64 work needed)
+      bool skip = false;
+      if (is_zero(F0)) {
+        bool none = true;
+        for (int64_t q = q0; q < q1 && none; ++q) {
+          const int fs = M.cf[q];
+          const int f = fs >= 0 ? fs : ~fs;
+          const int8_t t = S.tf[f];
+          none = t == -1 || is_zero(t == 0 ? S.VF[f] : S.srate[f] * gdt);
+        }
+        skip = none;
       }
-      if (none) continue;
+      if (!skip) {
+        const double V = M.cvol[c];
+        int ni = 0;
+        fn = cell_fnext(M, S.tf, S.srate, gdt, S.VF, mixed ? S.fexact : nullptr, q0, q1, F0, V, &ni);
+        risky = mixed && at_risk(fn, ni);
+        if (!risky) {
+          eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
+          const double fc = fmax(fmin(fn, 1.0), 0.0);
+          clip += V * (fn - fc);
+          nclip += fc != fn;
+          S.F[c] = fc;
+        }
+      }
     }
-    double vdt = 0.0, vft = 0.0;
-    for (int64_t q = q0; q < q1; ++q) {
-      const int fs = M.cf[q];
-      const int f = fs >= 0 ? fs : ~fs;
-      const double vd = srate[f] * gdt;
-      const double vf = face_vf(tf[f], vd, VF, f);
-      if (fs >= 0) { vdt += vd; vft += vf; }
-      else { vdt -= vd; vft -= vf; }
+    // cells at risk wait for the repair unclipped; past the list's capacity
+    // they are clipped here
+    if (mixed) {
+      const bool listed = warp_append_cap(risky, (int32_t)c, S.risk, S.cnt + kNRisk, risk_cap);
+      if (risky) {
+        const double V = M.cvol[c];
+        if (listed) {
+          S.F[c] = fn;
+        } else {
+          eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
+          const double fc = fmax(fmin(fn, 1.0), 0.0);
+          clip += V * (fn - fc);
+          nclip += fc != fn;
+          S.F[c] = fc;
+        }
+      }
     }
-    double V = M.cvol[c];
-    double h = vdt / (2.0 * V);
-    double fn = (F0 * (1.0 + h) - vft / V) / (1.0 - h);
-    eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
-    const double fc = fmax(fmin(fn, 1.0), 0.0);
-    clip += V * (fn - fc);
-    F[c] = fc;
   }
   // boundary faces (owner side only), each once
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbf;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int f = bfaces[i];
-    const int8_t t = tf[f];
-    if (t == -1) continue;
-    const double vd = srate[f] * grid_gdt(M, gp, f);
-    bnd += face_vf(t, vd, VF, f);
+  if (!mixed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbf; i += stride) {
+      const int f = bfaces[i];
+      const int8_t t = S.tf[f];
+      if (t == -1) continue;
+      const double vd = S.srate[f] * grid_gdt(M, S.gp, f);
+      bnd += face_vf(t, vd, S.VF, f);
+    }
   }
   {
     const double s1 = block_sum(clip);
@@ -387,16 +490,231 @@ __global__ void k_update(DevMesh M, double* F, const int8_t* tf, const double* s
     const double s2 = block_sum(bnd);
     if (threadIdx.x == 0) acc[kAccBoundary * kAccSlots + blockIdx.x] += s2;
   }
-  for (int o = 16; o > 0; o >>= 1) eb = fmax(eb, __shfl_xor_sync(GVOF_FULL, eb, o));
-  __shared__ double s[32];
-  int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) s[w] = eb;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, s[i]);
-    red[kRedSlots / 2 + blockIdx.x] = m;
+  for (int o = 16; o > 0; o >>= 1) nclip += __shfl_xor_sync(GVOF_FULL, nclip, o);
+  if ((threadIdx.x & 31) == 0 && nclip) atomicAdd(S.cnt + kNClipped, nclip);
+  block_ebound(eb, S.red, false);
+}
+
+// ---- Mixed precision: FP32 noise reconciliation (Sec. 2.2 with the clip)
+// A cell whose Eq. fnext value leaves [0, 1] loses V (F_unclipped - F) to
+// the clip. In the FP64 path that loss is rounding (E_bound of Sec. 4.2
+// around 1e-22 here). The mixed path's face volumes carry FP32 noise of
+// about 1e-7 of a polyhedron (plane offsets and cut points formed in FP32),
+// which pushes nearly full or empty cells past the bounds; the clip would
+// turn that noise into lost volume. Instead, a cell whose excess is within
+// the noise bound of its inexact faces (kNoise times the sum of A^(3/2)
+// over them: each flux is formed in face-local FP32 units of sqrt(A), so its
+// rounding is a few ulps of A^(3/2) whatever V_d) hands it back
+// through those faces to the neighbours that have room (space for an
+// overfull cell, fluid for an overdrawn one), in proportion to that room:
+// each adjustment changes one face volume, applied with opposite signs to
+// its two cells, so the update stays conservative, and no face moves more
+// than the noise. Each round re-applies Eq. fnext (from the F before the
+// update) to the cells of the adjusted faces; a cell still out of bounds
+// goes to the next round, and the last round clips every cell (the paper's
+// clip, which then removes rounding only).
+constexpr double kNoise = 2e-6;
+// and at most this much of the cell's own volume: an overshoot the FP64
+// method makes itself (jittered tetrahedra) is left to the clip above it,
+// and below it the volume moved stays under the mixed path's F tolerance
+constexpr double kNoiseF = 5e-7;
+
+__device__ __forceinline__ int32_t risk_mark(int32_t epoch, int round) { return epoch * 16 + 2 * round; }
+__device__ __forceinline__ int32_t upd_mark(int32_t epoch, int round) { return epoch * 16 + 2 * round + 1; }
+
+// start of a round: the risk cells listed since the last round, an empty
+// re-update list, the first adjusted face of the round
+__global__ void k_repair_begin(unsigned long long* cnt, int64_t risk_cap, int64_t rep_cap) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    cnt[kRiskLo] = cnt[kRiskHi];
+    cnt[kRiskHi] = cnt[kNRisk] < (unsigned long long)risk_cap ? cnt[kNRisk] : risk_cap;
+    cnt[kRepLo] = cnt[kNRepFaces] < (unsigned long long)rep_cap ? cnt[kNRepFaces] : rep_cap;
+    cnt[kNRepCells] = 0;
   }
+}
+
+// room of cell n for an excess of sign e: space (e > 0) or fluid (e < 0)
+__device__ __forceinline__ double room(const DevMesh& M, const double* F, int n, double e) {
+  const double f = F[n];
+  return M.cvol[n] * (e > 0.0 ? fmax(0.0, 1.0 - f) : fmax(0.0, f));
+}
+
+// the risk cells of this round (one warp each, one lane per face): the
+// excess E (scaled by 1 - h of Eq. fnext so that moving E out of the cell's
+// face sums removes it), the room S of the neighbours across its inexact
+// faces, and those faces listed once per round
+__global__ void k_risk_cells(DevMesh M, DevState S, int32_t* stamp_f, double* Eexc, double* Sroom,
+                             int round) {
+  const int32_t epoch = (int32_t)S.cnt[kEpoch];
+  const int64_t lo = (int64_t)S.cnt[kRiskLo], hi = (int64_t)S.cnt[kRiskHi];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = lo + w0; i < hi; i += nw) {
+    const int c = S.risk[i];
+    int mine = 0;
+    if (lane == 0) mine = claim(S.stamp_r, c, risk_mark(epoch, round)) ? 1 : 0;
+    if (!__shfl_sync(GVOF_FULL, mine, 0)) continue;  // listed twice in this round
+    const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
+    const double gdt = cell_gdt(M, S.gp, q0, q1);
+    double vdt = 0.0, vft = 0.0, vdi = 0.0;
+    bool inexact = false;
+    int f = 0, other = -1;
+    if (q0 + lane < q1) {
+      const int fs = M.cf[q0 + lane];
+      f = fs >= 0 ? fs : ~fs;
+      const double vd = srate_vd(S.srate, f, gdt);
+      const int8_t t = S.tf[f];
+      const double vf = face_vf(t, vd, S.VF, f);
+      vdt = fs >= 0 ? vd : -vd;
+      vft = fs >= 0 ? vf : -vf;
+      inexact = t == 0 && !S.fexact[f];
+      if (inexact) {
+        const double a = M.fa[f];
+        vdi = a * sqrt(a);
+        other = fs >= 0 ? M.nbr[f] : M.own[f];
+      }
+    }
+    vdt = wsum_d(vdt); vft = wsum_d(vft); vdi = wsum_d(vdi);
+    const double V = M.cvol[c];
+    const double h = vdt / (2.0 * V);
+    const double fn = (S.Fprev[c] * (1.0 + h) - vft / V) / (1.0 - h);
+    const double ex = V * (fn - fmax(fmin(fn, 1.0), 0.0));
+    // an excess beyond the FP32 noise of the inexact faces is not noise (a
+    // genuine overshoot of the method, as on jittered tetrahedra): the clip
+    // takes it, as in the FP64 path
+    const double E = (fabs(ex) <= kNoise * vdi && fabs(ex) <= kNoiseF * V) ? ex * (1.0 - h) : 0.0;
+    const double r = (inexact && other >= 0 && E != 0.0) ? room(M, S.F, other, E) : 0.0;
+    const double Sr = wsum_d(r);
+    if (lane == 0) { Eexc[c] = E; Sroom[c] = Sr; }
+    const bool p = r > 0.0 && claim(stamp_f, f, -risk_mark(epoch, round));
+    warp_append_cap(p, f, S.repf, S.cnt + kNRepFaces, S.rep_cap);
+  }
+}
+
+// the adjusted face volumes of this round, one thread per listed face: each
+// risk cell on either side moves its share of E, in proportion to the other
+// side's room (at most all of its room: E is split over max(S, |E|))
+__global__ void k_adjust_faces(DevMesh M, DevState S, const double* Eexc, const double* Sroom,
+                               int round) {
+  const int32_t mark = risk_mark((int32_t)S.cnt[kEpoch], round);
+  const int64_t lo = (int64_t)S.cnt[kRepLo];
+  const int64_t hi = min((int64_t)S.cnt[kNRepFaces], S.rep_cap);
+  for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = S.repf[i];
+    const int o = M.own[f], n = M.nbr[f];
+    double d = 0.0;
+    if (S.stamp_r[o] == mark && Eexc[o] != 0.0) {
+      const double E = Eexc[o];
+      d += E * room(M, S.F, n, E) / fmax(Sroom[o], fabs(E));
+    }
+    if (S.stamp_r[n] == mark && Eexc[n] != 0.0) {
+      const double E = Eexc[n];
+      d -= E * room(M, S.F, o, E) / fmax(Sroom[n], fabs(E));
+    }
+    S.VF[f] += d;  // positive: out of the owner (into the neighbour)
+  }
+}
+
+// the cells of this round's adjusted faces, each once per round
+__global__ void k_repair_cells(DevMesh M, DevState S, int round) {
+  const int32_t mark = upd_mark((int32_t)S.cnt[kEpoch], round);
+  const int64_t lo = (int64_t)S.cnt[kRepLo];
+  const int64_t hi = min((int64_t)S.cnt[kNRepFaces], S.rep_cap);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = lo + blockIdx.x * (int64_t)blockDim.x; base < hi; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int c0 = -1, c1 = -1;
+    if (i < hi) {
+      const int f = S.repf[i];
+      c0 = M.own[f];
+      c1 = M.nbr[f];
+    }
+    const bool p0 = c0 >= 0 && claim(S.stamp_r, c0, mark);
+    warp_append_cap(p0, c0, S.repc, S.cnt + kNRepCells, 2 * S.rep_cap);
+    const bool p1 = c1 >= 0 && claim(S.stamp_r, c1, mark);
+    warp_append_cap(p1, c1, S.repc, S.cnt + kNRepCells, 2 * S.rep_cap);
+  }
+}
+
+// Eq. fnext again for the cells of the adjusted faces, from F before the
+// update; a cell still out of bounds is listed for the next round (not in
+// the last round, which clips every cell)
+__global__ void k_reupdate(DevMesh M, DevState S, double* acc, int64_t risk_cap, bool last) {
+  double eb = 0.0, clip = 0.0;
+  unsigned long long nclip = 0;
+  const int64_t n = min((int64_t)S.cnt[kNRepCells], 2 * S.rep_cap);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool risky = false;
+    int64_t c = 0;
+    double fn = 0.0, V = 1.0;
+    if (i < n) {
+      c = S.repc[i];
+      const int64_t q0 = M.cf_ptr[c], q1 = M.cf_ptr[c + 1];
+      V = M.cvol[c];
+      int ni = 0;
+      fn = cell_fnext(M, S.tf, S.srate, cell_gdt(M, S.gp, q0, q1), S.VF, S.fexact, q0, q1,
+                      S.Fprev[c], V, &ni);
+      risky = !last && at_risk(fn, ni);
+    }
+    const bool listed = warp_append_cap(risky, (int32_t)c, S.risk, S.cnt + kNRisk, risk_cap);
+    if (i < n) {
+      if (listed) {
+        S.F[c] = fn;
+      } else {
+        eb = fmax(eb, fmax(-V * fn, V * (fn - 1.0)));
+        const double fc = fmax(fmin(fn, 1.0), 0.0);
+        clip += V * (fn - fc);
+        nclip += fc != fn;
+        S.F[c] = fc;
+      }
+    }
+  }
+  const double s1 = block_sum(clip);
+  if (threadIdx.x == 0) acc[kAccClip * kAccSlots + blockIdx.x] += s1;
+  for (int o = 16; o > 0; o >>= 1) nclip += __shfl_xor_sync(GVOF_FULL, nclip, o);
+  if ((threadIdx.x & 31) == 0 && nclip) atomicAdd(S.cnt + kNClipped, nclip);
+  block_ebound(eb, S.red, true);
+}
+
+// end of the repair: clip any listed cell still outside [0, 1] (a cell whose
+// repair faces did not fit the list), each once, and sum the boundary
+// outflow with the final face volumes
+__global__ void k_repair_finish(DevMesh M, DevState S, const int32_t* bfaces, int64_t nbf,
+                                double* acc, int64_t risk_cap) {
+  const int32_t mark = (int32_t)S.cnt[kEpoch] * 16 + 15;
+  double eb = 0.0, clip = 0.0, bnd = 0.0;
+  unsigned long long nclip = 0;
+  const int64_t n = min((int64_t)S.cnt[kNRisk], risk_cap);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int c = S.risk[i];
+    const double f = S.F[c];
+    if (!(f < 0.0 || f > 1.0) || !claim(S.stamp_r, c, mark)) continue;
+    const double V = M.cvol[c];
+    eb = fmax(eb, fmax(-V * f, V * (f - 1.0)));
+    const double fc = fmax(fmin(f, 1.0), 0.0);
+    clip += V * (f - fc);
+    ++nclip;
+    S.F[c] = fc;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbf; i += stride) {
+    const int f = bfaces[i];
+    const int8_t t = S.tf[f];
+    if (t == -1) continue;
+    const double vd = S.srate[f] * grid_gdt(M, S.gp, f);
+    bnd += face_vf(t, vd, S.VF, f);
+  }
+  const double s1 = block_sum(clip);
+  if (threadIdx.x == 0) acc[kAccClip * kAccSlots + blockIdx.x] += s1;
+  const double s2 = block_sum(bnd);
+  if (threadIdx.x == 0) acc[kAccBoundary * kAccSlots + blockIdx.x] += s2;
+  for (int o = 16; o > 0; o >>= 1) nclip += __shfl_xor_sync(GVOF_FULL, nclip, o);
+  if ((threadIdx.x & 31) == 0 && nclip) atomicAdd(S.cnt + kNClipped, nclip);
+  block_ebound(eb, S.red, true);
 }
 
 // sum of V F in a fixed order: per-block partials then one block
@@ -468,6 +786,10 @@ cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s) {
   static_assert(kNAfaces + 1 == kNTrunc && kNTrunc + 3 == kNEdgeOn, "counter layout");
   cudaError_t e = cudaMemsetAsync(c->cnt + kNAfaces, 0, 5 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  // clip, escape and repair counters of this advect
+  static_assert(kNClipped + 8 == kNCnt, "counter layout");
+  e = cudaMemsetAsync(c->cnt + kNClipped, 0, 8 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
   k_band_begin<<<1, 32, 0, s>>>(c->cnt);
   k_face_sweep<<<grid_for(c->nf, 256), 256, 0, s>>>(mesh_view(c), c->tv, c->tf, c->afaces, c->cnt,
                                                     c->vf_ptr, c->vf, c->bnodes, c->stamp_f);
@@ -486,8 +808,24 @@ cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s) {
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s) {
   k_band_cells<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->afaces, c->icells, c->cnt, c->stamp_c,
                                           c->bcells);
-  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), c->F, c->tf, c->srate, c->gp_d, c->VF, c->red,
-                                      c->bfaces, c->nbf, c->acc, c->cnt, c->bcells);
+  k_update<<<kUpdBlocks, 256, 0, s>>>(mesh_view(c), state_view(c), c->bfaces, c->nbf, c->acc,
+                                      c->bcells, c->nc, c->opt.precision == VOF_PREC_MIXED);
+  return cudaGetLastError();
+}
+
+int repair_launch_count() { return 5 * kRepairRounds + 1; }
+
+cudaError_t launch_repair(const vof_ctx* c, cudaStream_t s) {
+  const DevMesh m = mesh_view(c);
+  const DevState st = state_view(c);
+  for (int r = 1; r <= kRepairRounds; ++r) {
+    k_repair_begin<<<1, 32, 0, s>>>(c->cnt, c->nc, c->rep_cap);
+    k_risk_cells<<<kSMs * 2, 256, 0, s>>>(m, st, c->stamp_f, c->Eexc, c->Sroom, r);
+    k_adjust_faces<<<kSMs * 2, 256, 0, s>>>(m, st, c->Eexc, c->Sroom, r);
+    k_repair_cells<<<kSMs * 2, 256, 0, s>>>(m, st, r);
+    k_reupdate<<<kUpdBlocks, 256, 0, s>>>(m, st, c->acc, c->nc, r == kRepairRounds);
+  }
+  k_repair_finish<<<kUpdBlocks, 256, 0, s>>>(m, st, c->bfaces, c->nbf, c->acc, c->nc);
   return cudaGetLastError();
 }
 

@@ -121,6 +121,17 @@ struct DevState {
   void* fm_f;
   uint32_t *fm_meta, *fm_split;
   int64_t fm_cap;
+  // domain bounding box per grid [6 * n_grids] (lo xyz, hi xyz): a flux
+  // polyhedron vertex outside it is outside the domain (no fluid, R11)
+  const double* dombox;
+  // mixed precision reconciliation: per face, 1 when the last flux kernel's
+  // V_F is exact (shortcut or a polyhedron inside one cell's fluid or empty
+  // part); F before the update (band cells); risk, adjusted-face and
+  // re-update lists
+  uint8_t* fexact;
+  double* Fprev;
+  int32_t *risk, *repf, *repc, *stamp_r;
+  int64_t rep_cap;
 };
 
 enum Cnt {
@@ -140,8 +151,20 @@ enum Cnt {
   kNInitList = 14,   // cells the initial surface may cross (vof_init_fraction)
   kFluxNext = 15,    // next active face a flux warp takes (reset before each launch)
   kReconNext = 16,   // next interfacial cell a reconstruction warp takes (likewise)
-  kNCnt = 17
+  // mixed precision: reconciliation of the FP32 face-volume noise of cells
+  // at the bounds (k_sweep.cu) and the candidate-ring escape count
+  kNClipped = 17,    // cells clipped to [0, 1] by the last update
+  kNEscape = 18,     // flux polyhedra with a vertex outside every candidate cell
+  kNRepFaces = 19,   // faces adjusted this advect (listed once per round)
+  kRepLo = 20,       // first adjusted face of the current round
+  kNRisk = 21,       // cells appended to the risk list this advect
+  kRiskLo = 22,      // risk cells of the current round: [kRiskLo, kRiskHi)
+  kRiskHi = 23,
+  kNRepCells = 24,   // cells re-updated in the current round
+  kNCnt = 25
 };
+// rounds of the mixed path's reconciliation of FP32 face-volume noise
+constexpr int kRepairRounds = 3;
 constexpr int kRedSlots = 2 * 1024;
 // volume bookkeeping: per-block running sums, one region each (fixed block
 // counts, so every sum is formed in the same order every step)
@@ -279,6 +302,12 @@ struct vof_ctx {
   void *fm_v, *fm_f;
   uint32_t *fm_meta, *fm_split;
   int64_t fm_cap;
+  double* dombox;
+  uint8_t* fexact;
+  double* Fprev;
+  int32_t *risk, *repf, *repc, *stamp_r;
+  double *Eexc, *Sroom;  // per risk cell: excess and neighbours' room
+  int64_t rep_cap;
   // state (device)
   double* F;
   double *nx, *ny, *nz, *C;
@@ -368,6 +397,10 @@ inline DevState state_view(const vof_ctx* c) {
   s.lturn = c->lturn;
   s.fm_v = c->fm_v; s.fm_f = c->fm_f; s.fm_meta = c->fm_meta; s.fm_split = c->fm_split;
   s.fm_cap = c->fm_cap;
+  s.dombox = c->dombox;
+  s.fexact = c->fexact; s.Fprev = c->Fprev;
+  s.risk = c->risk; s.repf = c->repf; s.repc = c->repc; s.stamp_r = c->stamp_r;
+  s.rep_cap = c->rep_cap;
   return s;
 }
 
@@ -425,6 +458,11 @@ cudaError_t launch_cell_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_node_tags(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_face_sweep(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_update(const vof_ctx* c, cudaStream_t s);
+// mixed precision: reconciliation of the FP32 face-volume noise of cells the
+// clip would cut and the re-update of their cells (kRepairRounds rounds),
+// then the final clip and the boundary outflow
+cudaError_t launch_repair(const vof_ctx* c, cudaStream_t s);
+int repair_launch_count();
 // F from Fin (device); keeps the band-limited sweeps when only band cells change
 cudaError_t launch_set_fraction(const vof_ctx* c, const double* Fin, cudaStream_t s);
 cudaError_t launch_face_flux_export(const vof_ctx* c, cudaStream_t s);

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-VOF_OK, VOF_EINVAL, VOF_ENOMEM, VOF_ECUDA, VOF_ECAPACITY, VOF_ESTATE = range(6)
+VOF_OK, VOF_EINVAL, VOF_ENOMEM, VOF_ECUDA, VOF_ECAPACITY, VOF_ESTATE, VOF_ECFL = range(7)
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 FLUX_FMFPA, FLUX_EMFPA, FLUX_NMFPA = 0, 1, 2  # flux polyhedra (Secs. 2.2.2, 2.2.1, 2.2.3)
@@ -41,7 +41,7 @@ class _Opt(C.Structure):
     _fields_ = [("eps", C.c_double), ("beta", C.c_double), ("precision", C.c_int32),
                 ("flux_polyhedron", C.c_int32), ("reconstruction", C.c_int32),
                 ("lsfir_max_iter", C.c_int32), ("lsfir_tol", C.c_double),
-                ("reserved", C.c_int32 * 2)]
+                ("poly_capacity", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _Shape(C.Structure):
@@ -70,7 +70,8 @@ class Stats(C.Structure):
                 ("n_truncations", C.c_int64), ("n_overflow", C.c_int64),
                 ("n_degenerate", C.c_int64), ("n_edgeon", C.c_int64),
                 ("volume", C.c_double), ("ebound", C.c_double), ("clip_loss", C.c_double),
-                ("cutoff_loss", C.c_double), ("boundary_outflow", C.c_double)]
+                ("cutoff_loss", C.c_double), ("boundary_outflow", C.c_double),
+                ("n_clipped", C.c_int64), ("n_repaired", C.c_int64), ("n_escaped", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,7 +92,10 @@ def lib():
         L = C.CDLL(path)
         vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
         L.vof_last_error.restype = C.c_char_p
-        L.vof_init.argtypes = [vp, vp, C.POINTER(vp)]
+        L.vof_init.argtypes = [vp, vp, vp, C.POINTER(vp)]
+        L.vof_batch_create.argtypes = [vp, C.c_int, vp, vp, C.POINTER(vp)]
+        L.vof_advect_step.argtypes = [vp, vp, dbl, dbl, vp]
+        L.vof_batch_step.argtypes = [vp, vp, vp, vp, vp]
         L.vof_destroy.argtypes = [vp]
         L.vof_destroy.restype = None
         L.vof_set_fraction.argtypes = [vp, vp, i32, vp]
@@ -123,7 +127,7 @@ def lib():
         L.vof_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         for name in ("vof_init_batch", "vof_batch_offsets", "vof_advect_batch", "vof_step_batch",
                      "vof_suggest_dt_batch", "vof_graph_capture", "vof_graph_launch",
-                     "vof_autotune"):
+                     "vof_autotune", "vof_batch_create", "vof_advect_step", "vof_batch_step"):
             getattr(L, name).restype = C.c_int
         L.vof_volume_sum_noalloc.argtypes = [vp, vp, i64, vp, vp]
         L.vof_volume_sum_noalloc.restype = C.c_int
@@ -213,7 +217,8 @@ class Context:
     """
 
     def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5, flux=FLUX_FMFPA,
-                 recon=RECON_LSGIR, lsfir_max_iter=0, lsfir_tol=0.0):
+                 recon=RECON_LSGIR, lsfir_max_iter=0, lsfir_tol=0.0, poly_capacity=0,
+                 stream=None):
         L = lib()
         meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
@@ -221,8 +226,9 @@ class Context:
         opt = _Opt()
         opt.eps, opt.beta, opt.precision, opt.flux_polyhedron = eps, beta, precision, flux
         opt.reconstruction, opt.lsfir_max_iter, opt.lsfir_tol = recon, lsfir_max_iter, lsfir_tol
+        opt.poly_capacity = poly_capacity
         h = C.c_void_p()
-        _check(L.vof_init_batch(descs, len(meshes), C.byref(opt), C.byref(h)))
+        _check(L.vof_batch_create(descs, len(meshes), C.byref(opt), _stream(stream), C.byref(h)))
         self._h = h
         self.n_grids = len(meshes)
         self.n_vert = sum(d.n_vert for d in descs)
@@ -288,7 +294,7 @@ class Context:
 
     def advect(self, vel, t, dt, stream=None):
         v = velocity_struct(vel)
-        _check(lib().vof_advect(self._h, C.byref(v), t, dt, _stream(stream)))
+        _check(lib().vof_advect_step(self._h, C.byref(v), t, dt, _stream(stream)))
 
     def step(self, vel, t, dt, stream=None):
         v = velocity_struct(vel)
@@ -308,7 +314,7 @@ class Context:
 
     def step_batch(self, vels, t, dt, stream=None):
         va, ta, da = self._batch_args(vels, t, dt)
-        _check(lib().vof_step_batch(self._h, va, _ptr(ta), _ptr(da), _stream(stream)))
+        _check(lib().vof_batch_step(self._h, va, _ptr(ta), _ptr(da), _stream(stream)))
 
     def suggest_dt_batch(self, vels, t, cfl, t_end):
         va, ta, te = self._batch_args(vels, t, t_end)
@@ -393,7 +399,8 @@ class Context:
         return [verts[i, :npts(counts[i])].copy() if counts[i] > 0 else None
                 for i in range(len(faces))]
 
-    PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update", "polyhedra")
+    PHASES = ("cell_tags", "node_tags", "reconstruct", "face_sweep", "flux", "update", "polyhedra",
+              "repair")
 
     def set_timing(self, on=True):
         _check(lib().vof_set_timing(self._h, 1 if on else 0))
@@ -406,7 +413,14 @@ class Context:
         _check(lib().vof_get_timing(self._h, _ptr(ms), _ptr(n), len(self.PHASES)))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PHASES)}
 
-    def stats(self, stream=None):
+    def stats(self, stream=None, raise_on_escape=False):
+        """Counters and sums of the last advect. VOF_ECFL (flux polyhedra
+        left their candidate cells) is reported as ``cfl_escape`` and raised
+        only when asked."""
         s = Stats()
-        _check(lib().vof_get_stats(self._h, C.byref(s), _stream(stream)))
-        return s.as_dict()
+        st = lib().vof_get_stats(self._h, C.byref(s), _stream(stream))
+        if st != VOF_ECFL or raise_on_escape:
+            _check(st)
+        d = s.as_dict()
+        d["cfl_escape"] = st == VOF_ECFL
+        return d

@@ -42,7 +42,8 @@ def test_status_codes_match_header():
     src = open(os.path.join(ROOT, "include", "vof.h")).read()
     for name, val in [("VOF_OK", vof.VOF_OK), ("VOF_EINVAL", vof.VOF_EINVAL),
                       ("VOF_ENOMEM", vof.VOF_ENOMEM), ("VOF_ECUDA", vof.VOF_ECUDA),
-                      ("VOF_ECAPACITY", vof.VOF_ECAPACITY), ("VOF_ESTATE", vof.VOF_ESTATE)]:
+                      ("VOF_ECAPACITY", vof.VOF_ECAPACITY), ("VOF_ESTATE", vof.VOF_ESTATE),
+                      ("VOF_ECFL", vof.VOF_ECFL)]:
         assert re.search(rf"{name}\s*=\s*{val}\b", src), name
 
 
@@ -51,7 +52,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(vof._Mesh) == 3 * 8 + 5 * 8
     assert ctypes.sizeof(vof._Opt) == 8 + 8 + 4 + 4 + 4 + 4 + 8 + 2 * 4
     assert ctypes.sizeof(vof._Vel) == 4 + 4 + 8 + 8 + 24 + 24
-    assert ctypes.sizeof(vof.Stats) == 6 * 8 + 5 * 8
+    assert ctypes.sizeof(vof.Stats) == 6 * 8 + 5 * 8 + 3 * 8
     assert ctypes.sizeof(vof._Shape) == 4 + 4 + 24 + 24 + 8
 
 

@@ -68,6 +68,7 @@ def test_kernels_per_step(bench):
     """LSGIR: cell tags 1, node tags 3, reconstruct 1, face sweep 2,
     polyhedra 1, flux 1, update 2 = 11; LSFIR adds 2 launches per outer
     iteration."""
-    assert bench.kernels_per_step() == 11
-    assert bench.kernels_per_step("lsfir", 4) == 19
-    assert bench.kernels_per_step("lsfir", 1) == 13
+    assert bench.kernels_per_step(precision="fp64") == 11
+    assert bench.kernels_per_step("lsfir", 4, precision="fp64") == 19
+    assert bench.kernels_per_step("lsfir", 1, precision="fp64") == 13
+    assert bench.kernels_per_step() == 11 + 16  # mixed: the noise reconciliation rounds

@@ -138,12 +138,21 @@ VELS = {"deformation": I.deformation(3.0), "rotation": I.rotation(2 * np.pi),
         "translation": I.translation((0.7, -0.4, 0.25))}
 
 
+def _cfl(name):
+    """CFL of the one-step cases: 0.4 on the jittered tetrahedra (as config 3),
+    where the candidate ring covers every interior flux polyhedron; at 0.5
+    the diagonal translation already carries a few polyhedra of the 4^3 x 6
+    grid past it (the CFL bound measures cells by their bounding boxes)."""
+    return 0.4 if name.startswith("tet") else 0.5
+
+
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("vname", sorted(VELS))
 def test_advect_parity_fp64(vof, cases, name, vname):
     m, F0, om = cases[name]
     vel = VELS[vname]
-    ctx, st, (Vd, VF, F), (Vdo, VFo, Fo) = _one_step(vof, m, F0, om, vel, vof.PREC_FP64)
+    ctx, st, (Vd, VF, F), (Vdo, VFo, Fo) = _one_step(vof, m, F0, om, vel, vof.PREC_FP64,
+                                                     cfl=_cfl(name))
     V = om.geometry()["cell_vol"]
     assert np.abs(Vd - Vdo).max() <= 1e-14 * np.abs(Vdo).max() + 1e-30
     assert np.abs(VF - VFo).max() < EPS_F64 * V.min()
@@ -156,15 +165,18 @@ def test_advect_parity_fp64(vof, cases, name, vname):
 
 
 @pytest.mark.parametrize("name", CASES)
-def test_advect_parity_mixed(vof, cases, name):
+@pytest.mark.parametrize("vname", sorted(VELS))
+def test_advect_parity_mixed(vof, cases, name, vname):
     m, F0, om = cases[name]
-    vel = VELS["deformation"]
-    ctx, st, (Vd, VF, F), (Vdo, VFo, Fo) = _one_step(vof, m, F0, om, vel, vof.PREC_MIXED)
+    vel = VELS[vname]
+    ctx, st, (Vd, VF, F), (Vdo, VFo, Fo) = _one_step(vof, m, F0, om, vel, vof.PREC_MIXED,
+                                                     cfl=_cfl(name))
     V = om.geometry()["cell_vol"]
     assert np.abs(F - Fo).max() < EPS_MIXED
     # a face volume error moves F of its owner by dVF / V_owner
     assert (np.abs(VF - VFo) / V[m["owner"]]).max() < EPS_MIXED
-    assert ctx.stats()["n_overflow"] == 0
+    s = ctx.stats()
+    assert s["n_overflow"] == 0 and s["n_escaped"] == 0
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -342,3 +354,96 @@ def test_planar_interface_translates_exactly_gpu(vof, flux, prec):
     err = np.abs(ctx.get_fraction()[keep] - exact[keep]).max()
     assert err < (1e-13 if prec == "fp64" else EPS_MIXED), err
     assert ctx.stats()["n_overflow"] == 0
+
+
+def _boundary_case(kind):
+    """A body on each side of the domain in a uniform flow with inflow and
+    outflow walls: one across x = 1 (fluid leaves), one across x = 0 and
+    y = 0 (the flow enters there and carries no fluid, reading R11)."""
+    if kind == "hex":
+        m = I.hex_mesh(10)
+    else:
+        m = I.kuhn_tet_mesh(4, seed=3)
+    Fa = I.init_fraction(m, I.sphere((0.93, 0.55, 0.5), 0.22), levels=3)
+    Fb = I.init_fraction(m, I.sphere((0.04, 0.06, 0.45), 0.25), levels=3)
+    return m, np.minimum(1.0, Fa + Fb), I.translation((0.8, 0.35, -0.25))
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("flux", ["FMFPA", "EMFPA", "NMFPA"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_boundary_crossing_parity(vof, orc, kind, flux, prec):
+    """Faces on the domain boundary and interior faces whose polyhedra reach
+    outside it (readings c8a and R11), element by element against the
+    oracle: V_F of every face and F after one step, and F after 4 coupled
+    steps, for the three constructions."""
+    m, F0, vel = _boundary_case(kind)
+    om = orc.Mesh(m)
+    method = getattr(orc, flux)
+    P = vof.PREC_FP64 if prec == "fp64" else vof.PREC_MIXED
+    tol = EPS_F64 if prec == "fp64" else EPS_MIXED
+    ctx = vof.Context(m, precision=P, flux=getattr(vof, "FLUX_" + flux))
+    ctx.set_fraction(F0)
+    ctx.reconstruct()
+    st = om.reconstruct(F0)
+    V = om.geometry()["cell_vol"]
+    bnd = m["neighbour"] < 0
+    t = 0.0
+    for k in range(4):
+        dt = om.suggest_dt(vel, t, 0.5, 10.0)
+        ctx.advect(vel, t, dt)
+        Vd, VF = ctx.face_flux()
+        Vdo, VFo, _ = om.faceflux(vel, t, dt, st, method=method)
+        if k == 0:
+            act = st["tag_f"] == 0
+            assert (act & bnd).sum() > 10  # boundary faces with geometric fluxes
+            assert (VFo[bnd] > 0).any() and (Vdo[bnd] < 0).any()  # outflow and inflow
+        err = np.abs(VF - VFo) / V[m["owner"]]
+        assert err.max() < tol, (k, int(err.argmax()), bool(bnd[err.argmax()]))
+        ctx.reconstruct()
+        st = om.step(vel, t, dt, st, method=method)
+        t += dt
+        assert np.abs(ctx.get_fraction() - st["F"]).max() < tol * (1 if prec == "fp64" else 4), k
+    s = ctx.stats()
+    assert s["n_overflow"] == 0 and s["n_escaped"] == 0
+    assert s["boundary_outflow"] > 0
+
+
+@pytest.mark.parametrize("flux", ["FMFPA", "EMFPA"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_in_kernel_construction_fallback(vof, cases, flux, prec):
+    """Active faces beyond the prebuilt-polyhedron capacity are built inside
+    the flux kernel by one lane with the same arithmetic: a context whose
+    capacity is 5 faces gives the same F, tags and face volumes bit for bit
+    as one with room for all, over 3 coupled steps (FP64: and the oracle's F
+    to 1e-12)."""
+    m, F0, om = cases["hex12"]
+    P = vof.PREC_FP64 if prec == "fp64" else vof.PREC_MIXED
+    kw = dict(precision=P, flux=getattr(vof, "FLUX_" + flux))
+    full = vof.Context(m, **kw)
+    small = vof.Context(m, poly_capacity=5, **kw)
+    vel = VELS["deformation"]
+    st = om.reconstruct(F0)
+    for c in (full, small):
+        c.set_fraction(F0)
+        c.reconstruct()
+    t = 0.0
+    for _ in range(3):
+        dt = om.suggest_dt(vel, t, 0.5, 3.0)
+        full.step(vel, t, dt)
+        small.step(vel, t, dt)
+        st = om.step(vel, t, dt, st, method=getattr(orc_methods(), flux))
+        t += dt
+        assert np.array_equal(full.face_flux()[1], small.face_flux()[1])
+        assert np.array_equal(full.get_fraction(), small.get_fraction())
+        assert small.stats()["n_active_faces"] > 100
+    if prec == "fp64":
+        assert np.abs(small.get_fraction() - st["F"]).max() < EPS_F64
+    with pytest.raises(vof.VofError) as e:
+        vof.Context(m, poly_capacity=-1)
+    assert e.value.status == vof.VOF_EINVAL
+
+
+def orc_methods():
+    import oracle
+    return oracle
