@@ -71,8 +71,9 @@ FLUX_NCU = {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66c
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 # kernels one step launches: reconstruction (cell tags 1, node tags 3,
 # LSGIR 1 or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,
-# flux 1, update 2, and in mixed precision the reconciliation of FP32 noise:
-# 5 per round x 3 rounds + 1); the phase timers count the same kernels
+# flux 1, update 2, and in mixed precision the
+# reconciliation of FP32 noise: 5 per round x 3 rounds + 1); the phase
+# timers count the same kernels
 REPAIR_LAUNCHES = 5 * 3 + 1
 
 
@@ -106,10 +107,11 @@ def parse():
     p.add_argument("--no-init", action="store_true", help="skip timing the device initialisation")
     p.add_argument("--cpu-steps", type=int, default=1)
     p.add_argument("--workload", default="deformation",
-                   choices=["deformation", "tets", "batch", "serve", "deform2d"],
+                   choices=["deformation", "tets", "batch", "serve", "deform2d", "cycle128"],
                    help="deformation: hex grid, Enright field (default line); tets: jittered Kuhn "
                         "tets in rotation; batch: 64 distorted grids advanced together; serve: "
-                        "Poisson request stream; deform2d: 2D deformation on a quasi-2D grid")
+                        "Poisson request stream; deform2d: 2D deformation on a quasi-2D grid; "
+                        "cycle128: the whole 128^3 run of the oracle beside both GPU paths")
     p.add_argument("--requests", type=int, default=48)
     return p.parse_args()
 
@@ -236,10 +238,13 @@ def run_steps(ctx, vel, cfl, t_end, t, n, stream, timing=False):
     return t, evs
 
 
-def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision, flux="fmfpa"):
+def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision, flux="fmfpa",
+             oflops=None):
     """Roofline of the dominant phase's main kernel: algorithmic HBM bytes per
     launch for the sweeps, algorithmic flops per launch for the band kernels.
-    Each phase runs once per step; the flux phase is the one k_flux launch."""
+    Each phase runs once per step; the flux phase is the one k_flux launch.
+    oflops: the oracle's op count for the truncations of the same state's
+    active faces (flops per active face), which replaces the estimate."""
     ms, calls = phase["ms"], phase["calls"]
     per_launch_ms = ms / max(calls, 1)
     nc, nf, nv = grid_counts["n_cell"], grid_counts["n_face"], grid_counts["n_vert"]
@@ -261,8 +266,15 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
     # the counters describe the last advect (one launch of each band kernel);
     # the flux kernel truncates polyhedra built by the polyhedra phase
     f_face, f_trunc = FLOPS[flux]
+    flops_src = "estimate"
     if name == "polyhedra":
         fl = ctx_counts["n_active_faces"] * f_face
+    elif oflops is not None:
+        fl = ctx_counts["n_active_faces"] * oflops["flops_per_active_face"]
+        flops_src = ("oracle op counter: the FP64 oracle's arithmetic for the truncations of the "
+               "same state's active faces (tetrahedral decomposition, "
+               f"{oflops['flops_per_truncation']:.0f} flops per truncation), per active face "
+               "x this launch's active faces")
     else:
         fl = ctx_counts["n_truncations"] * f_trunc
     traffic, ncu = None, None
@@ -281,7 +293,7 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
     achieved = fl / (per_launch_ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "ncu": ncu,
-            "algorithmic_flops_per_launch": fl,
+            "algorithmic_flops_per_launch": fl, "flops_source": flops_src,
             "peak_source": f"{'FP32' if precision == 'mixed' else 'FP64'} FMA lanes x SMs x "
                            f"median SM clock {mhz:.0f} MHz"}
 
@@ -308,49 +320,126 @@ def cpu_baseline(mesh, F0, vel, cfl, t_end, steps, flux="fmfpa", recon="lsgir"):
                       f"from t=0 (FP64 C oracle, OpenMP; mesh build excluded)"}
 
 
+def midcycle_state(a, mesh, F0, vel, cfl, t_end):
+    """F at the first warm-up step of the default line's timed segment, and
+    the segment's time levels: the run from t = 0 is advanced to there with
+    the library (mixed precision) when a GPU is present; it prepares the
+    input of the oracle's timed steps and is not timed."""
+    import torch
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import vof as V
+    B.build()
+    ctx = V.Context(mesh, precision=V.PREC_MIXED)
+    ctx.set_fraction(torch.from_numpy(F0).cuda())
+    ctx.reconstruct()
+    levels = cycle_levels(ctx, vel, cfl, t_end)
+    N = len(levels)
+    s0 = max(a.warmup, N // 2 - a.steps // 2)
+    for t, dt in levels[:s0 - a.warmup]:
+        ctx.step(vel, t, dt)
+    F = ctx.get_fraction()
+    del ctx
+    torch.cuda.empty_cache()
+    return F, levels[s0 - a.warmup:s0 + a.steps], N, s0
+
+
 def main_reference(a):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     mesh, F0, vel, cfl, t_end = workload(a.grid)
+    counts = I.mesh_counts(mesh)
+    F, seg, N, s0 = midcycle_state(a, mesh, F0, vel, cfl, t_end)
     import oracle
     oracle.build()
     om = oracle.Mesh(mesh)
-    st = om.reconstruct(F0)
     method = {"emfpa": oracle.EMFPA, "nmfpa": oracle.NMFPA}.get(a.flux, oracle.FMFPA)
     rc = oracle.LSFIR if a.recon == "lsfir" else oracle.LSGIR
-    if rc == oracle.LSFIR:
-        st = om.reconstruct(F0, recon=rc)
-    t = 0.0
-    for _ in range(a.warmup):
-        dt = om.suggest_dt(vel, t, cfl, t_end)
+    st = om.reconstruct(F, recon=rc)
+    for t, dt in seg[:a.warmup]:
         st = om.step(vel, t, dt, st, method=method, recon=rc)
-        t += dt
     lat = []
     t0 = time.perf_counter()
-    for _ in range(a.steps):
-        s0 = time.perf_counter()
-        dt = om.suggest_dt(vel, t, cfl, t_end)
+    for t, dt in seg[a.warmup:]:
+        s_ = time.perf_counter()
         st = om.step(vel, t, dt, st, method=method, recon=rc)
-        t += dt
-        lat.append((time.perf_counter() - s0) * 1e3)
+        lat.append((time.perf_counter() - s_) * 1e3)
     el = time.perf_counter() - t0
     value = om.n_cell * a.steps / el
+    sample = (f"{a.steps} full oracle steps (after {a.warmup} untimed) of the segment: the state "
+              f"at step {s0 - a.warmup} of the {N}-step run was prepared by the library (mixed "
+              f"precision, not timed), then only the FP64 C oracle (OpenMP) runs")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": el * 1e3 / a.steps,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"3D deformation, hex {a.grid}^3, T=3, "
-                                                        "CFL 0.5, sphere r=0.15",
-                                            "grid": a.grid, "cells": om.n_cell,
-                                            "flux_polyhedron": a.flux,
-                                            "reconstruction": a.recon},
+            "data": "synthetic", "config": segment_config(a, counts, N, s0),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                             "kind": "oracle",
-                             "sample": f"{a.steps} full steps of the {a.grid}^3 workload"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+    return 0
+
+
+def main_cycle(a):
+    """Config 2 at 128^3 to t = 3: the oracle's whole run (multi-core) beside
+    the mixed and FP64 GPU paths; end-of-run shape error (Sec. 4.2, E_shape
+    against the initial shape, which the field returns to at t = T) and the
+    volume of each, and the mixed path's F against the oracle's."""
+    import torch
+    from paper_2111_01524_gb300 import build as B
+    from paper_2111_01524_gb300 import vof as V
+    B.build()
+    grid = 128 if a.grid == 256 else a.grid
+    mesh, F0, vel, cfl, t_end = workload(grid)
+    res = {}
+    Vc = None
+    for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
+        ctx = V.Context(mesh, precision=prec)
+        ctx.set_fraction(torch.from_numpy(F0).cuda())
+        ctx.reconstruct()
+        levels = cycle_levels(ctx, vel, cfl, t_end)
+        Vc = ctx.geometry()["cell_vol"]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for t, dt in levels:
+            ctx.step(vel, t, dt)
+        e1.record()
+        torch.cuda.synchronize()
+        F = ctx.get_fraction()
+        s = ctx.stats()
+        res[name] = {"F": F, "ms": e0.elapsed_time(e1), "steps": len(levels), "stats": s}
+        del ctx
+    import oracle
+    oracle.build()
+    om = oracle.Mesh(mesh)
+    st = om.reconstruct(F0)
+    t0 = time.perf_counter()
+    for t, dt in levels:
+        st = om.step(vel, t, dt, st)
+    el = time.perf_counter() - t0
+    Fo = st["F"]
+    vol0 = float((Vc * F0).sum())
+    out = {"workload": f"3D deformation, hex {grid}^3, sphere r=0.15, T=3, CFL 0.5, whole run",
+           "steps": len(levels), "oracle": {"s": el, "cores": oracle.num_threads(),
+                                            "cell_steps_per_s": om.n_cell * len(levels) / el,
+                                            "e_shape": float((Vc * np.abs(Fo - F0)).sum()),
+                                            "volume_rel_change": float((Vc * Fo).sum() / vol0 - 1)}}
+    for name, r in res.items():
+        F = r["F"]
+        out[name] = {"ms": r["ms"], "cell_steps_per_s": om.n_cell * r["steps"] / (r["ms"] * 1e-3),
+                     "e_shape": float((Vc * np.abs(F - F0)).sum()),
+                     "volume_rel_change": float((Vc * F).sum() / vol0 - 1),
+                     "volume_rel_diff_vs_oracle": float(abs((Vc * F).sum() - (Vc * Fo).sum()) / vol0),
+                     "max_abs_F_diff_vs_oracle": float(np.abs(F - Fo).max()),
+                     "l1_rel_F_diff_vs_oracle": float((Vc * np.abs(F - Fo)).sum() / vol0),
+                     "e_shape_rel_diff_vs_oracle": float(
+                         abs((Vc * np.abs(F - F0)).sum() - (Vc * np.abs(Fo - F0)).sum())
+                         / (Vc * np.abs(Fo - F0)).sum())}
+    print(json.dumps(out))
     return 0
 
 
@@ -707,6 +796,35 @@ def main_serve(a):
     return 0
 
 
+def cycle_levels(ctx, vel, cfl, t_end):
+    """(t, dt) of every step of the run to t_end: Eq. eq:cfl depends on the
+    velocity field and t only, so the whole sequence is known up front."""
+    out, t = [], 0.0
+    while t < t_end - 1e-12:
+        dt = ctx.suggest_dt(vel, t, cfl, t_end)
+        out.append((t, dt))
+        t += dt
+    return out
+
+
+def segment_config(a, counts, n_steps, s0):
+    """The workload of the default line (shared by both arms)."""
+    return {"workload": f"3D deformation (Enright), uniform hex {a.grid}^3 on the unit cube, "
+                        f"sphere r=0.15 at (0.35,0.35,0.35), T=3, CFL 0.5, run to t=3 "
+                        f"({n_steps} steps); timed: steps {s0}..{s0 + a.steps - 1}, centred on "
+                        f"t=T/2 where the interface sheet is largest",
+            "grid": a.grid, "cells": counts["n_cell"], "faces": counts["n_face"],
+            "flux_polyhedron": a.flux, "reconstruction": a.recon,
+            "parallelism": "replicas x1" if int(os.environ.get("WORLD_SIZE", "1")) == 1
+            else f"replicas x{os.environ.get('WORLD_SIZE')}",
+            "l2": "inputs larger than L2 (mesh + state ~10 GB), no flush"}
+
+
+def oracle_state(om, F):
+    """The oracle's reconstruction of F (tags, planes) to step from."""
+    return om.reconstruct(np.ascontiguousarray(F, np.float64))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -719,6 +837,8 @@ def main():
         return main_serve(a)
     if a.workload == "deform2d":
         return main_deform2d(a)
+    if a.workload == "cycle128":
+        return main_cycle(a)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -736,116 +856,165 @@ def main():
     recon = V.RECON_LSFIR if a.recon == "lsfir" else V.RECON_LSGIR
     stream = torch.cuda.current_stream()
     F0_dev = torch.from_numpy(F0).cuda()
+    K, W = a.steps, a.warmup
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    def measure(precision, steps, warmup, with_phases):
-        ctx = V.Context(mesh, precision=precision, flux=flux, recon=recon)
-        ctx.set_fraction(F0_dev, stream=stream)
-        ctx.reconstruct(stream=stream)
-        t, _ = run_steps(ctx, vel, cfl, t_end, 0.0, warmup, stream)
+    def ctx_from(precision, state=None, F=None):
+        c = V.Context(mesh, precision=precision, flux=flux, recon=recon)
+        if state is not None:
+            c.set_state(state, stream=stream)
+        else:
+            c.set_fraction(F0_dev if F is None else F, stream=stream)
+            c.reconstruct(stream=stream)
+        return c
+
+    def timed(ctx, levels, with_phases):
+        """W untimed steps, then exactly K steps between two barriers, timed
+        with CUDA events on the launching stream."""
+        for t, dt in levels[:W]:
+            ctx.step(vel, t, dt, stream=stream)
         barrier()
         if with_phases:
             ctx.set_timing(True)
         clk = ClockSampler(local)
         clk.start()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        t, evs = run_steps(ctx, vel, cfl, t_end, t, steps, stream, timing=True)
-        end.record(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        per = []
+        e0.record(stream)
+        for t, dt in levels[W:W + K]:
+            s0_ = torch.cuda.Event(enable_timing=True)
+            s1_ = torch.cuda.Event(enable_timing=True)
+            s0_.record(stream)
+            ctx.step(vel, t, dt, stream=stream)
+            s1_.record(stream)
+            per.append((s0_, s1_))
+        e1.record(stream)
         barrier()
         clocks = clk.stop()
-        total_ms = start.elapsed_time(end)
-        per_step = [e0.elapsed_time(e1) for e0, e1 in evs]
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
         phases = ctx.timing() if with_phases else None
         if with_phases:
             ctx.set_timing(False)
-        st = ctx.stats(stream=stream)
-        return ctx, total_ms, per_step, phases, clocks, st, t
+        return ms, [x.elapsed_time(y) for x, y in per], phases, clocks, ctx.stats(stream=stream)
 
-    ctx, total_ms, per_step, phases, clocks, stats, t_end_run = measure(prec, a.steps, a.warmup, True)
-    ms = total_ms
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = ws * counts["n_cell"] * a.steps / (ms * 1e-3)
+    # ---- A: the whole cycle t = 0 -> 3, one event per step; the state at
+    # the start of the timed segment's warm-up is kept (host copies, outside
+    # the per-step intervals)
+    ctxA = ctx_from(prec)
+    levels = cycle_levels(ctxA, vel, cfl, t_end)
+    N = len(levels)
+    s0 = max(W, N // 2 - K // 2)  # first timed step, centred on t = T/2
+    g = ctxA.geometry()
+    V_c = g["cell_vol"]
+    vol0 = float((V_c * F0).sum())
+    band_path = []
+    ck = None
+    starts, ends = [], []
+    ev = torch.cuda.Event(enable_timing=True)
+    ev.record(stream)
+    for i, (t, dt) in enumerate(levels):
+        if i == s0 - W or i % 200 == 0:
+            torch.cuda.synchronize()
+            st_i = ctxA.stats(stream=stream)
+            band_path.append({"step": i, "t": t, "interfacial_cells": st_i["n_interfacial"],
+                              "active_faces": st_i["n_active_faces"]})
+            if i == s0 - W:
+                ck = ctxA.get_state(stream=stream)
+                F_ck = ctxA.get_fraction()
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+        starts.append(ev)
+        ctxA.step(vel, t, dt, stream=stream)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        ends.append(ev)
+    torch.cuda.synchronize()
+    whole_ms = float(sum(x.elapsed_time(y) for x, y in zip(starts, ends)))
+    stA = ctxA.stats(stream=stream)
+    FT = ctxA.get_fraction()
+    whole = {"steps": N, "ms": whole_ms, "value": ws * counts["n_cell"] * N / (whole_ms * 1e-3),
+             "unit": UNIT, "volume_rel_change": (stA["volume"] - vol0) / vol0,
+             "clip_loss_rel": stA["clip_loss"] / vol0,
+             "e_shape": float((V_c * np.abs(FT - F0)).sum()),
+             "band_path": band_path,
+             "note": "per-step CUDA-event intervals summed over all steps of the run; host "
+                     "read-backs between steps excluded"}
+    del ctxA
 
-    # F error of the measured path against the FP64 GPU path and the oracle is
-    # established by the parity tests; here the path's own conservation is
-    # reported: relative change of sum(V F) over the run (clip and cut-off only)
-    g = ctx.geometry()
-    vol0 = float((g["cell_vol"] * F0).sum())
-    vol_rel = abs(stats["volume"] - vol0) / vol0
-    # the library's bookkeeping: what clip, cut-off and boundary removed
-    book_rel = abs(stats["volume"] - (vol0 - stats["clip_loss"] - stats["cutoff_loss"]
-                                      - stats["boundary_outflow"])) / vol0
+    # ---- B: the timed segment centred on T/2 (the default line's value)
+    seg = levels[s0 - W:s0 + K]
+    ctxB = ctx_from(prec, state=ck)
+    ms, per_step, phases, clocks, stats = timed(ctxB, seg, True)
+    value = ws * counts["n_cell"] * K / (ms * 1e-3)
+    FB = ctxB.get_fraction()
+    volB = float((V_c * FB).sum())
 
+    # ---- C: the FP64 path on the same segment from the same state
     fp64 = None
     if not a.no_fp64 and prec == V.PREC_MIXED:
-        fsteps = max(3, a.steps // 2)
-        ctx64, ms64, per64, ph64, clk64, st64, _ = measure(V.PREC_FP64, fsteps, a.warmup, False)
-        if dist is not None:
-            tt = torch.tensor([ms64], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms64 = float(tt.item())
-        v64 = ws * counts["n_cell"] * fsteps / (ms64 * 1e-3)
-        # mixed vs FP64 after the same number of steps from the same F0
-        ctxm, _, _, _, _, _, _ = measure(prec, fsteps, a.warmup, False)
-        Fm = ctxm.get_fraction()
-        F64 = ctx64.get_fraction()
-        fp64 = {"value": v64, "unit": UNIT, "steps": fsteps, "ms_per_step": ms64 / fsteps,
+        c64 = ctx_from(V.PREC_FP64, state=ck)
+        ms64, per64, _, clk64, st64 = timed(c64, seg, False)
+        v64 = ws * counts["n_cell"] * K / (ms64 * 1e-3)
+        F64 = c64.get_fraction()
+        fp64 = {"value": v64, "unit": UNIT, "steps": K, "ms_per_step": ms64 / K,
+                "mixed_over_fp64": value / v64,
                 "band": {"interfacial_cells": st64["n_interfacial"],
                          "active_faces": st64["n_active_faces"]},
-                "mixed_over_fp64": value / v64,
-                "max_abs_F_diff_mixed_vs_fp64": float(np.abs(Fm - F64).max()),
-                # the integral measure (as E_shape, Sec. 4.2): robust where a
-                # discontinuous decision (LSFIR's acceptance) flips in a few cells
-                "l1_rel_F_diff_mixed_vs_fp64": float((g["cell_vol"] * np.abs(Fm - F64)).sum()
-                                                     / (g["cell_vol"] * F64).sum()),
-                "after_steps": fsteps + a.warmup}
-        del ctx64, ctxm
+                "max_abs_F_diff_mixed_vs_fp64": float(np.abs(FB - F64).max()),
+                "l1_rel_F_diff_mixed_vs_fp64": float((V_c * np.abs(FB - F64)).sum()
+                                                     / (V_c * F64).sum()),
+                "volume_rel_diff_mixed_vs_fp64": float(abs(volB - (V_c * F64).sum()) / vol0),
+                "after_steps": W + K,
+                "from": f"the state at step {s0 - W}, the same for both paths"}
+        del c64
 
-    # end-to-end through the C-ABI with host buffers: each step copies F in
-    # from pinned host memory, runs reconstruct + advect, and reads F back
+    # ---- D: the same K steps from t = 0 (the smallest band of the run)
+    ctxD = ctx_from(prec)
+    msD, _, _, _, stD = timed(ctxD, levels[:W + K], False)
+    from_t0 = {"value": ws * counts["n_cell"] * K / (msD * 1e-3), "unit": UNIT,
+               "ms_per_step": msD / K, "interfacial_cells": stD["n_interfacial"],
+               "active_faces": stD["n_active_faces"]}
+    del ctxD
+
+    # ---- E: end to end through the C-ABI with host buffers: each step sets
+    # F from pinned host memory, reconstructs, advects, reads F back
     e2e = None
     if not a.no_e2e:
         ctxe = V.Context(mesh, precision=prec, flux=flux, recon=recon)
-        Fh = torch.from_numpy(F0.copy()).pin_memory().numpy()
+        Fh = torch.from_numpy(np.ascontiguousarray(F_ck)).pin_memory().numpy()
         ctxe.set_fraction(Fh, stream=stream)
-        t = 0.0
-        for _ in range(a.warmup):
+        for t, dt in seg[:W]:
             ctxe.reconstruct(stream=stream)
-            dt = ctxe.suggest_dt(vel, t, cfl, t_end)
             ctxe.advect(vel, t, dt, stream=stream)
-            t += dt
         ctxe.get_fraction(out=Fh, stream=stream)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(a.steps):
+        for t, dt in seg[W:]:
             ctxe.set_fraction(Fh, stream=stream)
             ctxe.reconstruct(stream=stream)
-            dt = ctxe.suggest_dt(vel, t, cfl, t_end)
             ctxe.advect(vel, t, dt, stream=stream)
             ctxe.get_fraction(out=Fh, stream=stream)
-            t += dt
         barrier()
         el = time.perf_counter() - t0
         if dist is not None:
             tt = torch.tensor([el], device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             el = float(tt.item())
-        e2e = {"value": ws * counts["n_cell"] * a.steps / el, "unit": UNIT,
+        e2e = {"value": ws * counts["n_cell"] * K / el, "unit": UNIT,
                "h2d_bytes_per_step": 8 * counts["n_cell"],
                "d2h_bytes_per_step": 8 * counts["n_cell"]}
         del ctxe
 
-    # the initial F computed on the device (initfgrid, Sec. 3.2: ndiv = 10, the
-    # paper's refinement) for the same sphere: time and volume error
+    # ---- F: the initial F computed on the device (initfgrid, Sec. 3.2, ndiv = 10)
     init = None
     if not a.no_init:
         ctxi = V.Context(mesh, precision=prec, flux=flux, recon=recon)
@@ -860,49 +1029,64 @@ def main():
         Fi = ctxi.get_fraction()
         exact = 4.0 / 3.0 * np.pi * 0.15 ** 3
         init = {"ms": e0.elapsed_time(e1), "ndiv": 10,
-                "volume_rel_error": float(abs((g["cell_vol"] * Fi).sum() - exact) / exact),
+                "volume_rel_error": float(abs((V_c * Fi).sum() - exact) / exact),
                 "interfacial_cells": int(((Fi > 0) & (Fi < 1)).sum())}
         del ctxi
+
+    # ---- G: the oracle, one step from the state at the segment (CPU baseline;
+    # its op counter gives the truncation flops of this step's active faces)
+    cpu, oflops = None, None
+    if rank == 0 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        om = oracle.Mesh(mesh)
+        st_o = oracle_state(om, F_ck)
+        t_ck, dt_ck = seg[0]
+        method = {"emfpa": oracle.EMFPA, "nmfpa": oracle.NMFPA}.get(a.flux, oracle.FMFPA)
+        rc = oracle.LSFIR if a.recon == "lsfir" else oracle.LSGIR
+        t0 = time.perf_counter()
+        new = om.step(vel, t_ck, dt_ck, st_o, method=method, recon=rc)
+        el = time.perf_counter() - t0
+        ostats = new["stats"]
+        oflops = {"flops_per_active_face": float(ostats[4]) / max(int(ostats[0]), 1),
+                  "flops_per_truncation": float(ostats[4]) / max(int(ostats[3]), 1),
+                  "active_faces": int(ostats[0]), "truncations": int(ostats[3])}
+        cpu = {"value": om.n_cell / el, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": f"1 full step (faceflux, vofadv, taggrid, LSGIR, plane constants) of "
+                         f"the {a.grid}^3 workload from the state at step {s0 - W} (t = "
+                         f"{t_ck:.3f}), FP64 C oracle, OpenMP; mesh build and the oracle's "
+                         f"reconstruction of that state excluded"}
 
     peaks, peak_kind = measured_peaks()
     # the dominant kernel: the phase with the longest average launch (the flux
     # phase is its one k_flux launch per step; LSFIR's reconstruction phase
     # takes longer in total but over 1 + 2 n_out shorter launches)
     dom = max(phases.items(), key=lambda kv: kv[1][0] / max(kv[1][1], 1))
-    phase = {"name": dom[0], "ms": dom[1][0], "calls": a.steps}
-    rl = roofline(stats, phase, counts, peaks, peak_kind, clocks, a.precision, a.flux)
+    phase = {"name": dom[0], "ms": dom[1][0], "calls": K}
+    rl = roofline(stats, phase, counts, peaks, peak_kind, clocks, a.precision, a.flux, oflops)
     launches = sum(n for _, n in phases.values())
-
-    cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(mesh, F0, vel, cfl, t_end, a.cpu_steps, a.flux, a.recon)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": ms / K,
             "p50_ms": float(np.percentile(per_step, 50)),
             "p99_ms": float(np.percentile(per_step, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": f"3D deformation (Enright), uniform hex {a.grid}^3 on the "
-                                   f"unit cube, sphere r=0.15 at (0.35,0.35,0.35), T=3, CFL 0.5, "
-                                   f"steps from t=0",
-                       "grid": a.grid, "cells": counts["n_cell"], "faces": counts["n_face"],
-                       "precision": a.precision, "flux_polyhedron": a.flux,
-                       "reconstruction": a.recon,
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (mesh + state ~10 GB), no flush"},
+            "config": segment_config(a, counts, N, s0),
+            "precision": a.precision,
             "gpu_launches": launches,
             "phases_ms": {k: v[0] for k, v in phases.items()},
             "band": {"interfacial_cells": stats["n_interfacial"],
                      "active_faces": stats["n_active_faces"],
                      "truncations_last_step": stats["n_truncations"],
-                     "overflow": stats["n_overflow"]},
-            "volume_rel_change": vol_rel,
-            "volume_bookkeeping_rel_residual": book_rel,
-            "clip_loss_rel": stats["clip_loss"] / vol0,
-            "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "device_init": init,
+                     "overflow": stats["n_overflow"], "escaped": stats["n_escaped"],
+                     "clipped_last_step": stats["n_clipped"],
+                     "reconciled_faces_last_step": stats["n_repaired"]},
+            "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
+            "from_t0": from_t0, "whole_cycle": whole, "device_init": init,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -305,7 +305,7 @@ class Mesh:
     def faceflux(self, vel, t, dt, st, method=FMFPA):
         Vd = np.empty(self.n_face)
         VF = np.empty(self.n_face)
-        stats = np.zeros(4, np.int64)
+        stats = np.zeros(5, np.int64)
         v = _vel(vel)
         lib().orc_faceflux(self._m, C.byref(v), t, dt, _p(st["F"]), _p(st["tag_f"]),
                            _p(st["tag_c"]), _p(st["nrm"]), _p(st["C"]), _p(Vd), _p(VF),

@@ -57,6 +57,15 @@ struct orc_mesh {
   uint8_t* convex;
 };
 
+/* ------------------------------------------------------------- op counter */
+/* floating-point operations of the truncations, per thread: each counted
+ * routine adds the adds, subtracts, multiplies and divides it performs (a
+ * comparison or a sign change is not counted). orc_faceflux reports the sum
+ * over its (face, cell) truncations in stats[4]; the count measures the work
+ * of this plain algorithm, it does not change any result. */
+static _Thread_local int64_t g_flops;
+#define ORC_FLOPS(n) (g_flops += (n))
+
 /* ---------------------------------------------------------------- vectors */
 static void sub3(const double* a, const double* b, double* r) {
   r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2];
@@ -1123,9 +1132,13 @@ int orc_fmfpa(const orc_mesh* m, int64_t f, const orc_velocity* vel, double th,
 /* volume of tetrahedron T clipped by planes[k] (a.x + b > 0), recursively:
  * each plane leaves 0, 1 or 3 tetrahedra */
 static double tet_clip(const double T[4][3], const double* planes, int np) {
-  if (np == 0) return fabs(det6(T[0], T[1], T[2], T[3])) / 6.0;
+  if (np == 0) {
+    ORC_FLOPS(24);  /* det6 (23) and the division */
+    return fabs(det6(T[0], T[1], T[2], T[3])) / 6.0;
+  }
   double s[4];
   int in[4], ni = 0, out[4], no = 0;
+  ORC_FLOPS(24);  /* four plane values: 3 mul + 3 add each */
   for (int i = 0; i < 4; ++i) {
     s[i] = planes[0] * T[i][0] + planes[1] * T[i][1] + planes[2] * T[i][2] + planes[3];
     if (s[i] > 0) in[ni++] = i; else out[no++] = i;
@@ -1133,6 +1146,8 @@ static double tet_clip(const double T[4][3], const double* planes, int np) {
   if (ni == 0) return 0.0;
   if (ni == 4) return tet_clip(T, planes + 4, np - 1);
   double R[4][3];
+  /* each cut point: t (sub, div) and three (sub, mul, add) */
+  ORC_FLOPS(ni == 2 ? 4 * 11 : 3 * 11);
   if (ni == 1) {
     int p = in[0];
     for (int d = 0; d < 3; ++d) R[0][d] = T[p][d];
@@ -1215,6 +1230,7 @@ double orc_poly_clip_volume(int nv, const double* V, int nf, const int* fp,
       for (int k = 0; k < 4; ++k)
         for (int d = 0; d < 3; ++d) T[k][d] = p[k][d];
       double d6 = det6(T[0], T[1], T[2], T[3]);
+      ORC_FLOPS(23 + 2);  /* det6, the signed sum */
       if (d6 == 0.0) continue;
       double sgn = d6 > 0 ? 1.0 : -1.0;
       vol += sgn * tet_clip(T, planes, np);
@@ -1226,6 +1242,7 @@ double orc_poly_clip_volume(int nv, const double* V, int nf, const int* fp,
 /* inward half-space of the plane through p with outward normal nout,
  * expressed in the frame with origin o:  -nout.(x + o - p) > 0 */
 static void inward_plane(const double* nout, const double* p, const double* o, double* pl) {
+  ORC_FLOPS(8);  /* sub3, dot3 */
   pl[0] = -nout[0]; pl[1] = -nout[1]; pl[2] = -nout[2];
   double d[3];
   sub3(o, p, d);
@@ -1250,6 +1267,7 @@ static double truncate_in_cell(const orc_mesh* m, int nv, const double* V, int n
       /* fluid side n.(x - xc) + C > 0 */
       const double* n = nrm + 3 * k;
       double d[3];
+      ORC_FLOPS(9);  /* sub3, dot3, add */
       sub3(o, m->cc + 3 * k, d);
       planes[4 * np] = n[0]; planes[4 * np + 1] = n[1]; planes[4 * np + 2] = n[2];
       planes[4 * np + 3] = dot3(n, d) + Cp[k];
@@ -1279,6 +1297,9 @@ static double truncate_in_cell(const orc_mesh* m, int nv, const double* V, int n
       for (int a = 0; a < 4; ++a)
         for (int d = 0; d < 3; ++d) T[a][d] = pts[a][d];
       double d6 = det6(T[0], T[1], T[2], T[3]);
+      /* two sub3, det6, four planes (two sub3, cross, scale, dot) and the
+       * PLIC plane */
+      ORC_FLOPS(6 + 23 + 4 * 23 + (tag == 0 ? 9 : 0) + 2);
       if (d6 == 0.0) continue;
       double sg = d6 > 0 ? 1.0 : -1.0;
       /* the 4 inward planes of tetrahedron T */
@@ -1315,8 +1336,8 @@ void orc_faceflux(const orc_mesh* m, const orc_velocity* vel, double t, double d
                   int64_t* stats, int method) {
   (void)F;
   double th = t + 0.5 * dt;
-  int64_t n_geo = 0, n_deg = 0, n_edge = 0, n_trunc = 0;
-#pragma omp parallel for schedule(dynamic, 16) reduction(+ : n_geo, n_deg, n_edge, n_trunc)
+  int64_t n_geo = 0, n_deg = 0, n_edge = 0, n_trunc = 0, n_flops = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : n_geo, n_deg, n_edge, n_trunc, n_flops)
   for (int64_t f = 0; f < m->nf; ++f) {
     double c[3];
     memcpy(c, m->fc + 3 * f, sizeof c);
@@ -1359,11 +1380,15 @@ void orc_faceflux(const orc_mesh* m, const orc_velocity* vel, double t, double d
             hi[2] > bb[2] && lo[2] < bb[5]))
         continue;
       ++n_trunc;
+      const int64_t f0 = g_flops;
       vf += truncate_in_cell(m, nvp, P, nfp, fp, fi, kc, tag_c[kc], nrm, Cp, c);
+      n_flops += g_flops - f0 + 1;  /* and the sum over cells */
     }
     VF[f] = vf;
   }
-  if (stats) { stats[0] = n_geo; stats[1] = n_deg; stats[2] = n_edge; stats[3] = n_trunc; }
+  if (stats) {
+    stats[0] = n_geo; stats[1] = n_deg; stats[2] = n_edge; stats[3] = n_trunc; stats[4] = n_flops;
+  }
 }
 
 /* --------------------------------------------------------- vofadv (Eq fnext) */

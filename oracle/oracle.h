@@ -144,7 +144,9 @@ int orc_nmfpa(const orc_mesh* m, int64_t face, const orc_velocity* v,
 /* faceflux (Sec. 3.5 with Sec. 2.2): V_d and V_F for every face, with the
  * flux polyhedra of `method` (0: FMFPA, 1: EMFPA, 2: NMFPA). stats[0] = geometric
  * faces, [1] = degenerate-line fallbacks, [2] = edge-on faces, [3] =
- * (face, cell) truncations evaluated. Threads: OpenMP over faces. */
+ * (face, cell) truncations evaluated, [4] = floating-point operations of those
+ * truncations (op counter of this algorithm). stats has 5 entries. Threads:
+ * OpenMP over faces. */
 void orc_faceflux(const orc_mesh* m, const orc_velocity* v, double t,
                   double dt, const double* F, const int8_t* tag_f,
                   const int8_t* tag_c, const double* nrm, const double* C,

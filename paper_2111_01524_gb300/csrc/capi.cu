@@ -52,7 +52,7 @@ void free_all(vof_ctx* c) {
                    c->lzp, c->lxr, c->lyr, c->lzr, c->lnx, c->lny, c->lnz, c->lnx32, c->lny32,
                    c->lnz32, c->lturn, c->fm_v, c->fm_f, c->fm_meta, c->fm_split, c->dombox,
                    c->fexact, c->Fprev, c->risk, c->repf, c->repc, c->stamp_r, c->Eexc,
-                   c->Sroom};
+                   c->Sroom, c->cover8, c->rstar};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -379,6 +379,7 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
     c->bytes += (int64_t)(gs * (3 * kFmSlots + 7) * c->fm_cap);
     CKI(dalloc(c, &c->fm_meta, c->fm_cap));
     CKI(dalloc(c, &c->fm_split, c->fm_cap));
+    CKI(dalloc(c, &c->cover8, nf));
   }
   if (o.reconstruction == VOF_RECON_LSFIR) {
     // PLIC centres by cell, accepted normals by band position, max turn per iteration
@@ -432,8 +433,10 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
   CKI(cudaMemsetAsync(c->tc, 0xff, nc, s));
   CKI(cudaMemsetAsync(c->Vd, 0, sizeof(double) * nf, s));
   CKI(cudaMemsetAsync(c->VF, 0, sizeof(double) * nf, s));
+  CKI(dalloc(c, &c->rstar, nv));
   CKI(launch_face_geometry(c, s));
   CKI(launch_cell_geometry(c, s));
+  CKI(launch_node_star(c, s));
   if (o.precision == VOF_PREC_MIXED) CKI(launch_mixed_copies(c, s));
   CKI(cudaStreamSynchronize(s));
   {

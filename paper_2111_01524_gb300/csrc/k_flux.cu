@@ -852,53 +852,79 @@ __device__ __noinline__ bool point_in_cell(const DevMesh& M, const GeoView<G>& G
   return wn != 0;
 }
 
-// the vertices (bits of `need`) of the base polyhedron that lie in cell k
-// (one lane); an axis-aligned box cell by its bounds
+// p in cell k (one thread): the cell's bounding box first, then an
+// axis-aligned box cell is its box, any other cell point_in_cell
 template <typename G>
-__device__ unsigned cover_bits(const DevMesh& M, const GeoView<G>& Gv, const FaceFrame<G>& fr,
-                               const Poly<G>& P, int k, unsigned need) {
-  const G tol = sizeof(G) == 8 ? G(1e-9) : G(2e-5);
-  unsigned bits = 0u;
-  if (M.convex[k] == 2) {
-    const int64_t nc = M.nc;
-    const G lx = rel(Gv.bb[k], fr.cx) * fr.sc - tol, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc + tol;
-    const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc - tol, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc + tol;
-    const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc - tol, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc + tol;
-    while (need) {
-      const int v = __ffs(need) - 1;
-      need &= need - 1u;
-      const G x = P.bx[v], y = P.by[v], z = P.bz[v];
-      if (x >= lx && x <= hx && y >= ly && y <= hy && z >= lz && z <= hz) bits |= 1u << v;
-    }
-    return bits;
-  }
-  while (need) {
-    const int v = __ffs(need) - 1;
-    need &= need - 1u;
-    if (point_in_cell(M, Gv, fr, k, P.bx[v], P.by[v], P.bz[v], tol)) bits |= 1u << v;
-  }
-  return bits;
+__device__ __forceinline__ bool in_cell(const DevMesh& M, const GeoView<G>& Gv, const FaceFrame<G>& fr,
+                                        int k, G px, G py, G pz, G tol) {
+  const int64_t nc = M.nc;
+  const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
+  if (px < lx - tol || px > hx + tol) return false;
+  const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
+  if (py < ly - tol || py > hy + tol) return false;
+  const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
+  if (pz < lz - tol || pz > hz + tol) return false;
+  return M.convex[k] == 2 || point_in_cell(M, Gv, fr, k, px, py, pz, tol);
 }
 
-// coverage bits of face j from the vertices no candidate cell holds (miss):
-// kUncovered, and kEscaped for one inside the grid's domain box (lanes over
-// vertices; FP64 arithmetic for this rare case)
-template <typename G>
-__device__ __noinline__ unsigned cover_result(const DevMesh& M, const DevState& S, const FaceFrame<G>& fr,
-                                 const Poly<G>& P, int j, unsigned miss, int lane) {
-  if (miss == 0u) return 0u;
-  bool esc = false;
-  if ((miss >> lane) & 1u) {
+// coverage bits of the flux polyhedron of face j (one thread; vertices in
+// the face-local frame fr). Each vertex to locate (back-traced points and
+// apex; EMFPA's side centres are averages of them) is looked up first in
+// the cells around the face node it was traced from (the apex: around any
+// node of the face), all of them candidate cells, then in the whole
+// candidate set (owner, neighbour and their node neighbours); a vertex in no
+// candidate cell sets kUncovered, and kEscaped when it lies inside the
+// grid's domain box (outside it there is no fluid, R11). A polyhedron whose
+// box is flat along an axis has no volume and is not tested.
+template <typename G, int KIND>
+__device__ __noinline__ unsigned poly_coverage(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
+                                               int j, const G* vx, const G* vy, const G* vz,
+                                               const FaceFrame<G>& fr) {
+  const G tol = sizeof(G) == 8 ? G(1e-9) : G(2e-5);
+  if (!(fr.hi[0] - fr.lo[0] > tol && fr.hi[1] - fr.lo[1] > tol && fr.hi[2] - fr.lo[2] > tol)) return 0u;
+  const int I = fr.I, nvb = base_verts<KIND>(I);
+  const int64_t fb = M.fptr[j];
+  const int own = M.own[j], nbr = M.nbr[j];
+  unsigned bits = 0u;
+  for (int v = I; v < nvb; ++v) {
+    if (KIND == VOF_FLUX_EMFPA && v >= 2 * I && v < 3 * I) continue;  // side centres
+    const G px = vx[v], py = vy[v], pz = vz[v];
+    bool found = false;
+    // the star of the node it was traced from (apex: of any face node): a
+    // point within the node's ball lies in one of its cells; else the cells
+    // around that node
+    const int i0 = v < 2 * I ? v - I : 0, i1 = v < 2 * I ? v - I + 1 : I;
+    for (int i = i0; i < i1 && !found; ++i) {
+      const G rs = (G)M.rstar[M.fvert[fb + i]] * fr.sc;
+      const G dx = px - vx[i], dy = py - vy[i], dz = pz - vz[i];
+      found = dx * dx + dy * dy + dz * dz < rs * rs;
+    }
+    for (int i = i0; i < i1 && !found; ++i) {
+      const int node = M.fvert[fb + i];
+      for (int64_t q = M.vc_ptr[node]; q < M.vc_ptr[node + 1] && !found; ++q)
+        found = in_cell(M, Gv, fr, M.vc[q], px, py, pz, tol);
+    }
+    // the whole candidate set
+    for (int pass = 0; pass < 2 && !found; ++pass) {
+      const int c0 = pass == 0 ? own : nbr;
+      if (c0 < 0) break;
+      found = in_cell(M, Gv, fr, c0, px, py, pz, tol);
+      for (int64_t q = M.nb_ptr[c0]; q < M.nb_ptr[c0 + 1] && !found; ++q)
+        found = in_cell(M, Gv, fr, M.nb[q], px, py, pz, tol);
+    }
+    if (found) continue;
+    bits |= kUncovered;
     const int g = M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j);
     const double* b = S.dombox + 6 * g;
     const double L = (double)fr.L;
-    const double ax = absd(fr.cx) + L * (double)P.bx[lane], ay = absd(fr.cy) + L * (double)P.by[lane],
-                 az = absd(fr.cz) + L * (double)P.bz[lane];
+    const double ax = absd(fr.cx) + L * (double)px, ay = absd(fr.cy) + L * (double)py,
+                 az = absd(fr.cz) + L * (double)pz;
     const double eps = 1e-9 * L;
-    esc = ax > b[0] + eps && ax < b[3] - eps && ay > b[1] + eps && ay < b[4] - eps &&
-          az > b[2] + eps && az < b[5] - eps;
+    if (ax > b[0] + eps && ax < b[3] - eps && ay > b[1] + eps && ay < b[4] - eps && az > b[2] + eps &&
+        az < b[5] - eps)
+      bits |= kEscaped;
   }
-  return kUncovered | (__any_sync(GVOF_FULL, esc) ? kEscaped : 0u);
+  return bits;
 }
 
 // the polyhedron of face j into shared memory by lane 0 (the other lanes
@@ -909,6 +935,24 @@ __device__ __noinline__ bool build_polyhedron(const DevMesh& M, const GeoView<G>
                                               int j, double Vd, Poly<G>& P, FaceFrame<G>& frs, int lane) {
   int ok = 0;
   if (lane == 0) ok = poly_scalar<G, KIND>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
+  ok = __shfl_sync(GVOF_FULL, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+// the polyhedron of active face w built by lane 0 (past the prebuilt
+// capacity), with its coverage bits written as k_prebuild writes them
+template <typename G, int KIND>
+__device__ __noinline__ bool build_polyhedron_cov(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
+                                                  const GridParam& p, int j, unsigned w, double Vd,
+                                                  Poly<G>& P, FaceFrame<G>& frs, int lane) {
+  int ok = 0;
+  if (lane == 0) {
+    ok = poly_scalar<G, KIND>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
+    const unsigned cov = ok ? poly_coverage<G, KIND>(M, Gv, S, j, P.bx, P.by, P.bz, frs) : 0u;
+    S.cover8[w] = (uint8_t)cov;
+    if (cov & kEscaped) atomicAdd(S.cnt + kNEscape, 1ull);
+  }
   ok = __shfl_sync(GVOF_FULL, ok, 0);
   __syncwarp();
   return ok != 0;
@@ -1191,13 +1235,12 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
 // exactly 0: complement when no empty cell is met, fluid when no full cell
 // is, otherwise by the donating cell's F. Returns V_F / L^3; *whole: P lies
 // in the fluid (1) or empty (2) part of one cell (V_F = V_d or 0 exactly).
-// *cover: the coverage bits of P (cover_result), found while the candidate
-// cells are scanned: each candidate met by the box of P tests the vertices
-// not yet located; the complement form needs a covered P.
+// cover: the coverage bits of P (poly_coverage); the complement form needs a
+// covered P.
 template <typename G, int KIND>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, double Vd, G Vl, Poly<G>& P, int lane,
-                              unsigned& err, int* whole, bool* complement, unsigned* cover,
+                              unsigned& err, int* whole, bool* complement, unsigned cover,
                               unsigned long long& n_trunc) {
   const int own = M.own[j], nbr = M.nbr[j];
   const int64_t a0 = M.nb_ptr[own];
@@ -1206,19 +1249,6 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
   int n = cap + 1;  // FP64: the fluid form, no list (the cells are scanned once)
   bool neg = false, pos = false;
   if (sizeof(G) == 4) n = 0;
-  // the vertices located: back-traced points and apex (EMFPA's side centres
-  // are averages of located points)
-  // (a polyhedron whose box is flat along an axis has no volume to miss:
-  // the cells its box touches do not pass the strict box test)
-  const int nvb = base_verts<KIND>(fr.I);
-  const G flat = sizeof(G) == 8 ? G(1e-9) : G(2e-5);
-  const bool solid = fr.hi[0] - fr.lo[0] > flat && fr.hi[1] - fr.lo[1] > flat && fr.hi[2] - fr.lo[2] > flat;
-  const unsigned need = !solid ? 0u
-                               : (((1u << nvb) - 1u) & ~((1u << fr.I) - 1u)) &
-                                     ~(KIND == VOF_FLUX_EMFPA ? ((1u << (3 * fr.I)) - 1u) & ~((1u << (2 * fr.I)) - 1u)
-                                                              : 0u);
-  unsigned found = 0u;
-  *cover = 0u;
   for (int pass = 0; sizeof(G) == 4 && pass < 2; ++pass) {
     const int c0 = pass == 0 ? own : nbr;
     if (c0 < 0) break;
@@ -1227,8 +1257,6 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
       const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
-      const unsigned todo = need & ~found;
-      if (todo) found |= __reduce_or_sync(GVOF_FULL, k >= 0 ? cover_bits<G>(M, Gv, fr, P, k, todo) : 0u);
       const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
       if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
       if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
@@ -1238,9 +1266,8 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     }
   }
   __syncwarp();
-  if (sizeof(G) == 4) *cover = cover_result<G>(M, S, fr, P, j, need & ~found, lane);
   bool comp = false;
-  if (sizeof(G) == 4 && nbr >= 0 && !(*cover & kUncovered)) {
+  if (sizeof(G) == 4 && nbr >= 0 && !(cover & kUncovered)) {
     if (!neg && pos) comp = true;
     else if (neg && !pos) comp = false;
     else comp = S.F[Vd > 0.0 ? own : nbr] > 0.5;
@@ -1257,7 +1284,7 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
       int w = 0;
       v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
       ++n_trunc;
-      if (w) { *whole = comp ? 2 : 1; *cover = 0u; return G(0); }  // no other cell meets P
+      if (w) { *whole = comp ? 2 : 1; return G(0); }  // no other cell meets P
     }
     return v;
   }
@@ -1270,10 +1297,6 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     for (int base = 0; base < nb; base += 32) {
       int8_t tk;
       const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
-      if (sizeof(G) == 8) {
-        const unsigned todo = need & ~found;
-        if (todo) found |= __reduce_or_sync(GVOF_FULL, k >= 0 ? cover_bits<G>(M, Gv, fr, P, k, todo) : 0u);
-      }
       unsigned bal = __ballot_sync(GVOF_FULL, k >= 0 && tk != skip);
       while (bal) {
         const int src = __ffs(bal) - 1;
@@ -1282,11 +1305,10 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
         int w = 0;
         v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
         ++n_trunc;
-        if (w) { *whole = comp ? 2 : 1; *cover = 0u; return G(0); }
+        if (w) { *whole = comp ? 2 : 1; return G(0); }
       }
     }
   }
-  if (sizeof(G) == 8) *cover = cover_result<G>(M, S, fr, P, j, need & ~found, lane);
   return v;
 }
 
@@ -1307,6 +1329,9 @@ __global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevS
     const bool ok = poly_scalar<G, KIND>(M, Gv, gp, j, Vd, vx, vy, vz, fr);
     S.fm_meta[w] = (uint32_t)fr.I | ((uint32_t)fr.degenerate << 8) | ((uint32_t)fr.edgeon << 16) |
                    ((uint32_t)(ok ? 1 : 0) << 24);
+    const unsigned cov = ok ? poly_coverage<G, KIND>(M, Gv, S, j, vx, vy, vz, fr) : 0u;
+    S.cover8[w] = (uint8_t)cov;
+    if (cov & kEscaped) atomicAdd(S.cnt + kNEscape, 1ull);
     if (!ok) continue;
     S.fm_split[w] = fr.split;
     G* f = ff + (size_t)w * 7;
@@ -1326,7 +1351,7 @@ template <typename G, int KIND>
 __device__ bool poly_for_face(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, unsigned w,
                               int j, const GridParam& p, double Vd, Poly<G>& P, FaceFrame<G>& fr,
                               int lane) {
-  if ((int64_t)w >= S.fm_cap) return build_polyhedron<G, KIND>(M, Gv, p, j, Vd, P, fr, lane);
+  if ((int64_t)w >= S.fm_cap) return build_polyhedron_cov<G, KIND>(M, Gv, S, p, j, w, Vd, P, fr, lane);
   const uint32_t meta = S.fm_meta[w];
   const int I = (int)(meta & 255u);
   const bool ok = (meta >> 24) & 1u;
@@ -1370,7 +1395,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
   Poly<G>& P = polys[wib];
   FaceFrame<G>& fr = wfr[wib];
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
-  unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0, n_esc = 0;
+  unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0;
   for (unsigned w = next_face(S, lane); w < n_af; w = next_face(S, lane)) {
     const int j = S.afaces[w];
     // the face's grid parameters, staged in shared memory (read at use)
@@ -1396,10 +1421,8 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     const G L3 = fr.L * fr.L * fr.L;
     int wh = 0;
     bool comp = false;
-    unsigned cov = 0u;
-    const G v = sweep_candidates<G, KIND>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp, &cov,
-                                          n_trunc);
-    if (cov & kEscaped) ++n_esc;
+    const G v = sweep_candidates<G, KIND>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp,
+                                          (unsigned)S.cover8[w], n_trunc);
     double VFj;
     if (wh == 1) VFj = Vd;  // P inside the fluid of one cell: exactly V_d
     else if (wh == 2) VFj = 0.0;  // P inside the empty part of one cell
@@ -1417,7 +1440,6 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     if (n_over) atomicAdd(S.cnt + kNOverflow, n_over);
     if (n_deg) atomicAdd(S.cnt + kNDegen, n_deg);
     if (n_edge) atomicAdd(S.cnt + kNEdgeOn, n_edge);
-    if (n_esc) atomicAdd(S.cnt + kNEscape, n_esc);
   }
 }
 

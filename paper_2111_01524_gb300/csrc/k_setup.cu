@@ -138,6 +138,52 @@ __global__ void k_cell_geometry(DevMesh M, double* ccx, double* ccy, double* ccz
 // flux rate (u0(x_f).n_f) A_f of every face and max |u0| per axis over the
 // face centres of each grid (for Eq. eq:cfl); the velocity of a face is the
 // one of its grid
+// radius of a ball about each node inside the union of its cells (the
+// node's star): the distance from the node to the nearest plane of a fan
+// triangle (face vertex average, edge) of a face of those cells that does
+// not contain the node, times 0.999. Faces through the node are shared by
+// two cells of the star, so the star's boundary is made of the others, and
+// a distance to a triangle's plane is at most the distance to the triangle.
+// A node on a boundary face gets 0 (its star does not surround it).
+__global__ void k_node_star(DevMesh M, float* rstar) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < M.nv;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const double x = M.x[v], y = M.y[v], z = M.z[v];
+    double r = 1e300;
+    bool boundary = false;
+    for (int64_t q = M.vc_ptr[v]; q < M.vc_ptr[v + 1] && !boundary; ++q) {
+      const int c = M.vc[q];
+      for (int64_t e = M.cf_ptr[c]; e < M.cf_ptr[c + 1]; ++e) {
+        const int fs = M.cf[e];
+        const int f = fs >= 0 ? fs : ~fs;
+        const int64_t b = M.fptr[f];
+        const int I = (int)(M.fptr[f + 1] - b);
+        bool has = false;
+        for (int i = 0; i < I; ++i) has |= M.fvert[b + i] == v;
+        if (has) {
+          if (M.nbr[f] < 0) { boundary = true; break; }
+          continue;
+        }
+        double px = 0, py = 0, pz = 0;
+        for (int i = 0; i < I; ++i) {
+          const int a = M.fvert[b + i];
+          px += M.x[a]; py += M.y[a]; pz += M.z[a];
+        }
+        px /= I; py /= I; pz /= I;
+        for (int i = 0; i < I; ++i) {
+          const int a = M.fvert[b + i], bb = M.fvert[b + (i + 1 == I ? 0 : i + 1)];
+          const double ax = M.x[a] - px, ay = M.y[a] - py, az = M.z[a] - pz;
+          const double bx = M.x[bb] - px, by = M.y[bb] - py, bz = M.z[bb] - pz;
+          const double nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
+          const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+          if (nn > 0.0) r = fmin(r, fabs(nx * (x - px) + ny * (y - py) + nz * (z - pz)) / nn);
+        }
+      }
+    }
+    rstar[v] = boundary || !(r < 1e300) ? 0.0f : (float)(0.999 * r);
+  }
+}
+
 __global__ void k_velocity_setup(DevMesh M, const GridParam* gp, double* srate,
                                  unsigned long long* umax) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -228,6 +274,11 @@ cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s) {
 cudaError_t launch_cell_geometry(const vof_ctx* c, cudaStream_t s) {
   k_cell_geometry<<<grid_for(c->nc, 256), 256, 0, s>>>(mesh_view(c), c->ccx, c->ccy, c->ccz,
                                                        c->cvol, c->bb, c->convex);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_star(const vof_ctx* c, cudaStream_t s) {
+  k_node_star<<<kSMs * 8, 256, 0, s>>>(mesh_view(c), c->rstar);
   return cudaGetLastError();
 }
 

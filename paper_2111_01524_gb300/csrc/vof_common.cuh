@@ -90,6 +90,9 @@ struct DevMesh {
   // d = n.(p_face - x_cell), so that the cell is n.(x - x_cell) >= d on
   // every face plane (convex cells; FP32, mixed only)
   const float4* cpl32;
+  // per node: radius of a ball about the node that its cells cover (0 on
+  // the domain boundary); a point that close to the node lies in one of them
+  const float* rstar;
 };
 
 struct DevState {
@@ -131,7 +134,11 @@ struct DevState {
   uint8_t* fexact;
   double* Fprev;
   int32_t *risk, *repf, *repc, *stamp_r;
+  double *Eexc, *Sroom;  // per risk cell: excess and neighbours' room
   int64_t rep_cap;
+  // coverage bits of each active face's flux polyhedron by active position
+  // (k_coverage in k_flux.cu)
+  uint8_t* cover8;
 };
 
 enum Cnt {
@@ -292,6 +299,7 @@ struct vof_ctx {
   float2 *vx2, *vy2, *vz2, *fcx2, *fcy2, *fcz2, *ccx2, *ccy2, *ccz2, *bb2;
   float *fnx32, *fny32, *fnz32, *fa32, *cvol32;
   float4* cpl32;
+  float* rstar;
   float *nx32, *ny32, *nz32, *C32;
   // LSFIR scratch (see DevState)
   double *lxp, *lyp, *lzp;
@@ -308,6 +316,7 @@ struct vof_ctx {
   int32_t *risk, *repf, *repc, *stamp_r;
   double *Eexc, *Sroom;  // per risk cell: excess and neighbours' room
   int64_t rep_cap;
+  uint8_t* cover8;
   // state (device)
   double* F;
   double *nx, *ny, *nz, *C;
@@ -380,6 +389,7 @@ inline DevMesh mesh_view(const vof_ctx* c) {
   m.fnx32 = c->fnx32; m.fny32 = c->fny32; m.fnz32 = c->fnz32; m.fa32 = c->fa32;
   m.ccx2 = c->ccx2; m.ccy2 = c->ccy2; m.ccz2 = c->ccz2; m.bb2 = c->bb2; m.cvol32 = c->cvol32;
   m.cpl32 = c->cpl32;
+  m.rstar = c->rstar;
   return m;
 }
 
@@ -400,7 +410,9 @@ inline DevState state_view(const vof_ctx* c) {
   s.dombox = c->dombox;
   s.fexact = c->fexact; s.Fprev = c->Fprev;
   s.risk = c->risk; s.repf = c->repf; s.repc = c->repc; s.stamp_r = c->stamp_r;
+  s.Eexc = c->Eexc; s.Sroom = c->Sroom;
   s.rep_cap = c->rep_cap;
+  s.cover8 = c->cover8;
   return s;
 }
 
@@ -451,6 +463,7 @@ void set_last_error(const char* msg);
 // set-up (k_setup.cu)
 cudaError_t launch_face_geometry(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_cell_geometry(const vof_ctx* c, cudaStream_t s);
+cudaError_t launch_node_star(const vof_ctx* c, cudaStream_t s);  // rstar
 cudaError_t launch_velocity_setup(const vof_ctx* c, cudaStream_t s);  // velocities in gp_d
 cudaError_t launch_mixed_copies(const vof_ctx* c, cudaStream_t s);
 // sweeps (k_sweep.cu)

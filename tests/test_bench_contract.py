@@ -67,8 +67,22 @@ def test_sweep_roofline_is_hbm_bytes_over_one_launch(bench):
 def test_kernels_per_step(bench):
     """LSGIR: cell tags 1, node tags 3, reconstruct 1, face sweep 2,
     polyhedra 1, flux 1, update 2 = 11; LSFIR adds 2 launches per outer
-    iteration."""
+    iteration; the mixed path adds 16 (3 reconciliation rounds of 5 and the
+    final clip)."""
     assert bench.kernels_per_step(precision="fp64") == 11
     assert bench.kernels_per_step("lsfir", 4, precision="fp64") == 19
     assert bench.kernels_per_step("lsfir", 1, precision="fp64") == 13
-    assert bench.kernels_per_step() == 11 + 16  # mixed: the noise reconciliation rounds
+    assert bench.kernels_per_step() == 11 + 16
+
+
+def test_flux_roofline_uses_the_oracle_op_count(bench):
+    """With the oracle's op count of the same state's truncations, the
+    numerator is its flops per active face times the launch's active faces."""
+    counts = dict(COUNTS)
+    phase = {"name": "flux", "ms": 10.0, "calls": 10}
+    ofl = {"flops_per_active_face": 27000.0, "flops_per_truncation": 13000.0}
+    r = bench.roofline(counts, phase, GRID, {"hbm_gbs": 6684.8}, "measured", CLOCKS, "mixed",
+                       "fmfpa", ofl)
+    assert r["algorithmic_flops_per_launch"] == counts["n_active_faces"] * 27000.0
+    assert "oracle op counter" in r["flops_source"]
+    assert r["achieved"] == pytest.approx(counts["n_active_faces"] * 27000.0 / 1e-3 / 1e12)
