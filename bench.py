@@ -1083,6 +1083,8 @@ def main():
                      "active_faces": stats["n_active_faces"],
                      "truncations_last_step": stats["n_truncations"],
                      "overflow": stats["n_overflow"], "escaped": stats["n_escaped"],
+                     "degenerate_lines_last_step": stats["n_degenerate"],
+                     "edge_on_last_step": stats["n_edgeon"],
                      "clipped_last_step": stats["n_clipped"],
                      "reconciled_faces_last_step": stats["n_repaired"]},
             "roofline": rl, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
