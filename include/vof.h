@@ -374,6 +374,66 @@ vof_status vof_volume_sum_noalloc(const double* w, const double* F, int64_t n, d
                                   void* stream);
 /* bytes of device memory held by the context */
 int64_t vof_device_bytes(const vof_ctx* ctx);
+/* bytes of device memory that vof_batch_create(meshes, n_grids, opt) would
+ * allocate (equal to the new context's vof_device_bytes), computed on the
+ * host from the mesh sizes and their derived connectivity; opt may be NULL
+ * (defaults). No GPU work. VOF_EINVAL for an invalid mesh. */
+vof_status vof_estimate_bytes(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                              int64_t* bytes);
+
+/* Serving (continuous batching of "advance this interface N steps"
+ * requests; no counterpart in the paper, whose tests are single runs).
+ * A request is a mesh, its initial F, a velocity field of Sec. 4.2/4.3, a
+ * number of steps, a CFL number and an end time (Eq. eq:cfl gives each
+ * step). vof_server_step is one scheduling tick: it collects the results of
+ * requests whose last step completed, admits queued requests (in arrival
+ * order) as the grids ("slots") of one new batched context while the summed
+ * vof_estimate_bytes of the live contexts fits the budget, and advances
+ * every live context by one step (one captured CUDA graph per context on
+ * its own stream; every slot with its own field, time and step; a slot
+ * whose request is done moves no more). A context is freed when all its
+ * requests are done. Each result equals the request run alone (vof_init +
+ * vof_step with the same CFL), bit for bit.
+ * budget_bytes: device memory the contexts may hold (0: 80% of the free
+ * memory at creation). max_batch: requests per admitted batch (0: no
+ * limit). reserved: zero. */
+typedef struct vof_server vof_server;
+typedef struct {
+  int64_t budget_bytes;
+  int32_t precision;
+  int32_t flux_polyhedron;
+  int32_t reconstruction;
+  int32_t max_batch;
+  int32_t reserved[2];
+} vof_server_options;
+typedef struct {
+  int64_t n_submitted, n_queued, n_active, n_done;
+  int64_t cell_steps;        /* cells x steps of the done requests */
+  int64_t device_bytes;      /* held by the live contexts */
+  int64_t peak_device_bytes;
+  int64_t budget_bytes;
+  int64_t n_batches;         /* contexts created */
+  int64_t max_active;        /* most requests advanced in one tick */
+  double p50_latency_s, p99_latency_s;  /* submit -> result, done requests */
+  double elapsed_s;          /* first submit -> last result */
+} vof_server_stats;
+enum { VOF_REQ_QUEUED = 0, VOF_REQ_RUNNING = 1, VOF_REQ_DONE = 2 };
+vof_status vof_server_create(const vof_server_options* opt, vof_server** out);
+/* copies the request (HOST mesh arrays and F0 [n_cell]); *id identifies it */
+vof_status vof_server_submit(vof_server* s, const vof_mesh_desc* mesh, const double* F0,
+                             const vof_velocity* vel, int32_t n_steps, double cfl, double t_end,
+                             int64_t* id);
+/* one scheduling tick; *n_active (may be NULL): requests advanced. VOF_ENOMEM
+ * if the first queued request alone exceeds the budget. */
+vof_status vof_server_step(vof_server* s, int32_t* n_active);
+/* ticks until every submitted request is done */
+vof_status vof_server_drain(vof_server* s);
+/* *state: VOF_REQ_*; when done, F (HOST [n_cell], may be NULL) receives the
+ * result and *latency_s (may be NULL) the submit-to-result time (-1 before) */
+vof_status vof_server_poll(vof_server* s, int64_t id, int32_t* state, double* F,
+                           double* latency_s);
+vof_status vof_server_get_stats(vof_server* s, vof_server_stats* out);
+void vof_server_destroy(vof_server* s);
 
 #ifdef __cplusplus
 }

@@ -77,6 +77,27 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class _ServerOpt(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("precision", C.c_int32),
+                ("flux_polyhedron", C.c_int32), ("reconstruction", C.c_int32),
+                ("max_batch", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("n_submitted", C.c_int64), ("n_queued", C.c_int64), ("n_active", C.c_int64),
+                ("n_done", C.c_int64), ("cell_steps", C.c_int64), ("device_bytes", C.c_int64),
+                ("peak_device_bytes", C.c_int64), ("budget_bytes", C.c_int64),
+                ("n_batches", C.c_int64), ("max_active", C.c_int64),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
+                ("elapsed_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
+
+
 def library_path():
     return _build.LIB
 
@@ -128,6 +149,19 @@ def lib():
         for name in ("vof_init_batch", "vof_batch_offsets", "vof_advect_batch", "vof_step_batch",
                      "vof_suggest_dt_batch", "vof_graph_capture", "vof_graph_launch",
                      "vof_autotune", "vof_batch_create", "vof_advect_step", "vof_batch_step"):
+            getattr(L, name).restype = C.c_int
+        L.vof_estimate_bytes.argtypes = [vp, C.c_int, vp, C.POINTER(i64)]
+        L.vof_server_create.argtypes = [vp, C.POINTER(vp)]
+        L.vof_server_submit.argtypes = [vp, vp, vp, vp, i32, dbl, dbl, C.POINTER(i64)]
+        L.vof_server_step.argtypes = [vp, C.POINTER(i32)]
+        L.vof_server_drain.argtypes = [vp]
+        L.vof_server_poll.argtypes = [vp, i64, C.POINTER(i32), vp, C.POINTER(dbl)]
+        L.vof_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.vof_server_destroy.argtypes = [vp]
+        L.vof_server_destroy.restype = None
+        for name in ("vof_estimate_bytes", "vof_server_create", "vof_server_submit",
+                     "vof_server_step", "vof_server_drain", "vof_server_poll",
+                     "vof_server_get_stats"):
             getattr(L, name).restype = C.c_int
         L.vof_volume_sum_noalloc.argtypes = [vp, vp, i64, vp, vp]
         L.vof_volume_sum_noalloc.restype = C.c_int
@@ -184,6 +218,81 @@ def volume_sum_noalloc(w, F, out, n=None, stream=None):
     if n is None:
         n = w.numel()
     return lib().vof_volume_sum_noalloc(_ptr(w), _ptr(F), int(n), _ptr(out), _stream(stream))
+
+
+def estimate_bytes(meshes, precision=PREC_MIXED, flux=FLUX_FMFPA, recon=RECON_LSGIR,
+                   poly_capacity=0):
+    """Device bytes vof_batch_create would allocate for these meshes (host
+    arithmetic on their sizes and connectivity)."""
+    meshes = meshes if isinstance(meshes, (list, tuple)) else [meshes]
+    keep = []
+    descs = (_Mesh * len(meshes))(*[_mesh_desc(m, keep) for m in meshes])
+    opt = _Opt()
+    opt.eps, opt.beta, opt.precision, opt.flux_polyhedron = 1e-12, 1.5, precision, flux
+    opt.reconstruction, opt.poly_capacity = recon, poly_capacity
+    out = C.c_int64()
+    _check(lib().vof_estimate_bytes(descs, len(meshes), C.byref(opt), C.byref(out)))
+    return out.value
+
+
+class Server:
+    """Continuous batching of "advance this interface N steps" requests on
+    the device (vof_server_*): requests are admitted, within a device-byte
+    budget, as the slots of batched contexts, and every live context advances
+    one step per tick."""
+
+    def __init__(self, budget_bytes=0, precision=PREC_MIXED, flux=FLUX_FMFPA, recon=RECON_LSGIR,
+                 max_batch=0):
+        o = _ServerOpt()
+        o.budget_bytes, o.precision, o.flux_polyhedron = int(budget_bytes), precision, flux
+        o.reconstruction, o.max_batch = recon, max_batch
+        h = C.c_void_p()
+        _check(lib().vof_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self.n_cell = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vof_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, mesh, F0, vel, n_steps, cfl=0.5, t_end=1e9):
+        keep = []
+        d = _mesh_desc(mesh, keep)
+        F0 = np.ascontiguousarray(F0, np.float64)
+        v = velocity_struct(vel)
+        rid = C.c_int64()
+        _check(lib().vof_server_submit(self._h, C.byref(d), _ptr(F0), C.byref(v), int(n_steps),
+                                       float(cfl), float(t_end), C.byref(rid)))
+        self.n_cell[rid.value] = int(mesh["n_cell"])
+        return rid.value
+
+    def step(self):
+        n = C.c_int32()
+        _check(lib().vof_server_step(self._h, C.byref(n)))
+        return n.value
+
+    def drain(self):
+        _check(lib().vof_server_drain(self._h))
+
+    def poll(self, rid):
+        """(state, F or None, latency_s) of a request"""
+        st = C.c_int32()
+        lat = C.c_double()
+        F = np.empty(self.n_cell[rid])
+        _check(lib().vof_server_poll(self._h, int(rid), C.byref(st), _ptr(F), C.byref(lat)))
+        return st.value, (F if st.value == REQ_DONE else None), lat.value
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().vof_server_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
 
 
 def velocity_struct(v):

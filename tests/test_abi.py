@@ -25,6 +25,29 @@ def test_library_builds_and_exports_header_symbols():
         assert hasattr(lib, s), s
 
 
+def test_the_boundary_calls_are_exported():
+    """The calls of the C-ABI boundary: context, state, the method's steps,
+    batching, serving and the read-backs."""
+    from paper_2111_01524_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    for s in ("vof_init", "vof_destroy", "vof_last_error", "vof_set_fraction", "vof_get_fraction",
+              "vof_reconstruct", "vof_advect_step", "vof_suggest_dt", "vof_get_planes",
+              "vof_get_face_flux", "vof_get_candidates", "vof_get_state", "vof_set_state",
+              "vof_batch_create", "vof_batch_step", "vof_server_create", "vof_server_submit",
+              "vof_server_step", "vof_server_poll", "vof_server_get_stats", "vof_server_destroy",
+              "vof_estimate_bytes", "vof_get_stats"):
+        assert hasattr(lib, s), s
+    assert "vof_init" in declared_symbols() and "vof_server_submit" in declared_symbols()
+
+
+def test_server_options_are_checked_on_the_host():
+    from paper_2111_01524_gb300 import vof
+    for kw in ({"precision": 5}, {"budget_bytes": -1}, {"max_batch": -2}):
+        with pytest.raises(vof.VofError) as e:
+            vof.Server(**kw)
+        assert e.value.status == vof.VOF_EINVAL
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2111_01524_gb300 import build, vof
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))

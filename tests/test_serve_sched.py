@@ -1,7 +1,10 @@
-"""Host logic of the serving loop on CPU with a simulated device:
-admission by memory budget, FIFO order, overlap, completion and latency."""
+"""Host logic of the trace replay on CPU with a simulated server: requests
+are submitted at their arrival times, the server is ticked while requests
+are pending, every result is collected once with its latency, and the trace
+generator is deterministic. (The device-resident scheduler itself, its
+admission by budget and its batching, runs in the library and is tested on
+the GPU in tests/test_gpu_server.py.)"""
 import numpy as np
-import pytest
 
 from paper_2111_01524_gb300 import serve
 
@@ -17,89 +20,89 @@ class SimClock:
         self.t += max(d, 1e-4)
 
 
-class FakeBackend:
-    """Each step takes `step_s` of simulated device time per request; requests
-    run concurrently (separate streams)."""
+class SimServer:
+    """Admits every submitted request at the next tick; each tick advances
+    every admitted request one step and takes `tick_s` of simulated time; a
+    request is done one tick after its last step (the result copy)."""
 
-    def __init__(self, clock, step_s=0.01):
+    def __init__(self, clock, tick_s=0.001):
         self.clock = clock
-        self.step_s = step_s
-        self.open_log = []
-        self.live = set()
-        self.peak_live = 0
+        self.tick_s = tick_s
+        self.reqs = []
+        self.submit_log = []
 
-    def free_bytes(self):
-        return 10 ** 9
+    def submit(self, mesh, F0, vel, n_steps, cfl, t_end):
+        sid = len(self.reqs)
+        self.reqs.append({"k": -1, "n": n_steps, "F": np.array(F0, float), "t0": self.clock(),
+                          "done": None, "cfl": cfl})
+        self.submit_log.append((self.clock(), sid))
+        return sid
 
-    def open(self, r):
-        self.open_log.append((self.clock(), r.rid))
-        self.live.add(r.rid)
-        self.peak_live = max(self.peak_live, len(self.live))
-        return {"rid": r.rid, "k": 0, "busy_until": self.clock(), "steps": []}
+    def step(self):
+        n = 0
+        for r in self.reqs:
+            if r["done"] is not None:
+                continue
+            if r["k"] < 0:
+                r["k"] = 0
+            elif r["k"] < r["n"]:
+                r["k"] += 1
+                r["F"] = np.clip(0.5 * (r["F"] + np.roll(r["F"], 1)) + 1e-3 * r["k"], 0, 1)
+                n += 1
+            else:
+                r["done"] = self.clock() + self.tick_s
+        self.clock.t += self.tick_s
+        return n
 
-    def step(self, h, r):
-        start = max(self.clock(), h["busy_until"])
-        h["busy_until"] = start + self.step_s
-        h["steps"].append(h["busy_until"])
-        h["k"] += 1
-        self.clock.t += 1e-5  # host cost of issuing
-
-    def pending(self, h):
-        h["steps"] = [t for t in h["steps"] if t > self.clock()]
-        return len(h["steps"])
-
-    def finish(self, h):
-        return np.full(3, float(h["rid"]))
-
-    def close(self, h):
-        self.live.discard(h["rid"])
+    def poll(self, sid):
+        r = self.reqs[sid]
+        if r["done"] is not None and r["done"] <= self.clock():
+            return serve.REQ_DONE, r["F"].copy(), r["done"] - r["t0"]
+        return serve.REQ_RUNNING, None, -1.0
 
 
 def _req(rid, n_cells, steps, arrival):
-    mesh = {"n_cell": n_cells, "X": np.zeros((1, 3)), "owner": np.zeros(1, np.int32),
-            "face_ptr": np.zeros(2, np.int64)}
-    return serve.Request(rid=rid, mesh=mesh, F0=np.zeros(n_cells), vel=None, n_steps=steps,
-                         arrival=arrival)
+    mesh = {"n_cell": n_cells}
+    return serve.Request(rid=rid, mesh=mesh, F0=np.linspace(0, 1, n_cells), vel=None,
+                         n_steps=steps, arrival=arrival)
 
 
-def test_budget_admission_and_completion():
+def test_requests_are_submitted_at_their_arrival_and_all_finish():
     clock = SimClock()
-    be = FakeBackend(clock)
-    reqs = [_req(i, 100, 5, 0.001 * i) for i in range(6)]
-    # every request "needs" 40 bytes; the budget fits two at a time
-    srv = serve.Server(be, budget_bytes=80, clock=clock, sleep=clock.sleep)
-    st = srv.run(reqs, estimate=lambda m: 40)
-    assert len(st.latencies) == 6
-    assert st.max_bytes <= 80 and st.max_active == 2 and be.peak_live == 2
-    # admitted in arrival order
-    assert [rid for _, rid in be.open_log] == list(range(6))
+    srv = SimServer(clock)
+    reqs = [_req(0, 5, 4, 0.0), _req(1, 7, 2, 0.05), _req(2, 3, 6, 0.0021)]
+    st = serve.replay(srv, reqs, clock=clock, sleep=clock.sleep)
+    # submitted in arrival order, none before its arrival
+    order = [sid for _, sid in srv.submit_log]
+    assert [reqs[0].sid, reqs[2].sid, reqs[1].sid] == order
     for r in reqs:
-        assert r.t_admit >= r.arrival and r.t_done > r.t_admit
-        assert np.all(r.result == r.rid)
-    assert st.cell_steps == 6 * 100 * 5
+        assert r.t_submit >= r.arrival
+        assert r.result is not None and r.t_done >= r.t_submit
+        assert r.latency > 0
+    assert st.cell_steps == 5 * 4 + 7 * 2 + 3 * 6
+    assert len(st.latencies) == 3 and st.max_active >= 2
+    assert st.summary()["requests"] == 3
 
 
-def test_requests_overlap_when_budget_allows():
-    clock = SimClock()
-    be = FakeBackend(clock, step_s=0.01)
-    reqs = [_req(i, 10, 10, 0.0) for i in range(8)]
-    srv = serve.Server(be, budget_bytes=10 ** 6, clock=clock, sleep=clock.sleep)
-    st = srv.run(reqs, estimate=lambda m: 10)
-    # 8 concurrent requests of 10 steps x 10 ms finish in about 100 ms, not 800
-    assert st.wall < 0.2 and be.peak_live == 8
+def test_results_do_not_depend_on_the_other_requests():
+    """The simulated result of a request is a function of the request only:
+    replayed alone or in a mix it is the same."""
+    def run(reqs):
+        clock = SimClock()
+        serve.replay(SimServer(clock), reqs, clock=clock, sleep=clock.sleep)
+        return {r.rid: r.result for r in reqs}
+    mix = run([_req(i, 4 + i, 2 + i, 0.003 * i) for i in range(6)])
+    for i in range(6):
+        alone = run([_req(i, 4 + i, 2 + i, 0.0)])
+        assert np.array_equal(alone[i], mix[i])
 
 
-def test_oversized_request_is_rejected():
-    clock = SimClock()
-    srv = serve.Server(FakeBackend(clock), budget_bytes=10, clock=clock, sleep=clock.sleep)
-    with pytest.raises(ValueError):
-        srv.run([_req(0, 10, 1, 0.0)], estimate=lambda m: 11)
-
-
-def test_poisson_trace_is_seeded_and_sorted():
-    mk = lambda rid, rng: _req(rid, 1, 1, 0.0)
+def test_poisson_trace_is_deterministic():
+    def mk(rid, rng):
+        return _req(rid, 10, int(rng.integers(1, 5)), 0.0)
     a = serve.poisson_trace(20, 200.0, 7, mk)
     b = serve.poisson_trace(20, 200.0, 7, mk)
     assert [r.arrival for r in a] == [r.arrival for r in b]
-    assert all(x.arrival < y.arrival for x, y in zip(a, a[1:]))
-    assert 0.05 < a[-1].arrival < 0.2
+    assert [r.n_steps for r in a] == [r.n_steps for r in b]
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert (gaps > 0).all() and abs(gaps.mean() - 1 / 200.0) < 3 / 200.0

@@ -55,39 +55,43 @@ class _SimClock:
         self.t += max(d, 1e-4)
 
 
-class _SimBackend:
-    """Deterministic simulated device: the result of a request depends on the
-    request only (so it must not depend on which rank serves it)."""
+class _SimServer:
+    """A stand-in for the device-resident server (the GPU is not needed for
+    the host logic): every submitted request is admitted at the next tick
+    and advanced one step per tick; its result is a fixed map of its own F0
+    and step count, so it must not depend on which rank serves it."""
 
-    def __init__(self, clock, step_s=0.01):
+    def __init__(self, clock, tick_s=0.001):
         self.clock = clock
-        self.step_s = step_s
+        self.tick_s = tick_s
+        self.reqs = []
 
-    def free_bytes(self):
-        return 10 ** 9
+    def submit(self, mesh, F0, vel, n_steps, cfl, t_end):
+        self.reqs.append({"k": -1, "n": n_steps, "F": np.array(F0, float), "t0": self.clock(),
+                          "done": None})
+        return len(self.reqs) - 1
 
-    def open(self, r):
-        return {"rid": r.rid, "k": 0, "busy_until": self.clock(), "steps": [],
-                "F": np.array(r.F0, dtype=np.float64)}
+    def step(self):
+        n = 0
+        for r in self.reqs:
+            if r["done"] is not None:
+                continue
+            if r["k"] < 0:
+                r["k"] = 0
+            elif r["k"] < r["n"]:
+                r["k"] += 1
+                r["F"] = np.clip(0.5 * (r["F"] + np.roll(r["F"], 1)) + 1e-3 * r["k"], 0.0, 1.0)
+                n += 1
+            else:
+                r["done"] = self.clock() + self.tick_s
+        self.clock.t += self.tick_s
+        return n
 
-    def step(self, h, r):
-        start = max(self.clock(), h["busy_until"])
-        h["busy_until"] = start + self.step_s * r.n_cell / 100.0
-        h["steps"].append(h["busy_until"])
-        h["k"] += 1
-        # a stand-in for one step of the method: any fixed map of the state
-        h["F"] = np.clip(0.5 * (h["F"] + np.roll(h["F"], 1)) + 1e-3 * h["k"], 0.0, 1.0)
-        self.clock.t += 1e-5
-
-    def pending(self, h):
-        h["steps"] = [t for t in h["steps"] if t > self.clock()]
-        return len(h["steps"])
-
-    def finish(self, h):
-        return h["F"]
-
-    def close(self, h):
-        pass
+    def poll(self, sid):
+        r = self.reqs[sid]
+        if r["done"] is not None and r["done"] <= self.clock():
+            return serve.REQ_DONE, r["F"].copy(), r["done"] - r["t0"]
+        return serve.REQ_RUNNING, None, -1.0
 
 
 def _requests():
@@ -95,8 +99,7 @@ def _requests():
     out = []
     for rid in range(23):
         n = int(rng.integers(50, 400))
-        mesh = {"n_cell": n, "X": np.zeros((1, 3)), "owner": np.zeros(1, np.int32),
-                "face_ptr": np.zeros(2, np.int64)}
+        mesh = {"n_cell": n}
         out.append(serve.Request(rid=rid, mesh=mesh, F0=rng.random(n), vel=None,
                                  n_steps=int(rng.integers(3, 12)), arrival=0.002 * rid))
     return out
@@ -104,8 +107,7 @@ def _requests():
 
 def _serve(reqs):
     clock = _SimClock()
-    srv = serve.Server(_SimBackend(clock), budget_bytes=10 ** 6, clock=clock, sleep=clock.sleep)
-    st = srv.run(reqs, estimate=lambda m: 1000)
+    st = serve.replay(_SimServer(clock), reqs, clock=clock, sleep=clock.sleep)
     return st, {r.rid: r.result for r in reqs}
 
 
