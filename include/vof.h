@@ -103,7 +103,16 @@ typedef struct {
  * it are built inside the flux kernel by one lane, with the same arithmetic,
  * so results do not depend on it. 0 means min(n_face, 4 Mi); otherwise
  * 1..n_face (VOF_EINVAL if negative). A GPU memory/latency trade-off with no
- * counterpart in the paper. reserved: must be zero. */
+ * counterpart in the paper.
+ * faces_per_warp: flux polyhedra truncated by one warp: 1, or 2 (each face
+ * by half a warp, 16 lanes, which holds at most 16 face loops; allowed for
+ * FMFPA and NMFPA on grids whose cells are all convex and where the
+ * polyhedron's faces (3I+1 for FMFPA, I+2 for NMFPA, I the most nodes of a
+ * face) plus the most faces of a cell plus one number at most 16, e.g.
+ * FMFPA on tetrahedra and NMFPA on hexahedra; VOF_EINVAL otherwise), or 0
+ * for the library's choice (1). Every reduction keeps its order, so the
+ * results are the same bit for bit either way. vof_autotune_ex
+ * may change it. */
 typedef struct {
   double eps;
   double beta;
@@ -113,7 +122,7 @@ typedef struct {
   int32_t lsfir_max_iter;
   double lsfir_tol;
   int32_t poly_capacity;
-  int32_t reserved;
+  int32_t faces_per_warp;
 } vof_options;
 
 /* Prescribed velocity of the test problems (Sec. 4.2, Sec. 4.3):
@@ -285,11 +294,19 @@ vof_status vof_graph_launch(vof_ctx* ctx, const vof_velocity* vels, const double
                             const double* dt, void* stream);
 
 /* Launch-shape autotuner: times the flux and reconstruction kernels on the
- * current state for 2..16 blocks per SM and keeps the fastest grid sizes
- * (returned when the pointers are not NULL). F and the reconstruction are
- * left unchanged; the face volumes are those of a step (t, dt). */
+ * current state and keeps the fastest: blocks per SM of each (2..16), faces
+ * per warp of the flux kernel (1, and 2 where vof_options.faces_per_warp
+ * allows it) and whether the flux polyhedra are prebuilt into the
+ * poly_capacity buffer ahead of the flux kernel or built inside it. The
+ * choices are returned through the pointers that are not NULL
+ * (prebuilt: 1 or 0). Results do not depend on any of them. F and the
+ * reconstruction are left unchanged; the face volumes are those of a step
+ * (t, dt). Re-capture a graph after it. */
 vof_status vof_autotune(vof_ctx* ctx, const vof_velocity* vels, const double* t, const double* dt,
                         void* stream, int* flux_blocks, int* recon_blocks);
+vof_status vof_autotune_ex(vof_ctx* ctx, const vof_velocity* vels, const double* t,
+                           const double* dt, void* stream, int* flux_blocks, int* recon_blocks,
+                           int* faces_per_warp, int* prebuilt);
 
 /* planes [4*n_cell]: nx, ny, nz, C per cell (zeros for non-interfacial). */
 vof_status vof_get_planes(vof_ctx* ctx, double* planes, int mem, void* stream);

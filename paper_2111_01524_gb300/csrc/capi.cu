@@ -242,7 +242,8 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
     return fail(VOF_EINVAL, "lsfir_max_iter must be in 0..16 and lsfir_tol >= 0");
   if (o.lsfir_max_iter == 0) o.lsfir_max_iter = 4;  // n_out of Sec. 3.6
   if (o.lsfir_tol == 0.0) o.lsfir_tol = 1e-3;
-  if (o.reserved != 0) return fail(VOF_EINVAL, "reserved options must be zero");
+  if (o.faces_per_warp < 0 || o.faces_per_warp > 2)
+    return fail(VOF_EINVAL, "faces_per_warp must be 0, 1 or 2");
   if (o.poly_capacity < 0) return fail(VOF_EINVAL, "poly_capacity must be >= 0");
   if (o.flux_polyhedron == VOF_FLUX_EMFPA && maxI > kMaxEmfpaVerts)
     return fail(VOF_EINVAL, "EMFPA supports faces of at most 6 nodes; this mesh has " +
@@ -377,6 +378,7 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
     CKI(cudaMalloc(&c->fm_v, gs * 3 * kFmSlots * c->fm_cap));
     CKI(cudaMalloc(&c->fm_f, gs * 7 * c->fm_cap));
     c->bytes += (int64_t)(gs * (3 * kFmSlots + 7) * c->fm_cap);
+    c->fm_use = c->fm_cap;
     CKI(dalloc(c, &c->fm_meta, c->fm_cap));
     CKI(dalloc(c, &c->fm_split, c->fm_cap));
     CKI(dalloc(c, &c->cover8, nf));
@@ -439,6 +441,23 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
   CKI(launch_node_star(c, s));
   if (o.precision == VOF_PREC_MIXED) CKI(launch_mixed_copies(c, s));
   CKI(cudaStreamSynchronize(s));
+  {
+    // two faces per warp (a half warp holds at most 16 face loops): an
+    // FMFPA polyhedron has up to 3I+1 faces (the cell face, I side quads
+    // each split in two, I apex triangles), an NMFPA one I+2; truncation by
+    // a convex cell of m faces and the PLIC plane adds at most m+1 more, so
+    // base faces + m + 1 <= 16 bounds every loop list the kernel builds
+    std::vector<uint8_t> cvx(nc);
+    CKI(cudaMemcpy(cvx.data(), c->convex, nc, cudaMemcpyDeviceToHost));
+    const int base_faces = o.flux_polyhedron == VOF_FLUX_NMFPA ? maxI + 2 : 3 * maxI + 1;
+    bool ok = o.flux_polyhedron != VOF_FLUX_EMFPA && base_faces + hc.max_cell_faces + 1 <= 16;
+    for (int64_t k = 0; k < nc && ok; ++k) ok = cvx[k] != 0;
+    c->half_ok = ok;
+    if (o.faces_per_warp == 2 && !ok)
+      return cleanup(VOF_EINVAL, "faces_per_warp = 2 needs FMFPA or NMFPA polyhedra whose faces plus "
+                                 "the faces of a convex cell plus one number at most 16");
+    c->faces_per_warp = o.faces_per_warp == 0 ? 1 : o.faces_per_warp;
+  }
   {
     std::vector<double> bb(6 * nc);
     CKI(cudaMemcpyAsync(bb.data(), c->bb, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost, s));
@@ -758,8 +777,9 @@ vof_status vof_graph_launch(vof_ctx* c, const vof_velocity* vels, const double* 
   return VOF_OK;
 }
 
-vof_status vof_autotune(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
-                        void* stream, int* flux_blocks, int* recon_blocks) {
+vof_status vof_autotune_ex(vof_ctx* c, const vof_velocity* vels, const double* t,
+                           const double* dt, void* stream, int* flux_blocks, int* recon_blocks,
+                           int* faces_per_warp, int* prebuilt) {
   if (!c) return fail(VOF_EINVAL, "NULL context");
   if (!c->recon_valid) return fail(VOF_ESTATE, "autotune needs a reconstruction of the current F");
   vof_status st = check_steps(c, t, dt);
@@ -772,37 +792,66 @@ vof_status vof_autotune(vof_ctx* c, const vof_velocity* vels, const double* t, c
   const bool timing = c->timing;
   c->timing = false;
   CK(launch_face_sweep(c, s));  // active faces of the current state (F is not changed)
-  CK(launch_prebuild(c, s));     // their flux polyhedra, which the flux launches only read
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   const int cand[] = {kSMs * 2, kSMs * 4, kSMs * 6, kSMs * 8, kSMs * 12, kSMs * 16};
+  // the flux phase: faces per warp x polyhedra prebuilt (their
+  // construction timed with the truncations) or built in the flux kernel
+  // x blocks; then the reconstruction's blocks
+  const int64_t fm_alloc = c->fm_cap;
   float best_f = 1e30f, best_r = 1e30f;
-  int bf = kSMs * 8, br = kSMs * 8;
-  for (int which = 0; which < 2; ++which)
-    for (int g : cand) {
-      float tot = 0.f;
-      for (int rep = 0; rep < 4; ++rep) {
-        if (which == 0) c->flux_blocks = g; else c->recon_blocks = g;
-        CK(cudaEventRecord(e0, s));
-        CK(which == 0 ? launch_flux(c, s) : launch_reconstruct(c, s));
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0) tot += ms;  // first launch warms caches
+  int bf = kSMs * 8, br = kSMs * 8, bw = 1, bp = 1;
+  for (int fpw = 1; fpw <= (c->half_ok ? 2 : 1); ++fpw)
+    for (int pb = 1; pb >= 0; --pb)
+      for (int g : cand) {
+        c->faces_per_warp = fpw;
+        c->fm_use = pb ? fm_alloc : 0;
+        c->flux_blocks = g;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+          CK(cudaEventRecord(e0, s));
+          CK(launch_prebuild(c, s));
+          CK(launch_flux(c, s));
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep > 0) tot += ms;  // first launch warms caches
+        }
+        if (tot < best_f) { best_f = tot; bf = g; bw = fpw; bp = pb; }
       }
-      if (which == 0 && tot < best_f) { best_f = tot; bf = g; }
-      if (which == 1 && tot < best_r) { best_r = tot; br = g; }
+  c->faces_per_warp = bw;
+  c->fm_use = bp ? fm_alloc : 0;
+  c->flux_blocks = bf;
+  for (int g : cand) {
+    c->recon_blocks = g;
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      CK(launch_reconstruct(c, s));
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;
     }
+    if (tot < best_r) { best_r = tot; br = g; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->flux_blocks = bf;
   c->recon_blocks = br;
   c->timing = timing;
   if (flux_blocks) *flux_blocks = bf;
   if (recon_blocks) *recon_blocks = br;
+  if (faces_per_warp) *faces_per_warp = bw;
+  if (prebuilt) *prebuilt = bp;
   return VOF_OK;
+}
+
+vof_status vof_autotune(vof_ctx* c, const vof_velocity* vels, const double* t, const double* dt,
+                        void* stream, int* flux_blocks, int* recon_blocks) {
+  return vof_autotune_ex(c, vels, t, dt, stream, flux_blocks, recon_blocks, nullptr, nullptr);
 }
 
 namespace {

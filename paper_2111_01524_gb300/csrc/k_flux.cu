@@ -80,13 +80,18 @@ constexpr int kWarps = 4;
 constexpr int MAXI = kMaxFaceVerts;   // face vertices
 // base polyhedron vertices: 2I+1 (FMFPA, I <= 8) or 3I+1 (EMFPA, I <= 6)
 constexpr int NB = VOF_MAX_POLY_VERTS;
-constexpr int NV = 80;                // vertex table capacity
-constexpr int NF = 32;                // face capacity (one lane each)
-constexpr int LM = 32;                // loop length capacity
 constexpr int NR = 32;                // new vertices per clip
 
-template <typename G>
+// A flux polyhedron is worked on by a group of GW lanes: a whole warp (GW =
+// 32), or half of one (GW = 16: two faces per warp, for polyhedra of at
+// most 16 base vertices and face loops against convex cells of at most 16
+// faces, which is every hex and tetrahedral grid). Capacities per group:
+// vertex table, face loops (one lane each), loop length.
+template <typename G, int GW = 32>
 struct __align__(16) Poly {
+  static constexpr int NV = GW == 32 ? 80 : 64;
+  static constexpr int NF = GW;
+  static constexpr int LM = GW == 32 ? 32 : 24;
   G vx[NV], vy[NV], vz[NV];
   G phi[NV];
   G bx[NB], by[NB], bz[NB];  // base polyhedron
@@ -100,35 +105,37 @@ struct __align__(16) Poly {
   G pl[NF + 1][4];           // half-spaces of the current candidate cell; [NF]: PLIC
   int32_t cand[sizeof(G) == 4 ? 128 : 1];  // candidate cells met by the box of P (FP32)
 };
+
+// warp primitives over the lane group of the calling thread (the group's
+// lanes are consecutive and aligned: threadIdx.x & 16 is the first lane of
+// a half warp); ballots are returned in the group's own lane numbering
+template <int GW>
+__device__ __forceinline__ unsigned gmask() {
+  return GW == 32 ? GVOF_FULL : (0xffffu << (threadIdx.x & 16));
+}
+template <int GW>
+__device__ __forceinline__ unsigned gballot(bool p) {
+  if constexpr (GW == 32) return __ballot_sync(GVOF_FULL, p);
+  else return (__ballot_sync(gmask<GW>(), p) >> (threadIdx.x & 16)) & 0xffffu;
+}
+template <int GW>
+__device__ __forceinline__ bool gany(bool p) { return __any_sync(gmask<GW>(), p); }
+template <int GW, typename T>
+__device__ __forceinline__ T gshfl(T v, int src) { return __shfl_sync(gmask<GW>(), v, src, GW); }
+template <int GW, typename T>
+__device__ __forceinline__ T gshfl_up(T v, int d) { return __shfl_up_sync(gmask<GW>(), v, d, GW); }
+// sum over the group's lanes: a butterfly from GW/2 down; lanes that hold
+// 0 leave the others' partial sums exact, so a whole warp whose upper half
+// holds 0 sums as a half warp does, bit for bit
+template <int GW, typename T>
+__device__ __forceinline__ T gsum(T v) {
+  for (int o = GW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask<GW>(), v, o);
+  return v;
+}
+template <int GW>
+__device__ __forceinline__ void gsync() { __syncwarp(gmask<GW>()); }
 template <typename G>
 __host__ __device__ constexpr int cand_cap() { return sizeof(G) == 4 ? 128 : 0; }
-
-template <typename T>
-__device__ __forceinline__ T wsum(T v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GVOF_FULL, v, o);
-  return v;
-}
-// warp min / max of a float by the integer reduction unit: the map
-// i -> i ^ ((i >> 31) & 0x7fffffff) of its bit pattern is monotonic
-__device__ __forceinline__ int fkey(float v) {
-  const int i = __float_as_int(v);
-  return i ^ ((i >> 31) & 0x7fffffff);
-}
-__device__ __forceinline__ float fkey_inv(int k) {
-  return __int_as_float(k ^ ((k >> 31) & 0x7fffffff));
-}
-__device__ __forceinline__ float wmin(float v) { return fkey_inv(__reduce_min_sync(GVOF_FULL, fkey(v))); }
-__device__ __forceinline__ float wmax(float v) { return fkey_inv(__reduce_max_sync(GVOF_FULL, fkey(v))); }
-template <typename T>
-__device__ __forceinline__ T wmin(T v) {
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(GVOF_FULL, v, o));
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ T wmax(T v) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(GVOF_FULL, v, o));
-  return v;
-}
 
 __device__ __forceinline__ double absval(double a) { return a; }
 __device__ __forceinline__ float absval(float2 a) { return a.x + a.y; }
@@ -157,8 +164,8 @@ __device__ __forceinline__ int base_verts(int I) {
 // bottom triangles.
 // NMFPA (Sec. 2.2.3): the first 2I vertices only; faces: the cell face, I
 // planar side quads, the back-traced face (reversed: its normal is -n).
-template <typename G, int KIND>
-__device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, int lane) {
+template <typename G, int KIND, int GW>
+__device__ void restore_base(Poly<G, GW>& P, PolyState& st, int I, unsigned split, int lane) {
   if constexpr (KIND == VOF_FLUX_NMFPA) {
     const int nvb = 2 * I;
     if (lane < nvb) { P.vx[lane] = P.bx[lane]; P.vy[lane] = P.by[lane]; P.vz[lane] = P.bz[lane]; }
@@ -179,7 +186,7 @@ __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, i
     st.nv = nvb;
     st.nf = I + 2;
     st.cur = 0;
-    __syncwarp();
+    gsync<GW>();
     return;
   } else if constexpr (KIND == VOF_FLUX_EMFPA) {
     const int nvb = 3 * I + 1, nfb = 5 * I + 1;
@@ -206,7 +213,7 @@ __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, i
     st.nv = nvb;
     st.nf = nfb;
     st.cur = 0;
-    __syncwarp();
+    gsync<GW>();
     return;
   } else {
   const int nvb = 2 * I + 1;
@@ -247,72 +254,75 @@ __device__ void restore_base(Poly<G>& P, PolyState& st, int I, unsigned split, i
   st.nv = nvb;
   st.nf = nvb + nsplit;
   st.cur = 0;
-  __syncwarp();
+  gsync<GW>();
   }
 }
 
 // drop unreferenced vertices and renumber (keeps room for a clip)
-template <typename G>
-__device__ __noinline__ void compact(Poly<G>& P, PolyState& st, int lane) {
-  for (int v = lane; v < NV; v += 32) P.newid[v] = 0;
-  __syncwarp();
+template <typename G, int GW>
+__device__ __noinline__ void compact(Poly<G, GW>& P, PolyState& st, int lane) {
+  constexpr int NV = Poly<G, GW>::NV;
+  constexpr int VPL = (NV + GW - 1) / GW;  // vertex slots per lane
+  for (int v = lane; v < NV; v += GW) P.newid[v] = 0;
+  gsync<GW>();
   if (lane < st.nf) {
     const int L = P.flen[st.cur][lane];
     for (int k = 0; k < L; ++k) P.newid[P.fv[st.cur][k][lane]] = 1;
   }
-  __syncwarp();
-  int m[3], s = 0;
-  for (int r = 0; r < 3; ++r) {
-    const int v = lane * 3 + r;
+  gsync<GW>();
+  int m[VPL], s = 0;
+  for (int r = 0; r < VPL; ++r) {
+    const int v = lane * VPL + r;
     m[r] = (v < st.nv) ? P.newid[v] : 0;
     s += m[r];
   }
   int incl = s;
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(GVOF_FULL, incl, d);
+  for (int d = 1; d < GW; d <<= 1) {
+    const int t = gshfl_up<GW>(incl, d);
     if (lane >= d) incl += t;
   }
-  const int total = __shfl_sync(GVOF_FULL, incl, 31);
+  const int total = gshfl<GW>(incl, GW - 1);
   int base = incl - s;
-  G x[3], y[3], z[3];
-  for (int r = 0; r < 3; ++r) {
-    const int v = lane * 3 + r;
+  G x[VPL], y[VPL], z[VPL];
+  for (int r = 0; r < VPL; ++r) {
+    const int v = lane * VPL + r;
     if (v < st.nv && m[r]) { x[r] = P.vx[v]; y[r] = P.vy[v]; z[r] = P.vz[v]; }
   }
-  __syncwarp();
-  for (int r = 0; r < 3; ++r) {
-    const int v = lane * 3 + r;
+  gsync<GW>();
+  for (int r = 0; r < VPL; ++r) {
+    const int v = lane * VPL + r;
     if (v < st.nv && m[r]) {
       P.vx[base] = x[r]; P.vy[base] = y[r]; P.vz[base] = z[r];
       P.newid[v] = (uint8_t)base;
       ++base;
     }
   }
-  __syncwarp();
+  gsync<GW>();
   if (lane < st.nf) {
     const int L = P.flen[st.cur][lane];
     for (int k = 0; k < L; ++k) P.fv[st.cur][k][lane] = P.newid[P.fv[st.cur][k][lane]];
   }
   st.nv = total;
-  __syncwarp();
+  gsync<GW>();
 }
 
 // clip the closed surface by the half-space a.x + b >= 0.
 // returns 0: unchanged, 1: clipped, 2: empty. err bit0: capacity overflow
 // or inconsistent topology (the face's V_F is then unreliable and counted).
-template <typename G>
-__device__ GVOF_CLIP_ATTR int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, G b, int lane,
+template <typename G, int GW>
+__device__ GVOF_CLIP_ATTR int clip(Poly<G, GW>& P, PolyState& st, G a0, G a1, G a2, G b, int lane,
                                  unsigned& err) {
+  constexpr int NV = Poly<G, GW>::NV, NF = Poly<G, GW>::NF, LM = Poly<G, GW>::LM;
   if (st.nv > NV - NR) compact(P, st, lane);
   bool vout = false;
-  for (int v = lane; v < st.nv; v += 32) {
+  for (int v = lane; v < st.nv; v += GW) {
     const G ph = a0 * P.vx[v] + a1 * P.vy[v] + a2 * P.vz[v] + b;
     P.phi[v] = ph;
     P.rfirst[v] = -1;
     vout |= !(ph >= G(0));
   }
-  if (!__any_sync(GVOF_FULL, vout)) return 0;  // no vertex outside: unchanged
-  __syncwarp();
+  if (!gany<GW>(vout)) return 0;  // no vertex outside: unchanged
+  gsync<GW>();
   const int cur = st.cur, nf = st.nf, nv = st.nv;
   const int fl = lane < NF ? lane : 0;
   bool has_in = false, has_out = false;
@@ -329,16 +339,16 @@ __device__ GVOF_CLIP_ATTR int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, 
     const unsigned nxt_in = ((inmask >> 1) | (inmask << (L - 1))) & full;
     nexit = __popc(inmask & ~nxt_in);
   }
-  const unsigned bin = __ballot_sync(GVOF_FULL, has_in);
-  const unsigned bout = __ballot_sync(GVOF_FULL, has_out);
+  const unsigned bin = gballot<GW>(has_in);
+  const unsigned bout = gballot<GW>(has_out);
   if (bout == 0) return 0;
   if (bin == 0) { st.nf = 0; return 2; }
   int incl = nexit;
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(GVOF_FULL, incl, d);
+  for (int d = 1; d < GW; d <<= 1) {
+    const int t = gshfl_up<GW>(incl, d);
     if (lane >= d) incl += t;
   }
-  const int total = __shfl_sync(GVOF_FULL, incl, 31);
+  const int total = gshfl<GW>(incl, GW - 1);
   const int off = incl - nexit;
   if (total > NR || nv + total > NV) { err |= 1u; st.nf = 0; return 2; }
   // new vertices on the cut edges, created by the face leaving the half-space
@@ -362,7 +372,7 @@ __device__ GVOF_CLIP_ATTR int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, 
       }
     }
   }
-  __syncwarp();
+  gsync<GW>();
   const int nxt = cur ^ 1;
   const int slot = __popc(bin & ((1u << lane) - 1u));
   bool bad = false;
@@ -395,8 +405,8 @@ __device__ GVOF_CLIP_ATTR int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, 
     if (n > LM) bad = true;
     P.flen[nxt][slot] = (uint8_t)(n > LM ? LM : n);
   }
-  if (__any_sync(GVOF_FULL, bad)) { err |= 1u; st.nf = 0; return 2; }
-  __syncwarp();
+  if (gany<GW>(bad)) { err |= 1u; st.nf = 0; return 2; }
+  gsync<GW>();
   // cap loops
   int nfo = __popc(bin);
   if (lane == 0) {
@@ -414,17 +424,17 @@ __device__ GVOF_CLIP_ATTR int clip(Poly<G>& P, PolyState& st, G a0, G a1, G a2, 
       if (n >= 3) { P.flen[nxt][nfo] = (uint8_t)n; ++nfo; }
     }
   }
-  nfo = __shfl_sync(GVOF_FULL, nfo, 0);
+  nfo = gshfl<GW>(nfo, 0);
   st.nv = nv + total;
   st.nf = nfo;
   st.cur = nxt;
-  __syncwarp();
+  gsync<GW>();
   return 1;
 }
 
 // signed volume of the surface: each lane fans one face loop
-template <typename G>
-__device__ __noinline__ G volume(const Poly<G>& P, const PolyState& st, int lane) {
+template <typename G, int GW>
+__device__ __noinline__ G volume(const Poly<G, GW>& P, const PolyState& st, int lane) {
   G acc = G(0);
   if (st.nf > 0) {
     const int o = P.fv[st.cur][0][0];
@@ -442,15 +452,15 @@ __device__ __noinline__ G volume(const Poly<G>& P, const PolyState& st, int lane
       }
     }
   }
-  return wsum(acc) / G(6);
+  return gsum<GW>(acc) / G(6);
 }
 
 // volume of the part of the surface on the inner side a.x + b >= 0 of a
 // plane, without building the cut: each lane clips its face loop on the fly
 // (Sutherland-Hodgman) and fans it with the origin ON the plane, so the cap
 // the cut would close contributes nothing to the divergence sum
-template <typename G>
-__device__ GVOF_CLIP_ATTR G volume_cut(const Poly<G>& P, const PolyState& st, G a0, G a1, G a2, G b,
+template <typename G, int GW>
+__device__ GVOF_CLIP_ATTR G volume_cut(const Poly<G, GW>& P, const PolyState& st, G a0, G a1, G a2, G b,
                                      int lane) {
   // origin: projection onto the plane of a vertex on the inner side, so that
   // the fan terms are of the size of the part that is kept (which may be a
@@ -463,9 +473,9 @@ __device__ GVOF_CLIP_ATTR G volume_cut(const Poly<G>& P, const PolyState& st, G 
       if (a0 * P.vx[v] + a1 * P.vy[v] + a2 * P.vz[v] + b >= G(0)) { myv = v; break; }
     }
   }
-  const unsigned have = __ballot_sync(GVOF_FULL, myv >= 0);
+  const unsigned have = gballot<GW>(myv >= 0);
   if (have == 0u) return G(0);  // no vertex on the inner side: nothing is kept
-  const int v0 = __shfl_sync(GVOF_FULL, myv, __ffs(have) - 1);
+  const int v0 = gshfl<GW>(myv, __ffs(have) - 1);
   G acc = G(0);
   if (lane < st.nf) {
     const G aa = a0 * a0 + a1 * a1 + a2 * a2;
@@ -508,7 +518,7 @@ __device__ GVOF_CLIP_ATTR G volume_cut(const Poly<G>& P, const PolyState& st, G 
       ax = bx; ay = by; az = bz; pa = pb;
     }
   }
-  return wsum(acc) / G(6);
+  return gsum<GW>(acc) / G(6);
 }
 
 template <typename G>
@@ -930,22 +940,22 @@ __device__ __noinline__ unsigned poly_coverage(const DevMesh& M, const GeoView<G
 // the polyhedron of face j into shared memory by lane 0 (the other lanes
 // wait): the flux kernel's fallback beyond the prebuilt capacity and the
 // polyhedron export
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ __noinline__ bool build_polyhedron(const DevMesh& M, const GeoView<G>& Gv, const GridParam& p,
-                                              int j, double Vd, Poly<G>& P, FaceFrame<G>& frs, int lane) {
+                                              int j, double Vd, Poly<G, GW>& P, FaceFrame<G>& frs, int lane) {
   int ok = 0;
   if (lane == 0) ok = poly_scalar<G, KIND>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
-  ok = __shfl_sync(GVOF_FULL, ok, 0);
-  __syncwarp();
+  ok = gshfl<GW>(ok, 0);
+  gsync<GW>();
   return ok != 0;
 }
 
 // the polyhedron of active face w built by lane 0 (past the prebuilt
 // capacity), with its coverage bits written as k_prebuild writes them
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ __noinline__ bool build_polyhedron_cov(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
                                                   const GridParam& p, int j, unsigned w, double Vd,
-                                                  Poly<G>& P, FaceFrame<G>& frs, int lane) {
+                                                  Poly<G, GW>& P, FaceFrame<G>& frs, int lane) {
   int ok = 0;
   if (lane == 0) {
     ok = poly_scalar<G, KIND>(M, Gv, p, j, Vd, P.bx, P.by, P.bz, frs) ? 1 : 0;
@@ -953,8 +963,8 @@ __device__ __noinline__ bool build_polyhedron_cov(const DevMesh& M, const GeoVie
     S.cover8[w] = (uint8_t)cov;
     if (cov & kEscaped) atomicAdd(S.cnt + kNEscape, 1ull);
   }
-  ok = __shfl_sync(GVOF_FULL, ok, 0);
-  __syncwarp();
+  ok = gshfl<GW>(ok, 0);
+  gsync<GW>();
   return ok != 0;
 }
 
@@ -979,9 +989,10 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* a, int n, int key
 // the volume of P itself). Vertices within tol of a plane count as on its
 // inner side; tol is a few ulps of the face-local unit, so the volume this
 // neglects is of the order of the rounding of the plane itself.
-template <typename G, int KIND>
-__device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic, const FaceFrame<G>& fr,
+template <typename G, int KIND, int GW>
+__device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G, GW>& P, int np, bool has_plic, const FaceFrame<G>& fr,
                                           G Vl, int lane, unsigned& err, int* whole) {
+  constexpr int NF = Poly<G, GW>::NF;
   const G tol = sizeof(G) == 8 ? G(1e-14) : G(2e-7);
   *whole = 0;
   const bool hv = lane < base_verts<KIND>(fr.I);
@@ -989,16 +1000,16 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
   unsigned cut = 0u;
   for (int g = 0; g < np; ++g) {
     const G ph = P.pl[g][0] * bx + P.pl[g][1] * by + P.pl[g][2] * bz + P.pl[g][3];
-    const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
-    const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
+    const unsigned out = gballot<GW>(hv && ph < -tol);
+    const unsigned in = gballot<GW>(hv && ph > tol);
     if (in == 0u && out != 0u) return G(0);  // P on the outer side of a plane
     if (out) cut |= 1u << g;
   }
   bool plic = false;
   if (has_plic) {
     const G ph = P.pl[NF][0] * bx + P.pl[NF][1] * by + P.pl[NF][2] * bz + P.pl[NF][3];
-    const unsigned out = __ballot_sync(GVOF_FULL, hv && ph < -tol);
-    const unsigned in = __ballot_sync(GVOF_FULL, hv && ph > tol);
+    const unsigned out = gballot<GW>(hv && ph < -tol);
+    const unsigned in = gballot<GW>(hv && ph > tol);
     if (in == 0u && out != 0u) return G(0);  // P on the other side of the interface
     plic = out != 0u;
   }
@@ -1032,10 +1043,13 @@ __device__ GVOF_PLANES_ATTR G truncate_planes(Poly<G>& P, int np, bool has_plic,
 // that join its centroid to the fan triangles of its faces (winding-number
 // decomposition, valid for any closed cell); the PLIC half-space, if any, is
 // already in P.pl[NF]
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>& Gv, int k,
                                              int64_t c0, int nfk, bool tag0, const FaceFrame<G>& fr,
-                                             G Vl, Poly<G>& P, int lane, unsigned& err) {
+                                             G Vl, Poly<G, GW>& P, int lane, unsigned& err) {
+  // one lane per face of the cell: a half-warp group takes cells of at most
+  // 16 faces (the flux kernel uses it only on such grids)
+  if (nfk > GW) { err |= 1u; return G(0); }
   const G rx = rel(Gv.ccx[k], fr.cx) * fr.sc, ry = rel(Gv.ccy[k], fr.cy) * fr.sc,
           rz = rel(Gv.ccz[k], fr.cz) * fr.sc;
   // fan triangles per face, and their running count (lanes over faces)
@@ -1048,15 +1062,15 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
     ntri = (int)(M.fptr[f + 1] - fb_l) - 2;
   }
   int incl = ntri;
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(GVOF_FULL, incl, d);
+  for (int d = 1; d < GW; d <<= 1) {
+    const int t = gshfl_up<GW>(incl, d);
     if (lane >= d) incl += t;
   }
-  const int total = __shfl_sync(GVOF_FULL, incl, 31);
+  const int total = gshfl<GW>(incl, GW - 1);
   const int first = incl - ntri;
   G v = G(0);
-  // lanes over tetrahedra, 32 at a time: build, orient, reject by bounding box
-  for (int base = 0; base < total; base += 32) {
+  // lanes over tetrahedra, GW at a time: build, orient, reject by bounding box
+  for (int base = 0; base < total; base += GW) {
     const int id = base + lane;
     G T[4][3];
     G sgn = G(0);
@@ -1064,12 +1078,12 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
     // face holding tetrahedron id: the last face whose first <= id
     int q = 0;
     for (int r = 0; r < nfk; ++r) {
-      const int fr_first = __shfl_sync(GVOF_FULL, first, r);
+      const int fr_first = gshfl<GW>(first, r);
       if (fr_first <= id) q = r;
     }
-    const int fs = __shfl_sync(GVOF_FULL, fs_l, q & 31);
-    const int64_t fb = __shfl_sync(GVOF_FULL, fb_l, q & 31);
-    const int fq_first = __shfl_sync(GVOF_FULL, first, q & 31);
+    const int fs = gshfl<GW>(fs_l, q & (GW - 1));
+    const int64_t fb = gshfl<GW>(fb_l, q & (GW - 1));
+    const int fq_first = gshfl<GW>(first, q & (GW - 1));
     if (id < total) {
       const int t = id - fq_first + 1;
       int ia = M.fvert[fb], ib = M.fvert[fb + t], ic = M.fvert[fb + t + 1];
@@ -1095,14 +1109,14 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
       keep = det != G(0) && fr.hi[0] > lo0 && fr.lo[0] < hi0 && fr.hi[1] > lo1 &&
              fr.lo[1] < hi1 && fr.hi[2] > lo2 && fr.lo[2] < hi2;
     }
-    unsigned bal = __ballot_sync(GVOF_FULL, keep);
+    unsigned bal = gballot<GW>(keep);
     while (bal) {
       const int src = __ffs(bal) - 1;
       bal &= bal - 1u;
       G Tq[4][3];
       for (int a = 0; a < 4; ++a)
-        for (int d = 0; d < 3; ++d) Tq[a][d] = __shfl_sync(GVOF_FULL, T[a][d], src);
-      const G sg = __shfl_sync(GVOF_FULL, sgn, src);
+        for (int d = 0; d < 3; ++d) Tq[a][d] = gshfl<GW>(T[a][d], src);
+      const G sg = gshfl<GW>(sgn, src);
       // inward planes of the tetrahedron: face opposite vertex a, outward
       // normal (q1 - q0) x (q2 - q0) for a positive tetrahedron
       if (lane < 4) {
@@ -1117,7 +1131,7 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
         P.pl[lane][0] = -nx; P.pl[lane][1] = -ny; P.pl[lane][2] = -nz;
         P.pl[lane][3] = nx * Tq[o0][0] + ny * Tq[o0][1] + nz * Tq[o0][2];
       }
-      __syncwarp();
+      gsync<GW>();
       int w = 0;
       v += sg * truncate_planes<G, KIND>(P, 4, tag0, fr, Vl, lane, err, &w);
     }
@@ -1132,11 +1146,12 @@ __device__ __noinline__ G truncate_nonconvex(const DevMesh& M, const GeoView<G>&
 // is the intersection of its face half-spaces; a non-convex cell is the
 // signed sum of the tetrahedra that join its centroid to the fan triangles of
 // its faces (winding-number decomposition, valid for any closed cell).
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ GVOF_CELL_ATTR G truncate_in_cell(const DevMesh& M, const GeoView<G>& Gv,
                                            const DevState& S, int k, const FaceFrame<G>& fr, G Vl,
-                                           Poly<G>& P, int lane, unsigned& err, bool empty_side,
+                                           Poly<G, GW>& P, int lane, unsigned& err, bool empty_side,
                                            int* whole) {
+  constexpr int NF = Poly<G, GW>::NF;
   *whole = 0;
   const int8_t tk = S.tc[k];
   if (tk == (empty_side ? 1 : -1)) return G(0);
@@ -1171,22 +1186,22 @@ __device__ GVOF_CELL_ATTR G truncate_in_cell(const DevMesh& M, const GeoView<G>&
       P.pl[lane][3] = -(ox * rel(fr.cx, Gv.fcx[f]) + oy * rel(fr.cy, Gv.fcy[f]) +
                         oz * rel(fr.cz, Gv.fcz[f])) * fr.sc;
     }
-    __syncwarp();
+    gsync<GW>();
     return truncate_planes<G, KIND>(P, nfk, tag0, fr, Vl, lane, err, whole);
   }
   return truncate_nonconvex<G, KIND>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
 }
 
-// one chunk of up to 32 candidate cells of face j (pass 0: the owner's node
+// one chunk of up to GW candidate cells of face j (pass 0: the owner's node
 // neighbours and the owner; pass 1: the neighbour's and the neighbour, minus
 // those already seen), filtered by the local bounding box of the
 // polyhedron and (FP32, convex cells other than axis-aligned boxes, whose box
 // test is already this one) by the cell's face planes: a cell with a plane
 // that has every vertex of P strictly outside cannot meet P; returns the
 // lane's cell (-1: none) and its tag
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
-                                         const FaceFrame<G>& fr, const Poly<G>& P, int own, int64_t a0,
+                                         const FaceFrame<G>& fr, const Poly<G, GW>& P, int own, int64_t a0,
                                          int na, int pass, int c0, int64_t b0, int nb, int idx,
                                          int8_t& tk) {
   const int64_t nc = M.nc;
@@ -1237,9 +1252,9 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
 // in the fluid (1) or empty (2) part of one cell (V_F = V_d or 0 exactly).
 // cover: the coverage bits of P (poly_coverage); the complement form needs a
 // covered P.
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
-                              const FaceFrame<G>& fr, double Vd, G Vl, Poly<G>& P, int lane,
+                              const FaceFrame<G>& fr, double Vd, G Vl, Poly<G, GW>& P, int lane,
                               unsigned& err, int* whole, bool* complement, unsigned cover,
                               unsigned long long& n_trunc) {
   const int own = M.own[j], nbr = M.nbr[j];
@@ -1254,18 +1269,18 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     if (c0 < 0) break;
     const int64_t b0 = M.nb_ptr[c0];
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
-    for (int base = 0; base < nb; base += 32) {
+    for (int base = 0; base < nb; base += GW) {
       int8_t tk;
       const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
-      const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
-      if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
-      if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
+      const unsigned bal = gballot<GW>(k >= 0);
+      if (gany<GW>(k >= 0 && tk == -1)) neg = true;
+      if (gany<GW>(k >= 0 && tk == 1)) pos = true;
       const int at = n + __popc(bal & ((1u << lane) - 1u));
       if (k >= 0 && at < cap) P.cand[at] = k;
       n += __popc(bal);
     }
   }
-  __syncwarp();
+  gsync<GW>();
   bool comp = false;
   if (sizeof(G) == 4 && nbr >= 0 && !(cover & kUncovered)) {
     if (!neg && pos) comp = true;
@@ -1294,14 +1309,14 @@ __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>
     if (c0 < 0) break;
     const int64_t b0 = M.nb_ptr[c0];
     const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
-    for (int base = 0; base < nb; base += 32) {
+    for (int base = 0; base < nb; base += GW) {
       int8_t tk;
       const int k = candidate<G, KIND>(M, Gv, S, fr, P, own, a0, na, pass, c0, b0, nb, base + lane, tk);
-      unsigned bal = __ballot_sync(GVOF_FULL, k >= 0 && tk != skip);
+      unsigned bal = gballot<GW>(k >= 0 && tk != skip);
       while (bal) {
         const int src = __ffs(bal) - 1;
         bal &= bal - 1u;
-        const int kk = __shfl_sync(GVOF_FULL, k, src);
+        const int kk = gshfl<GW>(k, src);
         int w = 0;
         v += truncate_in_cell<G, KIND>(M, Gv, S, kk, fr, Vl, P, lane, err, comp, &w);
         ++n_trunc;
@@ -1347,9 +1362,9 @@ __global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevS
 
 // the flux polyhedron of active face w: prebuilt below fm_cap, else built
 // here by lane 0 with the same arithmetic
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 __device__ bool poly_for_face(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, unsigned w,
-                              int j, const GridParam& p, double Vd, Poly<G>& P, FaceFrame<G>& fr,
+                              int j, const GridParam& p, double Vd, Poly<G, GW>& P, FaceFrame<G>& fr,
                               int lane) {
   if ((int64_t)w >= S.fm_cap) return build_polyhedron_cov<G, KIND>(M, Gv, S, p, j, w, Vd, P, fr, lane);
   const uint32_t meta = S.fm_meta[w];
@@ -1373,37 +1388,43 @@ __device__ bool poly_for_face(const DevMesh& M, const GeoView<G>& Gv, const DevS
     const G* v = (const G*)S.fm_v + ((size_t)w * kFmSlots + lane) * 3;
     P.bx[lane] = v[0]; P.by[lane] = v[1]; P.bz[lane] = v[2];
   }
-  __syncwarp();
+  gsync<GW>();
   return ok;
 }
 
-// the next active face for this warp: faces are dealt one at a time from a
-// counter, so a warp that drew cheap faces takes more and none idles while
-// another still holds a queue (the results do not depend on the order)
+// the next active face for this lane group: faces are dealt one at a time
+// from a counter, so a group that drew cheap faces takes more and none idles
+// while another still holds a queue (the results do not depend on the order)
+template <int GW>
 __device__ __forceinline__ unsigned next_face(const DevState& S, int lane) {
   unsigned w = 0u;
   if (lane == 0) w = (unsigned)atomicAdd(S.cnt + kFluxNext, 1ull);
-  return __shfl_sync(GVOF_FULL, w, 0);
+  return gshfl<GW>(w, 0);
 }
 
-template <typename G, int KIND>
+static_assert(sizeof(GridParam) % sizeof(double) == 0 && sizeof(GridParam) / sizeof(double) <= 16,
+              "a half warp stages the grid parameters");
+
+// one lane group (a warp, GW = 32, or a half warp, GW = 16) per active face
+template <typename G, int KIND, int GW>
 __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M, GeoView<G> Gv, DevState S) {
-  __shared__ Poly<G> polys[kWarps];
-  __shared__ GridParam wgp[kWarps];
-  __shared__ FaceFrame<G> wfr[kWarps];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  Poly<G>& P = polys[wib];
+  constexpr int kGroups = kWarps * 32 / GW;
+  __shared__ Poly<G, GW> polys[kGroups];
+  __shared__ GridParam wgp[kGroups];
+  __shared__ FaceFrame<G> wfr[kGroups];
+  const int lane = threadIdx.x & (GW - 1), wib = threadIdx.x / GW;
+  Poly<G, GW>& P = polys[wib];
   FaceFrame<G>& fr = wfr[wib];
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
   unsigned long long n_trunc = 0, n_over = 0, n_deg = 0, n_edge = 0;
-  for (unsigned w = next_face(S, lane); w < n_af; w = next_face(S, lane)) {
+  for (unsigned w = next_face<GW>(S, lane); w < n_af; w = next_face<GW>(S, lane)) {
     const int j = S.afaces[w];
     // the face's grid parameters, staged in shared memory (read at use)
     {
       const int gi = M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j);
       constexpr int nw = (int)(sizeof(GridParam) / sizeof(double));
       if (lane < nw) ((double*)&wgp[wib])[lane] = ((const double*)&S.gp[gi])[lane];
-      __syncwarp();
+      gsync<GW>();
     }
     const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
     if (!poly_for_face<G, KIND>(M, Gv, S, w, j, wgp[wib], Vd, P, fr, lane)) {
@@ -1536,16 +1557,35 @@ void prebuild_launch_kind(const vof_ctx* c, cudaStream_t s) {
     default: prebuild_launch<G, VOF_FLUX_FMFPA>(c, s); break;
   }
 }
-template <typename G, int KIND>
+template <typename G, int KIND, int GW>
 void flux_launch(const vof_ctx* c, int grid, cudaStream_t s) {
-  k_flux<G, KIND><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
+  if constexpr (GW == 16) {
+    // eight half-warp polyhedra per block: ask for the largest shared-memory
+    // carve-out so that as many blocks stay resident as with whole warps
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_flux<G, KIND, GW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      set = true;
+    }
+  }
+  k_flux<G, KIND, GW><<<grid, kWarps * 32, 0, s>>>(mesh_view(c), geo_view<G>(c), state_view(c));
 }
 template <typename G>
 void flux_launch_kind(const vof_ctx* c, int grid, cudaStream_t s) {
+  // two faces per warp where the context allows it (FMFPA and NMFPA on
+  // grids of convex cells with at most 16 faces and faces of at most 5
+  // nodes; see vof_options.faces_per_warp)
+  const bool half = c->faces_per_warp == 2;
   switch (c->opt.flux_polyhedron) {
-    case VOF_FLUX_EMFPA: flux_launch<G, VOF_FLUX_EMFPA>(c, grid, s); break;
-    case VOF_FLUX_NMFPA: flux_launch<G, VOF_FLUX_NMFPA>(c, grid, s); break;
-    default: flux_launch<G, VOF_FLUX_FMFPA>(c, grid, s); break;
+    case VOF_FLUX_EMFPA: flux_launch<G, VOF_FLUX_EMFPA, 32>(c, grid, s); break;
+    case VOF_FLUX_NMFPA:
+      if (half) flux_launch<G, VOF_FLUX_NMFPA, 16>(c, grid, s);
+      else flux_launch<G, VOF_FLUX_NMFPA, 32>(c, grid, s);
+      break;
+    default:
+      if (half) flux_launch<G, VOF_FLUX_FMFPA, 16>(c, grid, s);
+      else flux_launch<G, VOF_FLUX_FMFPA, 32>(c, grid, s);
+      break;
   }
 }
 template <typename G, int KIND>

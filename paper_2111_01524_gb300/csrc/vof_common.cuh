@@ -359,6 +359,9 @@ struct vof_ctx {
   int graph_step;                           // 1: advect + reconstruct, 0: advect only
   // launch shapes (autotuned)
   int flux_blocks, recon_blocks;
+  int faces_per_warp;   // 1 or 2: lane-group width 32 or 16 of the flux kernel
+  bool half_ok;         // the grid allows faces_per_warp = 2
+  int64_t fm_use;       // faces whose polyhedra are prebuilt (0 or fm_cap)
   // optional per-phase timing (events recorded around each launch)
   bool timing;
   int n_ev_pairs;
@@ -406,7 +409,7 @@ inline DevState state_view(const vof_ctx* c) {
   s.lnx32 = c->lnx32; s.lny32 = c->lny32; s.lnz32 = c->lnz32;
   s.lturn = c->lturn;
   s.fm_v = c->fm_v; s.fm_f = c->fm_f; s.fm_meta = c->fm_meta; s.fm_split = c->fm_split;
-  s.fm_cap = c->fm_cap;
+  s.fm_cap = c->fm_use;
   s.dombox = c->dombox;
   s.fexact = c->fexact; s.Fprev = c->Fprev;
   s.risk = c->risk; s.repf = c->repf; s.repc = c->repc; s.stamp_r = c->stamp_r;

@@ -41,7 +41,7 @@ class _Opt(C.Structure):
     _fields_ = [("eps", C.c_double), ("beta", C.c_double), ("precision", C.c_int32),
                 ("flux_polyhedron", C.c_int32), ("reconstruction", C.c_int32),
                 ("lsfir_max_iter", C.c_int32), ("lsfir_tol", C.c_double),
-                ("poly_capacity", C.c_int32), ("reserved", C.c_int32)]
+                ("poly_capacity", C.c_int32), ("faces_per_warp", C.c_int32)]
 
 
 class _Shape(C.Structure):
@@ -146,9 +146,11 @@ def lib():
         L.vof_graph_capture.argtypes = [vp, C.c_int, vp]
         L.vof_graph_launch.argtypes = [vp, vp, vp, vp, vp]
         L.vof_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.vof_autotune_ex.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         for name in ("vof_init_batch", "vof_batch_offsets", "vof_advect_batch", "vof_step_batch",
                      "vof_suggest_dt_batch", "vof_graph_capture", "vof_graph_launch",
-                     "vof_autotune", "vof_batch_create", "vof_advect_step", "vof_batch_step"):
+                     "vof_autotune", "vof_autotune_ex", "vof_batch_create", "vof_advect_step",
+                     "vof_batch_step"):
             getattr(L, name).restype = C.c_int
         L.vof_estimate_bytes.argtypes = [vp, C.c_int, vp, C.POINTER(i64)]
         L.vof_server_create.argtypes = [vp, C.POINTER(vp)]
@@ -327,7 +329,7 @@ class Context:
 
     def __init__(self, mesh, precision=PREC_FP64, eps=1e-12, beta=1.5, flux=FLUX_FMFPA,
                  recon=RECON_LSGIR, lsfir_max_iter=0, lsfir_tol=0.0, poly_capacity=0,
-                 stream=None):
+                 faces_per_warp=0, stream=None):
         L = lib()
         meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
         keep = []
@@ -336,6 +338,7 @@ class Context:
         opt.eps, opt.beta, opt.precision, opt.flux_polyhedron = eps, beta, precision, flux
         opt.reconstruction, opt.lsfir_max_iter, opt.lsfir_tol = recon, lsfir_max_iter, lsfir_tol
         opt.poly_capacity = poly_capacity
+        opt.faces_per_warp = faces_per_warp
         h = C.c_void_p()
         _check(L.vof_batch_create(descs, len(meshes), C.byref(opt), _stream(stream), C.byref(h)))
         self._h = h
@@ -438,11 +441,15 @@ class Context:
         va, ta, da = self._batch_args(vels, t, dt)
         _check(lib().vof_graph_launch(self._h, va, _ptr(ta), _ptr(da), _stream(stream)))
 
-    def autotune(self, vels, t, dt, stream=None):
+    def autotune(self, vels, t, dt, stream=None, full=False):
+        """The tuned launch shape: (flux blocks, reconstruction blocks), and
+        with full=True also faces per warp and prebuilt polyhedra (1/0)."""
         va, ta, da = self._batch_args(vels, t, dt)
-        fb, rb = C.c_int(), C.c_int()
-        _check(lib().vof_autotune(self._h, va, _ptr(ta), _ptr(da), _stream(stream), C.byref(fb),
-                                  C.byref(rb)))
+        fb, rb, fw, pb = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().vof_autotune_ex(self._h, va, _ptr(ta), _ptr(da), _stream(stream), C.byref(fb),
+                                     C.byref(rb), C.byref(fw), C.byref(pb)))
+        if full:
+            return fb.value, rb.value, fw.value, pb.value
         return fb.value, rb.value
 
     def suggest_dt(self, vel, t, cfl, t_end):
