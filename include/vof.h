@@ -282,6 +282,44 @@ vof_status vof_batch_step(vof_ctx* ctx, const vof_velocity* vels, const double* 
 vof_status vof_suggest_dt_batch(vof_ctx* ctx, const vof_velocity* vels, const double* t,
                                 double cfl, const double* t_end, double* dt_out);
 
+/* ---- Partitioned grids (domain decomposition) ----------------------------
+ * One grid split into parts, each part a context of its own on the part's
+ * cells plus a halo of node-neighbour rings (a sub-mesh, cells and faces in
+ * the grid's order); every step each part advects, the halo cells receive
+ * F of their owning parts, and each part reconstructs. With a halo deep
+ * enough for the step's stencils (Secs. 2.1, 2.2, 3.5: the donating-region
+ * candidates of a face are the node neighbours of its two cells, and a
+ * plane reads F of its cell's node neighbours), the owned cells' F equals
+ * the unpartitioned grid's bit for bit.
+ *
+ * vof_halo_lists: the context's cell lists (HOST arrays): list k is
+ * cells[ptr[k] .. ptr[k+1]-1], cell indices of this context (any order,
+ * repeats allowed); ptr has n_lists + 1 entries, ptr[0] = 0, non-decreasing.
+ * Copied to the device (the context owns the copy; earlier lists are
+ * replaced; waits for the device). VOF_EINVAL for a bad ptr or an index
+ * outside 0..n_cell-1. */
+vof_status vof_halo_lists(vof_ctx* ctx, int n_lists, const int64_t* ptr, const int32_t* cells);
+/* out[i] = F[cells[i]] over list `list` (out: DEVICE, list size doubles),
+ * asynchronous on `stream` */
+vof_status vof_halo_export(vof_ctx* ctx, int list, double* out, void* stream);
+/* F[cells[i]] = in[i] over list `list` (in: DEVICE), asynchronous on
+ * `stream`; like vof_set_fraction the next advect needs a vof_reconstruct,
+ * and the next sweeps stay band-limited only if every changed cell was in
+ * the band of the last advect */
+vof_status vof_halo_import(vof_ctx* ctx, int list, const double* in, void* stream);
+/* *vol = sum of V_k F_k over the cells of list `list`, in a fixed order
+ * (HOST result; synchronises `stream`) */
+vof_status vof_list_volume(vof_ctx* ctx, int list, double* vol, void* stream);
+/* The bounds Eq. eq:cfl takes over a grid: per axis the smallest cell
+ * bounding-box size and the largest face-centre speed of the velocity
+ * field's spatial part (HOST double[3] each; single-grid contexts). The
+ * bounds of a partitioned grid are the minimum and maximum over its parts,
+ * and vof_dt_from_bounds turns them into vof_suggest_dt's time step: the
+ * same value, bit for bit, as the unpartitioned grid's. */
+vof_status vof_dt_bounds(vof_ctx* ctx, const vof_velocity* vel, double* hmin, double* umax);
+vof_status vof_dt_from_bounds(const vof_velocity* vel, const double* hmin, const double* umax,
+                              double t, double cfl, double t_end, double* dt);
+
 /* CUDA graph of one step: vof_graph_capture records the launches of one
  * vof_advect (with_reconstruct = 0) or vof_step (1) on `stream` (not the
  * legacy default stream) into a graph; vof_graph_launch writes the step's

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libgvof.so")
-UNITS = ["capi.cu", "k_setup.cu", "k_sweep.cu", "k_recon.cu", "k_flux.cu", "k_init.cu", "noalloc.cu",
+UNITS = ["capi.cu", "k_setup.cu", "k_sweep.cu", "k_recon.cu", "k_flux.cu", "k_init.cu", "noalloc.cu", "halo.cu",
          "server.cu", "mesh_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -52,7 +52,7 @@ void free_all(vof_ctx* c) {
                    c->lzp, c->lxr, c->lyr, c->lzr, c->lnx, c->lny, c->lnz, c->lnx32, c->lny32,
                    c->lnz32, c->lturn, c->fm_v, c->fm_f, c->fm_meta, c->fm_split, c->dombox,
                    c->fexact, c->Fprev, c->risk, c->repf, c->repc, c->stamp_r, c->Eexc,
-                   c->Sroom, c->cover8, c->rstar};
+                   c->Sroom, c->cover8, c->rstar, c->lists, c->list_part};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -63,6 +63,7 @@ void free_all(vof_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   delete c->cell_off; delete c->face_off; delete c->vert_off;
   delete c->hmin_g; delete c->umax_g; delete c->vel_g;
+  delete c->list_ptr;
 }
 
 cudaMemcpyKind kind_from_dev(int mem) {
@@ -181,6 +182,25 @@ double dt_from(const double hmin[3], const double um[3], double cfl) {
   for (int d = 0; d < 3; ++d)
     if (um[d] > 0.0) dt = std::min(dt, hmin[d] / um[d]);
   return dt * cfl;
+}
+
+// the time step of Eq. eq:cfl from the smallest cell extents and the
+// largest speeds of the spatial field per axis: the CFL step at t, then
+// again with the speeds at the end of that step (a time-modulated field),
+// cut at t_end
+double dt_for(const Vel& v, const double* hmin, const double* u0, double t, double cfl,
+              double t_end) {
+  double um[3];
+  const double g0 = std::fabs(time_factor(v, t));
+  for (int d = 0; d < 3; ++d) um[d] = g0 * u0[d];
+  double d1 = dt_from(hmin, um, cfl);
+  if (t + d1 > t_end) d1 = t_end - t;
+  const double g1 = std::fabs(time_factor(v, t + d1));
+  for (int d = 0; d < 3; ++d) um[d] = std::max(um[d], g1 * u0[d]);
+  const double d2 = dt_from(hmin, um, cfl);
+  double r = std::min(d1, d2);
+  if (t + r > t_end) r = t_end - t;
+  return r;
 }
 
 }  // namespace
@@ -714,22 +734,33 @@ vof_status vof_suggest_dt_batch(vof_ctx* c, const vof_velocity* vels, const doub
   if (!(cfl > 0)) return fail(VOF_EINVAL, "cfl must be > 0");
   vof_status st = ensure_velocity(c, vels, 0);
   if (st != VOF_OK) return st;
-  for (int gi = 0; gi < c->n_grids; ++gi) {
-    const Vel& v = (*c->vel_g)[gi];
-    const double* hmin = c->hmin_g->data() + 3 * gi;
-    const double* u0 = c->umax_g->data() + 3 * gi;
-    double um[3];
-    const double g0 = std::fabs(time_factor(v, t[gi]));
-    for (int d = 0; d < 3; ++d) um[d] = g0 * u0[d];
-    double d1 = dt_from(hmin, um, cfl);
-    if (t[gi] + d1 > t_end[gi]) d1 = t_end[gi] - t[gi];
-    const double g1 = std::fabs(time_factor(v, t[gi] + d1));
-    for (int d = 0; d < 3; ++d) um[d] = std::max(um[d], g1 * u0[d]);
-    const double d2 = dt_from(hmin, um, cfl);
-    double r = std::min(d1, d2);
-    if (t[gi] + r > t_end[gi]) r = t_end[gi] - t[gi];
-    dt_out[gi] = r;
+  for (int gi = 0; gi < c->n_grids; ++gi)
+    dt_out[gi] = dt_for((*c->vel_g)[gi], c->hmin_g->data() + 3 * gi, c->umax_g->data() + 3 * gi,
+                        t[gi], cfl, t_end[gi]);
+  return VOF_OK;
+}
+
+vof_status vof_dt_bounds(vof_ctx* c, const vof_velocity* vel, double* hmin, double* umax) {
+  if (!c || !vel || !hmin || !umax) return fail(VOF_EINVAL, "NULL argument");
+  if (c->n_grids != 1) return fail(VOF_EINVAL, "batch context: one grid only");
+  vof_status st = ensure_velocity(c, vel, 0);
+  if (st != VOF_OK) return st;
+  for (int d = 0; d < 3; ++d) {
+    hmin[d] = (*c->hmin_g)[d];
+    umax[d] = (*c->umax_g)[d];
   }
+  return VOF_OK;
+}
+
+vof_status vof_dt_from_bounds(const vof_velocity* vel, const double* hmin, const double* umax,
+                              double t, double cfl, double t_end, double* dt) {
+  if (!vel || !hmin || !umax || !dt) return fail(VOF_EINVAL, "NULL argument");
+  if (!(cfl > 0)) return fail(VOF_EINVAL, "cfl must be > 0");
+  vof_status st = check_velocity(*vel);
+  if (st != VOF_OK) return st;
+  for (int d = 0; d < 3; ++d)
+    if (!(hmin[d] > 0.0) || !(umax[d] >= 0.0)) return fail(VOF_EINVAL, "bad bounds");
+  *dt = dt_for(to_vel(*vel), hmin, umax, t, cfl, t_end);
   return VOF_OK;
 }
 

@@ -317,6 +317,12 @@ struct vof_ctx {
   double *Eexc, *Sroom;  // per risk cell: excess and neighbours' room
   int64_t rep_cap;
   uint8_t* cover8;
+  // cell lists of a partitioned grid (vof_halo_lists): entries, offsets
+  // (host), and the partial sums of vof_list_volume
+  int32_t* lists;
+  int64_t n_list_cells;
+  std::vector<int64_t>* list_ptr;
+  double* list_part;
   // state (device)
   double* F;
   double *nx, *ny, *nz, *C;

@@ -165,6 +165,15 @@ def lib():
                      "vof_server_step", "vof_server_drain", "vof_server_poll",
                      "vof_server_get_stats"):
             getattr(L, name).restype = C.c_int
+        L.vof_halo_lists.argtypes = [vp, C.c_int, vp, vp]
+        L.vof_halo_export.argtypes = [vp, C.c_int, vp, vp]
+        L.vof_halo_import.argtypes = [vp, C.c_int, vp, vp]
+        L.vof_list_volume.argtypes = [vp, C.c_int, C.POINTER(dbl), vp]
+        L.vof_dt_bounds.argtypes = [vp, vp, vp, vp]
+        L.vof_dt_from_bounds.argtypes = [vp, vp, vp, dbl, dbl, dbl, C.POINTER(dbl)]
+        for name in ("vof_halo_lists", "vof_halo_export", "vof_halo_import", "vof_list_volume",
+                     "vof_dt_bounds", "vof_dt_from_bounds"):
+            getattr(L, name).restype = C.c_int
         L.vof_volume_sum_noalloc.argtypes = [vp, vp, i64, vp, vp]
         L.vof_volume_sum_noalloc.restype = C.c_int
         L.vof_device_bytes.restype = i64
@@ -195,6 +204,26 @@ def _ptr(a):
 
 def _mem(a):
     return MEM_DEVICE if hasattr(a, "data_ptr") and a.is_cuda else MEM_HOST
+
+
+def dt_from_bounds(vel, hmin, umax, t, cfl, t_end):
+    """vof_suggest_dt's time step from per-axis bounds reduced over the parts
+    of a partitioned grid (``Context.dt_bounds``)."""
+    v = velocity_struct(vel)
+    h = np.ascontiguousarray(hmin, np.float64)
+    u = np.ascontiguousarray(umax, np.float64)
+    if h.shape != (3,) or u.shape != (3,):
+        raise ValueError("hmin and umax hold three values each")
+    d = C.c_double()
+    _check(lib().vof_dt_from_bounds(C.byref(v), _ptr(h), _ptr(u), t, cfl, t_end, C.byref(d)))
+    return d.value
+
+
+def _need_device(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and t.numel() >= n):
+        raise ValueError(f"expected a contiguous CUDA float64 tensor of at least {n} values")
 
 
 def _stream(stream):
@@ -457,6 +486,42 @@ class Context:
         d = C.c_double()
         _check(lib().vof_suggest_dt(self._h, C.byref(v), t, cfl, t_end, C.byref(d)))
         return d.value
+
+    # --- partitioned grids: cell lists, halo gather / scatter, dt bounds
+    def set_lists(self, lists):
+        """Upload cell lists (a sequence of int arrays of this context's cell
+        indices); list k is then addressed by k."""
+        lists = [np.ascontiguousarray(a, np.int32).ravel() for a in lists]
+        ptr = np.zeros(len(lists) + 1, np.int64)
+        for k, a in enumerate(lists):
+            ptr[k + 1] = ptr[k] + a.size
+        cells = np.concatenate(lists) if lists else np.zeros(1, np.int32)
+        cells = np.ascontiguousarray(cells, np.int32)
+        _check(lib().vof_halo_lists(self._h, len(lists), _ptr(ptr), _ptr(cells)))
+        self._list_sizes = [int(a.size) for a in lists]
+
+    def export_list(self, k, out, stream=None):
+        """out (a CUDA float64 tensor of the list's size) <- F over list k."""
+        _need_device(out, self._list_sizes[k])
+        _check(lib().vof_halo_export(self._h, int(k), C.c_void_p(out.data_ptr()), _stream(stream)))
+
+    def import_list(self, k, src, stream=None):
+        """F over list k <- src (a CUDA float64 tensor of the list's size)."""
+        _need_device(src, self._list_sizes[k])
+        _check(lib().vof_halo_import(self._h, int(k), C.c_void_p(src.data_ptr()), _stream(stream)))
+
+    def list_volume(self, k, stream=None):
+        v = C.c_double()
+        _check(lib().vof_list_volume(self._h, int(k), C.byref(v), _stream(stream)))
+        return v.value
+
+    def dt_bounds(self, vel):
+        """(hmin[3], umax[3]) of this grid for the field ``vel``."""
+        v = velocity_struct(vel)
+        h = np.empty(3)
+        u = np.empty(3)
+        _check(lib().vof_dt_bounds(self._h, C.byref(v), _ptr(h), _ptr(u)))
+        return h, u
 
     # --- read-back
     def planes(self, stream=None):
