@@ -493,47 +493,58 @@ def main_batch(a):
     from paper_2111_01524_gb300 import vof as V
     B.build()
     n = len(meshes)
-    ctx = V.Context(meshes, precision=V.PREC_MIXED)
-    stream = torch.cuda.Stream()
-    cells = int(ctx.n_cell)
     umax = np.array([np.abs(v.u0).max() for v in vels])
-    h = np.array([1.0 / s for s in sides])
-    # READING d4b: dt_g = min(CFL 0.5 step, 0.2 / (100 |U|_inf)) so that 100
-    # steps keep every body inside its domain
-    with torch.cuda.stream(stream):
-        ctx.set_fraction(np.concatenate(Fs))
-        ctx.reconstruct()
-        t = np.zeros(n)
-        dt_cfl = ctx.suggest_dt_batch(vels, t, 0.5, np.full(n, 1e9))
-        dt = np.minimum(dt_cfl, 0.2 / (100.0 * umax))
-        tuned = ctx.autotune(vels, t, dt)
-        ctx.graph_capture(with_reconstruct=True)
-        for _ in range(a.warmup):
-            ctx.graph_launch(vels, t, dt)
-            t = t + dt
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        clk = ClockSampler(local)
-        clk.start()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(a.steps):
-            ctx.graph_launch(vels, t, dt)
-            t = t + dt
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        clocks = clk.stop()
-        ms = over_ranks(dist, e0.elapsed_time(e1), "max")
-        st = ctx.stats()
+    stream = torch.cuda.Stream()
+    arms = {}
+    for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
+        ctx = V.Context(meshes, precision=prec)
+        cells = int(ctx.n_cell)
+        # READING d4b: dt_g = min(CFL 0.5 step, 0.2 / (100 |U|_inf)) so that
+        # 100 steps keep every body inside its domain
+        with torch.cuda.stream(stream):
+            ctx.set_fraction(np.concatenate(Fs))
+            ctx.reconstruct()
+            t = np.zeros(n)
+            dt_cfl = ctx.suggest_dt_batch(vels, t, 0.5, np.full(n, 1e9))
+            dt = np.minimum(dt_cfl, 0.2 / (100.0 * umax))
+            tuned = ctx.autotune(vels, t, dt, full=True)
+            ctx.graph_capture(with_reconstruct=True)
+            for _ in range(a.warmup):
+                ctx.graph_launch(vels, t, dt)
+                t = t + dt
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            clk = ClockSampler(local)
+            clk.start()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                ctx.graph_launch(vels, t, dt)
+                t = t + dt
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            clocks = clk.stop()
+            ms = over_ranks(dist, e0.elapsed_time(e1), "max")
+            st = ctx.stats()
+            F = ctx.get_fraction()
+        arms[name] = {"ms": ms, "st": st, "F": F, "clocks": clocks, "faces": int(ctx.n_face),
+                      "tuned": {"flux_blocks": tuned[0], "recon_blocks": tuned[1],
+                                "faces_per_warp": tuned[2], "prebuilt_polyhedra": tuned[3]}}
+        del ctx
+        torch.cuda.empty_cache()
     total_cells = over_ranks(dist, cells, "sum")
+    dF = over_ranks(dist, float(np.abs(arms["mixed"]["F"] - arms["fp64"]["F"]).max()), "max")
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
         return 0
+    mx, f64 = arms["mixed"], arms["fp64"]
+    ms, st, clocks = mx["ms"], mx["st"], mx["clocks"]
+    v64 = total_cells * a.steps / (f64["ms"] * 1e-3)
     line = {"metric": METRIC, "value": total_cells * a.steps / (ms * 1e-3), "unit": UNIT,
             "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
@@ -543,12 +554,21 @@ def main_batch(a):
                                    "log-uniform 16..96, jitter 0.3h, non-convex cells), ellipsoids, "
                                    "uniform translation, one CUDA graph per step",
                        "cells": int(total_cells), "grids": len(all_sides),
-                       "rank0": {"grids": n, "cells": cells, "faces": int(ctx.n_face),
-                                 "sides": [int(x) for x in sides], "autotuned_blocks": list(tuned)},
+                       "rank0": {"grids": n, "cells": cells, "faces": mx["faces"],
+                                 "sides": [int(x) for x in sides]},
                        "parallelism": f"grids sharded over {ws} rank(s) by cells"},
+            "autotuned": mx["tuned"],
             "gpu_launches": kernels_per_step() * a.steps,
             "band": {"interfacial_cells": st["n_interfacial"], "active_faces": st["n_active_faces"],
-                     "truncations_last_step": st["n_truncations"], "overflow": st["n_overflow"]},
+                     "truncations_last_step": st["n_truncations"], "overflow": st["n_overflow"],
+                     "escaped": st["n_escaped"]},
+            "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": f64["ms"] / a.steps,
+                          "mixed_over_fp64": (total_cells * a.steps / (ms * 1e-3)) / v64,
+                          "autotuned": f64["tuned"], "clocks": f64["clocks"],
+                          "max_abs_F_diff_mixed_vs_fp64": dF,
+                          "after_steps": a.warmup + a.steps,
+                          "volume_rel_diff_mixed_vs_fp64":
+                              (st["volume"] - f64["st"]["volume"]) / f64["st"]["volume"]},
             "clocks": clocks}
     print(json.dumps(line))
     return 0
