@@ -367,7 +367,7 @@ __device__ __forceinline__ double cell_fnext(const DevMesh& M, const int8_t* tf,
 
 // the mixed path defers the clip of a cell whose Eq. fnext value leaves
 // [0, 1] by more than FP64 rounding while some of its face volumes carry
-// FP32 error: those faces are recomputed in FP64 first (launch_repair)
+// FP32 error: the reconciliation of that noise comes first (launch_repair)
 constexpr double kRiskTol = 1e-14;
 static_assert(kRepairRounds >= 1 && kRepairRounds <= 6, "stamp marks epoch * 16 + 2 round (+1)");
 __device__ __forceinline__ bool at_risk(double fn, int n_inexact) {
@@ -408,7 +408,7 @@ __device__ __forceinline__ void block_ebound(double eb, double* red, bool merge)
 
 // Eq. fnext per band cell and the clip of Sec. 2.2. Mixed path: F before
 // the update is kept (Fprev) and a cell at risk (at_risk) is written
-// unclipped and listed for the FP64 repair instead of being clipped; the
+// unclipped and listed for the reconciliation instead of being clipped; the
 // boundary outflow is then summed after the repair (k_repair_finish).
 __global__ void k_update(DevMesh M, DevState S, const int32_t* bfaces, int64_t nbf, double* acc,
                          const int32_t* bcells, int64_t risk_cap, bool mixed) {
