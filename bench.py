@@ -71,15 +71,23 @@ FLUX_NCU = {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66c
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 # kernels one step launches: reconstruction (cell tags 1, node tags 3,
 # LSGIR 1 or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,
-# flux 1, update 2, and in mixed precision the
-# reconciliation of FP32 noise: 5 per round x 3 rounds + 1); the phase
-# timers count the same kernels
+# flux 1, update 2, and in mixed precision the candidate lists of the
+# prebuilt polyhedra 1 and the reconciliation of FP32 noise: 5 per round x 3
+# rounds + 1); the phase timers count the same kernels
 REPAIR_LAUNCHES = 5 * 3 + 1
 
 
-def kernels_per_step(recon="lsgir", n_out=4, precision="mixed"):
-    return (4 + (1 + 2 * n_out if recon == "lsfir" else 1) + 6
-            + (REPAIR_LAUNCHES if precision == "mixed" else 0))
+def recon_kernels(recon="lsgir", n_out=4):
+    return 4 + (1 + 2 * n_out if recon == "lsfir" else 1)
+
+
+def advect_kernels(precision="mixed", prebuilt=True):
+    # the mixed path with prebuilt polyhedra also lists their candidate cells
+    return 6 + ((1 if prebuilt else 0) + REPAIR_LAUNCHES if precision == "mixed" else 0)
+
+
+def kernels_per_step(recon="lsgir", n_out=4, precision="mixed", prebuilt=True):
+    return recon_kernels(recon, n_out) + advect_kernels(precision, prebuilt)
 
 
 FP32_LANES_PER_SM = 128
@@ -558,7 +566,8 @@ def main_batch(a):
                                  "sides": [int(x) for x in sides]},
                        "parallelism": f"grids sharded over {ws} rank(s) by cells"},
             "autotuned": mx["tuned"],
-            "gpu_launches": kernels_per_step() * a.steps,
+            "gpu_launches": kernels_per_step(prebuilt=bool(mx["tuned"]["prebuilt_polyhedra"]))
+                            * a.steps,
             "band": {"interfacial_cells": st["n_interfacial"], "active_faces": st["n_active_faces"],
                      "truncations_last_step": st["n_truncations"], "overflow": st["n_overflow"],
                      "escaped": st["n_escaped"]},
@@ -630,7 +639,9 @@ def main_tets(a):
                                    "rigid rotation, CFL 0.4", "cells": int(m["n_cell"]),
                        "flux_polyhedron": a.flux, "reconstruction": a.recon,
                        "parallelism": f"replicas x{ws}"},
-            "gpu_launches": kernels_per_step(a.recon) * a.steps, "clocks": res["mixed"]["clocks"],
+            # tetrahedral grids get no prebuilt candidate lists (many node neighbours)
+            "gpu_launches": kernels_per_step(a.recon, prebuilt=False) * a.steps,
+            "clocks": res["mixed"]["clocks"],
             "fp64_path": {"value": res["fp64"]["value"],
                           "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
                           "max_abs_F_diff_mixed_vs_fp64":
@@ -817,6 +828,13 @@ def main_serve(a):
                 "p50_ms": float(np.percentile(lat, 50)) * 1e3,
                 "p99_ms": float(np.percentile(lat, 99)) * 1e3,
                 "ticks": st.ticks, "max_active": ss["max_active"], "batches": ss["n_batches"],
+                "batch_steps": ss["batch_steps"],
+                # one captured step per live batch per tick (the candidate-list
+                # kernel, which batches of tetrahedral grids skip, not counted);
+                # a new batch runs its geometry (5), set_fraction (1),
+                # reconstruction and velocity setup (1)
+                "gpu_launches": int(ss["batch_steps"] * kernels_per_step(prebuilt=False)
+                                    + ss["n_batches"] * (5 + 1 + recon_kernels() + 1)),
                 "peak_device_bytes": ss["peak_device_bytes"], "budget_bytes": ss["budget_bytes"],
                 "budget_bound": bool(ss["peak_device_bytes"] > 0.5 * ss["budget_bytes"]),
                 "clocks": clocks}
@@ -844,8 +862,7 @@ def main_serve(a):
                                    "memory as slots of batched contexts (vof_server_*)",
                        "requests": n, "cells_total": int(sum(cells)),
                        "parallelism": f"requests sharded over {ws} rank(s) by cell-steps"},
-            "gpu_launches": int(sum(kernels_per_step() - 6 + kernels_per_step() * r.n_steps
-                                    for r in reqs)),
+            "gpu_launches": first["gpu_launches"],
             "clocks": first["clocks"], "serve": first,
             "serve_70pct": dict(second, rate_req_per_s=rate70)}
     print(json.dumps(line))
@@ -1014,10 +1031,12 @@ def main():
     FB = ctxB.get_fraction()
     volB = float((V_c * FB).sum())
 
-    # ---- C: the FP64 path on the same segment from the same state
+    # ---- C: the FP64 path on the same segment from the same F (reconstructed
+    # by the FP64 path itself: the mixed path's planes would carry its FP32
+    # plane constants into the first FP64 step)
     fp64 = None
     if not a.no_fp64 and prec == V.PREC_MIXED:
-        c64 = ctx_from(V.PREC_FP64, state=ck)
+        c64 = ctx_from(V.PREC_FP64, F=torch.from_numpy(np.ascontiguousarray(F_ck)).cuda())
         ms64, per64, _, clk64, st64 = timed(c64, seg, False)
         v64 = ws * counts["n_cell"] * K / (ms64 * 1e-3)
         F64 = c64.get_fraction()
@@ -1030,7 +1049,7 @@ def main():
                                                      / (V_c * F64).sum()),
                 "volume_rel_diff_mixed_vs_fp64": float(abs(volB - (V_c * F64).sum()) / vol0),
                 "after_steps": W + K,
-                "from": f"the state at step {s0 - W}, the same for both paths"}
+                "from": f"F at step {s0 - W}, the same for both paths, each reconstructing it"}
         del c64
 
     # ---- D: the same K steps from t = 0 (the smallest band of the run)

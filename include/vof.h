@@ -478,6 +478,7 @@ typedef struct {
   int64_t max_active;        /* most requests advanced in one tick */
   double p50_latency_s, p99_latency_s;  /* submit -> result, done requests */
   double elapsed_s;          /* first submit -> last result */
+  int64_t batch_steps;       /* steps launched: one graph launch per live batch per tick */
 } vof_server_stats;
 enum { VOF_REQ_QUEUED = 0, VOF_REQ_RUNNING = 1, VOF_REQ_DONE = 2 };
 vof_status vof_server_create(const vof_server_options* opt, vof_server** out);

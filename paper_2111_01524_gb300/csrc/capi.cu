@@ -52,7 +52,8 @@ void free_all(vof_ctx* c) {
                    c->lzp, c->lxr, c->lyr, c->lzr, c->lnx, c->lny, c->lnz, c->lnx32, c->lny32,
                    c->lnz32, c->lturn, c->fm_v, c->fm_f, c->fm_meta, c->fm_split, c->dombox,
                    c->fexact, c->Fprev, c->risk, c->repf, c->repc, c->stamp_r, c->Eexc,
-                   c->Sroom, c->cover8, c->rstar, c->lists, c->list_part};
+                   c->Sroom, c->cover8, c->rstar, c->lists, c->list_part, c->fm_cand,
+                   c->fm_cinfo};
   for (void* p : ptrs2)
     if (p) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -402,6 +403,10 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
     CKI(dalloc(c, &c->fm_meta, c->fm_cap));
     CKI(dalloc(c, &c->fm_split, c->fm_cap));
     CKI(dalloc(c, &c->cover8, nf));
+    if (cand_lists_on(o, c->nnb, nc)) {
+      CKI(dalloc(c, &c->fm_cand, kPreCand * c->fm_cap));
+      CKI(dalloc(c, &c->fm_cinfo, c->fm_cap));
+    }
   }
   if (o.reconstruction == VOF_RECON_LSFIR) {
     // PLIC centres by cell, accepted normals by band position, max turn per iteration
@@ -659,7 +664,7 @@ vof_status vof_reconstruct(vof_ctx* c, void* stream) {
 static vof_status advect_launches(vof_ctx* c, cudaStream_t s) {
   // launch counts: the kernels each phase launches (band-list kernels included)
   { PhaseTimer tm(c, VOF_PHASE_FACE_SWEEP, s, 2); CK(launch_face_sweep(c, s)); }
-  { PhaseTimer tm(c, VOF_PHASE_POLYHEDRA, s); CK(launch_prebuild(c, s)); }
+  { PhaseTimer tm(c, VOF_PHASE_POLYHEDRA, s, prebuild_lists(c) ? 2 : 1); CK(launch_prebuild(c, s)); }
   { PhaseTimer tm(c, VOF_PHASE_FLUX, s); CK(launch_flux(c, s)); }
   { PhaseTimer tm(c, VOF_PHASE_UPDATE, s, 2); CK(launch_update(c, s)); }
   if (c->opt.precision == VOF_PREC_MIXED) {

@@ -1192,33 +1192,25 @@ __device__ GVOF_CELL_ATTR G truncate_in_cell(const DevMesh& M, const GeoView<G>&
   return truncate_nonconvex<G, KIND>(M, Gv, k, c0, nfk, tag0, fr, Vl, P, lane, err);
 }
 
-// one chunk of up to GW candidate cells of face j (pass 0: the owner's node
-// neighbours and the owner; pass 1: the neighbour's and the neighbour, minus
-// those already seen), filtered by the local bounding box of the
-// polyhedron and (FP32, convex cells other than axis-aligned boxes, whose box
-// test is already this one) by the cell's face planes: a cell with a plane
-// that has every vertex of P strictly outside cannot meet P; returns the
-// lane's cell (-1: none) and its tag
-template <typename G, int KIND, int GW>
-__device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
-                                         const FaceFrame<G>& fr, const Poly<G, GW>& P, int own, int64_t a0,
-                                         int na, int pass, int c0, int64_t b0, int nb, int idx,
-                                         int8_t& tk) {
+// the filters of a candidate cell k: the local bounding box of the
+// polyhedron, then (FP32, convex cells other than axis-aligned boxes, whose
+// box test is already this one) the cell's face planes: a cell with a plane
+// that has every base vertex (bx, by, bz) strictly outside cannot meet P.
+// The flux kernel and the prebuild thread call this one function, so both
+// take the same decisions.
+template <typename G, int KIND>
+__device__ __forceinline__ bool cell_may_meet(const DevMesh& M, const GeoView<G>& Gv,
+                                              const FaceFrame<G>& fr, const G* bx, const G* by,
+                                              const G* bz, int k) {
   const int64_t nc = M.nc;
-  int k = -1;
-  if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
-  if (k >= 0 && pass == 1 && (k == own || sorted_contains(M.nb + a0, na, k))) k = -1;
-  tk = 0;
-  if (k >= 0) {
-    const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
-    const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
-    const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
-    if (!(fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy && fr.hi[2] > lz &&
-          fr.lo[2] < hz))
-      k = -1;
-  }
+  const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
+  const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
+  const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
+  if (!(fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy && fr.hi[2] > lz &&
+        fr.lo[2] < hz))
+    return false;
   if constexpr (sizeof(G) == 4) {
-    if (k >= 0 && M.convex[k] == 1) {
+    if (M.convex[k] == 1) {
       const int64_t q0 = M.cf_ptr[k];
       const int nfk = (int)(M.cf_ptr[k + 1] - q0);
       const int nvb = base_verts<KIND>(fr.I);
@@ -1227,14 +1219,38 @@ __device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv,
         const float4 q = M.cpl32[q0 + g];
         const G b = (q.x * rx + q.y * ry + q.z * rz - q.w) * fr.sc;
         bool out = true;
-        for (int v = 0; v < nvb && out; ++v)
-          out = q.x * P.bx[v] + q.y * P.by[v] + q.z * P.bz[v] + b < G(-2e-7);
-        if (out) { k = -1; break; }
+        for (int v = 0; v < nvb && out; ++v) out = q.x * bx[v] + q.y * by[v] + q.z * bz[v] + b < G(-2e-7);
+        if (out) return false;
       }
     }
   }
+  return true;
+}
+
+// candidate idx of one pass over face j's candidate cells (pass 0: the
+// owner's node neighbours and the owner; pass 1: the neighbour's and the
+// neighbour, minus those already seen), filtered by cell_may_meet with the
+// base vertices (bx, by, bz); returns the cell (-1: none) and its tag
+template <typename G, int KIND>
+__device__ __forceinline__ int candidate_at(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
+                                            const FaceFrame<G>& fr, const G* bx, const G* by,
+                                            const G* bz, int own, int64_t a0, int na, int pass, int c0,
+                                            int64_t b0, int nb, int idx, int8_t& tk) {
+  int k = -1;
+  if (idx < nb) k = (idx == nb - 1) ? c0 : M.nb[b0 + idx];
+  if (k >= 0 && pass == 1 && (k == own || sorted_contains(M.nb + a0, na, k))) k = -1;
+  tk = 0;
+  if (k >= 0 && !cell_may_meet<G, KIND>(M, Gv, fr, bx, by, bz, k)) k = -1;
   if (k >= 0) tk = S.tc[k];
   return k;
+}
+
+template <typename G, int KIND, int GW>
+__device__ __forceinline__ int candidate(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,
+                                         const FaceFrame<G>& fr, const Poly<G, GW>& P, int own, int64_t a0,
+                                         int na, int pass, int c0, int64_t b0, int nb, int idx,
+                                         int8_t& tk) {
+  return candidate_at<G, KIND>(M, Gv, S, fr, P.bx, P.by, P.bz, own, a0, na, pass, c0, b0, nb, idx, tk);
 }
 
 // V_F of face j in face-local units (Sec. 2.2): the candidate cells (owner,
@@ -1256,15 +1272,30 @@ template <typename G, int KIND, int GW>
 __device__ GVOF_OUTER_ATTR G sweep_candidates(const DevMesh& M, const GeoView<G>& Gv, const DevState& S, int j,
                               const FaceFrame<G>& fr, double Vd, G Vl, Poly<G, GW>& P, int lane,
                               unsigned& err, int* whole, bool* complement, unsigned cover,
-                              unsigned long long& n_trunc) {
+                              unsigned long long& n_trunc, unsigned w) {
   const int own = M.own[j], nbr = M.nbr[j];
   const int64_t a0 = M.nb_ptr[own];
   const int na = (int)(M.nb_ptr[own + 1] - a0);
   constexpr int cap = cand_cap<G>();
   int n = cap + 1;  // FP64: the fluid form, no list (the cells are scanned once)
   bool neg = false, pos = false;
-  if (sizeof(G) == 4) n = 0;
-  for (int pass = 0; sizeof(G) == 4 && pass < 2; ++pass) {
+  bool listed = false;
+  if constexpr (sizeof(G) == 4) {
+    n = 0;
+    // the list built with the polyhedron, when it fits
+    if (S.fm_cand != nullptr && (int64_t)w < S.fm_cap) {
+      const unsigned info = S.fm_cinfo[w];
+      const int cnt = (int)(info & 63u);
+      if (cnt <= kPreCand) {
+        listed = true;
+        n = cnt;
+        neg = ((info >> 6) & 1u) != 0u;
+        pos = ((info >> 7) & 1u) != 0u;
+        for (int i = lane; i < cnt; i += GW) P.cand[i] = S.fm_cand[(size_t)w * kPreCand + i];
+      }
+    }
+  }
+  for (int pass = 0; sizeof(G) == 4 && !listed && pass < 2; ++pass) {
     const int c0 = pass == 0 ? own : nbr;
     if (c0 < 0) break;
     const int64_t b0 = M.nb_ptr[c0];
@@ -1348,6 +1379,7 @@ __global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevS
     S.cover8[w] = (uint8_t)cov;
     if (cov & kEscaped) atomicAdd(S.cnt + kNEscape, 1ull);
     if (!ok) continue;
+
     S.fm_split[w] = fr.split;
     G* f = ff + (size_t)w * 7;
     f[0] = fr.L;
@@ -1357,6 +1389,66 @@ __global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevS
     for (int q = 0; q < base_verts<KIND>(fr.I); ++q) {
       v[3 * q] = vx[q]; v[3 * q + 1] = vy[q]; v[3 * q + 2] = vz[q];
     }
+  }
+}
+
+// the candidate lists of the prebuilt polyhedra (FP32 path), one warp per
+// face: the search the flux kernel's sweep_candidates would make, in the
+// same order with the census of the tags, done here by warps that hold
+// little state, so that many of them hide the gathers' latency. A face
+// whose list exceeds kPreCand is left to the flux kernel's own search.
+constexpr int kListWarps = 8;
+template <typename G, int KIND>
+__global__ void __launch_bounds__(kListWarps * 32) k_candlist(DevMesh M, GeoView<G> Gv, DevState S) {
+  __shared__ G bv[kListWarps][3][kFmSlots];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned n_af = (unsigned)S.cnt[kNAfaces];
+  const unsigned nw = (unsigned)min((int64_t)n_af, S.fm_cap);
+  G* bx = bv[wib][0];
+  G* by = bv[wib][1];
+  G* bz = bv[wib][2];
+  for (unsigned w = blockIdx.x * kListWarps + wib; w < nw; w += gridDim.x * kListWarps) {
+    const uint32_t meta = S.fm_meta[w];
+    if (!((meta >> 24) & 1u)) continue;  // no polyhedron: the flux kernel skips the face
+    const int j = S.afaces[w];
+    FaceFrame<G> fr;
+    fr.I = (int)(meta & 255u);
+    const G* f = (const G*)S.fm_f + (size_t)w * 7;
+    fr.cx = Gv.fcx[j]; fr.cy = Gv.fcy[j]; fr.cz = Gv.fcz[j];
+    fr.L = f[0];
+    fr.sc = G(1) / fr.L;
+    fr.lo[0] = f[1]; fr.lo[1] = f[2]; fr.lo[2] = f[3];
+    fr.hi[0] = f[4]; fr.hi[1] = f[5]; fr.hi[2] = f[6];
+    if (lane < base_verts<KIND>(fr.I)) {
+      const G* v = (const G*)S.fm_v + ((size_t)w * kFmSlots + lane) * 3;
+      bx[lane] = v[0]; by[lane] = v[1]; bz[lane] = v[2];
+    }
+    __syncwarp();
+    const int own = M.own[j], nbr = M.nbr[j];
+    const int64_t a0 = M.nb_ptr[own];
+    const int na = (int)(M.nb_ptr[own + 1] - a0);
+    int n = 0;
+    bool neg = false, pos = false;
+    int32_t* out = S.fm_cand + (size_t)w * kPreCand;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int c0 = pass == 0 ? own : nbr;
+      if (c0 < 0) break;
+      const int64_t b0 = M.nb_ptr[c0];
+      const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
+      for (int base = 0; base < nb; base += 32) {
+        int8_t tk;
+        const int k = candidate_at<G, KIND>(M, Gv, S, fr, bx, by, bz, own, a0, na, pass, c0, b0, nb,
+                                            base + lane, tk);
+        const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
+        if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
+        if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
+        const int at = n + __popc(bal & ((1u << lane) - 1u));
+        if (k >= 0 && at < kPreCand) out[at] = k;
+        n += __popc(bal);
+      }
+    }
+    if (lane == 0) S.fm_cinfo[w] = (uint8_t)((n <= kPreCand ? n : 63) | (neg ? 64 : 0) | (pos ? 128 : 0));
+    __syncwarp();
   }
 }
 
@@ -1443,7 +1535,7 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
     int wh = 0;
     bool comp = false;
     const G v = sweep_candidates<G, KIND>(M, Gv, S, j, fr, Vd, Vl, P, lane, err, &wh, &comp,
-                                          (unsigned)S.cover8[w], n_trunc);
+                                          (unsigned)S.cover8[w], n_trunc, w);
     double VFj;
     if (wh == 1) VFj = Vd;  // P inside the fluid of one cell: exactly V_d
     else if (wh == 2) VFj = 0.0;  // P inside the empty part of one cell
@@ -1605,9 +1697,25 @@ void polyhedra_launch_kind(const vof_ctx* c, const int32_t* faces, int n, double
 }
 }  // namespace
 
+bool prebuild_lists(const vof_ctx* c) { return c->fm_cand != nullptr && c->fm_use > 0; }
+
 cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s) {
-  if (c->opt.precision == VOF_PREC_MIXED) prebuild_launch_kind<float>(c, s);
-  else prebuild_launch_kind<double>(c, s);
+  if (c->opt.precision != VOF_PREC_MIXED) {
+    prebuild_launch_kind<double>(c, s);
+    return cudaGetLastError();
+  }
+  prebuild_launch_kind<float>(c, s);
+  if (prebuild_lists(c)) {
+    const DevMesh m = mesh_view(c);
+    const GeoView<float> g = geo_view<float>(c);
+    const DevState st = state_view(c);
+    const int grid = kSMs * 8;
+    switch (c->opt.flux_polyhedron) {
+      case VOF_FLUX_EMFPA: k_candlist<float, VOF_FLUX_EMFPA><<<grid, kListWarps * 32, 0, s>>>(m, g, st); break;
+      case VOF_FLUX_NMFPA: k_candlist<float, VOF_FLUX_NMFPA><<<grid, kListWarps * 32, 0, s>>>(m, g, st); break;
+      default: k_candlist<float, VOF_FLUX_FMFPA><<<grid, kListWarps * 32, 0, s>>>(m, g, st); break;
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -77,6 +77,8 @@ int64_t context_bytes(const CtxSizes& z, const vof_options& o) {
   const int64_t gs = o.precision == VOF_PREC_MIXED ? 4 : 8;
   b += gs * (3 * kFmSlots + 7) * fm_cap;                               // prebuilt polyhedra
   b += 2 * bytes_of<uint32_t>(fm_cap) + bytes_of<uint8_t>(nf);         // meta, split, coverage
+  if (cand_lists_on(o, z.nnb, nc))
+    b += bytes_of<int32_t>(kPreCand * fm_cap) + bytes_of<uint8_t>(fm_cap);  // candidate lists
   if (o.reconstruction == VOF_RECON_LSFIR) {
     b += o.precision == VOF_PREC_MIXED ? 6 * bytes_of<float>(nc) : 6 * bytes_of<double>(nc);
     b += bytes_of<unsigned long long>(kMaxLsfirIter + 1);
@@ -153,7 +155,7 @@ struct vof_server {
   std::vector<Request> reqs;
   std::deque<int64_t> queue;
   std::vector<Batch> batches;
-  int64_t bytes_live = 0, peak_bytes = 0, max_active = 0, n_batches = 0;
+  int64_t bytes_live = 0, peak_bytes = 0, max_active = 0, n_batches = 0, batch_steps = 0;
   int64_t cell_steps = 0;
   double t0 = -1.0;
 };
@@ -373,6 +375,7 @@ static vof_status advance(vof_server* s, int32_t* n_active) {
     if (!any) continue;
     vof_status st = vof_graph_launch(b.ctx, vels.data(), t.data(), dt.data(), b.stream);
     if (st != VOF_OK) return st;
+    ++s->batch_steps;
     for (int i = 0; i < n; ++i) {
       if (!moving[i]) continue;
       Request& r = s->reqs[b.reqs[i]];
@@ -459,6 +462,7 @@ vof_status vof_server_get_stats(vof_server* s, vof_server_stats* out) {
   out->peak_device_bytes = s->peak_bytes;
   out->budget_bytes = s->budget;
   out->n_batches = s->n_batches;
+  out->batch_steps = s->batch_steps;
   out->max_active = s->max_active;
   out->elapsed_s = s->t0 >= 0 ? last - s->t0 : 0.0;
   if (!lat.empty()) {

@@ -21,6 +21,15 @@ constexpr int kMaxLsfirIter = 16;  // LSFIR outer iterations at most
 // the faces a context keeps room for (later active faces are built in the
 // flux kernel itself, with the same arithmetic)
 constexpr int kFmSlots = VOF_MAX_POLY_VERTS;
+// candidate cells listed per prebuilt polyhedron (FP32 path); a face with
+// more is left to the flux kernel's own search
+constexpr int kPreCand = 32;
+// the lists are built where cells have few node neighbours (hexahedral
+// grids: 26); on tetrahedral grids (50 and more) most faces' candidate sets
+// exceed the list and the flux kernel's truncations dominate anyway
+inline bool cand_lists_on(const vof_options& o, int64_t nnb, int64_t nc) {
+  return o.precision == VOF_PREC_MIXED && nnb <= 30 * nc;
+}
 constexpr int64_t kFmCap = int64_t(4) << 20;
 static_assert(3 * kMaxEmfpaVerts + 1 <= VOF_MAX_POLY_VERTS && 2 * kMaxFaceVerts + 1 <= VOF_MAX_POLY_VERTS,
               "polyhedron export stride");
@@ -124,6 +133,10 @@ struct DevState {
   void* fm_f;
   uint32_t *fm_meta, *fm_split;
   int64_t fm_cap;
+  // FP32 path: the candidate cells of each prebuilt polyhedron [w kPreCand]
+  // and their count | any empty << 6 | any full << 7 (count 63: not listed)
+  int32_t* fm_cand;
+  uint8_t* fm_cinfo;
   // domain bounding box per grid [6 * n_grids] (lo xyz, hi xyz): a flux
   // polyhedron vertex outside it is outside the domain (no fluid, R11)
   const double* dombox;
@@ -310,6 +323,8 @@ struct vof_ctx {
   void *fm_v, *fm_f;
   uint32_t *fm_meta, *fm_split;
   int64_t fm_cap;
+  int32_t* fm_cand;
+  uint8_t* fm_cinfo;
   double* dombox;
   uint8_t* fexact;
   double* Fprev;
@@ -415,6 +430,7 @@ inline DevState state_view(const vof_ctx* c) {
   s.lnx32 = c->lnx32; s.lny32 = c->lny32; s.lnz32 = c->lnz32;
   s.lturn = c->lturn;
   s.fm_v = c->fm_v; s.fm_f = c->fm_f; s.fm_meta = c->fm_meta; s.fm_split = c->fm_split;
+  s.fm_cand = c->fm_cand; s.fm_cinfo = c->fm_cinfo;
   s.fm_cap = c->fm_use;
   s.dombox = c->dombox;
   s.fexact = c->fexact; s.Fprev = c->Fprev;
@@ -497,7 +513,8 @@ cudaError_t launch_reconstruct(const vof_ctx* c, cudaStream_t s);
 int reconstruct_launch_count(const vof_ctx* c);
 // flux (k_flux.cu)
 // the flux polyhedra of the active faces (up to fm_cap), then the truncations
-cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s);
+cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s);  // + candidate lists (FP32)
+bool prebuild_lists(const vof_ctx* c);  // launch_prebuild also builds the candidate lists
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int64_t cap_per_face,
                               int32_t* out, int32_t* counts, cudaStream_t s);

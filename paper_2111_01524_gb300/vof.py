@@ -89,7 +89,7 @@ class ServerStats(C.Structure):
                 ("peak_device_bytes", C.c_int64), ("budget_bytes", C.c_int64),
                 ("n_batches", C.c_int64), ("max_active", C.c_int64),
                 ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
-                ("elapsed_s", C.c_double)]
+                ("elapsed_s", C.c_double), ("batch_steps", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
