@@ -60,13 +60,18 @@ FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0
 # dram__bytes_write.sum per active face (the face and node data, the prebuilt
 # polyhedron, the candidate cells' tags, boxes and planes), issue-slot and FMA-pipe
 # use; valid only for the source it was taken on (traffic is null for any other)
-FLUX_NCU = {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66cc0f6bb326d8456",
-            "fmfpa": {"dram_bytes_per_active_face": 588.0, "issue_active": 0.549,
-                      "fma_pipe_active": 0.140, "capture": "profiles/k_flux_deformation128_mixed.md"},
-            "emfpa": {"dram_bytes_per_active_face": 590.0, "issue_active": 0.573,
+# ncu figures of k_flux per flux polyhedron (one launch, --set full), valid
+# for the k_flux.cu source whose sha256 they carry
+FLUX_NCU = {"fmfpa": {"source_sha256": "6fde283a283d74a872b7c371d52877febd9b84803e9e8050b327f92a93926910",
+                      "dram_bytes_per_active_face": 591.0, "issue_active": 0.684,
+                      "fma_pipe_active": 0.181,
+                      "capture": "profiles/k_flux_deformation128_midrun_mixed.md"},
+            "emfpa": {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66cc0f6bb326d8456",
+                      "dram_bytes_per_active_face": 590.0, "issue_active": 0.573,
                       "fma_pipe_active": 0.149,
                       "capture": "profiles/k_flux_deformation128_mixed_emfpa.md"},
-            "nmfpa": {"dram_bytes_per_active_face": 566.0, "issue_active": 0.528,
+            "nmfpa": {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66cc0f6bb326d8456",
+                      "dram_bytes_per_active_face": 566.0, "issue_active": 0.528,
                       "fma_pipe_active": 0.136,
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 # kernels one step launches: reconstruction (cell tags 1, node tags 3,
@@ -293,9 +298,9 @@ def roofline(ctx_counts, phase, grid_counts, peaks, peak_kind, clocks, precision
     if name == "flux" and precision == "mixed":
         import hashlib
         src = os.path.join(ROOT, "paper_2111_01524_gb300", "csrc", "k_flux.cu")
-        rec = None  # the capture's figures, if it was taken on this source
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() == FLUX_NCU["source_sha256"]:
-            rec = FLUX_NCU.get(flux)
+        rec = FLUX_NCU.get(flux)  # the capture's figures, if it was taken on this source
+        if rec is not None and hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+            rec = None
         if rec is not None:
             traffic = rec["dram_bytes_per_active_face"] * ctx_counts["n_active_faces"]
             ncu = {k: rec[k] for k in ("issue_active", "fma_pipe_active", "capture")}

@@ -43,15 +43,18 @@ def test_flux_roofline_traffic_only_for_the_captured_source(bench, monkeypatch):
     src = os.path.join(ROOT, "paper_2111_01524_gb300", "csrc", "k_flux.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     phase = {"name": "flux", "ms": 28.47, "calls": 20}
-    ncu = dict(bench.FLUX_NCU)
-    monkeypatch.setattr(bench, "FLUX_NCU", dict(ncu, source_sha256=sha))
+    rec = dict(bench.FLUX_NCU["fmfpa"])
+    monkeypatch.setattr(bench, "FLUX_NCU", {"fmfpa": dict(rec, source_sha256=sha)})
     r = bench.roofline(COUNTS, phase, GRID, {}, "fallback", CLOCKS, "mixed", "fmfpa")
-    assert r["traffic"] == pytest.approx(ncu["fmfpa"]["dram_bytes_per_active_face"] * 229090)
+    assert r["traffic"] == pytest.approx(rec["dram_bytes_per_active_face"] * 229090)
     assert r["ncu"]["capture"].startswith("profiles/")
     assert os.path.exists(os.path.join(ROOT, r["ncu"]["capture"]))
-    monkeypatch.setattr(bench, "FLUX_NCU", dict(ncu, source_sha256="0" * 64))
+    monkeypatch.setattr(bench, "FLUX_NCU", {"fmfpa": dict(rec, source_sha256="0" * 64)})
     r = bench.roofline(COUNTS, phase, GRID, {}, "fallback", CLOCKS, "mixed", "fmfpa")
     assert r["traffic"] is None and r["ncu"] is None
+    # every record names a committed capture
+    for kind, rec in bench.FLUX_NCU.items():
+        assert os.path.exists(os.path.join(ROOT, rec["capture"])), kind
 
 
 def test_sweep_roofline_is_hbm_bytes_over_one_launch(bench):
