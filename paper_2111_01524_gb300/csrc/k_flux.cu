@@ -1392,22 +1392,32 @@ __global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevS
   }
 }
 
-// the candidate lists of the prebuilt polyhedra (FP32 path), one warp per
-// face: the search the flux kernel's sweep_candidates would make, in the
-// same order with the census of the tags, done here by warps that hold
-// little state, so that many of them hide the gathers' latency. A face
-// whose list exceeds kPreCand is left to the flux kernel's own search.
+// the candidate lists of the prebuilt polyhedra (FP32 path), 16 lanes per
+// face: the search the flux kernel's sweep_candidates would make, with the
+// same filter (candidate_at), in the same order, with the census of the
+// tags. Each lane takes two cells of a pass at once so that their gathers
+// are in flight together, and the groups hold little state, so that many of
+// them hide the gathers' latency. The neighbour's pass drops the cells the
+// owner's pass accepted (a cell of both rings passes the same filter in
+// both, so this is the flux kernel's de-duplication). A face whose list
+// exceeds kPreCand is left to the flux kernel's own search.
 constexpr int kListWarps = 8;
+constexpr int kListGroups = 2 * kListWarps;
 template <typename G, int KIND>
 __global__ void __launch_bounds__(kListWarps * 32) k_candlist(DevMesh M, GeoView<G> Gv, DevState S) {
-  __shared__ G bv[kListWarps][3][kFmSlots];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  __shared__ G bv[kListGroups][3][kFmSlots];
+  __shared__ int32_t seen[kListGroups][kPreCand];
+  const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+  const unsigned sh = threadIdx.x & 16u;
+  const unsigned gm = 0xffffu << sh;
+  const unsigned lt = (1u << lane) - 1u;
   const unsigned n_af = (unsigned)S.cnt[kNAfaces];
   const unsigned nw = (unsigned)min((int64_t)n_af, S.fm_cap);
-  G* bx = bv[wib][0];
-  G* by = bv[wib][1];
-  G* bz = bv[wib][2];
-  for (unsigned w = blockIdx.x * kListWarps + wib; w < nw; w += gridDim.x * kListWarps) {
+  G* bx = bv[grp][0];
+  G* by = bv[grp][1];
+  G* bz = bv[grp][2];
+  int32_t* sn = seen[grp];
+  for (unsigned w = blockIdx.x * kListGroups + grp; w < nw; w += gridDim.x * kListGroups) {
     const uint32_t meta = S.fm_meta[w];
     if (!((meta >> 24) & 1u)) continue;  // no polyhedron: the flux kernel skips the face
     const int j = S.afaces[w];
@@ -1419,15 +1429,13 @@ __global__ void __launch_bounds__(kListWarps * 32) k_candlist(DevMesh M, GeoView
     fr.sc = G(1) / fr.L;
     fr.lo[0] = f[1]; fr.lo[1] = f[2]; fr.lo[2] = f[3];
     fr.hi[0] = f[4]; fr.hi[1] = f[5]; fr.hi[2] = f[6];
-    if (lane < base_verts<KIND>(fr.I)) {
-      const G* v = (const G*)S.fm_v + ((size_t)w * kFmSlots + lane) * 3;
-      bx[lane] = v[0]; by[lane] = v[1]; bz[lane] = v[2];
+    for (int v = lane; v < base_verts<KIND>(fr.I); v += 16) {
+      const G* p = (const G*)S.fm_v + ((size_t)w * kFmSlots + v) * 3;
+      bx[v] = p[0]; by[v] = p[1]; bz[v] = p[2];
     }
-    __syncwarp();
+    __syncwarp(gm);
     const int own = M.own[j], nbr = M.nbr[j];
-    const int64_t a0 = M.nb_ptr[own];
-    const int na = (int)(M.nb_ptr[own + 1] - a0);
-    int n = 0;
+    int n = 0, n0 = 0;
     bool neg = false, pos = false;
     int32_t* out = S.fm_cand + (size_t)w * kPreCand;
     for (int pass = 0; pass < 2; ++pass) {
@@ -1435,20 +1443,42 @@ __global__ void __launch_bounds__(kListWarps * 32) k_candlist(DevMesh M, GeoView
       if (c0 < 0) break;
       const int64_t b0 = M.nb_ptr[c0];
       const int nb = (int)(M.nb_ptr[c0 + 1] - b0) + 1;
+      const int m0 = n0 < kPreCand ? n0 : kPreCand;
       for (int base = 0; base < nb; base += 32) {
-        int8_t tk;
-        const int k = candidate_at<G, KIND>(M, Gv, S, fr, bx, by, bz, own, a0, na, pass, c0, b0, nb,
-                                            base + lane, tk);
-        const unsigned bal = __ballot_sync(GVOF_FULL, k >= 0);
-        if (__any_sync(GVOF_FULL, k >= 0 && tk == -1)) neg = true;
-        if (__any_sync(GVOF_FULL, k >= 0 && tk == 1)) pos = true;
-        const int at = n + __popc(bal & ((1u << lane) - 1u));
-        if (k >= 0 && at < kPreCand) out[at] = k;
-        n += __popc(bal);
+        int8_t t0, t1;
+        // pass 0 semantics of candidate_at: the filter alone (no de-duplication)
+        int k0 = candidate_at<G, KIND>(M, Gv, S, fr, bx, by, bz, own, 0, 0, 0, c0, b0, nb, base + lane, t0);
+        int k1 = candidate_at<G, KIND>(M, Gv, S, fr, bx, by, bz, own, 0, 0, 0, c0, b0, nb, base + 16 + lane,
+                                       t1);
+        if (pass == 1) {
+          for (int i = 0; i < m0 && (k0 >= 0 || k1 >= 0); ++i) {
+            const int q = sn[i];
+            if (q == k0) k0 = -1;
+            if (q == k1) k1 = -1;
+          }
+        }
+        const unsigned b0m = (__ballot_sync(gm, k0 >= 0) >> sh) & 0xffffu;
+        const unsigned b1m = (__ballot_sync(gm, k1 >= 0) >> sh) & 0xffffu;
+        if (__any_sync(gm, (k0 >= 0 && t0 == -1) || (k1 >= 0 && t1 == -1))) neg = true;
+        if (__any_sync(gm, (k0 >= 0 && t0 == 1) || (k1 >= 0 && t1 == 1))) pos = true;
+        const int at0 = n + __popc(b0m & lt);
+        if (k0 >= 0 && at0 < kPreCand) {
+          out[at0] = k0;
+          if (pass == 0) sn[at0] = k0;
+        }
+        n += __popc(b0m);
+        const int at1 = n + __popc(b1m & lt);
+        if (k1 >= 0 && at1 < kPreCand) {
+          out[at1] = k1;
+          if (pass == 0) sn[at1] = k1;
+        }
+        n += __popc(b1m);
       }
+      if (pass == 0) n0 = n;
+      __syncwarp(gm);
     }
     if (lane == 0) S.fm_cinfo[w] = (uint8_t)((n <= kPreCand ? n : 63) | (neg ? 64 : 0) | (pos ? 128 : 0));
-    __syncwarp();
+    __syncwarp(gm);
   }
 }
 
@@ -1709,7 +1739,7 @@ cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s) {
     const DevMesh m = mesh_view(c);
     const GeoView<float> g = geo_view<float>(c);
     const DevState st = state_view(c);
-    const int grid = kSMs * 8;
+    const int grid = kSMs * 8;  // 16 face groups per block
     switch (c->opt.flux_polyhedron) {
       case VOF_FLUX_EMFPA: k_candlist<float, VOF_FLUX_EMFPA><<<grid, kListWarps * 32, 0, s>>>(m, g, st); break;
       case VOF_FLUX_NMFPA: k_candlist<float, VOF_FLUX_NMFPA><<<grid, kListWarps * 32, 0, s>>>(m, g, st); break;
