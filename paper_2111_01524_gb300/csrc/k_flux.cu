@@ -867,12 +867,13 @@ __device__ __noinline__ bool point_in_cell(const DevMesh& M, const GeoView<G>& G
 template <typename G>
 __device__ __forceinline__ bool in_cell(const DevMesh& M, const GeoView<G>& Gv, const FaceFrame<G>& fr,
                                         int k, G px, G py, G pz, G tol) {
-  const int64_t nc = M.nc;
-  const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
+  typename Prec<G>::A b[6];
+  cell_box<G>(Gv.bb, M.nc, k, b);
+  const G lx = rel(b[0], fr.cx) * fr.sc, hx = rel(b[3], fr.cx) * fr.sc;
   if (px < lx - tol || px > hx + tol) return false;
-  const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
+  const G ly = rel(b[1], fr.cy) * fr.sc, hy = rel(b[4], fr.cy) * fr.sc;
   if (py < ly - tol || py > hy + tol) return false;
-  const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
+  const G lz = rel(b[2], fr.cz) * fr.sc, hz = rel(b[5], fr.cz) * fr.sc;
   if (pz < lz - tol || pz > hz + tol) return false;
   return M.convex[k] == 2 || point_in_cell(M, Gv, fr, k, px, py, pz, tol);
 }
@@ -1202,10 +1203,11 @@ template <typename G, int KIND>
 __device__ __forceinline__ bool cell_may_meet(const DevMesh& M, const GeoView<G>& Gv,
                                               const FaceFrame<G>& fr, const G* bx, const G* by,
                                               const G* bz, int k) {
-  const int64_t nc = M.nc;
-  const G lx = rel(Gv.bb[k], fr.cx) * fr.sc, hx = rel(Gv.bb[3 * nc + k], fr.cx) * fr.sc;
-  const G ly = rel(Gv.bb[nc + k], fr.cy) * fr.sc, hy = rel(Gv.bb[4 * nc + k], fr.cy) * fr.sc;
-  const G lz = rel(Gv.bb[2 * nc + k], fr.cz) * fr.sc, hz = rel(Gv.bb[5 * nc + k], fr.cz) * fr.sc;
+  typename Prec<G>::A b[6];
+  cell_box<G>(Gv.bb, M.nc, k, b);
+  const G lx = rel(b[0], fr.cx) * fr.sc, hx = rel(b[3], fr.cx) * fr.sc;
+  const G ly = rel(b[1], fr.cy) * fr.sc, hy = rel(b[4], fr.cy) * fr.sc;
+  const G lz = rel(b[2], fr.cz) * fr.sc, hz = rel(b[5], fr.cz) * fr.sc;
   if (!(fr.hi[0] > lx && fr.lo[0] < hx && fr.hi[1] > ly && fr.lo[1] < hy && fr.hi[2] > lz &&
         fr.lo[2] < hz))
     return false;

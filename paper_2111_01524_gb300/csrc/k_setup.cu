@@ -238,7 +238,7 @@ __global__ void k_mixed_copies(DevMesh M, float2* vx2, float2* vy2, float2* vz2,
   for (int64_t c = t0; c < M.nc; c += stride) {
     ccx2[c] = split(M.ccx[c]); ccy2[c] = split(M.ccy[c]); ccz2[c] = split(M.ccz[c]);
     cvol32[c] = (float)M.cvol[c];
-    for (int d = 0; d < 6; ++d) bb2[d * M.nc + c] = split(M.bb[d * M.nc + c]);
+    for (int d = 0; d < 6; ++d) bb2[6 * c + d] = split(M.bb[d * M.nc + c]);  // one record per cell
   }
 }
 

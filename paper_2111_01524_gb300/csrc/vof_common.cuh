@@ -271,6 +271,23 @@ struct Prec<float> {
 __device__ __forceinline__ double rel(double a, double b) { return a - b; }
 __device__ __forceinline__ float rel(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
+// the bounding box of cell k (lo x y z, hi x y z) from GeoView::bb: the FP64
+// path keeps six arrays of n_cell; the FP32 path one 48-byte record of (hi,
+// lo) pairs per cell, read as three 16-byte loads
+template <typename G>
+__device__ __forceinline__ void cell_box(const typename Prec<G>::A* bb, int64_t nc, int64_t k,
+                                         typename Prec<G>::A* b) {
+  if constexpr (sizeof(G) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(bb) + 3 * k;
+    const float4 u = q[0], v = q[1], w = q[2];
+    b[0] = make_float2(u.x, u.y); b[1] = make_float2(u.z, u.w);
+    b[2] = make_float2(v.x, v.y); b[3] = make_float2(v.z, v.w);
+    b[4] = make_float2(w.x, w.y); b[5] = make_float2(w.z, w.w);
+  } else {
+    for (int d = 0; d < 6; ++d) b[d] = bb[d * nc + k];
+  }
+}
+
 // mesh and plane arrays as seen by the band kernels of precision G
 template <typename G>
 struct GeoView {
@@ -280,7 +297,7 @@ struct GeoView {
   const G *fnx, *fny, *fnz;   // face unit normals (out of the owner)
   const G* fa;                // face areas
   const A *ccx, *ccy, *ccz;   // cell centroids
-  const A* bb;                // cell bounding boxes [6 * nc]
+  const A* bb;                // cell bounding boxes [6 * nc] (read with cell_box)
   const G* cvol;              // cell volumes
   const G *pnx, *pny, *pnz, *pC;  // PLIC planes (read)
 };
@@ -309,7 +326,8 @@ struct vof_ctx {
   double *ccx, *ccy, *ccz, *cvol;
   double* bb;
   uint8_t* convex;
-  float2 *vx2, *vy2, *vz2, *fcx2, *fcy2, *fcz2, *ccx2, *ccy2, *ccz2, *bb2;
+  float2 *vx2, *vy2, *vz2, *fcx2, *fcy2, *fcz2, *ccx2, *ccy2, *ccz2;
+  float2* bb2;  // [6 n_cell]: lo xyz, hi xyz of cell c at 6 c .. 6 c + 5
   float *fnx32, *fny32, *fnz32, *fa32, *cvol32;
   float4* cpl32;
   float* rstar;
