@@ -1752,7 +1752,7 @@ cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s) {
 }
 
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s) {
-  const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * 8;
+  const int grid = c->flux_blocks > 0 ? c->flux_blocks : kSMs * GVOF_FLUX_MINB;
   const cudaError_t e = cudaMemsetAsync(c->cnt + kFluxNext, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (c->opt.precision == VOF_PREC_MIXED) flux_launch_kind<float>(c, grid, s);
