@@ -482,7 +482,13 @@ typedef struct {
 } vof_server_stats;
 enum { VOF_REQ_QUEUED = 0, VOF_REQ_RUNNING = 1, VOF_REQ_DONE = 2 };
 vof_status vof_server_create(const vof_server_options* opt, vof_server** out);
-/* copies the request (HOST mesh arrays and F0 [n_cell]); *id identifies it */
+/* copies the request (HOST mesh arrays and F0 [n_cell]); *id identifies it.
+ * The mesh's structure is checked here (VOF_EINVAL); its derived
+ * connectivity, and with it the request's exact device footprint, is built
+ * once when the request reaches the front of the queue and handed on to
+ * its batched context. A mesh the library cannot take (a cell too large)
+ * is refused there: vof_server_step returns VOF_EINVAL once, and
+ * vof_server_poll of the request returns VOF_EINVAL with the reason. */
 vof_status vof_server_submit(vof_server* s, const vof_mesh_desc* mesh, const double* F0,
                              const vof_velocity* vel, int32_t n_steps, double cfl, double t_end,
                              int64_t* id);

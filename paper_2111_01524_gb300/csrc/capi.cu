@@ -222,7 +222,7 @@ int64_t vof_device_bytes(const vof_ctx* c) { return c ? c->bytes : 0; }
 static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, cudaStream_t s,
                             vof_ctx** out, const std::vector<int64_t>& cell_off,
                             const std::vector<int64_t>& face_off,
-                            const std::vector<int64_t>& vert_off) {
+                            const std::vector<int64_t>& vert_off, const HostConn* pre = nullptr) {
   const int64_t nv = mesh->n_vert, nf = mesh->n_face, nc = mesh->n_cell;
   if (nv <= 0 || nf <= 0 || nc <= 0) return fail(VOF_EINVAL, "empty mesh");
   if (nv >= (1LL << 31) || nf >= (1LL << 31) || nc >= (1LL << 31))
@@ -270,11 +270,13 @@ static vof_status init_impl(const vof_mesh_desc* mesh, const vof_options* opt, c
     return fail(VOF_EINVAL, "EMFPA supports faces of at most 6 nodes; this mesh has " +
                                 std::to_string(maxI));
 
-  HostConn hc;
+  // the derived connectivity, unless the caller built it already
+  HostConn built;
   std::string err;
-  if (!build_connectivity(nv, nf, nc, mesh->face_ptr, mesh->face_vert, mesh->owner,
-                          mesh->neighbour, hc, err))
+  if (!pre && !build_connectivity(nv, nf, nc, mesh->face_ptr, mesh->face_vert, mesh->owner,
+                                  mesh->neighbour, built, err))
     return fail(VOF_EINVAL, err);
+  const HostConn& hc = pre ? *pre : built;
   if (hc.max_cell_faces > 32 || hc.max_cell_verts > 32 || hc.max_cell_entries > 128)
     return fail(VOF_EINVAL, "cell too large (<= 32 faces, 32 nodes, 128 face-node entries)");
 
@@ -508,11 +510,24 @@ vof_status vof_init(const vof_mesh_desc* mesh, const vof_options* opt, void* str
   return init_impl(mesh, opt, (cudaStream_t)stream, out, co, fo, vo);
 }
 
+static vof_status batch_create_impl(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                                    void* stream, vof_ctx** out, const HostConn* const* conns);
+
 vof_status vof_batch_create(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
                             void* stream, vof_ctx** out) {
+  return batch_create_impl(meshes, n_grids, opt, stream, out, nullptr);
+}
+
+static vof_status batch_create_impl(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                                    void* stream, vof_ctx** out, const HostConn* const* conns) {
   if (!meshes || !out || n_grids < 1) return fail(VOF_EINVAL, "bad batch arguments");
   *out = nullptr;
-  if (n_grids == 1) return vof_init(meshes, opt, stream, out);
+  if (n_grids == 1) {
+    if (!conns) return vof_init(meshes, opt, stream, out);
+    const std::vector<int64_t> co{0, meshes[0].n_cell}, fo{0, meshes[0].n_face},
+        vo{0, meshes[0].n_vert};
+    return init_impl(meshes, opt, (cudaStream_t)stream, out, co, fo, vo, conns[0]);
+  }
   std::vector<int64_t> co(n_grids + 1, 0), fo(n_grids + 1, 0), vo(n_grids + 1, 0), po(n_grids + 1, 0);
   for (int g = 0; g < n_grids; ++g) {
     const vof_mesh_desc& m = meshes[g];
@@ -544,8 +559,22 @@ vof_status vof_batch_create(const vof_mesh_desc* meshes, int n_grids, const vof_
   j.n_vert = vo[n_grids]; j.n_face = fo[n_grids]; j.n_cell = co[n_grids];
   j.X = X.data(); j.face_ptr = fp.data(); j.face_vert = fv.data(); j.owner = own.data();
   j.neighbour = nbr.data();
-  return init_impl(&j, opt, (cudaStream_t)stream, out, co, fo, vo);
+  if (!conns) return init_impl(&j, opt, (cudaStream_t)stream, out, co, fo, vo);
+  HostConn joined;
+  join_connectivity(std::vector<const HostConn*>(conns, conns + n_grids), co, fo, vo, joined);
+  return init_impl(&j, opt, (cudaStream_t)stream, out, co, fo, vo, &joined);
 }
+
+}  // extern "C"
+
+namespace gvof {
+vof_status batch_create_with_conn(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                                  void* stream, vof_ctx** out, const HostConn* const* conns) {
+  return batch_create_impl(meshes, n_grids, opt, stream, out, conns);
+}
+}  // namespace gvof
+
+extern "C" {
 
 vof_status vof_init_batch(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
                           vof_ctx** out) {

@@ -1371,6 +1371,13 @@ __global__ void __launch_bounds__(128) k_prebuild(DevMesh M, GeoView<G> Gv, DevS
   for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < nb; w += gridDim.x * blockDim.x) {
     const int j = S.afaces[w];
     const GridParam& gp = S.gp[M.n_grids == 1 ? 0 : grid_of(M.face_off, M.n_grids, j)];
+    if (gp.gdt == 0.0) {
+      // a grid that does not move this step (a batch slot whose request is
+      // done): the flux kernel gives its faces V_F = 0 without a polyhedron
+      S.fm_meta[w] = 0u;
+      S.cover8[w] = 0;
+      continue;
+    }
     const double Vd = S.srate[j] * gp.gdt;
     G vx[kFmSlots], vy[kFmSlots], vz[kFmSlots];
     FaceFrame<G> fr;
@@ -1549,6 +1556,16 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_FLUX_MINB) k_flux(DevMesh M,
       constexpr int nw = (int)(sizeof(GridParam) / sizeof(double));
       if (lane < nw) ((double*)&wgp[wib])[lane] = ((const double*)&S.gp[gi])[lane];
       gsync<GW>();
+    }
+    if (wgp[wib].gdt == 0.0) {
+      // no displacement this step (g dt = 0: a batch slot that does not
+      // move): every back-traced point is its face point, so the flux
+      // polyhedron is the face itself and V_F = 0 exactly
+      if (lane == 0) {
+        S.VF[j] = 0.0;
+        if constexpr (sizeof(G) == 4) S.fexact[j] = 1;
+      }
+      continue;
     }
     const double Vd = S.srate[j] * wgp[wib].gdt;  // V_d of Eq. a-donacion
     if (!poly_for_face<G, KIND>(M, Gv, S, w, j, wgp[wib], Vd, P, fr, lane)) {

@@ -152,4 +152,43 @@ bool build_connectivity(int64_t nv, int64_t nf, int64_t nc, const int64_t* fptr,
   return true;
 }
 
+void join_connectivity(const std::vector<const HostConn*>& parts, const std::vector<int64_t>& co,
+                       const std::vector<int64_t>& fo, const std::vector<int64_t>& vo, HostConn& out) {
+  const int ng = (int)parts.size();
+  // one CSR: grid g's rows follow grid g-1's, offsets shifted by the entries
+  // before it, entries shifted by shift(g, x)
+  auto join = [&](std::vector<int64_t>& ptr, std::vector<int32_t>& idx,
+                  const std::vector<int64_t> HostConn::*pp, const std::vector<int32_t> HostConn::*pi,
+                  const std::vector<int64_t>& rows, auto shift) {
+    int64_t tot = 0;
+    for (int g = 0; g < ng; ++g) tot += (parts[g]->*pi).size();
+    ptr.assign(rows[ng] + 1, 0);
+    idx.resize(tot);
+    int64_t e0 = 0;
+    for (int g = 0; g < ng; ++g) {
+      const std::vector<int64_t>& p = parts[g]->*pp;
+      const std::vector<int32_t>& x = parts[g]->*pi;
+      const int64_t nr = rows[g + 1] - rows[g];
+      for (int64_t r = 0; r <= nr; ++r) ptr[rows[g] + r] = e0 + p[r];
+      for (size_t k = 0; k < x.size(); ++k) idx[e0 + k] = shift(g, x[k]);
+      e0 += (int64_t)x.size();
+    }
+  };
+  join(out.cf_ptr, out.cf, &HostConn::cf_ptr, &HostConn::cf, co, [&](int g, int32_t f) {
+    return f >= 0 ? (int32_t)(f + fo[g]) : ~(int32_t)(~f + fo[g]);
+  });
+  join(out.cv_ptr, out.cv, &HostConn::cv_ptr, &HostConn::cv, co,
+       [&](int g, int32_t v) { return (int32_t)(v + vo[g]); });
+  join(out.vc_ptr, out.vc, &HostConn::vc_ptr, &HostConn::vc, vo,
+       [&](int g, int32_t c) { return (int32_t)(c + co[g]); });
+  join(out.nb_ptr, out.nb, &HostConn::nb_ptr, &HostConn::nb, co,
+       [&](int g, int32_t c) { return (int32_t)(c + co[g]); });
+  out.max_cell_faces = out.max_cell_verts = out.max_cell_entries = 0;
+  for (const HostConn* h : parts) {
+    out.max_cell_faces = std::max(out.max_cell_faces, h->max_cell_faces);
+    out.max_cell_verts = std::max(out.max_cell_verts, h->max_cell_verts);
+    out.max_cell_entries = std::max(out.max_cell_entries, h->max_cell_entries);
+  }
+}
+
 }  // namespace gvof

@@ -17,4 +17,12 @@ bool build_connectivity(int64_t nv, int64_t nf, int64_t nc, const int64_t* fptr,
                         const int32_t* fvert, const int32_t* own, const int32_t* nbr,
                         HostConn& out, std::string& err);
 
+// the connectivity of grids joined into one index space (grid g's cells,
+// faces and vertices shifted by cell_off[g], face_off[g], vert_off[g]): the
+// same arrays build_connectivity makes for the joined mesh, without
+// rebuilding them
+void join_connectivity(const std::vector<const HostConn*>& parts, const std::vector<int64_t>& cell_off,
+                       const std::vector<int64_t>& face_off, const std::vector<int64_t>& vert_off,
+                       HostConn& out);
+
 }  // namespace gvof

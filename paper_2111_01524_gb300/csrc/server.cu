@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -125,7 +126,9 @@ struct Request {
   vof_velocity vel;
   int n_steps;
   double cfl, t_end;
-  int64_t bytes;
+  int64_t bytes = -1;               // device footprint alone (sized at admission)
+  std::unique_ptr<HostConn> conn;   // its connectivity, built once, until its batch exists
+  std::string refused;              // why admission refused it (empty: not refused)
   int state = kQueued;
   int batch = -1, slot = -1;
   int k = 0;            // steps queued
@@ -242,9 +245,16 @@ vof_status vof_server_submit(vof_server* s, const vof_mesh_desc* mesh, const dou
   r.n_steps = n_steps;
   r.cfl = cfl;
   r.t_end = t_end;
-  const vof_mesh_desc d = m.desc();
-  vof_status st = vof_estimate_bytes(&d, 1, &s->copt, &r.bytes);
-  if (st != VOF_OK) return st;
+  // structure checks here; the connectivity (and with it the footprint) is
+  // built once, when the request reaches the front of the queue
+  if (m.fp[0] != 0) return sfail(VOF_EINVAL, "face_ptr[0] != 0");
+  for (int64_t f = 0; f < m.nf; ++f) {
+    if (m.fp[f + 1] < m.fp[f] + 3) return sfail(VOF_EINVAL, "a face has fewer than 3 nodes");
+    if (m.own[f] < 0 || m.own[f] >= m.nc || m.nbr[f] < -1 || m.nbr[f] >= m.nc || m.nbr[f] == m.own[f])
+      return sfail(VOF_EINVAL, "bad owner/neighbour");
+  }
+  for (int32_t v : m.fv)
+    if (v < 0 || v >= m.nv) return sfail(VOF_EINVAL, "face_vert entry out of range");
   r.t_submit = now_s();
   if (s->t0 < 0) s->t0 = r.t_submit;
   *id = r.id;
@@ -291,12 +301,41 @@ static vof_status retire(vof_server* s) {
   return VOF_OK;
 }
 
+// the connectivity and the device footprint of request r alone
+static vof_status size_request(vof_server* s, Request& r) {
+  if (r.bytes >= 0) return VOF_OK;
+  r.conn.reset(new HostConn());
+  std::string err;
+  const MeshCopy& m = r.mesh;
+  if (!build_connectivity(m.nv, m.nf, m.nc, m.fp.data(), m.fv.data(), m.own.data(), m.nbr.data(),
+                          *r.conn, err)) {
+    r.conn.reset();
+    r.refused = err;
+    return sfail(VOF_EINVAL, "request " + std::to_string(r.id) + ": " + err);
+  }
+  CtxSizes z{};
+  z.ng = 1;
+  z.nv = m.nv; z.nf = m.nf; z.nc = m.nc; z.nfv = m.fp[m.nf];
+  z.ncf = r.conn->cf_ptr[m.nc]; z.ncv = r.conn->cv_ptr[m.nc]; z.nvc = r.conn->vc_ptr[m.nv];
+  z.nnb = r.conn->nb_ptr[m.nc];
+  for (int64_t f = 0; f < m.nf; ++f) z.nbf += m.nbr[f] < 0;
+  r.bytes = context_bytes(z, s->copt);
+  return VOF_OK;
+}
+
 static vof_status admit(vof_server* s) {
   std::vector<int64_t> take;
   int64_t need = 0;
   while (!s->queue.empty()) {
-    const Request& r = s->reqs[s->queue.front()];
+    Request& r = s->reqs[s->queue.front()];
     if (s->opt.max_batch > 0 && (int)take.size() >= s->opt.max_batch) break;
+    if (r.bytes < 0) {
+      const vof_status st = size_request(s, r);
+      if (st != VOF_OK) {
+        s->queue.pop_front();  // refused: poll reports why
+        return st;
+      }
+    }
     // the batch's footprint is at most the sum of its grids' own (the
     // per-context tables are shared), so the sum is admitted against
     if (s->bytes_live + need + r.bytes > s->budget) {
@@ -313,12 +352,16 @@ static vof_status admit(vof_server* s) {
   Batch b;
   SCK(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
   std::vector<vof_mesh_desc> descs;
+  std::vector<const HostConn*> conns;
   std::vector<double> F;
   for (int64_t q : take) {
     descs.push_back(s->reqs[q].mesh.desc());
+    conns.push_back(s->reqs[q].conn.get());
     F.insert(F.end(), s->reqs[q].F0.begin(), s->reqs[q].F0.end());
   }
-  vof_status st = vof_batch_create(descs.data(), (int)descs.size(), &s->copt, b.stream, &b.ctx);
+  vof_status st = batch_create_with_conn(descs.data(), (int)descs.size(), &s->copt, b.stream, &b.ctx,
+                                         conns.data());
+  for (int64_t q : take) s->reqs[q].conn.reset();
   if (st != VOF_OK) { cudaStreamDestroy(b.stream); return st; }
   b.cell_off.resize(take.size() + 1);
   int ng = 0;
@@ -432,6 +475,7 @@ vof_status vof_server_poll(vof_server* s, int64_t id, int32_t* state, double* F,
   vof_status st = retire(s);
   if (st != VOF_OK) return st;
   const Request& r = s->reqs[id];
+  if (!r.refused.empty()) return sfail(VOF_EINVAL, "request " + std::to_string(id) + " refused: " + r.refused);
   if (state) *state = r.state;
   if (r.state == kDone) {
     if (F) std::memcpy(F, r.result.data(), sizeof(double) * r.result.size());

@@ -533,6 +533,11 @@ int reconstruct_launch_count(const vof_ctx* c);
 // the flux polyhedra of the active faces (up to fm_cap), then the truncations
 cudaError_t launch_prebuild(const vof_ctx* c, cudaStream_t s);  // + candidate lists (FP32)
 bool prebuild_lists(const vof_ctx* c);  // launch_prebuild also builds the candidate lists
+struct HostConn;
+// vof_batch_create with each grid's connectivity already built (the server
+// builds it once, to size the request, and hands it on)
+vof_status batch_create_with_conn(const vof_mesh_desc* meshes, int n_grids, const vof_options* opt,
+                                  void* stream, vof_ctx** out, const HostConn* const* conns);
 cudaError_t launch_flux(const vof_ctx* c, cudaStream_t s);
 cudaError_t launch_candidates(const vof_ctx* c, const int32_t* faces, int n, int64_t cap_per_face,
                               int32_t* out, int32_t* counts, cudaStream_t s);

@@ -48,6 +48,30 @@ def test_server_options_are_checked_on_the_host():
         assert e.value.status == vof.VOF_EINVAL
 
 
+def test_server_checks_a_request_mesh_on_submit():
+    """The structure of a request's mesh is checked on the host when it is
+    submitted (its connectivity is built later, once, at admission)."""
+    import numpy as np
+    from paper_2111_01524_gb300 import inputs as I, vof
+    srv = vof.Server(budget_bytes=1 << 30)
+    try:
+        m = I.hex_mesh(3)
+        F0 = np.zeros(27)
+        assert srv.submit(m, F0, I.rotation(1.0), 5) == 0
+        bad = dict(m, owner=np.array(m["owner"]).copy())
+        bad["owner"][4] = 27  # not a cell
+        with pytest.raises(vof.VofError) as e:
+            srv.submit(bad, F0, I.rotation(1.0), 5)
+        assert e.value.status == vof.VOF_EINVAL
+        bad = dict(m, face_vert=np.array(m["face_vert"]).copy())
+        bad["face_vert"][0] = -1
+        with pytest.raises(vof.VofError):
+            srv.submit(bad, F0, I.rotation(1.0), 5)
+        assert srv.stats()["n_submitted"] == 1
+    finally:
+        srv.close()
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2111_01524_gb300 import build, vof
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))

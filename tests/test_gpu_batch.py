@@ -115,3 +115,44 @@ def test_autotune_keeps_results(vof):
         b.step_batch(vels, t, dt)
         t = t + dt
     assert np.array_equal(a.get_fraction(), b.get_fraction())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_a_grid_that_pauses_keeps_its_state_and_resumes_exactly(vof, prec):
+    """A grid of a batch that takes dt = 0 for some steps (a served request
+    that is done, or waits) keeps F bit for bit, costs no flux polyhedra,
+    and when it moves again continues exactly as a single grid that simply
+    skipped those steps; the other grids are unaffected."""
+    P = vof.PREC_FP64 if prec == "fp64" else vof.PREC_MIXED
+    grids = _grids()
+    vels = [v for _, _, v in grids]
+    batch = vof.Context([m for m, _, _ in grids], precision=P)
+    batch.set_fraction(np.concatenate([F for _, F, _ in grids]))
+    batch.reconstruct()
+    singles = []
+    for m, F, _ in grids:
+        c = vof.Context(m, precision=P)
+        c.set_fraction(F)
+        c.reconstruct()
+        singles.append(c)
+    n = len(grids)
+    t = np.zeros(n)
+    pause = 1  # the tet grid stops for steps 2..4
+    for k in range(7):
+        dt = batch.suggest_dt_batch(vels, t, 0.5, np.full(n, 10.0))
+        if 2 <= k <= 4:
+            dt[pause] = 0.0
+        for i, c in enumerate(singles):
+            if dt[i] > 0.0:
+                c.step(vels[i], t[i], dt[i])
+        before = batch.get_fraction()
+        batch.step_batch(vels, t, dt)
+        after = batch.get_fraction()
+        t = t + dt
+        Fb = np.split(after, np.cumsum([int(m["n_cell"]) for m, _, _ in grids])[:-1])
+        for i, c in enumerate(singles):
+            assert np.array_equal(Fb[i], c.get_fraction()), (k, i)
+        if 2 <= k <= 4:
+            Fp = np.split(before, np.cumsum([int(m["n_cell"]) for m, _, _ in grids])[:-1])[pause]
+            assert np.array_equal(Fb[pause], Fp)
+    assert batch.stats()["n_overflow"] == 0
