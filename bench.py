@@ -62,9 +62,9 @@ FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0
 # use; valid only for the source it was taken on (traffic is null for any other)
 # ncu figures of k_flux per flux polyhedron (one launch, --set full), valid
 # for the k_flux.cu source whose sha256 they carry
-FLUX_NCU = {"fmfpa": {"source_sha256": "c244ffa4f7c70f1d5fe6baece6399cec44e8f5aec7320fd2d5acd91365d18660",
-                      "dram_bytes_per_active_face": 591.0, "issue_active": 0.677,
-                      "fma_pipe_active": 0.178,
+FLUX_NCU = {"fmfpa": {"source_sha256": "c23d2cae46d6636816681b15de757448690a2ea51d92eb7a9fb06120c6d7f5d5",
+                      "dram_bytes_per_active_face": 586.0, "issue_active": 0.674,
+                      "fma_pipe_active": 0.176,
                       "capture": "profiles/k_flux_deformation128_midrun_mixed.md"},
             "emfpa": {"source_sha256": "f73470b1044dd746c14f9f88973f6e28d1146cc8accd65f66cc0f6bb326d8456",
                       "dram_bytes_per_active_face": 590.0, "issue_active": 0.573,
