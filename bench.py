@@ -75,15 +75,17 @@ FLUX_NCU = {"fmfpa": {"source_sha256": "c23d2cae46d6636816681b15de757448690a2ea5
                       "fma_pipe_active": 0.136,
                       "capture": "profiles/k_flux_deformation128_mixed_nmfpa.md"}}
 # kernels one step launches: reconstruction (cell tags 1, node tags 3,
-# LSGIR 1 or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,
+# LSGIR 1, in mixed precision 2, or LSFIR 1 + 2 n_out) and advection (face sweep 2, polyhedra 1,
 # flux 1, update 2, and in mixed precision the candidate lists of the
 # prebuilt polyhedra 1 and the reconciliation of FP32 noise: 5 per round x 3
 # rounds + 1); the phase timers count the same kernels
 REPAIR_LAUNCHES = 5 * 3 + 1
 
 
-def recon_kernels(recon="lsgir", n_out=4):
-    return 4 + (1 + 2 * n_out if recon == "lsfir" else 1)
+def recon_kernels(recon="lsgir", n_out=4, precision="mixed"):
+    # LSGIR: the warp kernel, and in the mixed path the closed form of the
+    # box cells' plane constants
+    return 4 + (1 + 2 * n_out if recon == "lsfir" else (2 if precision == "mixed" else 1))
 
 
 def advect_kernels(precision="mixed", prebuilt=True):
@@ -92,7 +94,7 @@ def advect_kernels(precision="mixed", prebuilt=True):
 
 
 def kernels_per_step(recon="lsgir", n_out=4, precision="mixed", prebuilt=True):
-    return recon_kernels(recon, n_out) + advect_kernels(precision, prebuilt)
+    return recon_kernels(recon, n_out, precision) + advect_kernels(precision, prebuilt)
 
 
 FP32_LANES_PER_SM = 128

@@ -787,6 +787,18 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
     nx = gx / gn; ny = gy / gn; nz = gz / gn;
     }
 
+    if constexpr (MODE == 0 && kMixed) {
+      if (M.convex[c] == 2) {
+        // an axis-aligned box: its plane constant is taken by
+        // k_box_constant, one thread per cell
+        if (lane == 0) {
+          S.nx[c] = (double)nx; S.ny[c] = (double)ny; S.nz[c] = (double)nz;
+          if (kMixed) { S.nx32[c] = (float)nx; S.ny32[c] = (float)ny; S.nz32[c] = (float)nz; }
+        }
+        __syncwarp();
+        continue;
+      }
+    }
     // ---- plane constant
     const int nfc = (int)(M.cf_ptr[c + 1] - M.cf_ptr[c]);
     const int64_t v0 = M.cv_ptr[c];
@@ -878,10 +890,130 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
   }
 }
 
+// ---- the plane constant of an axis-aligned box (Eq. plic-eq on a cuboid),
+// mixed path
+//
+// In box coordinates u in [0, 1]^3 the fluid of the plane n.(x - x_c) + C = 0
+// is {sum a_i (u_i - 1/2) + C + d >= 0}, a_i = n_i h_i (h the box sides), d
+// = n.(box centre - x_c). Mirroring the axes with a_i < 0 and dividing by S
+// = sum |a_i| gives {m.u >= 1/2 - (C + d)/S}, m_i = |a_i| / S, sum m_i = 1.
+// With V(b) = vol{m.u <= b} the fluid fraction is 1 - V(1/2 - (C + d)/S),
+// and V(1 - b) = 1 - V(b), so with g the root of V(g) = min(F, 1 - F) in
+// [0, 1/2]: C + d = S (1/2 - g) for F >= 1/2 and S (g - 1/2) below.
+// For m_1 <= m_2 <= m_3, V(b) is the mean over u_1 of A2(b - m_1 u_1), the
+// area of {m_2 y + m_3 z <= t} in the unit square, a piecewise quadratic in
+// t with breakpoints 0, m_2, m_3, m_2 + m_3. The mean is integrated exactly,
+// piece by piece, in s = b - t in [0, m_1] (so that no width is formed as a
+// difference of two numbers of the size of b, which a small m_1 would
+// cancel): midpoint value plus the curvature term w^3 A2''/24.
+template <typename T>
+__device__ __forceinline__ T box_area(T t, T m2, T m3) {
+  const T s = m2 + m3;
+  if (t <= T(0)) return T(0);
+  if (t >= s) return T(1);
+  if (t < m2) return (t / m2) * t / (T(2) * m3);                   // triangle
+  if (t <= m3) return (t - T(0.5) * m2) / m3;                      // band
+  const T r = s - t;
+  return T(1) - (r / m2) * r / (T(2) * m3);                        // square less a triangle
+}
+
+// A2' and A2'' at t (within a piece)
+template <typename T>
+__device__ __forceinline__ void box_area_d(T t, T m2, T m3, T* d1, T* d2) {
+  const T s = m2 + m3;
+  if (t <= T(0) || t >= s) { *d1 = T(0); *d2 = T(0); return; }
+  if (t < m2) { *d1 = t / (m2 * m3); *d2 = T(1) / (m2 * m3); return; }
+  if (t <= m3) { *d1 = T(1) / m3; *d2 = T(0); return; }
+  *d1 = (s - t) / (m2 * m3);
+  *d2 = -T(1) / (m2 * m3);
+}
+
+// V(b) and V'(b) for b in [0, 1/2]
+template <typename T>
+__device__ __forceinline__ T box_volume(T b, T m1, T m2, T m3, T* slope) {
+  if (!(m1 > T(0))) {
+    T d2;
+    box_area_d(b, m2, m3, slope, &d2);
+    return box_area(b, m2, m3);
+  }
+  // breakpoints of A2 in s = b - t, increasing: b - m3 <= b - m2 <= b
+  const T cut[3] = {b - m3, b - m2, b};
+  T s0 = T(0), acc = T(0), dacc = T(0);
+  for (int i = 0; i <= 3; ++i) {
+    T s1 = m1;
+    if (i < 3) {
+      if (!(cut[i] > s0 && cut[i] < m1)) continue;
+      s1 = cut[i];
+    }
+    const T w = s1 - s0;
+    if (w > T(0)) {
+      const T tm = b - T(0.5) * (s0 + s1);
+      T d1, d2;
+      box_area_d(tm, m2, m3, &d1, &d2);
+      acc += w * box_area(tm, m2, m3) + d2 * w * w * w / T(24);
+      dacc += w * d1;  // A2' is linear on the piece: its midpoint value is its mean
+    }
+    s0 = s1;
+  }
+  *slope = dacc / m1;
+  return acc / m1;
+}
+
+// the root g in [0, 1/2] of V(g) = v, v in [0, 1/2]: Newton steps kept
+// inside a bisection bracket
+template <typename T>
+__device__ T box_root(T v, T m1, T m2, T m3) {
+  T lo = T(0), hi = T(0.5), g = v < T(0.5) ? v : T(0.5);
+  for (int it = 0; it < 40; ++it) {
+    T d;
+    const T f = box_volume(g, m1, m2, m3, &d) - v;
+    if (f == T(0)) return g;
+    if (f < T(0)) lo = g; else hi = g;
+    T gn = d > T(0) ? g - f / d : T(0.5) * (lo + hi);
+    if (!(gn > lo && gn < hi)) gn = T(0.5) * (lo + hi);
+    if (gn == g || !(hi > lo)) return gn;
+    g = gn;
+  }
+  return g;
+}
+
+// plane constants of the interfacial box cells of the mixed path, one
+// thread per cell; the root g in FP32 (relative to the corner it bounds, so
+// a nearly full or empty cell keeps its precision), C from it in FP64; the
+// normals come from k_reconstruct
+__global__ void k_box_constant(DevMesh M, DevState S) {
+  const int64_t n = (int64_t)S.cnt[kNIcells];
+  const int64_t nc = M.nc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = S.icells[i];
+    if (M.convex[c] != 2) continue;
+    const double F = S.F[c];
+    const double n0 = S.nx[c], n1 = S.ny[c], n2 = S.nz[c];
+    const double lx = M.bb[c], ly = M.bb[nc + c], lz = M.bb[2 * nc + c];
+    const double hx = M.bb[3 * nc + c], hy = M.bb[4 * nc + c], hz = M.bb[5 * nc + c];
+    const double a0 = fabs(n0 * (hx - lx)), a1 = fabs(n1 * (hy - ly)), a2 = fabs(n2 * (hz - lz));
+    const double Sa = a0 + a1 + a2;
+    const double d = n0 * (0.5 * (lx + hx) - M.ccx[c]) + n1 * (0.5 * (ly + hy) - M.ccy[c]) +
+                     n2 * (0.5 * (lz + hz) - M.ccz[c]);
+    float m1 = (float)(a0 / Sa), m2 = (float)(a1 / Sa), m3 = (float)(a2 / Sa);
+    if (m1 > m2) { const float t = m1; m1 = m2; m2 = t; }
+    if (m2 > m3) { const float t = m2; m2 = m3; m3 = t; }
+    if (m1 > m2) { const float t = m1; m1 = m2; m2 = t; }
+    const float v = (float)(F < 0.5 ? F : 1.0 - F);
+    const double g = (double)box_root<float>(v, m1, m2, m3);
+    const double C = (F >= 0.5 ? Sa * (0.5 - g) : Sa * (g - 0.5)) - d;
+    S.C[c] = C;
+    S.C32[c] = (float)C;
+  }
+}
+
 }  // namespace
 
 int reconstruct_launch_count(const vof_ctx* c) {
-  return c->opt.reconstruction == VOF_RECON_LSFIR ? 1 + 2 * c->opt.lsfir_max_iter : 1;
+  // LSGIR: the warp kernel, and in the mixed path the box cells' constants
+  if (c->opt.reconstruction == VOF_RECON_LSFIR) return 1 + 2 * c->opt.lsfir_max_iter;
+  return c->opt.precision == VOF_PREC_MIXED ? 2 : 1;
 }
 
 namespace {
@@ -900,6 +1032,7 @@ cudaError_t reconstruct_launches(const vof_ctx* c, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (c->opt.reconstruction != VOF_RECON_LSFIR) {
     k_reconstruct<G, kMixed, 0><<<grid, kWarps * 32, 0, s>>>(m, g, st, beta, 0, 0.0);
+    if (kMixed) k_box_constant<<<kSMs * 4, 128, 0, s>>>(m, st);
     return cudaGetLastError();
   }
   // LSFIR (Sec. 2.1.2): LSGIR start, then the outer iterations; each

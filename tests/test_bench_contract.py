@@ -69,15 +69,18 @@ def test_sweep_roofline_is_hbm_bytes_over_one_launch(bench):
 
 def test_kernels_per_step(bench):
     """LSGIR: cell tags 1, node tags 3, reconstruct 1, face sweep 2,
-    polyhedra 1, flux 1, update 2 = 11; LSFIR adds 2 launches per outer
-    iteration; the mixed path adds 16 (3 reconciliation rounds of 5 and the
-    final clip) and, with prebuilt polyhedra, their candidate lists (1)."""
+    polyhedra 1, flux 1, update 2 = 11; LSFIR replaces the reconstruction's
+    1 by 1 + 2 per outer iteration; the mixed path adds the closed form of
+    the box cells' plane constants (1), the reconciliation of FP32 noise (16:
+    3 rounds of 5 and the final clip) and, with prebuilt polyhedra, their
+    candidate lists (1)."""
     assert bench.kernels_per_step(precision="fp64") == 11
     assert bench.kernels_per_step("lsfir", 4, precision="fp64") == 19
     assert bench.kernels_per_step("lsfir", 1, precision="fp64") == 13
-    assert bench.kernels_per_step() == 11 + 1 + 16
-    assert bench.kernels_per_step(prebuilt=False) == 11 + 16
-    assert bench.recon_kernels() + bench.advect_kernels("fp64") == 11
+    assert bench.kernels_per_step() == 11 + 1 + 16 + 1
+    assert bench.kernels_per_step(prebuilt=False) == 11 + 1 + 16
+    assert bench.kernels_per_step("lsfir", 4) == 19 + 16 + 1
+    assert bench.recon_kernels(precision="fp64") + bench.advect_kernels("fp64") == 11
 
 
 def test_flux_roofline_uses_the_oracle_op_count(bench):
