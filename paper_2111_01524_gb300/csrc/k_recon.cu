@@ -14,10 +14,13 @@
 // (sample, face) pairs over the lanes.
 // Precision: the FP64 path works in double. The mixed path works in FP32 in
 // cell-local coordinates scaled by V^(-1/3) (absolute positions as (hi, lo)
-// float pairs) and switches to FP64 for the plane constant of cells with F
-// or 1 - F below 1e-3, where an FP32 cut volume is too coarse to place the
-// plane.
+// float pairs); for cells with F or 1 - F below 1e-3, where an FP32 cut
+// volume is too coarse to place the plane, it takes the corner closed form
+// (FP32 relative to the corner) or the FP64 bracket. Axis-aligned boxes of
+// the mixed LSGIR path take the cuboid closed form of box_plane.cuh instead,
+// one thread per cell after the normals (k_box_constant).
 #include "vof_common.cuh"
+#include "box_plane.cuh"
 
 namespace gvof {
 namespace {
@@ -890,93 +893,6 @@ __global__ void __launch_bounds__(kWarps * 32, GVOF_RECON_MINB) k_reconstruct(De
   }
 }
 
-// ---- the plane constant of an axis-aligned box (Eq. plic-eq on a cuboid),
-// mixed path
-//
-// In box coordinates u in [0, 1]^3 the fluid of the plane n.(x - x_c) + C = 0
-// is {sum a_i (u_i - 1/2) + C + d >= 0}, a_i = n_i h_i (h the box sides), d
-// = n.(box centre - x_c). Mirroring the axes with a_i < 0 and dividing by S
-// = sum |a_i| gives {m.u >= 1/2 - (C + d)/S}, m_i = |a_i| / S, sum m_i = 1.
-// With V(b) = vol{m.u <= b} the fluid fraction is 1 - V(1/2 - (C + d)/S),
-// and V(1 - b) = 1 - V(b), so with g the root of V(g) = min(F, 1 - F) in
-// [0, 1/2]: C + d = S (1/2 - g) for F >= 1/2 and S (g - 1/2) below.
-// For m_1 <= m_2 <= m_3, V(b) is the mean over u_1 of A2(b - m_1 u_1), the
-// area of {m_2 y + m_3 z <= t} in the unit square, a piecewise quadratic in
-// t with breakpoints 0, m_2, m_3, m_2 + m_3. The mean is integrated exactly,
-// piece by piece, in s = b - t in [0, m_1] (so that no width is formed as a
-// difference of two numbers of the size of b, which a small m_1 would
-// cancel): midpoint value plus the curvature term w^3 A2''/24.
-template <typename T>
-__device__ __forceinline__ T box_area(T t, T m2, T m3) {
-  const T s = m2 + m3;
-  if (t <= T(0)) return T(0);
-  if (t >= s) return T(1);
-  if (t < m2) return (t / m2) * t / (T(2) * m3);                   // triangle
-  if (t <= m3) return (t - T(0.5) * m2) / m3;                      // band
-  const T r = s - t;
-  return T(1) - (r / m2) * r / (T(2) * m3);                        // square less a triangle
-}
-
-// A2' and A2'' at t (within a piece)
-template <typename T>
-__device__ __forceinline__ void box_area_d(T t, T m2, T m3, T* d1, T* d2) {
-  const T s = m2 + m3;
-  if (t <= T(0) || t >= s) { *d1 = T(0); *d2 = T(0); return; }
-  if (t < m2) { *d1 = t / (m2 * m3); *d2 = T(1) / (m2 * m3); return; }
-  if (t <= m3) { *d1 = T(1) / m3; *d2 = T(0); return; }
-  *d1 = (s - t) / (m2 * m3);
-  *d2 = -T(1) / (m2 * m3);
-}
-
-// V(b) and V'(b) for b in [0, 1/2]
-template <typename T>
-__device__ __forceinline__ T box_volume(T b, T m1, T m2, T m3, T* slope) {
-  if (!(m1 > T(0))) {
-    T d2;
-    box_area_d(b, m2, m3, slope, &d2);
-    return box_area(b, m2, m3);
-  }
-  // breakpoints of A2 in s = b - t, increasing: b - m3 <= b - m2 <= b
-  const T cut[3] = {b - m3, b - m2, b};
-  T s0 = T(0), acc = T(0), dacc = T(0);
-  for (int i = 0; i <= 3; ++i) {
-    T s1 = m1;
-    if (i < 3) {
-      if (!(cut[i] > s0 && cut[i] < m1)) continue;
-      s1 = cut[i];
-    }
-    const T w = s1 - s0;
-    if (w > T(0)) {
-      const T tm = b - T(0.5) * (s0 + s1);
-      T d1, d2;
-      box_area_d(tm, m2, m3, &d1, &d2);
-      acc += w * box_area(tm, m2, m3) + d2 * w * w * w / T(24);
-      dacc += w * d1;  // A2' is linear on the piece: its midpoint value is its mean
-    }
-    s0 = s1;
-  }
-  *slope = dacc / m1;
-  return acc / m1;
-}
-
-// the root g in [0, 1/2] of V(g) = v, v in [0, 1/2]: Newton steps kept
-// inside a bisection bracket
-template <typename T>
-__device__ T box_root(T v, T m1, T m2, T m3) {
-  T lo = T(0), hi = T(0.5), g = v < T(0.5) ? v : T(0.5);
-  for (int it = 0; it < 40; ++it) {
-    T d;
-    const T f = box_volume(g, m1, m2, m3, &d) - v;
-    if (f == T(0)) return g;
-    if (f < T(0)) lo = g; else hi = g;
-    T gn = d > T(0) ? g - f / d : T(0.5) * (lo + hi);
-    if (!(gn > lo && gn < hi)) gn = T(0.5) * (lo + hi);
-    if (gn == g || !(hi > lo)) return gn;
-    g = gn;
-  }
-  return g;
-}
-
 // plane constants of the interfacial box cells of the mixed path, one
 // thread per cell; the root g in FP32 (relative to the corner it bounds, so
 // a nearly full or empty cell keeps its precision), C from it in FP64; the
@@ -996,12 +912,9 @@ __global__ void k_box_constant(DevMesh M, DevState S) {
     const double Sa = a0 + a1 + a2;
     const double d = n0 * (0.5 * (lx + hx) - M.ccx[c]) + n1 * (0.5 * (ly + hy) - M.ccy[c]) +
                      n2 * (0.5 * (lz + hz) - M.ccz[c]);
-    float m1 = (float)(a0 / Sa), m2 = (float)(a1 / Sa), m3 = (float)(a2 / Sa);
-    if (m1 > m2) { const float t = m1; m1 = m2; m2 = t; }
-    if (m2 > m3) { const float t = m2; m2 = m3; m3 = t; }
-    if (m1 > m2) { const float t = m1; m1 = m2; m2 = t; }
+    const BoxSlopes B = box_slopes((float)(a0 / Sa), (float)(a1 / Sa), (float)(a2 / Sa));
     const float v = (float)(F < 0.5 ? F : 1.0 - F);
-    const double g = (double)box_root<float>(v, m1, m2, m3);
+    const double g = (double)box_root(v, B);
     const double C = (F >= 0.5 ? Sa * (0.5 - g) : Sa * (g - 0.5)) - d;
     S.C[c] = C;
     S.C32[c] = (float)C;
