@@ -103,7 +103,10 @@ __host__ __device__ inline float box_root(float v, const BoxSlopes& B, int* iter
     float gn = 0.5f * (lo + hi);
     if (d > 0.f) {
       const float step = f / d;
-      if (fabsf(step) <= 2.5e-7f * g) { g -= step; break; }  // within ~2 ulp of the root
+      if (fabsf(step) <= 2.5e-7f * g) {  // within ~2 ulp of the root
+        g = fminf(fmaxf(g - step, lo), hi);
+        break;
+      }
       if (g - step > lo && g - step < hi) gn = g - step;
     }
     const bool done = gn == g || !(hi > lo);
