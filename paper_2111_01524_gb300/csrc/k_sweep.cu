@@ -148,6 +148,35 @@ __global__ void k_node_tags(DevMesh M, const double* F, double eps, int8_t* tv,
   }
 }
 
+// a list whose items each own a short CSR range (the faces of a node, the
+// nodes of a cell), taken by sub-warps of S lanes: 32 / S items per warp at
+// once, each sub-warp's lanes striding over its item's range. The warp's
+// loops keep a uniform trip count (the longest range among its items), so
+// warp-wide ballots (warp_append) see the whole warp.
+template <int S>
+struct SubWarp {
+  static_assert(32 % S == 0, "S divides the warp");
+  const int sub, sl;
+  __device__ SubWarp() : sub((threadIdx.x & 31) / S), sl(threadIdx.x % S) {}
+  // the warp's first item and the stride over the list
+  __device__ int64_t first() const {
+    return ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / S);
+  }
+  __device__ int64_t stride() const { return (((int64_t)gridDim.x * blockDim.x) >> 5) * (32 / S); }
+  // the longest of the warp's ranges
+  __device__ int64_t max_len(int64_t len) const {
+    for (int o = S; o < 32; o <<= 1) {
+      const int64_t x = __shfl_xor_sync(GVOF_FULL, len, o);
+      len = x > len ? x : len;
+    }
+    return len;
+  }
+};
+// lanes per band node in the face sweep (a hex grid's node has 12 faces)
+// and per band cell in the node list (a hex has 8 nodes)
+constexpr int kSweepLanes = 16;
+constexpr int kNodeLanes = 8;
+
 // face sweep: face tags from node tags, V_d = g(t+dt/2) (u0.n) A dt,
 // V_F = 0 on tag -1 faces, V_F = V_d on tag 1 faces (no geometry, Sec. 3.3);
 // tag 0 faces are appended to the active list for the flux kernel
@@ -170,8 +199,8 @@ __global__ void k_band_begin(unsigned long long* cnt) {
   }
 }
 
-// face tags and the active list: all faces, or (band nodes valid) one warp
-// per band node over the faces that contain it
+// face tags and the active list: all faces, or (band nodes valid) one
+// sub-warp per band node over the faces that contain it
 __global__ void k_face_sweep(DevMesh M, const int8_t* tv, int8_t* tf, int32_t* afaces,
                              unsigned long long* cnt, const int64_t* vf_ptr, const int32_t* vf,
                              const int32_t* bnodes, int32_t* stamp_f) {
@@ -191,20 +220,23 @@ __global__ void k_face_sweep(DevMesh M, const int8_t* tv, int8_t* tf, int32_t* a
   }
   const int32_t epoch = (int32_t)cnt[kEpoch];
   const int64_t nb = (int64_t)cnt[kNBandNodes];
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = w0; i < nb; i += nw) {
-    const int v = bnodes[i];
-    const int64_t q0 = vf_ptr[v], q1 = vf_ptr[v + 1];
-    for (int64_t base = q0; base < q1; base += 32) {
-      const int64_t q = base + lane;
+  SubWarp<kSweepLanes> sw;
+  for (int64_t i0 = sw.first(); i0 < nb; i0 += sw.stride()) {
+    const int64_t i = i0 + sw.sub;
+    int64_t q0 = 0, q1 = 0;
+    if (i < nb) {
+      const int v = bnodes[i];
+      q0 = vf_ptr[v];
+      q1 = vf_ptr[v + 1];
+    }
+    const int64_t len = q1 - q0, rounds = sw.max_len(len);
+    for (int64_t k = sw.sl; k - sw.sl < rounds; k += kSweepLanes) {
       bool act = false;
       int f = 0;
-      if (q < q1) {
-        f = vf[q];
+      if (k < len) {
+        f = vf[q0 + k];
         const int8_t t = face_tag(M, tv, f);
-        tf[f] = t;  // every warp that meets f writes the same tag
+        tf[f] = t;  // every sub-warp that meets f writes the same tag
         act = t == 0 && claim(stamp_f, f, epoch);
       }
       warp_append(act, f, afaces, cnt + kNAfaces);
@@ -238,24 +270,27 @@ __global__ void k_band_cells(DevMesh M, const int32_t* afaces, const int32_t* ic
   if (blockIdx.x == 0 && threadIdx.x == 0) cnt[kBandCellsOk] = 1;
 }
 
-// band nodes: the nodes of the band cells, each once (one warp per cell)
+// band nodes: the nodes of the band cells, each once (one sub-warp per cell)
 __global__ void k_band_nodes(DevMesh M, const int32_t* bcells, unsigned long long* cnt,
                              int32_t* stamp_v, int32_t* bnodes) {
   if (cnt[kBandCellsOk] == 0) return;
   const int32_t epoch = (int32_t)cnt[kEpoch];
   const int64_t n = (int64_t)cnt[kNBandCells];
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = w0; i < n; i += nw) {
-    const int c = bcells[i];
-    const int64_t q0 = M.cv_ptr[c], q1 = M.cv_ptr[c + 1];
-    for (int64_t base = q0; base < q1; base += 32) {
-      const int64_t q = base + lane;
+  SubWarp<kNodeLanes> sw;
+  for (int64_t i0 = sw.first(); i0 < n; i0 += sw.stride()) {
+    const int64_t i = i0 + sw.sub;
+    int64_t q0 = 0, q1 = 0;
+    if (i < n) {
+      const int c = bcells[i];
+      q0 = M.cv_ptr[c];
+      q1 = M.cv_ptr[c + 1];
+    }
+    const int64_t len = q1 - q0, rounds = sw.max_len(len);
+    for (int64_t k = sw.sl; k - sw.sl < rounds; k += kNodeLanes) {
       int v = 0;
       bool p = false;
-      if (q < q1) {
-        v = M.cv[q];
+      if (k < len) {
+        v = M.cv[q0 + k];
         p = claim(stamp_v, v, epoch);
       }
       warp_append(p, v, bnodes, cnt + kNBandNodes);
