@@ -402,7 +402,7 @@ def main_reference(a):
 
 
 def main_cycle(a):
-    """Config 2 at 128^3 to t = 3: the oracle's whole run (multi-core) beside
+    """The hex deformation at 128^3 to t = 3: the oracle's whole run (multi-core) beside
     the mixed and FP64 GPU paths; end-of-run shape error (Sec. 4.2, E_shape
     against the initial shape, which the field returns to at t = T) and the
     volume of each, and the mixed path's F against the oracle's."""
@@ -772,7 +772,7 @@ def _make_request_inputs(args):
 
 
 def serve_trace(n, seed=20211107):
-    """The request stream of config 5: hex or jittered-tet grids (50/50) of
+    """The serving request stream: hex or jittered-tet grids (50/50) of
     side log-uniform in 24..160 (tets: side^3 cubes of 6 Kuhn tetrahedra),
     sphere r = 0.15 or an axis-aligned ellipsoid (semi-axes U[0.1, 0.25]),
     field deformation (T = 3) / rotation / translation U[-1, 1]^3, N ~
@@ -801,8 +801,8 @@ def serve_trace(n, seed=20211107):
 
 
 def main_serve(a):
-    """Config 5 through the library's device-resident serving loop
-    (vof_server_*): the survey's trace replayed at its arrival times, then
+    """The serving workload through the library's device-resident serving
+    loop (vof_server_*): the request trace replayed at its arrival times, then
     the same requests with arrivals rescaled to 70% of the capacity the first
     replay measured. Requests are sharded over ranks by estimated cell-steps."""
     import multiprocessing as mp

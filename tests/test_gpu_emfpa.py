@@ -116,7 +116,7 @@ def test_emfpa_advect_parity_mixed(vof, cases, name, vname):
     assert ctx.stats()["n_overflow"] == 0
 
 
-def test_emfpa_multistep_parity_config1(vof, cases):
+def test_emfpa_multistep_parity_hex32_deformation(vof, cases):
     """32^3 deformation, 10 coupled steps at CFL 0.5 with EMFPA: the GPU and
     the oracle each run the loop on their own; F agrees to 1e-12 after every
     step and the volume bookkeeping closes."""

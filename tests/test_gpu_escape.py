@@ -70,8 +70,9 @@ def test_escape_is_counted_and_reported(vof, case, prec, flux):
 
 
 def test_paper_workloads_do_not_escape(vof):
-    """The hex deformation at CFL 0.5 (config 1) and the tets in rotation at
-    CFL 0.4 (config 3) stay inside the candidate ring for 10 steps."""
+    """The hex deformation at CFL 0.5 and the jittered tets in rotation at
+    CFL 0.4 (the paper's workloads here) stay inside the candidate ring for
+    10 steps."""
     for m, body, vel, cfl in [
             (I.hex_mesh(24), I.sphere((0.35, 0.35, 0.35), 0.15), I.deformation(3.0), 0.5),
             (I.kuhn_tet_mesh(6, seed=4), I.sphere((0.5, 0.75, 0.5), 0.15), I.rotation(2 * np.pi),

@@ -98,7 +98,7 @@ def test_lsfir_advect_parity(vof, orc, cases, name, prec):
     assert ctx.stats()["n_overflow"] == 0
 
 
-def test_lsfir_multistep_parity_config1(vof, orc, cases):
+def test_lsfir_multistep_parity_hex32_deformation(vof, orc, cases):
     """32^3 deformation, 6 coupled steps at CFL 0.5 with LSFIR: each side
     runs the loop on its own; F within 1e-12 after every step. The planes
     after the last step are compared at 1e-10: each side reconstructs its own

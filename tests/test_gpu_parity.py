@@ -139,7 +139,7 @@ VELS = {"deformation": I.deformation(3.0), "rotation": I.rotation(2 * np.pi),
 
 
 def _cfl(name):
-    """CFL of the one-step cases: 0.4 on the jittered tetrahedra (as config 3),
+    """CFL of the one-step cases: 0.4 on the jittered tetrahedra (as their rotation workload),
     where the candidate ring covers every interior flux polyhedron; at 0.5
     the diagonal translation already carries a few polyhedra of the 4^3 x 6
     grid past it (the CFL bound measures cells by their bounding boxes)."""
@@ -207,7 +207,7 @@ def test_multistep_tags_and_band_sweeps(vof, cases, name):
     assert ctx.stats()["n_interfacial"] == int((st["tag_c"] == 0).sum())
 
 
-def test_multistep_parity_config1(vof, cases):
+def test_multistep_parity_hex32_deformation(vof, cases):
     """32^3 deformation, 10 steps at CFL 0.5: the GPU and the oracle each
     run the whole loop on their own; F agrees to 1e-12 after every step."""
     m, F0, om = cases["hex32"]
@@ -231,7 +231,7 @@ def test_multistep_parity_config1(vof, cases):
     assert s["n_overflow"] == 0
 
 
-def test_full_cycle_config1(vof, cases):
+def test_full_cycle_hex32_deformation(vof, cases):
     """32^3 deformation over the whole cycle (t = 0 -> T = 3, 250 steps at
     CFL 0.5): the FP64 path stays within 1e-12 of the oracle at every step
     although each side feeds back its own results; the mixed path's shape
