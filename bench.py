@@ -62,7 +62,7 @@ FLOPS = {"fmfpa": (FLOPS_PER_ACTIVE_FACE, FLOPS_PER_TRUNCATION), "emfpa": (400.0
 # use; valid only for the source it was taken on (traffic is null for any other)
 # ncu figures of k_flux per flux polyhedron (one launch, --set full), valid
 # for the k_flux.cu source whose sha256 they carry
-FLUX_NCU = {"fmfpa": {"source_sha256": "c23d2cae46d6636816681b15de757448690a2ea51d92eb7a9fb06120c6d7f5d5",
+FLUX_NCU = {"fmfpa": {"source_sha256": "cc7141663a57a88a91845e222e8372ba1d47e60e63fad7ad505f10462c452892",
                       "dram_bytes_per_active_face": 586.0, "issue_active": 0.674,
                       "fma_pipe_active": 0.176,
                       "capture": "profiles/k_flux_deformation128_midrun_mixed.md"},
@@ -514,8 +514,8 @@ def main_batch(a):
     for name, prec in (("mixed", V.PREC_MIXED), ("fp64", V.PREC_FP64)):
         ctx = V.Context(meshes, precision=prec)
         cells = int(ctx.n_cell)
-        # READING d4b: dt_g = min(CFL 0.5 step, 0.2 / (100 |U|_inf)) so that
-        # 100 steps keep every body inside its domain
+        # each grid's step: dt_g = min(CFL 0.5 step, 0.2 / (100 |U|_inf)) so
+        # that 100 steps keep every body inside its domain
         with torch.cuda.stream(stream):
             ctx.set_fraction(np.concatenate(Fs))
             ctx.reconstruct()

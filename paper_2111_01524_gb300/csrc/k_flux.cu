@@ -787,8 +787,8 @@ __device__ __forceinline__ bool poly_scalar(const DevMesh& M, const GeoView<G>& 
 // tetrahedra that join its centroid to its fan triangles. A vertex in no
 // candidate cell sets kUncovered (the complement form of the mixed path,
 // which counts what is not empty as fluid, is then not used); if it lies
-// inside the domain's bounding box as well (outside it there is no fluid,
-// R11), kEscaped: the candidate ring does not cover the polyhedron and its
+// inside the domain's bounding box as well (outside it there is no fluid:
+// outflow), kEscaped: the candidate ring does not cover the polyhedron and its
 // V_F misses that part (counted, vof_get_stats returns VOF_ECFL).
 constexpr unsigned kUncovered = 1u, kEscaped = 2u;
 
@@ -885,7 +885,7 @@ __device__ __forceinline__ bool in_cell(const DevMesh& M, const GeoView<G>& Gv, 
 // node of the face), all of them candidate cells, then in the whole
 // candidate set (owner, neighbour and their node neighbours); a vertex in no
 // candidate cell sets kUncovered, and kEscaped when it lies inside the
-// grid's domain box (outside it there is no fluid, R11). A polyhedron whose
+// grid's domain box (outside it there is no fluid). A polyhedron whose
 // box is flat along an axis has no volume and is not tested.
 template <typename G, int KIND>
 __device__ __noinline__ unsigned poly_coverage(const DevMesh& M, const GeoView<G>& Gv, const DevState& S,

@@ -449,7 +449,7 @@ __global__ void k_update(DevMesh M, DevState S, const int32_t* bfaces, int64_t n
                          const int32_t* bcells, int64_t risk_cap, bool mixed) {
   double eb = 0.0;
   double clip = 0.0;  // volume the clip to [0, 1] removes
-  double bnd = 0.0;   // fluid that leaves through the domain boundary (R11)
+  double bnd = 0.0;   // fluid that leaves through the domain boundary
   unsigned long long nclip = 0;
   const int64_t n = (int64_t)S.cnt[kNBandCells];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -138,7 +138,7 @@ struct DevState {
   int32_t* fm_cand;
   uint8_t* fm_cinfo;
   // domain bounding box per grid [6 * n_grids] (lo xyz, hi xyz): a flux
-  // polyhedron vertex outside it is outside the domain (no fluid, R11)
+  // polyhedron vertex outside it is outside the domain (no fluid there)
   const double* dombox;
   // mixed precision reconciliation: per face, 1 when the last flux kernel's
   // V_F is exact (shortcut or a polyhedron inside one cell's fluid or empty

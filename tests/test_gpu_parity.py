@@ -359,7 +359,7 @@ def test_planar_interface_translates_exactly_gpu(vof, flux, prec):
 def _boundary_case(kind):
     """A body on each side of the domain in a uniform flow with inflow and
     outflow walls: one across x = 1 (fluid leaves), one across x = 0 and
-    y = 0 (the flow enters there and carries no fluid, reading R11)."""
+    y = 0 (the flow enters there and carries no fluid from outside)."""
     if kind == "hex":
         m = I.hex_mesh(10)
     else:
@@ -374,7 +374,7 @@ def _boundary_case(kind):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_boundary_crossing_parity(vof, orc, kind, flux, prec):
     """Faces on the domain boundary and interior faces whose polyhedra reach
-    outside it (readings c8a and R11), element by element against the
+    outside it (no fluid outside the domain), element by element against the
     oracle: V_F of every face and F after one step, and F after 4 coupled
     steps, for the three constructions."""
     m, F0, vel = _boundary_case(kind)

@@ -7,14 +7,14 @@ free, each with planted mistakes that must fail it.
   weights in the normal equations and on the stencil's edge and corner
   neighbours; on the uniform hex grid it is a closed form in h, sqrt(2) h and
   sqrt(3) h.
-- FMFPA back-trace (Sec. 2.2.2, reading R6): each back-traced vertex lies on
+- FMFPA back-trace (Sec. 2.2.2): each back-traced vertex lies on
   the two side planes that meet at its face node (each side plane contains
   its edge and is parallel to the velocity at the edge centre), and it is the
   orthogonal projection of the streak-line point x_i - dt u(x_i) (Eq.
   streak-line2) on their line of intersection: the residual from that point
   is perpendicular to the line. Checked in rigid rotation and in the
   time-modulated Enright field, written out here, at t + dt/2.
-- IDW node values (Sec. 3.3, reading R1): a hand-computed F* at the centre
+- IDW node values (Sec. 3.3): a hand-computed F* at the centre
   node of a 2 x 2 x 2 grid whose cells have different widths.
 
 A planted mistake is a one-line change of oracle.c compiled into a separate
@@ -153,7 +153,7 @@ def _backtrace_residuals(om, m, vel, ufun, t, dt):
     for f in range(0, len(m["owner"]), 2):
         P, vd, fl = om.fmfpa(f, vel, th, dt)
         if fl & 1:
-            continue  # streak-line fallback (reading R7)
+            continue  # ill-conditioned side planes: the streak-line point itself is used
         X = m["X"][fv[fp[f]:fp[f + 1]]]
         nI = len(X)
         uv = ufun(X, th)
@@ -233,7 +233,7 @@ def test_idw_node_value_by_hand(orc):
     centre node (0.3, 0.5, 0.5) is shared by all eight; the left centroids
     (x = 0.15) are at sqrt(0.15^2 + 0.25^2 + 0.25^2) = sqrt(0.1475) from it,
     the right ones (x = 0.65) at sqrt(0.35^2 + 2 * 0.25^2) = sqrt(0.2475).
-    Inverse-distance weights (R1): F* = (0.2 / sqrt(0.1475) + 0.8 /
+    Inverse-distance weights (unsquared distances): F* = (0.2 / sqrt(0.1475) + 0.8 /
     sqrt(0.2475)) / (1 / sqrt(0.1475) + 1 / sqrt(0.2475)) = 0.461397...
     (squared distances would give 0.42405..., equal weights 0.5)."""
     m = _stretched_grid()
