@@ -13,8 +13,8 @@
  *   - the plane constant is found by bisection on the cut volume;
  *   - the 3x3 LSGIR system is solved by Gaussian elimination with pivoting.
  *
- * Readings of the paper taken where it is silent (listed with their reasons
- * in the design notes): IDW weights 1/|x_node - x_cell|; the cell "geometric
+ * Readings of the paper taken where it is silent: IDW weights
+ * 1/|x_node - x_cell|; the cell "geometric
  * centre" is the volume centroid; back-traced FMFPA vertices are the
  * orthogonal projection of the streak-line point onto the side-plane
  * intersection line; the apex of the bottom triangulation moves along the
